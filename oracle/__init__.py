@@ -1,0 +1,6 @@
+"""CPU oracle of the batched rigid-body step (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
+package. The product library never imports it.
+"""
+from .oracle import build, load, step, detect, OracleDetect, cores  # noqa: F401

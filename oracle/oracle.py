@@ -1,0 +1,187 @@
+"""ctypes front end of the C++ oracle (test infrastructure only).
+
+`build()` compiles oracle/msh_oracle.cpp with g++ (-O3, OpenMP,
+-ffp-contract=off so that FP32 collision results are bit-reproducible) into
+oracle/_build/liboracle.so. `step()` advances a batch of envs in FP32 or FP64;
+`detect()` returns the collision stage (AABBs, pairs, contacts, colouring) for
+given poses.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "msh_oracle.cpp")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle if the shared object is missing or older than its source."""
+    if (not force and os.path.exists(_OUT)
+            and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC)):
+        return _OUT
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    tmp = _OUT + f".{os.getpid()}.tmp"
+    cmd = ["g++", "-O3", "-std=c++17", "-march=x86-64-v2", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-fPIC", "-shared", _SRC, "-o", tmp]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _OUT)
+    return _OUT
+
+
+class _Scene(C.Structure):
+    _fields_ = [("num_envs", C.c_int32), ("body_off", C.c_void_p), ("static_off", C.c_void_p),
+                ("joint_off", C.c_void_p), ("max_dof", C.c_int32), ("body_shape", C.c_void_p),
+                ("body_dims", C.c_void_p), ("body_mass", C.c_void_p), ("static_pose", C.c_void_p),
+                ("static_half", C.c_void_p), ("joint_type", C.c_void_p), ("joint_parent", C.c_void_p),
+                ("joint_child", C.c_void_p), ("joint_dof", C.c_void_p), ("joint_frame_a", C.c_void_p),
+                ("joint_frame_b", C.c_void_p), ("joint_gains", C.c_void_p), ("joint_limits", C.c_void_p)]
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("dt", C.c_double), ("substeps", C.c_int32), ("iterations", C.c_int32),
+                ("mode", C.c_int32), ("gravity", C.c_double * 3), ("friction", C.c_double),
+                ("restitution", C.c_double), ("contact_offset", C.c_double), ("baumgarte", C.c_double),
+                ("joint_baumgarte", C.c_double), ("slop", C.c_double), ("max_contacts", C.c_int32),
+                ("max_pairs", C.c_int32)]
+
+
+def load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        P = C.c_void_p
+        for name in ("oracle_step_f32", "oracle_step_f64"):
+            fn = getattr(lib, name)
+            fn.argtypes = [P, P, P, P, P, P, P, C.c_int, P, C.c_int]
+            fn.restype = C.c_int
+        for name in ("oracle_detect_f32", "oracle_detect_f64"):
+            fn = getattr(lib, name)
+            fn.argtypes = [P] * 15
+            fn.restype = C.c_int
+        lib.oracle_max_threads.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def cores() -> int:
+    return int(load().oracle_max_threads())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+class _Keep:
+    """Holds contiguous copies of the descriptor arrays alive for a call."""
+
+    def __init__(self, scene):
+        c = np.ascontiguousarray
+        self.arrs = dict(
+            body_off=c(scene.body_off, np.int32), static_off=c(scene.static_off, np.int32),
+            joint_off=c(scene.joint_off, np.int32), body_shape=c(scene.body_shape, np.int32),
+            body_dims=c(scene.body_dims, np.float32), body_mass=c(scene.body_mass, np.float32),
+            static_pose=c(scene.static_pose, np.float32), static_half=c(scene.static_half, np.float32),
+            joint_type=c(scene.joint_type, np.int32), joint_parent=c(scene.joint_parent, np.int32),
+            joint_child=c(scene.joint_child, np.int32), joint_dof=c(scene.joint_dof, np.int32),
+            joint_frame_a=c(scene.joint_frame_a, np.float32),
+            joint_frame_b=c(scene.joint_frame_b, np.float32),
+            joint_gains=c(scene.joint_gains, np.float32), joint_limits=c(scene.joint_limits, np.float32))
+        s = _Scene()
+        s.num_envs = scene.num_envs
+        s.max_dof = scene.max_dof
+        for k, v in self.arrs.items():
+            setattr(s, k, v.ctypes.data)
+        self.struct = s
+
+
+def _cfg(cfg) -> _Cfg:
+    c = _Cfg()
+    c.dt = cfg.dt
+    c.substeps = cfg.substeps
+    c.iterations = cfg.iterations
+    c.mode = cfg.mode
+    for i in range(3):
+        c.gravity[i] = cfg.gravity[i]
+    c.friction = cfg.friction
+    c.restitution = cfg.restitution
+    c.contact_offset = cfg.contact_offset
+    c.baumgarte = cfg.baumgarte
+    c.joint_baumgarte = cfg.joint_baumgarte
+    c.slop = cfg.slop
+    c.max_contacts = cfg.max_contacts
+    c.max_pairs = cfg.max_pairs
+    return c
+
+
+def step(scene, cfg, state, targets=None, nsteps: int = 1, precision: str = "f32", threads: int = 0):
+    """Advances `state` = (pos, quat, linvel, angvel) by `nsteps` steps.
+
+    targets: f32 [nsteps, E, max_dof] absolute joint targets (None = zeros).
+    Returns (new_state, status[E]). The input arrays are not modified."""
+    lib = load()
+    dt = np.float32 if precision == "f32" else np.float64
+    st = [np.ascontiguousarray(a, dtype=dt).copy() for a in state]
+    E = scene.num_envs
+    md = max(scene.max_dof, 1)
+    if targets is None:
+        targets = np.zeros((nsteps, E, md), np.float32)
+    targets = np.ascontiguousarray(targets, dtype=np.float32).reshape(-1, E, md)
+    assert targets.shape[0] >= nsteps
+    status = np.zeros(E, np.int32)
+    keep = _Keep(scene)
+    c = _cfg(cfg)
+    fn = lib.oracle_step_f32 if precision == "f32" else lib.oracle_step_f64
+    rc = fn(C.byref(keep.struct), C.byref(c), _ptr(st[0]), _ptr(st[1]), _ptr(st[2]), _ptr(st[3]),
+            _ptr(targets), int(nsteps), _ptr(status), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle step failed: {rc}")
+    return tuple(st), status
+
+
+@dataclass
+class OracleDetect:
+    aabb_body: np.ndarray      # [B,6]
+    aabb_static: np.ndarray    # [S,6]
+    pair_count: np.ndarray     # [E]
+    pairs: np.ndarray          # [E,max_pairs,2]
+    contact_count: np.ndarray  # [E]
+    contact_ids: np.ndarray    # [E,max_contacts,2]
+    contact_geom: np.ndarray   # [E,max_contacts,10]  n, ra, rb, s0
+    manifold_count: np.ndarray  # [E]
+    colours: np.ndarray        # [J + E*max_pairs]
+    ncolours: np.ndarray       # [E]
+    status: np.ndarray         # [E]
+
+
+def detect(scene, cfg, pos, quat, precision: str = "f32") -> OracleDetect:
+    """Collision stage (AABB, broadphase, narrowphase, colouring) at the given poses."""
+    lib = load()
+    dt = np.float32 if precision == "f32" else np.float64
+    pos = np.ascontiguousarray(pos, dtype=dt)
+    quat = np.ascontiguousarray(quat, dtype=dt)
+    E, B, S, J = scene.num_envs, scene.num_bodies, scene.num_statics, scene.num_joints
+    P, K = cfg.max_pairs, cfg.max_contacts
+    out = OracleDetect(
+        aabb_body=np.zeros((B, 6), dt), aabb_static=np.zeros((S, 6), dt),
+        pair_count=np.zeros(E, np.int32), pairs=np.full((E, P, 2), -1, np.int32),
+        contact_count=np.zeros(E, np.int32), contact_ids=np.full((E, K, 2), -1, np.int32),
+        contact_geom=np.zeros((E, K, 10), dt), manifold_count=np.zeros(E, np.int32),
+        colours=np.full(J + E * P, -1, np.int32), ncolours=np.zeros(E, np.int32),
+        status=np.zeros(E, np.int32))
+    keep = _Keep(scene)
+    c = _cfg(cfg)
+    fn = lib.oracle_detect_f32 if precision == "f32" else lib.oracle_detect_f64
+    rc = fn(C.byref(keep.struct), C.byref(c), _ptr(pos), _ptr(quat), _ptr(out.aabb_body),
+            _ptr(out.aabb_static), _ptr(out.pair_count), _ptr(out.pairs), _ptr(out.contact_count),
+            _ptr(out.contact_ids), _ptr(out.contact_geom), _ptr(out.manifold_count),
+            _ptr(out.colours), _ptr(out.ncolours), _ptr(out.status))
+    if rc != 0:
+        raise RuntimeError(f"oracle detect failed: {rc}")
+    return out
