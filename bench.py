@@ -1,0 +1,321 @@
+"""Benchmark of the batched rigid-body step (one JSON line on stdout).
+
+Workload: the 4096-env apartment batch (uneven env sizes: U{4..48} objects +
+a 10-body mobile manipulator, U{10..60} static boxes, 4 substeps x 20
+coloured-PGS iterations, dt = 0.01 s), synthetic and seeded. A step is one
+env-step of every env. `value` is env-steps/s of the fused persistent,
+CUDA-graph-captured form with the state resident in HBM; the plain
+one-launch-per-stage form is timed beside it, and `e2e` times the same step
+through msh_step_host with pinned host buffers (copies in the timed region).
+
+--impl reference times the CPU oracle on the host cores (a bounded sample of
+envs per step) on the same metric.
+
+Multi-GPU (torchrun): every rank steps its own 4096 envs (weak scaling, no
+collective on the data path); the value is all ranks' env-steps over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/sec at 4096 envs (fwd and fwd+bwd) vs plain step; % HBM roofline"
+UNIT = "env-steps/s"
+# bytes per env-step the method must move when contacts stay on chip:
+# per dynamic body state read + write + params, per static box, plane, per
+# joint, per DoF target
+B_BODY, B_STATIC, B_PLANE, B_JOINT, B_DOF = 52 + 52 + 32, 40, 16, 80, 4
+# solver flops per row update (generic sequential-impulse row: J.v over four
+# 3-blocks, the impulse, its clamp and four 3-block velocity updates)
+FLOP_ROW = 55
+ROWS = {0: 6, 1: 8, 2: 6}   # rows per revolute / prismatic / planar joint with drive
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2032.0)), "measured"
+    except Exception:
+        return 6400.0, 2032.0, "fallback"
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def algorithmic(scene):
+    """Algorithmic bytes per step of the whole batch."""
+    nb, ns, nj = scene.env_counts()
+    return int((B_BODY * nb + B_STATIC * ns + B_PLANE + B_JOINT * nj).sum() + B_DOF * scene.max_dof * scene.num_envs)
+
+
+def row_count(scene, contact_count):
+    jt = scene.joint_type
+    joint_rows = sum(ROWS[int(t)] for t in jt)
+    return int(3 * np.asarray(contact_count).sum() + joint_rows)
+
+
+def run_reference(args, rank, world):
+    import oracle
+    from paper_2412_13211_b300 import scenes
+    if rank != 0:
+        return
+    scene, cfg = scenes.make_config(args.config, num_envs=args.envs)
+    n = min(args.ref_sample, scene.num_envs)
+    sample = np.linspace(0, scene.num_envs - 1, n).astype(int)
+    sub = scene.subset(sample)
+    tg = sub.target_walk(args.steps + args.warmup)
+    st = sub.state()
+    threads = os.cpu_count() or 1
+    for w in range(args.warmup):
+        st, _ = oracle.step(sub, cfg, st, tg[w:w + 1], 1, "f32", threads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        st, _ = oracle.step(sub, cfg, st, tg[args.warmup + k:args.warmup + k + 1], 1, "f32", threads=threads)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"config{args.config} apartment batch", "envs": scene.num_envs,
+                       "sampled_envs": n, "substeps": cfg.substeps, "iterations": cfg.iterations},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} of {scene.num_envs} envs per step, FP32 oracle, OpenMP over envs"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(scene, cfg, budget_s=12.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the batch."""
+    import oracle
+    threads = os.cpu_count() or 1
+    n = min(512, scene.num_envs)
+    sample = np.linspace(0, scene.num_envs - 1, n).astype(int)
+    sub = scene.subset(sample)
+    tg = sub.target_walk(64)
+    t0 = time.perf_counter()
+    st, _ = oracle.step(sub, cfg, sub.state(), tg[:1], 1, "f32", threads=threads)
+    one = time.perf_counter() - t0
+    steps = int(max(1, min(63, budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.step(sub, cfg, st, tg[1:1 + steps], steps, "f32", threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} evenly spaced envs of the {scene.num_envs}-env batch x {steps} steps, FP32"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="msh", choices=["msh", "reference"])
+    ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--envs", type=int, default=4096)
+    ap.add_argument("--threads-per-env", type=int, default=0)
+    ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2412_13211_b300 import scenes
+    from paper_2412_13211_b300.sim import MshSim
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    scene, cfg = scenes.make_config(args.config, num_envs=args.envs, env_start=rank * args.envs)
+    tpe = args.threads_per_env or 128
+    sim = MshSim(scene, cfg, device=dev, exec_form="fused", threads_per_env=tpe, use_graph=True)
+    total = args.warmup + args.steps
+    tg = torch.as_tensor(scene.target_walk(total)).to(dev)
+    init = tuple(t.clone() for t in (sim.pos, sim.quat, sim.linvel, sim.angvel))
+    det = sim.detect()
+    rows = row_count(scene, det["contact_count"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.Stream(dev)
+
+    def timed(step_fn, k0, n):
+        """Per-step CUDA-event times on `stream`, with an L2 flush between steps."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        with torch.cuda.stream(stream):
+            for i in range(n):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                step_fn(k0 + i)
+                ev[i][1].record(stream)
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    def fused_step(k):
+        sim.step(tg[k], stream=stream)
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            fused_step(k)
+    stream.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with Clocks(local) as clk:
+        ms = timed(fused_step, args.warmup, args.steps)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    t_step = float(np.mean(ms))
+    t_tot = float(np.sum(ms))
+    if dist:
+        tt = torch.tensor([t_tot], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_tot = float(tt.item())
+    value = world * scene.num_envs * args.steps / (t_tot / 1e3)
+    status = sim.status()
+
+    # plain form (one launch per stage), same inputs
+    plain = None
+    if not args.no_plain:
+        for t, s in zip((sim.pos, sim.quat, sim.linvel, sim.angvel), init):
+            t.copy_(s)
+        sim.set_exec("plain", tpe, True)
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup):
+                fused_step(k)
+        stream.synchronize()
+        n_plain = max(3, min(args.steps, 20))
+        pms = timed(fused_step, args.warmup, n_plain)
+        plain = {"value": scene.num_envs / (np.mean(pms) / 1e3), "unit": UNIT, "ms_per_step": float(np.mean(pms)),
+                 "launches_per_step": sim.launches_per_step, "steps": n_plain, "graph": True}
+        sim.set_exec("fused", tpe, True)
+
+    # end to end through the C ABI with pinned host buffers
+    host = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory() for a in scene.state()]
+    htg = torch.from_numpy(np.ascontiguousarray(scene.target_walk(total), np.float32)).pin_memory()
+    for k in range(args.warmup):
+        sim.step_host(*host, htg[k], stream=stream)
+    n_e2e = max(3, min(args.steps, 50))
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        sim.step_host(*host, htg[args.warmup + k], stream=stream)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    h2d = 52 * scene.num_bodies + 4 * scene.num_envs * scene.max_dof
+    d2h = 52 * scene.num_bodies
+
+    hbm_peak, sm_max, peak_kind = peaks()
+    bytes_step = algorithmic(scene)
+    flops_step = FLOP_ROW * rows * cfg.substeps * cfg.iterations
+    alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x clock, TFLOP/s
+    achieved_tf = flops_step / (t_step / 1e3) / 1e12
+    achieved_gbs = bytes_step / (t_step / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"config{args.config} apartment batch, 4096 envs of uneven size",
+                   "envs": scene.num_envs, "bodies": scene.num_bodies, "static_boxes": scene.num_statics,
+                   "joints": scene.num_joints, "dt": cfg.dt, "substeps": cfg.substeps,
+                   "iterations": cfg.iterations, "solver": "coloured PGS", "form": "fused persistent + CUDA graph",
+                   "threads_per_env": tpe, "workspace_bytes_per_env": sim.workspace_bytes,
+                   "l2": "flushed between timed steps (256 MB write)", "contact_points": int(det["contact_count"].sum()),
+                   "rows_per_substep": rows},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tf / alu_peak, "traffic": None,
+                     "note": f"FP32 peak = 148 SMs x 128 lanes x 2 x {sm_max:.0f} MHz; achieved = {FLOP_ROW} flop x "
+                             f"solver rows x substeps x iterations / fused-kernel step time"},
+        "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_step": bytes_step},
+        "plain_step": plain,
+        "fwd_bwd": None,
+        "e2e": {"value": scene.num_envs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": n_e2e},
+        "gpu_launches": args.steps * sim.launches_per_step,
+        "status_nonzero_envs": int((status != 0).sum()),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, cfg)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * msh.h -- C ABI of the B300-native batched rigid-body step.
+ *
+ * The ManiSkill-HAB paper (Sec. 4.1-4.2, "Environment Design and
+ * Benchmarking") steps thousands of home-rearrangement environments in
+ * parallel on one GPU: a 100 Hz physics rate under a 20 Hz control rate, PD
+ * joint position targets for the arm and velocity control of the base, and a
+ * robot that collides with several dynamic objects. It does not describe the
+ * physics step itself. This library implements that step for a batch of
+ * independent environments:
+ *   a1 integrate velocities (gravity), per substep
+ *   a2 world AABBs of every body and static box (inflated by the contact offset)
+ *   a3 broadphase: all (i<j) pairs with overlapping AABBs, canonical order
+ *   a4 narrowphase: primitive pairs to contact manifolds (<= 4 points)
+ *   a5 greedy graph colouring of joints and manifolds; per substep row set-up
+ *   a6 fixed-iteration coloured projected Gauss-Seidel (or mass-split Jacobi)
+ *   a7 integrate positions, per substep
+ * Every environment is a set of dynamic bodies (spheres, capsules, boxes), a
+ * set of static boxes, the ground plane z = 0, and joints (revolute,
+ * prismatic, planar) with soft PD drives, in maximal coordinates.
+ *
+ * Conventions: SI units, z up, quaternions (w, x, y, z). Shapes: 0 sphere
+ * (dims r), 1 capsule (r, half segment length along local x), 2 box (half
+ * extents). Joints: 0 revolute, 1 prismatic (axis = joint frame x), 2 planar
+ * (normal = joint frame z; DoFs x, y, yaw).
+ *
+ * Threading: a handle may be used from one host thread at a time. Every
+ * device pointer passed in must stay valid until the work queued on `stream`
+ * has finished. `stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).
+ *
+ * Errors: every function returns an int status, MSH_OK (0) or a negative
+ * MSH_ERR_* code; msh_last_error() describes the last failure of the calling
+ * thread. Conditions met inside the step (capacity overflow, non-finite
+ * state) never trap: they set bits in a per-environment status word that
+ * msh_get_status() returns.
+ */
+#ifndef MSH_H_
+#define MSH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MSH_OK = 0,
+  MSH_ERR_INVALID_ARG = -1,  /* bad pointer, size, descriptor or configuration */
+  MSH_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  MSH_ERR_OOM = -3,          /* device allocation failed */
+  MSH_ERR_TIMEOUT = -4,      /* a bounded device wait expired */
+  MSH_ERR_UNSUPPORTED = -5   /* request outside what this build supports */
+};
+
+/* Per-environment status bits (accumulated until msh_clear_status). */
+enum {
+  MSH_ST_PAIR_OVERFLOW = 1,     /* more broadphase pairs than max_pairs; trailing pairs dropped */
+  MSH_ST_CONTACT_OVERFLOW = 2,  /* more contact points than max_contacts; trailing points dropped */
+  MSH_ST_COLOUR_OVERFLOW = 4,   /* a constraint found none of 64 colours free; it is skipped */
+  MSH_ST_NONFINITE = 8          /* a body state became NaN/Inf */
+};
+
+/* Execution forms of the step (msh_set_exec). */
+enum {
+  MSH_EXEC_PLAIN = 0,  /* one launch per stage, workspace in HBM, S x N solver launches */
+  MSH_EXEC_FUSED = 1   /* one persistent launch per step: env work queue, workspace in shared memory */
+};
+
+/* Solver modes. */
+enum { MSH_MODE_COLOURED = 0, MSH_MODE_JACOBI = 1 };
+
+/*
+ * Scene descriptor: HOST arrays, read during msh_create and not retained.
+ * CSR offsets per environment (length num_envs + 1, starting at 0) index the
+ * flat body, static-box and joint arrays; body, static and joint indices
+ * inside joints and contacts are env-local.
+ */
+typedef struct msh_scene_desc {
+  int32_t num_envs;
+  const int32_t* body_off;      /* [E+1] */
+  const int32_t* static_off;    /* [E+1] */
+  const int32_t* joint_off;     /* [E+1] */
+  int32_t max_dof;              /* joint-target slots per env (>= 0) */
+  const int32_t* body_shape;    /* [B]   0 sphere, 1 capsule, 2 box */
+  const float* body_dims;       /* [B,4] */
+  const float* body_mass;       /* [B]   > 0 */
+  const float* static_pose;     /* [S,7] position, unit quaternion */
+  const float* static_half;     /* [S,3] half extents */
+  const int32_t* joint_type;    /* [J]   0 revolute, 1 prismatic, 2 planar */
+  const int32_t* joint_parent;  /* [J]   env-local body, or -1 for the world */
+  const int32_t* joint_child;   /* [J]   env-local body */
+  const int32_t* joint_dof;     /* [J]   first target slot (planar uses 3) */
+  const float* joint_frame_a;   /* [J,7] joint frame in the parent frame (world if parent = -1) */
+  const float* joint_frame_b;   /* [J,7] joint frame in the child frame */
+  const float* joint_gains;     /* [J,4] stiffness, damping, force limit, unused */
+  const float* joint_limits;    /* [J,2] prismatic lower/upper (others ignore) */
+} msh_scene_desc;
+
+/* Solver parameters. */
+typedef struct msh_solver_cfg {
+  float dt;                /* step length [s] */
+  int32_t substeps;        /* S >= 1 */
+  int32_t iterations;      /* N >= 1 solver sweeps per substep */
+  int32_t mode;            /* MSH_MODE_COLOURED or MSH_MODE_JACOBI */
+  float gravity[3];
+  float friction;          /* Coulomb coefficient, per tangent axis */
+  float restitution;       /* applied to approach speeds above 1 m/s */
+  float contact_offset;    /* AABB inflation and contact keep distance [m] */
+  float baumgarte;         /* contact position correction factor */
+  float joint_baumgarte;   /* joint position correction factor */
+  float slop;              /* allowed contact penetration [m] */
+  int32_t max_contacts;    /* contact points per env, 1..1024 */
+  int32_t max_pairs;       /* broadphase pairs per env, 1..4096 */
+} msh_solver_cfg;
+
+/* Body state, structure of arrays over all bodies of all envs (DEVICE
+ * pointers, caller-owned, float32): pos [B,3], quat [B,4], linvel [B,3],
+ * angvel [B,3]. msh_step reads and overwrites them in place. */
+typedef struct msh_state {
+  float* pos;
+  float* quat;
+  float* linvel;
+  float* angvel;
+} msh_state;
+
+typedef struct msh_handle msh_handle;
+
+/*
+ * Validates the descriptor, uploads the scene to library-owned device memory
+ * (inverse masses and inertias are derived on the device), and sizes the
+ * per-env workspace from the largest env and the configured capacities.
+ * Allocates with cudaMalloc on the current device. On failure *out is NULL.
+ */
+int msh_create(const msh_scene_desc* desc, const msh_solver_cfg* cfg, msh_handle** out);
+
+/* Frees everything the handle owns (synchronises its streams first). */
+void msh_destroy(msh_handle* h);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* msh_last_error(void);
+
+/*
+ * Chooses the execution form: MSH_EXEC_PLAIN or MSH_EXEC_FUSED;
+ * threads_per_env in {32, 64, 128, 256, 512} (0 = library default);
+ * use_graph != 0 captures the step's launches in a CUDA graph on first use
+ * (re-captured when the state pointers, dt or substeps change).
+ * Returns MSH_ERR_UNSUPPORTED if the fused form cannot hold the workspace.
+ */
+int msh_set_exec(msh_handle* h, int32_t exec, int32_t threads_per_env, int32_t use_graph);
+
+/*
+ * One step of every env (Sec. 4.2: 100 Hz physics, i.e. dt = 0.01 s).
+ * joint_targets: DEVICE [num_envs, max_dof] absolute PD targets (rad or m),
+ * may be NULL when max_dof == 0. dt > 0 and substeps >= 1 override the
+ * configured values. Asynchronous on `stream`.
+ */
+int msh_step(msh_handle* h, const msh_state* st, const float* joint_targets, float dt,
+             int32_t substeps, void* stream);
+
+/*
+ * Same step with HOST state and targets: copies pos/quat/linvel/angvel and
+ * the targets into library-owned device buffers, steps, copies the state
+ * back, and synchronises `stream`. Host buffers should be pinned for speed.
+ */
+int msh_step_host(msh_handle* h, float* pos, float* quat, float* linvel, float* angvel,
+                  const float* joint_targets, float dt, int32_t substeps, void* stream);
+
+/*
+ * Collision stage only (a2-a5) at the given poses, for inspection and
+ * parity tests. DEVICE outputs (any may be NULL): aabb_body [B,6],
+ * aabb_static [S,6], pair_count [E], pairs [E,max_pairs,2], contact_count
+ * [E], contact_ids [E,max_contacts,2] (body a, collision index b: dynamic
+ * body, D + static box, or D + S for the plane), contact_geom
+ * [E,max_contacts,10] (normal a->b, anchor on a in a's frame, anchor on b in
+ * b's frame or world for statics, separation), manifold_count [E], colours
+ * [J + E*max_pairs] (joints, then manifolds per env), ncolours [E].
+ */
+int msh_detect(msh_handle* h, const msh_state* st, float* aabb_body, float* aabb_static,
+               int32_t* pair_count, int32_t* pairs, int32_t* contact_count,
+               int32_t* contact_ids, float* contact_geom, int32_t* manifold_count,
+               int32_t* colours, int32_t* ncolours, void* stream);
+
+/* Copies the per-env status words to host memory [num_envs] (synchronises
+ * `stream`). */
+int msh_get_status(msh_handle* h, int32_t* status_host, void* stream);
+
+/* Zeroes the per-env status words. */
+int msh_clear_status(msh_handle* h, void* stream);
+
+/* Bytes of device memory owned by the handle. */
+int64_t msh_scratch_bytes(const msh_handle* h);
+
+/* Per-env workspace bytes (shared memory in the fused form). */
+int64_t msh_workspace_bytes(const msh_handle* h);
+
+/* Number of kernel launches one msh_step issues in the current form. */
+int32_t msh_launches_per_step(const msh_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSH_H_ */

@@ -483,7 +483,9 @@ template <class R> int box_plane(const Shape<R>& box, R off, Pt<R>* out) {
 }
 
 // One Sutherland-Hodgman pass over a polygon in reference-face coordinates
-// (x, y, height), keeping the side where sg * coord - bound <= 0.
+// (x, y, height), keeping the side where sg * coord - bound <= 0. The output
+// is capped at 8 vertices (a convex quad never exceeds it; rounding on a
+// nearly degenerate polygon could).
 template <class R> int clip_poly(const R (*in)[3], int n, R (*out)[3], int axis, R sg, R bound) {
   int m = 0;
   for (int i = 0; i < n; ++i) {
@@ -491,8 +493,8 @@ template <class R> int clip_poly(const R (*in)[3], int n, R (*out)[3], int axis,
     const R* Q = in[(i + 1) % n];
     R dp = sg * P[axis] - bound;
     R dq = sg * Q[axis] - bound;
-    if (dp <= R(0)) { out[m][0] = P[0]; out[m][1] = P[1]; out[m][2] = P[2]; ++m; }
-    if ((dp < R(0) && dq > R(0)) || (dp > R(0) && dq < R(0))) {
+    if (dp <= R(0) && m < 8) { out[m][0] = P[0]; out[m][1] = P[1]; out[m][2] = P[2]; ++m; }
+    if (((dp < R(0) && dq > R(0)) || (dp > R(0) && dq < R(0))) && m < 8) {
       R t = dp / (dp - dq);
       for (int k = 0; k < 3; ++k) out[m][k] = P[k] + (Q[k] - P[k]) * t;
       ++m;

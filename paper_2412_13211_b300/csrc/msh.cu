@@ -1,0 +1,663 @@
+// Kernels and C ABI of the batched rigid-body step (see include/msh.h).
+//
+// Two execution forms share the stage functions of msh_stages.cuh:
+//   * plain: one launch per stage, one CTA per env, workspace slabs in HBM;
+//     per step: load, aabb, broadphase, narrowphase, colour, then per substep
+//     integrate-velocity, prep, N solver launches, integrate-position; store.
+//   * fused: one persistent launch per step; CTAs take envs from an atomic
+//     queue (largest first) and run every stage on a shared-memory workspace.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/msh.h"
+#include "msh_stages.cuh"
+
+using namespace msh;
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Ws plain_ws(const Params& p, int env) {
+  return make_ws(p.ws + (long long)env * p.ws_stride, p.L);
+}
+
+__global__ void k_load(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_load(p, e, plain_ws(p, blockIdx.x));
+}
+__global__ void k_aabb(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_aabb(p, e, plain_ws(p, blockIdx.x));
+}
+__global__ void k_broad(Params p) {
+  __shared__ int scr[33];
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_broadphase(p, e, plain_ws(p, blockIdx.x), scr);
+}
+__global__ void k_narrow(Params p) {
+  __shared__ int scr[33];
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_narrowphase(p, e, plain_ws(p, blockIdx.x), scr);
+}
+__global__ void k_colour(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_colour(p, e, plain_ws(p, blockIdx.x));
+}
+__global__ void k_intvel(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_integrate_vel(p, e, plain_ws(p, blockIdx.x));
+}
+__global__ void k_prep(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_prep(p, e, plain_ws(p, blockIdx.x));
+}
+__global__ void k_solve(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_solve_iter(p, e, plain_ws(p, blockIdx.x));
+}
+__global__ void k_intpos(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_integrate_pos(p, e, plain_ws(p, blockIdx.x));
+}
+__global__ void k_store(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  stage_store(p, e, plain_ws(p, blockIdx.x));
+}
+
+// One whole step per env; persistent CTAs pull envs from an atomic queue.
+__global__ void k_fused(Params p, int smem_ws) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int scr[33];
+  __shared__ int s_next;
+  char* base = smem_ws ? smem : p.ws + (long long)blockIdx.x * p.ws_stride;
+  Ws w = make_ws(base, p.L);
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
+    __syncthreads();
+    const int idx = s_next;
+    if (idx >= p.E) break;
+    EnvInfo e = env_info(p, p.env_order[idx]);
+    stage_load(p, e, w);
+    __syncthreads();
+    stage_aabb(p, e, w);
+    __syncthreads();
+    stage_broadphase(p, e, w, scr);
+    stage_narrowphase(p, e, w, scr);
+    stage_colour(p, e, w);
+    for (int s = 0; s < p.S; ++s) {
+      stage_integrate_vel(p, e, w);
+      __syncthreads();
+      stage_prep(p, e, w);
+      __syncthreads();
+      for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w);
+      stage_integrate_pos(p, e, w);
+      __syncthreads();
+    }
+    stage_store(p, e, w);
+    __syncthreads();
+  }
+}
+
+// Inverse mass and principal inverse inertia from mass and shape (solid
+// sphere 2/5 m r^2; box m/3 (h1^2 + h2^2); capsule = cylinder of length 2L
+// plus two hemispheres about its centre, axis = local x).
+__global__ void k_params(int B, const float* mass, const int* shape, const float* dims, float4* binv,
+                         float4* bdims) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B) return;
+  nf m = nf(mass[g]);
+  int sh = shape[g];
+  nf d0 = nf(dims[4 * g]), d1 = nf(dims[4 * g + 1]), d2 = nf(dims[4 * g + 2]);
+  const nf one = nf(1.f);
+  nf ix, iy, iz;
+  if (sh == SH_SPHERE) {
+    nf I = nf(0.4f) * m * d0 * d0;
+    ix = iy = iz = one / I;
+  } else if (sh == SH_BOX) {
+    nf hx2 = d0 * d0, hy2 = d1 * d1, hz2 = d2 * d2;
+    nf k = m / nf(3.f);
+    ix = one / (k * (hy2 + hz2)); iy = one / (k * (hx2 + hz2)); iz = one / (k * (hx2 + hy2));
+  } else {
+    nf r = d0, L = d1;
+    nf pi = nf(3.14159265358979323846f);
+    nf vc = pi * r * r * (nf(2.f) * L);
+    nf vs = nf(4.f) / nf(3.f) * pi * r * r * r;
+    nf mc = m * vc / (vc + vs);
+    nf ms = m * vs / (vc + vs);
+    nf H = nf(2.f) * L;
+    nf Ia = mc * r * r * nf(0.5f) + ms * nf(0.4f) * r * r;
+    nf Ip = mc * (H * H / nf(12.f) + r * r * nf(0.25f)) + ms * (nf(0.4f) * r * r + H * H * nf(0.25f) + nf(0.375f) * H * r);
+    ix = one / Ia; iy = iz = one / Ip;
+  }
+  binv[g] = make_float4((one / m).v, ix.v, iy.v, iz.v);
+  bdims[g] = make_float4(d0.v, d1.v, d2.v, __int_as_float(sh));
+}
+
+// Copies the collision stage results of every env out of the plain workspace.
+__global__ void k_export(Params p, float* aabb_body, float* aabb_static, int* pair_count, int* pairs,
+                         int* contact_count, int* contact_ids, float* contact_geom, int* manifold_count,
+                         int* colours, int* ncolours, int Jtot) {
+  const int env = blockIdx.x;
+  EnvInfo e = env_info(p, env);
+  Ws w = plain_ws(p, env);
+  const int np = w.misc[MC_PAIRS], nc = w.misc[MC_CONTACTS], nm = w.misc[MC_MANIFOLDS];
+  for (int i = threadIdx.x; i < e.D + e.S; i += blockDim.x) {
+    float* o = i < e.D ? (aabb_body ? aabb_body + 6 * (e.b0 + i) : nullptr)
+                       : (aabb_static ? aabb_static + 6 * (e.s0 + i - e.D) : nullptr);
+    if (!o) continue;
+    float4 lo = w.alo[i], hi = w.ahi[i];
+    o[0] = lo.x; o[1] = lo.y; o[2] = lo.z; o[3] = hi.x; o[4] = hi.y; o[5] = hi.z;
+  }
+  for (int k = threadIdx.x; k < np; k += blockDim.x) {
+    if (!pairs) break;
+    int pr = w.pairs[k];
+    pairs[((long long)env * p.P + k) * 2] = pr & 0xffff;
+    pairs[((long long)env * p.P + k) * 2 + 1] = pr >> 16;
+  }
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    long long q = (long long)env * p.C + c;
+    int id = w.cid[c];
+    if (contact_ids) { contact_ids[2 * q] = id & 0xffff; contact_ids[2 * q + 1] = id >> 16; }
+    if (contact_geom) {
+      float4 n = w.cn[c], a = w.cra[c], b = w.crb[c];
+      float* g = contact_geom + 10 * q;
+      g[0] = n.x; g[1] = n.y; g[2] = n.z; g[3] = a.x; g[4] = a.y; g[5] = a.z;
+      g[6] = b.x; g[7] = b.y; g[8] = b.z; g[9] = n.w;
+    }
+  }
+  if (colours) {
+    for (int k = threadIdx.x; k < e.J; k += blockDim.x) colours[e.j0 + k] = w.ccol[k];
+    for (int k = threadIdx.x; k < nm; k += blockDim.x) colours[Jtot + (long long)env * p.P + k] = w.ccol[e.J + k];
+  }
+  if (threadIdx.x == 0) {
+    if (pair_count) pair_count[env] = np;
+    if (contact_count) contact_count[env] = nc;
+    if (manifold_count) manifold_count[env] = nm;
+    if (ncolours) ncolours[env] = w.misc[MC_COLOURS];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess)                                                                \
+      return fail(_e == cudaErrorMemoryAllocation ? MSH_ERR_OOM : MSH_ERR_CUDA,           \
+                  std::string(#call) + ": " + cudaGetErrorString(_e));                    \
+  } while (0)
+
+int align16(int x) { return (x + 15) & ~15; }
+
+Layout make_layout(int Dm, int Sm, int Jm, int P, int C, bool jacobi) {
+  Layout L;
+  std::memset(&L, 0, sizeof(L));
+  L.Dm = Dm; L.Sm = Sm; L.Jm = Jm; L.P = P; L.C = C; L.K = Jm + P; L.R = Jm * ROWS_PER_JOINT;
+  int o = 0;
+  auto take = [&](int bytes) { int r = o; o = align16(o + bytes); return r; };
+  const int f4 = 16;
+  L.bx = take(Dm * f4); L.bq = take(Dm * f4); L.bv = take(Dm * f4); L.bw = take(Dm * f4);
+  L.bI = take(Dm * f4); L.bd = take(Dm * f4); L.bIw0 = take(Dm * f4); L.bIw1 = take(Dm * f4);
+  L.sc = take(Sm * f4); L.sM = take(3 * Sm * f4);
+  L.alo = take((Dm + Sm) * f4); L.ahi = take((Dm + Sm) * f4);
+  L.pairs = take(P * 4);
+  L.cn = take(C * f4); L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4);
+  L.kra = take(C * f4); L.krb = take(C * f4); L.kt1 = take(C * f4); L.kt2 = take(C * f4); L.klam = take(C * f4);
+  L.man = take(P * 16);
+  L.jr = take(L.R * 6 * f4);
+  L.ccol = take(L.K * 4); L.corder = take(L.K * 4); L.coff = take((MAX_COLOURS + 1) * 4);
+  L.masks = take(Dm * 8);
+  if (jacobi) {
+    L.jdv = take(L.K * 4 * f4); L.inc_off = take((Dm + 1) * 4); L.inc = take(2 * L.K * 4);
+  } else {
+    L.jdv = L.inc_off = L.inc = 0;
+  }
+  L.misc = take(MC_N * 4);
+  L.bytes = o;
+  return L;
+}
+
+}  // namespace
+
+struct msh_handle {
+  int E = 0, B = 0, S = 0, J = 0, max_dof = 0;
+  msh_solver_cfg cfg;
+  int Dm = 0, Sm = 0, Jm = 0;
+  Layout L;
+  // device scene
+  int *d_body_off = nullptr, *d_static_off = nullptr, *d_joint_off = nullptr, *d_env_order = nullptr;
+  float4 *d_bdims = nullptr, *d_binv = nullptr;
+  float *d_static_pose = nullptr, *d_static_half = nullptr;
+  JointDesc* d_joints = nullptr;
+  int* d_status = nullptr;
+  int* d_queue = nullptr;
+  float* d_targets = nullptr;   // library copy of the targets (graphs, host path)
+  float *d_pos = nullptr, *d_quat = nullptr, *d_lv = nullptr, *d_av = nullptr;   // host-path state
+  char* d_ws_plain = nullptr;   // E slabs
+  char* d_ws_fused = nullptr;   // per-CTA slabs when SMEM cannot hold the workspace
+  int64_t bytes = 0;
+  // execution
+  int exec = MSH_EXEC_FUSED, tpe = 128, use_graph = 0;
+  int num_sms = 0, smem_optin = 0, fused_grid = 0, fused_smem = 1;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  msh_state gkey{};
+  float gkey_dt = 0.f;
+  int gkey_S = 0, gkey_exec = -1, gkey_tpe = 0;
+  bool gkey_targets = false;
+};
+
+namespace {
+
+template <class T>
+int dalloc(msh_handle* h, T** p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? MSH_ERR_OOM : MSH_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  h->bytes += (int64_t)(n * sizeof(T));
+  return MSH_OK;
+}
+
+template <class T>
+int upload(msh_handle* h, T** p, const T* src, size_t n) {
+  int rc = dalloc(h, p, n);
+  if (rc) return rc;
+  if (n) CK(cudaMemcpy(*p, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  return MSH_OK;
+}
+
+Params make_params(const msh_handle* h, const msh_state* st, const float* targets, float dt, int S) {
+  Params p;
+  std::memset(&p, 0, sizeof(p));
+  p.E = h->E; p.max_dof = h->max_dof;
+  p.body_off = h->d_body_off; p.static_off = h->d_static_off; p.joint_off = h->d_joint_off;
+  p.bdims = h->d_bdims; p.binv = h->d_binv;
+  p.static_pose = h->d_static_pose; p.static_half = h->d_static_half;
+  p.joints = h->d_joints; p.env_order = h->d_env_order;
+  p.dt = dt; p.S = S; p.h = dt / (float)S; p.N = h->cfg.iterations; p.mode = h->cfg.mode;
+  p.gx = h->cfg.gravity[0]; p.gy = h->cfg.gravity[1]; p.gz = h->cfg.gravity[2];
+  p.mu = h->cfg.friction; p.rest = h->cfg.restitution; p.off = h->cfg.contact_offset;
+  p.beta = h->cfg.baumgarte; p.jbeta = h->cfg.joint_baumgarte; p.slop = h->cfg.slop;
+  p.C = h->cfg.max_contacts; p.P = h->cfg.max_pairs;
+  if (st) { p.pos = st->pos; p.quat = st->quat; p.lv = st->linvel; p.av = st->angvel; }
+  p.targets = h->max_dof > 0 ? targets : nullptr;
+  p.status = h->d_status;
+  p.L = h->L;
+  p.queue = h->d_queue;
+  return p;
+}
+
+int ensure_plain_ws(msh_handle* h) {
+  if (h->d_ws_plain) return MSH_OK;
+  return dalloc(h, &h->d_ws_plain, (size_t)h->E * h->L.bytes);
+}
+
+int launch_collision_plain(msh_handle* h, Params p, cudaStream_t s) {
+  int rc = ensure_plain_ws(h);
+  if (rc) return rc;
+  p.ws = h->d_ws_plain;
+  p.ws_stride = h->L.bytes;
+  const int T = h->tpe;
+  k_load<<<h->E, T, 0, s>>>(p);
+  k_aabb<<<h->E, T, 0, s>>>(p);
+  k_broad<<<h->E, T, 0, s>>>(p);
+  k_narrow<<<h->E, T, 0, s>>>(p);
+  k_colour<<<h->E, T, 0, s>>>(p);
+  CK(cudaGetLastError());
+  return MSH_OK;
+}
+
+int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
+  Params p = p0;
+  const int T = h->tpe;
+  if (h->exec == MSH_EXEC_PLAIN) {
+    int rc = launch_collision_plain(h, p, s);
+    if (rc) return rc;
+    p.ws = h->d_ws_plain;
+    p.ws_stride = h->L.bytes;
+    for (int sub = 0; sub < p.S; ++sub) {
+      k_intvel<<<h->E, T, 0, s>>>(p);
+      k_prep<<<h->E, T, 0, s>>>(p);
+      for (int it = 0; it < p.N; ++it) k_solve<<<h->E, T, 0, s>>>(p);
+      k_intpos<<<h->E, T, 0, s>>>(p);
+    }
+    k_store<<<h->E, T, 0, s>>>(p);
+    CK(cudaGetLastError());
+    return MSH_OK;
+  }
+  CK(cudaMemsetAsync(h->d_queue, 0, sizeof(int), s));
+  if (h->fused_smem) {
+    p.ws = nullptr;
+    p.ws_stride = 0;
+    k_fused<<<h->fused_grid, T, h->L.bytes, s>>>(p, 1);
+  } else {
+    p.ws = h->d_ws_fused;
+    p.ws_stride = h->L.bytes;
+    k_fused<<<h->fused_grid, T, 0, s>>>(p, 0);
+  }
+  CK(cudaGetLastError());
+  return MSH_OK;
+}
+
+int configure_fused(msh_handle* h) {
+  const int bytes = h->L.bytes;
+  h->fused_smem = bytes + 1024 <= h->smem_optin;
+  int blocks = 0;
+  if (h->fused_smem) {
+    CK(cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused, h->tpe, bytes));
+  } else {
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused, h->tpe, 0));
+  }
+  if (blocks < 1) return fail(MSH_ERR_UNSUPPORTED, "fused kernel cannot be resident with this block size");
+  h->fused_grid = std::min(h->E, blocks * h->num_sms);
+  if (!h->fused_smem) {
+    if (h->d_ws_fused) { cudaFree(h->d_ws_fused); h->d_ws_fused = nullptr; }
+    int rc = dalloc(h, &h->d_ws_fused, (size_t)h->fused_grid * bytes);
+    if (rc) return rc;
+  }
+  return MSH_OK;
+}
+
+void drop_graph(msh_handle* h) {
+  if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+  h->gkey_exec = -1;
+}
+
+int check_cfg(const msh_solver_cfg* c) {
+  if (!(c->dt > 0.f) || c->substeps < 1 || c->iterations < 1 || (c->mode != 0 && c->mode != 1))
+    return fail(MSH_ERR_INVALID_ARG, "solver cfg: need dt > 0, substeps >= 1, iterations >= 1, mode 0/1");
+  if (c->max_contacts < 1 || c->max_contacts > 1024 || c->max_pairs < 1 || c->max_pairs > 4096)
+    return fail(MSH_ERR_INVALID_ARG, "solver cfg: max_contacts in 1..1024, max_pairs in 1..4096");
+  if (!(c->contact_offset >= 0.f) || !(c->friction >= 0.f) || !(c->restitution >= 0.f) || !(c->slop >= 0.f))
+    return fail(MSH_ERR_INVALID_ARG, "solver cfg: negative offset, friction, restitution or slop");
+  return MSH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* msh_last_error(void) { return g_err.c_str(); }
+
+int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** out) {
+  if (!out) return fail(MSH_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d || !cfg) return fail(MSH_ERR_INVALID_ARG, "desc or cfg is NULL");
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  const int E = d->num_envs;
+  if (E < 1 || !d->body_off || !d->static_off || !d->joint_off)
+    return fail(MSH_ERR_INVALID_ARG, "num_envs < 1 or missing offsets");
+  if (d->body_off[0] != 0 || d->static_off[0] != 0 || d->joint_off[0] != 0 || d->max_dof < 0)
+    return fail(MSH_ERR_INVALID_ARG, "offsets must start at 0; max_dof >= 0");
+  int Dm = 0, Sm = 0, Jm = 0;
+  for (int e = 0; e < E; ++e) {
+    int D = d->body_off[e + 1] - d->body_off[e];
+    int S = d->static_off[e + 1] - d->static_off[e];
+    int J = d->joint_off[e + 1] - d->joint_off[e];
+    if (D < 0 || S < 0 || J < 0) return fail(MSH_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    if (D > 4096 || S > 4096 || J > 1024)
+      return fail(MSH_ERR_INVALID_ARG, "env too large: at most 4096 bodies, 4096 static boxes, 1024 joints");
+    Dm = std::max(Dm, D); Sm = std::max(Sm, S); Jm = std::max(Jm, J);
+  }
+  const int B = d->body_off[E], S = d->static_off[E], J = d->joint_off[E];
+  if ((B && (!d->body_shape || !d->body_dims || !d->body_mass)) || (S && (!d->static_pose || !d->static_half)) ||
+      (J && (!d->joint_type || !d->joint_parent || !d->joint_child || !d->joint_dof || !d->joint_frame_a ||
+             !d->joint_frame_b || !d->joint_gains || !d->joint_limits)))
+    return fail(MSH_ERR_INVALID_ARG, "missing descriptor array");
+  for (int g = 0; g < B; ++g) {
+    int sh = d->body_shape[g];
+    if (sh < 0 || sh > 2) return fail(MSH_ERR_INVALID_ARG, "body " + std::to_string(g) + ": bad shape type");
+    if (!(d->body_mass[g] > 0.f) || !std::isfinite(d->body_mass[g]))
+      return fail(MSH_ERR_INVALID_ARG, "body " + std::to_string(g) + ": mass must be finite and > 0");
+    int nd = sh == 0 ? 1 : (sh == 1 ? 2 : 3);
+    for (int k = 0; k < nd; ++k)
+      if (!(d->body_dims[4 * g + k] > 0.f) || !std::isfinite(d->body_dims[4 * g + k]))
+        return fail(MSH_ERR_INVALID_ARG, "body " + std::to_string(g) + ": dims must be finite and > 0");
+  }
+  for (int k = 0; k < S; ++k)
+    for (int c = 0; c < 3; ++c)
+      if (!(d->static_half[3 * k + c] >= 0.f)) return fail(MSH_ERR_INVALID_ARG, "static half extents must be >= 0");
+  std::vector<JointDesc> jd(J);
+  for (int e = 0; e < E; ++e) {
+    int D = d->body_off[e + 1] - d->body_off[e];
+    for (int g = d->joint_off[e]; g < d->joint_off[e + 1]; ++g) {
+      JointDesc& j = jd[g];
+      std::memset(&j, 0, sizeof(j));
+      j.type = d->joint_type[g]; j.parent = d->joint_parent[g]; j.child = d->joint_child[g]; j.dof = d->joint_dof[g];
+      if (j.type < 0 || j.type > 2) return fail(MSH_ERR_INVALID_ARG, "joint " + std::to_string(g) + ": bad type");
+      if (j.parent < -1 || j.parent >= D || j.child < 0 || j.child >= D || j.parent == j.child)
+        return fail(MSH_ERR_INVALID_ARG, "joint " + std::to_string(g) + ": bad parent/child");
+      int ndof = j.type == 2 ? 3 : 1;
+      const float* gn = d->joint_gains + 4 * g;
+      bool drive = gn[0] > 0.f || gn[1] > 0.f;
+      if (drive && (j.dof < 0 || j.dof + ndof > d->max_dof))
+        return fail(MSH_ERR_INVALID_ARG, "joint " + std::to_string(g) + ": dof slot outside max_dof");
+      if (gn[0] < 0.f || gn[1] < 0.f || gn[2] < 0.f)
+        return fail(MSH_ERR_INVALID_ARG, "joint " + std::to_string(g) + ": negative gains");
+      std::memcpy(j.pa, d->joint_frame_a + 7 * g, 3 * 4); std::memcpy(j.qa, d->joint_frame_a + 7 * g + 3, 4 * 4);
+      std::memcpy(j.pb, d->joint_frame_b + 7 * g, 3 * 4); std::memcpy(j.qb, d->joint_frame_b + 7 * g + 3, 4 * 4);
+      j.k = gn[0]; j.d = gn[1]; j.fmax = gn[2];
+      j.lo = d->joint_limits[2 * g]; j.hi = d->joint_limits[2 * g + 1];
+    }
+  }
+  msh_handle* h = new msh_handle();
+  h->E = E; h->B = B; h->S = S; h->J = J; h->max_dof = d->max_dof; h->cfg = *cfg;
+  h->Dm = std::max(Dm, 1); h->Sm = std::max(Sm, 1); h->Jm = std::max(Jm, 1);
+  h->L = make_layout(h->Dm, h->Sm, h->Jm, cfg->max_pairs, cfg->max_contacts, cfg->mode == MSH_MODE_JACOBI);
+  auto bail = [&](int code) { msh_destroy(h); return code; };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(MSH_ERR_CUDA, "no CUDA device"));
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // envs ordered by decreasing estimated cost (longest first)
+  std::vector<int> order(E);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> cost(E);
+  for (int e = 0; e < E; ++e) {
+    double D = d->body_off[e + 1] - d->body_off[e], Sb = d->static_off[e + 1] - d->static_off[e];
+    double Jn = d->joint_off[e + 1] - d->joint_off[e];
+    cost[e] = D * (D + Sb) * 0.05 + 4.0 * D + 6.0 * Jn;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  if ((rc = upload(h, &h->d_body_off, d->body_off, E + 1))) return bail(rc);
+  if ((rc = upload(h, &h->d_static_off, d->static_off, E + 1))) return bail(rc);
+  if ((rc = upload(h, &h->d_joint_off, d->joint_off, E + 1))) return bail(rc);
+  if ((rc = upload(h, &h->d_env_order, order.data(), E))) return bail(rc);
+  if ((rc = upload(h, &h->d_static_pose, d->static_pose, (size_t)7 * S))) return bail(rc);
+  if ((rc = upload(h, &h->d_static_half, d->static_half, (size_t)3 * S))) return bail(rc);
+  if ((rc = upload(h, &h->d_joints, jd.data(), J))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_bdims, B))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_binv, B))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_status, E))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_queue, 1))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_targets, (size_t)E * std::max(1, h->max_dof)))) return bail(rc);
+  if (cudaMemset(h->d_status, 0, E * sizeof(int)) != cudaSuccess) return bail(fail(MSH_ERR_CUDA, "memset"));
+  if (cudaMemset(h->d_targets, 0, (size_t)E * std::max(1, h->max_dof) * 4) != cudaSuccess)
+    return bail(fail(MSH_ERR_CUDA, "memset"));
+  if (B) {
+    float* tm = nullptr; int* ts = nullptr; float* td = nullptr;
+    if ((rc = dalloc(h, &tm, B)) || (rc = dalloc(h, &ts, B)) || (rc = dalloc(h, &td, (size_t)4 * B))) {
+      cudaFree(tm); cudaFree(ts); cudaFree(td);
+      return bail(rc);
+    }
+    cudaMemcpy(tm, d->body_mass, B * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(ts, d->body_shape, B * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(td, d->body_dims, (size_t)B * 16, cudaMemcpyHostToDevice);
+    k_params<<<(B + 255) / 256, 256>>>(B, tm, ts, td, h->d_binv, h->d_bdims);
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(tm); cudaFree(ts); cudaFree(td);
+    h->bytes -= (int64_t)B * (4 + 4 + 16);
+    if (e != cudaSuccess) return bail(fail(MSH_ERR_CUDA, std::string("k_params: ") + cudaGetErrorString(e)));
+  }
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(MSH_ERR_CUDA, "stream create"));
+  h->tpe = 128;
+  h->exec = MSH_EXEC_FUSED;
+  if ((rc = configure_fused(h))) return bail(rc);
+  *out = h;
+  return MSH_OK;
+}
+
+void msh_destroy(msh_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  drop_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  void* ptrs[] = {h->d_body_off, h->d_static_off, h->d_joint_off, h->d_env_order, h->d_bdims, h->d_binv,
+                  h->d_static_pose, h->d_static_half, h->d_joints, h->d_status, h->d_queue, h->d_targets,
+                  h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+int msh_set_exec(msh_handle* h, int32_t exec, int32_t tpe, int32_t use_graph) {
+  if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
+  if (exec != MSH_EXEC_PLAIN && exec != MSH_EXEC_FUSED) return fail(MSH_ERR_INVALID_ARG, "exec must be 0 or 1");
+  if (tpe == 0) tpe = 128;
+  if (tpe != 32 && tpe != 64 && tpe != 128 && tpe != 256 && tpe != 512)
+    return fail(MSH_ERR_INVALID_ARG, "threads_per_env must be 32, 64, 128, 256 or 512");
+  cudaDeviceSynchronize();
+  drop_graph(h);
+  h->exec = exec;
+  h->tpe = tpe;
+  h->use_graph = use_graph != 0;
+  if (exec == MSH_EXEC_FUSED) return configure_fused(h);
+  return ensure_plain_ws(h);
+}
+
+static int step_impl(msh_handle* h, const msh_state* st, const float* targets, float dt, int32_t substeps,
+                     cudaStream_t s) {
+  if (!h || !st || !st->pos || !st->quat || !st->linvel || !st->angvel)
+    return fail(MSH_ERR_INVALID_ARG, "handle or state pointer is NULL");
+  if (h->max_dof > 0 && !targets) return fail(MSH_ERR_INVALID_ARG, "joint_targets is NULL but max_dof > 0");
+  if (!(dt > 0.f)) dt = h->cfg.dt;
+  if (substeps < 1) substeps = h->cfg.substeps;
+  if (!h->use_graph) return enqueue_step(h, make_params(h, st, targets, dt, substeps), s);
+  // graph path: targets go through the library buffer so one graph serves every call
+  if (h->max_dof > 0)
+    CK(cudaMemcpyAsync(h->d_targets, targets, (size_t)h->E * h->max_dof * 4, cudaMemcpyDeviceToDevice, s));
+  bool hit = h->gexec && h->gkey.pos == st->pos && h->gkey.quat == st->quat && h->gkey.linvel == st->linvel &&
+             h->gkey.angvel == st->angvel && h->gkey_dt == dt && h->gkey_S == substeps && h->gkey_exec == h->exec &&
+             h->gkey_tpe == h->tpe;
+  if (!hit) {
+    drop_graph(h);
+    if (h->exec == MSH_EXEC_PLAIN) { int rc = ensure_plain_ws(h); if (rc) return rc; }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step(h, make_params(h, st, h->d_targets, dt, substeps), h->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ce != cudaSuccess) return fail(MSH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { h->gexec = nullptr; return fail(MSH_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce)); }
+    h->gkey = *st; h->gkey_dt = dt; h->gkey_S = substeps; h->gkey_exec = h->exec; h->gkey_tpe = h->tpe;
+  }
+  CK(cudaGraphLaunch(h->gexec, s));
+  return MSH_OK;
+}
+
+int msh_step(msh_handle* h, const msh_state* st, const float* joint_targets, float dt, int32_t substeps,
+             void* stream) {
+  return step_impl(h, st, joint_targets, dt, substeps, (cudaStream_t)stream);
+}
+
+int msh_step_host(msh_handle* h, float* pos, float* quat, float* linvel, float* angvel, const float* targets,
+                  float dt, int32_t substeps, void* stream) {
+  if (!h || !pos || !quat || !linvel || !angvel) return fail(MSH_ERR_INVALID_ARG, "NULL argument");
+  if (h->max_dof > 0 && !targets) return fail(MSH_ERR_INVALID_ARG, "joint_targets is NULL but max_dof > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc;
+  if (!h->d_pos) {
+    if ((rc = dalloc(h, &h->d_pos, (size_t)3 * h->B)) || (rc = dalloc(h, &h->d_quat, (size_t)4 * h->B)) ||
+        (rc = dalloc(h, &h->d_lv, (size_t)3 * h->B)) || (rc = dalloc(h, &h->d_av, (size_t)3 * h->B)))
+      return rc;
+  }
+  const size_t b3 = (size_t)3 * h->B * 4, b4 = (size_t)4 * h->B * 4;
+  CK(cudaMemcpyAsync(h->d_pos, pos, b3, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->d_quat, quat, b4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->d_lv, linvel, b3, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->d_av, angvel, b3, cudaMemcpyHostToDevice, s));
+  if (h->max_dof > 0)
+    CK(cudaMemcpyAsync(h->d_targets, targets, (size_t)h->E * h->max_dof * 4, cudaMemcpyHostToDevice, s));
+  msh_state st{h->d_pos, h->d_quat, h->d_lv, h->d_av};
+  if (h->use_graph) {
+    // the graph path copies targets device-to-device from the given pointer
+    rc = step_impl(h, &st, h->d_targets, dt, substeps, s);
+  } else {
+    rc = step_impl(h, &st, h->d_targets, dt, substeps, s);
+  }
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(pos, h->d_pos, b3, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(quat, h->d_quat, b4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(linvel, h->d_lv, b3, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(angvel, h->d_av, b3, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return MSH_OK;
+}
+
+int msh_detect(msh_handle* h, const msh_state* st, float* aabb_body, float* aabb_static, int32_t* pair_count,
+               int32_t* pairs, int32_t* contact_count, int32_t* contact_ids, float* contact_geom,
+               int32_t* manifold_count, int32_t* colours, int32_t* ncolours, void* stream) {
+  if (!h || !st || !st->pos || !st->quat || !st->linvel || !st->angvel)
+    return fail(MSH_ERR_INVALID_ARG, "handle or state pointer is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  Params p = make_params(h, st, nullptr, h->cfg.dt, h->cfg.substeps);
+  int rc = launch_collision_plain(h, p, s);
+  if (rc) return rc;
+  p.ws = h->d_ws_plain;
+  p.ws_stride = h->L.bytes;
+  k_export<<<h->E, 128, 0, s>>>(p, aabb_body, aabb_static, pair_count, pairs, contact_count, contact_ids,
+                                contact_geom, manifold_count, colours, ncolours, h->J);
+  CK(cudaGetLastError());
+  return MSH_OK;
+}
+
+int msh_get_status(msh_handle* h, int32_t* status_host, void* stream) {
+  if (!h || !status_host) return fail(MSH_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(status_host, h->d_status, (size_t)h->E * 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return MSH_OK;
+}
+
+int msh_clear_status(msh_handle* h, void* stream) {
+  if (!h) return fail(MSH_ERR_INVALID_ARG, "NULL handle");
+  CK(cudaMemsetAsync(h->d_status, 0, (size_t)h->E * 4, (cudaStream_t)stream));
+  return MSH_OK;
+}
+
+int64_t msh_scratch_bytes(const msh_handle* h) { return h ? h->bytes : 0; }
+int64_t msh_workspace_bytes(const msh_handle* h) { return h ? h->L.bytes : 0; }
+
+int32_t msh_launches_per_step(const msh_handle* h) {
+  if (!h) return 0;
+  if (h->exec == MSH_EXEC_FUSED) return 1;
+  return 6 + h->cfg.substeps * (3 + h->cfg.iterations);
+}
+
+}  // extern "C"

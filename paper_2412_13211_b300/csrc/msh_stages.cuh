@@ -1,0 +1,818 @@
+// Stages of the batched rigid-body step, written as block-cooperative device
+// functions over one environment's workspace. The fused persistent kernel
+// keeps the workspace in shared memory and calls every stage in sequence;
+// the plain form launches one kernel per stage with the workspace in HBM.
+// Both run the same functions with the same thread mapping, so their results
+// are bitwise identical.
+#pragma once
+#include "msh_collide.cuh"
+
+namespace msh {
+
+enum { ST_PAIR_OVERFLOW = 1, ST_CONTACT_OVERFLOW = 2, ST_COLOUR_OVERFLOW = 4, ST_NONFINITE = 8 };
+enum { JT_REVOLUTE = 0, JT_PRISMATIC = 1, JT_PLANAR = 2 };
+enum { MODE_COLOURED = 0, MODE_JACOBI = 1 };
+enum { MAX_COLOURS = 64, ROWS_PER_JOINT = 8 };
+// misc counters in the workspace
+enum { MC_PAIRS = 0, MC_CONTACTS = 1, MC_MANIFOLDS = 2, MC_COLOURS = 3, MC_STATUS = 4, MC_N = 8 };
+
+struct JointDesc {     // 96 bytes
+  int type, parent, child, dof;
+  float pa[3], qa[4], pb[3], qb[4];
+  float k, d, fmax, lo, hi, pad;
+};
+
+// Byte offsets of the per-env workspace arrays (16-byte aligned).
+struct Layout {
+  int Dm, Sm, Jm, P, C, K, R;
+  int bx, bq, bv, bw, bI, bd, bIw0, bIw1;
+  int sc, sM, alo, ahi;
+  int pairs, cn, cra, crb, cid;
+  int kra, krb, kt1, kt2, klam;
+  int man, jr, ccol, corder, coff, masks;
+  int jdv, inc_off, inc, misc;
+  int bytes;
+};
+
+struct Params {
+  // scene
+  int E, max_dof;
+  const int* body_off;
+  const int* static_off;
+  const int* joint_off;
+  const float4* bdims;   // (d0, d1, d2, shape)
+  const float4* binv;    // (invm, invIx, invIy, invIz)
+  const float* static_pose;
+  const float* static_half;
+  const JointDesc* joints;
+  const int* env_order;
+  // solver
+  float dt, h;
+  int S, N, mode;
+  float gx, gy, gz, mu, rest, off, beta, jbeta, slop;
+  int C, P;
+  // state
+  float* pos;
+  float* quat;
+  float* lv;
+  float* av;
+  const float* targets;
+  int* status;
+  // workspace
+  Layout L;
+  char* ws;              // HBM workspace base (plain form, or fused without room in SMEM)
+  long long ws_stride;   // bytes between per-env (plain) or per-CTA (fused) slabs
+  int* queue;
+};
+
+struct Ws {
+  float4 *bx, *bq, *bv, *bw, *bI, *bd, *bIw0, *bIw1;
+  float4 *sc, *sM, *alo, *ahi;
+  int* pairs;
+  float4 *cn, *cra, *crb;
+  int* cid;
+  float4 *kra, *krb, *kt1, *kt2, *klam;
+  int4* man;
+  float4* jr;
+  int *ccol, *corder, *coff;
+  unsigned long long* masks;
+  float4* jdv;
+  int *inc_off, *inc, *misc;
+};
+
+__device__ __forceinline__ Ws make_ws(char* b, const Layout& L) {
+  Ws w;
+  w.bx = (float4*)(b + L.bx); w.bq = (float4*)(b + L.bq); w.bv = (float4*)(b + L.bv); w.bw = (float4*)(b + L.bw);
+  w.bI = (float4*)(b + L.bI); w.bd = (float4*)(b + L.bd); w.bIw0 = (float4*)(b + L.bIw0); w.bIw1 = (float4*)(b + L.bIw1);
+  w.sc = (float4*)(b + L.sc); w.sM = (float4*)(b + L.sM); w.alo = (float4*)(b + L.alo); w.ahi = (float4*)(b + L.ahi);
+  w.pairs = (int*)(b + L.pairs);
+  w.cn = (float4*)(b + L.cn); w.cra = (float4*)(b + L.cra); w.crb = (float4*)(b + L.crb); w.cid = (int*)(b + L.cid);
+  w.kra = (float4*)(b + L.kra); w.krb = (float4*)(b + L.krb); w.kt1 = (float4*)(b + L.kt1); w.kt2 = (float4*)(b + L.kt2);
+  w.klam = (float4*)(b + L.klam);
+  w.man = (int4*)(b + L.man); w.jr = (float4*)(b + L.jr);
+  w.ccol = (int*)(b + L.ccol); w.corder = (int*)(b + L.corder); w.coff = (int*)(b + L.coff);
+  w.masks = (unsigned long long*)(b + L.masks);
+  w.jdv = (float4*)(b + L.jdv); w.inc_off = (int*)(b + L.inc_off); w.inc = (int*)(b + L.inc);
+  w.misc = (int*)(b + L.misc);
+  return w;
+}
+
+struct EnvInfo { int env, b0, D, s0, S, j0, J; };
+
+__device__ __forceinline__ EnvInfo env_info(const Params& p, int env) {
+  EnvInfo e;
+  e.env = env;
+  e.b0 = p.body_off[env]; e.D = p.body_off[env + 1] - e.b0;
+  e.s0 = p.static_off[env]; e.S = p.static_off[env + 1] - e.s0;
+  e.j0 = p.joint_off[env]; e.J = p.joint_off[env + 1] - e.j0;
+  return e;
+}
+
+// Exclusive block-wide prefix sum; every thread of the block must call it.
+// `scr` is 33 ints of shared memory.
+__device__ __forceinline__ int block_exscan(int v, int* scr, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scr[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int s = lane < nw ? scr[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) scr[lane] = s;
+  }
+  __syncthreads();
+  int off = warp > 0 ? scr[warp - 1] : 0;
+  *total = scr[nw - 1];
+  __syncthreads();
+  return off + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// a0: stage the env's bodies and statics
+// ---------------------------------------------------------------------------
+__device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    int g = e.b0 + i;
+    float4 inv = p.binv[g];
+    float4 dm = p.bdims[g];
+    w.bx[i] = make_float4(p.pos[3 * g], p.pos[3 * g + 1], p.pos[3 * g + 2], inv.x);
+    w.bq[i] = make_float4(p.quat[4 * g], p.quat[4 * g + 1], p.quat[4 * g + 2], p.quat[4 * g + 3]);
+    w.bv[i] = make_float4(p.lv[3 * g], p.lv[3 * g + 1], p.lv[3 * g + 2], 0.f);
+    w.bw[i] = make_float4(p.av[3 * g], p.av[3 * g + 1], p.av[3 * g + 2], 0.f);
+    w.bI[i] = make_float4(inv.y, inv.z, inv.w, dm.w);
+    w.bd[i] = make_float4(dm.x, dm.y, dm.z, 1.f);
+  }
+  for (int k = threadIdx.x; k < e.S; k += blockDim.x) {
+    const float* sp = p.static_pose + 7 * (e.s0 + k);
+    const float* sh = p.static_half + 3 * (e.s0 + k);
+    Q4<nf> q; q.w = nf(sp[3]); q.x = nf(sp[4]); q.y = nf(sp[5]); q.z = nf(sp[6]);
+    M3<nf> M = qmat(q);
+    w.sc[k] = make_float4(sp[0], sp[1], sp[2], 0.f);
+    for (int r = 0; r < 3; ++r) w.sM[3 * k + r] = make_float4(M.m[r][0].v, M.m[r][1].v, M.m[r][2].v, sh[r]);
+  }
+  if (threadIdx.x < MC_N) w.misc[threadIdx.x] = 0;
+}
+
+__device__ __forceinline__ int body_shape_type(const Ws& w, int i) { return __float_as_int(w.bI[i].w); }
+
+// Collision shape of index i: dynamic body, static box or the plane.
+__device__ __forceinline__ Shape<nf> coll_shape(const Ws& w, const EnvInfo& e, int i) {
+  Shape<nf> s;
+  if (i < e.D) {
+    float4 x = w.bx[i], q4 = w.bq[i], d = w.bd[i];
+    Q4<nf> q; q.w = nf(q4.x); q.x = nf(q4.y); q.y = nf(q4.z); q.z = nf(q4.w);
+    s.type = body_shape_type(w, i);
+    s.c = v3<nf>(nf(x.x), nf(x.y), nf(x.z));
+    s.M = qmat(q);
+    s.d0 = nf(d.x); s.d1 = nf(d.y); s.d2 = nf(d.z);
+  } else if (i < e.D + e.S) {
+    int k = i - e.D;
+    float4 c = w.sc[k];
+    float4 r0 = w.sM[3 * k], r1 = w.sM[3 * k + 1], r2 = w.sM[3 * k + 2];
+    s.type = SH_BOX;
+    s.c = v3<nf>(nf(c.x), nf(c.y), nf(c.z));
+    s.M.m[0][0] = nf(r0.x); s.M.m[0][1] = nf(r0.y); s.M.m[0][2] = nf(r0.z);
+    s.M.m[1][0] = nf(r1.x); s.M.m[1][1] = nf(r1.y); s.M.m[1][2] = nf(r1.z);
+    s.M.m[2][0] = nf(r2.x); s.M.m[2][1] = nf(r2.y); s.M.m[2][2] = nf(r2.z);
+    s.d0 = nf(r0.w); s.d1 = nf(r1.w); s.d2 = nf(r2.w);
+  } else {
+    s.type = SH_PLANE;
+    s.c = v3<nf>(nf(0.f), nf(0.f), nf(0.f));
+    s.d0 = s.d1 = s.d2 = nf(0.f);
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// a2: AABBs of bodies and static boxes
+// ---------------------------------------------------------------------------
+__device__ void stage_aabb(const Params& p, const EnvInfo& e, const Ws& w) {
+  for (int i = threadIdx.x; i < e.D + e.S; i += blockDim.x) {
+    Shape<nf> s = coll_shape(w, e, i);
+    AABBt<nf> b = shape_aabb(s, nf(p.off));
+    w.alo[i] = make_float4(b.lo.x.v, b.lo.y.v, b.lo.z.v, 0.f);
+    w.ahi[i] = make_float4(b.hi.x.v, b.hi.y.v, b.hi.z.v, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a3: broadphase over the flattened (i<j) candidate list, order-preserving
+// compaction with a block scan
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool jointed(const Params& p, const EnvInfo& e, int i, int j) {
+  for (int k = 0; k < e.J; ++k) {
+    const JointDesc& jd = p.joints[e.j0 + k];
+    if ((jd.parent == i && jd.child == j) || (jd.parent == j && jd.child == i)) return true;
+  }
+  return false;
+}
+
+__device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w, int* scr) {
+  const int D = e.D, W = e.D + e.S;   // j in (i, W]; W is the plane
+  // row i holds candidates j = i+1..W: W - i of them; start(i) = i*W - i*(i-1)/2
+  const long long total = (long long)D * W - (long long)D * (D - 1) / 2;
+  int count = 0;
+  int status = 0;
+  for (long long base = 0; base < total; base += blockDim.x) {
+    long long k = base + threadIdx.x;
+    int flag = 0, pi = 0, pj = 0;
+    if (k < total) {
+      int lo = 0, hi = D - 1;
+      while (lo < hi) {   // largest i with start(i) <= k
+        int mid = (lo + hi + 1) >> 1;
+        long long st = (long long)mid * W - (long long)mid * (mid - 1) / 2;
+        if (st <= k) lo = mid; else hi = mid - 1;
+      }
+      pi = lo;
+      long long st = (long long)pi * W - (long long)pi * (pi - 1) / 2;
+      pj = pi + 1 + (int)(k - st);
+      float4 al = w.alo[pi];
+      if (pj == W) {
+        flag = al.z <= 0.f;
+      } else {
+        float4 ah = w.ahi[pi], bl = w.alo[pj], bh = w.ahi[pj];
+        flag = al.x <= bh.x && bl.x <= ah.x && al.y <= bh.y && bl.y <= ah.y && al.z <= bh.z && bl.z <= ah.z;
+        if (flag && pj < D && jointed(p, e, pi, pj)) flag = 0;
+      }
+    }
+    int tot;
+    int pre = block_exscan(flag, scr, &tot);
+    if (flag) {
+      int slot = count + pre;
+      if (slot < p.P) w.pairs[slot] = pi | (pj << 16);
+    }
+    count += tot;
+  }
+  if (count > p.P) { status |= ST_PAIR_OVERFLOW; count = p.P; }
+  if (threadIdx.x == 0) {
+    w.misc[MC_PAIRS] = count;
+    w.misc[MC_STATUS] |= status;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// a4: narrowphase, pairs in order, points in routine order, truncated at C
+// ---------------------------------------------------------------------------
+__device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w, int* scr) {
+  const int npairs = w.misc[MC_PAIRS];
+  int cbase = 0, mbase = 0;
+  bool over = false;
+  for (int base = 0; base < npairs; base += blockDim.x) {
+    int idx = base + threadIdx.x;
+    Pt<nf> pts[4];
+    Shape<nf> Si, Sj;
+    int n = 0, pi = 0, pj = 0;
+    if (idx < npairs) {
+      int pr = w.pairs[idx];
+      pi = pr & 0xffff;
+      pj = pr >> 16;
+      Si = coll_shape(w, e, pi);
+      Sj = coll_shape(w, e, pj);
+      n = collide(Si, Sj, nf(p.off), pts);
+    }
+    int tot;
+    int pre = block_exscan(n, scr, &tot);
+    int start = cbase + pre;
+    int kept = n;
+    if (start + kept > p.C) kept = max(0, p.C - start);
+    if (idx < npairs && kept > 0) {
+      for (int k = 0; k < kept; ++k) {
+        int c = start + k;
+        V3<nf> ra = mulT(Si.M, pts[k].pa - Si.c);
+        V3<nf> rb = pj < e.D ? mulT(Sj.M, pts[k].pb - Sj.c) : pts[k].pb;
+        w.cn[c] = make_float4(pts[k].n.x.v, pts[k].n.y.v, pts[k].n.z.v, pts[k].s.v);
+        w.cra[c] = make_float4(ra.x.v, ra.y.v, ra.z.v, 0.f);
+        w.crb[c] = make_float4(rb.x.v, rb.y.v, rb.z.v, 0.f);
+        w.cid[c] = pi | (pj << 16);
+      }
+    }
+    int mt;
+    int mpre = block_exscan(kept > 0 ? 1 : 0, scr, &mt);
+    if (idx < npairs && kept > 0)
+      w.man[mbase + mpre] = make_int4(pi, pj < e.D ? pj : -1, start, kept);
+    if (cbase + tot > p.C) over = true;
+    cbase = min(cbase + tot, p.C);
+    mbase += mt;
+  }
+  if (threadIdx.x == 0) {
+    w.misc[MC_CONTACTS] = cbase;
+    w.misc[MC_MANIFOLDS] = mbase;
+    if (over) w.misc[MC_STATUS] |= ST_CONTACT_OVERFLOW;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// a5 (once per step): greedy colouring of joints then manifolds, colour-sorted
+// constraint order; Jacobi split counts and body incidence lists
+// ---------------------------------------------------------------------------
+__device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
+  const int J = e.J, M = w.misc[MC_MANIFOLDS], K = J + M;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < e.D; ++i) w.masks[i] = 0ull;
+    int ncol = 0, status = 0;
+    int cnt[MAX_COLOURS + 1];
+    for (int c = 0; c <= MAX_COLOURS; ++c) cnt[c] = 0;
+    for (int k = 0; k < K; ++k) {
+      int a, b;
+      if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
+      else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
+      unsigned long long msk = 0ull;
+      if (a >= 0) msk |= w.masks[a];
+      if (b >= 0) msk |= w.masks[b];
+      int c;
+      if (msk == ~0ull) { c = -1; status |= ST_COLOUR_OVERFLOW; }
+      else {
+        c = __ffsll((long long)~msk) - 1;
+        if (a >= 0) w.masks[a] |= 1ull << c;
+        if (b >= 0) w.masks[b] |= 1ull << c;
+        cnt[c]++;
+        if (c + 1 > ncol) ncol = c + 1;
+      }
+      w.ccol[k] = c;
+    }
+    int acc = 0;
+    for (int c = 0; c < ncol; ++c) { w.coff[c] = acc; acc += cnt[c]; cnt[c] = w.coff[c]; }
+    w.coff[ncol] = acc;
+    for (int k = 0; k < K; ++k) {
+      int c = w.ccol[k];
+      if (c >= 0) w.corder[cnt[c]++] = k;
+    }
+    w.misc[MC_COLOURS] = ncol;
+    w.misc[MC_STATUS] |= status;
+    if (p.mode == MODE_JACOBI) {
+      for (int i = 0; i <= e.D; ++i) w.inc_off[i] = 0;
+      for (int k = 0; k < K; ++k) {
+        int a, b;
+        if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
+        else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
+        if (a >= 0) w.inc_off[a + 1]++;
+        if (b >= 0) w.inc_off[b + 1]++;
+      }
+      for (int i = 0; i < e.D; ++i) {
+        int n = w.inc_off[i + 1];
+        w.bd[i].w = (float)(n > 0 ? n : 1);
+        w.inc_off[i + 1] += w.inc_off[i];
+      }
+      for (int i = 0; i < e.D; ++i) w.masks[i] = (unsigned long long)w.inc_off[i];   // fill cursor
+      for (int k = 0; k < K; ++k) {
+        int a, b;
+        if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
+        else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
+        if (a >= 0) w.inc[w.masks[a]++] = 2 * k;
+        if (b >= 0) w.inc[w.masks[b]++] = 2 * k + 1;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// a1: gravity; world inverse inertia
+// ---------------------------------------------------------------------------
+__device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws& w) {
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    float4 v = w.bv[i];
+    v.x = v.x + p.gx * p.h; v.y = v.y + p.gy * p.h; v.z = v.z + p.gz * p.h;
+    w.bv[i] = v;
+    float4 q4 = w.bq[i], I = w.bI[i];
+    Q4<float> q; q.w = q4.x; q.x = q4.y; q.y = q4.z; q.z = q4.w;
+    M3<float> R = qmat(q);
+    float d[3] = {I.x, I.y, I.z};
+    float W[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        W[a][b] = R.m[a][0] * d[0] * R.m[b][0] + R.m[a][1] * d[1] * R.m[b][1] + R.m[a][2] * d[2] * R.m[b][2];
+    w.bIw0[i] = make_float4(W[0][0], W[0][1], W[0][2], W[1][1]);
+    w.bIw1[i] = make_float4(W[1][2], W[2][2], 0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ Sym3 load_Iw(const Ws& w, int i) {
+  float4 a = w.bIw0[i], b = w.bIw1[i];
+  Sym3 S; S.xx = a.x; S.xy = a.y; S.xz = a.z; S.yy = a.w; S.yz = b.x; S.zz = b.y;
+  return S;
+}
+
+// ---------------------------------------------------------------------------
+// a5 (per substep): rows
+// ---------------------------------------------------------------------------
+// Generic joint row: 6 float4 = la|m, aa|bias, lb|gamma, ab|lam, Ia|lo, Ib|hi.
+struct JRow { V3<float> la, aa, lb, ab, Ia, Ib; float m, bias, gamma, lam, lo, hi; };
+
+__device__ __forceinline__ void put_row(float4* r, const JRow& x) {
+  r[0] = f4(x.la, x.m); r[1] = f4(x.aa, x.bias); r[2] = f4(x.lb, x.gamma);
+  r[3] = f4(x.ab, x.lam); r[4] = f4(x.Ia, x.lo); r[5] = f4(x.Ib, x.hi);
+}
+
+__device__ __forceinline__ JRow blank_row() {
+  JRow r;
+  V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  r.la = z; r.aa = z; r.lb = z; r.ab = z; r.Ia = z; r.Ib = z;
+  r.m = 0.f; r.bias = 0.f; r.gamma = 0.f; r.lam = 0.f; r.lo = -INFINITY; r.hi = INFINITY;
+  return r;
+}
+
+struct RowCtx { int a, b; float ima, imb, sa, sb; Sym3 Ia, Ib; };
+
+__device__ __forceinline__ void finish_row(JRow& r, const RowCtx& c, bool soft) {
+  float K = 0.f;
+  if (c.a >= 0) { r.Ia = smul(c.Ia, r.aa); K = K + c.sa * (c.ima * dot(r.la, r.la) + dot(r.aa, r.Ia)); }
+  if (c.b >= 0) { r.Ib = smul(c.Ib, r.ab); K = K + c.sb * (c.imb * dot(r.lb, r.lb) + dot(r.ab, r.Ib)); }
+  if (soft) r.m = 1.f / (K + r.gamma);
+  else r.m = K > 0.f ? 1.f / K : 0.f;
+}
+
+__device__ __forceinline__ JRow lin_row(const V3<float>& u, const V3<float>& ra, const V3<float>& rb) {
+  JRow r = blank_row();
+  r.la = -u; r.aa = -cross(ra, u); r.lb = u; r.ab = cross(rb, u);
+  return r;
+}
+__device__ __forceinline__ JRow ang_row(const V3<float>& u) {
+  JRow r = blank_row();
+  r.aa = -u; r.ab = u;
+  return r;
+}
+__device__ __forceinline__ void soft_row(JRow& r, float h, float C, float k, float d, float fmax) {
+  float den = d + h * k;
+  r.gamma = 1.f / (h * den);
+  r.bias = (h * k / den) / h * C;
+  r.lo = -fmax * h;
+  r.hi = fmax * h;
+}
+
+__device__ __forceinline__ Q4<float> ldq(const float* q) { Q4<float> r; r.w = q[0]; r.x = q[1]; r.y = q[2]; r.z = q[3]; return r; }
+__device__ __forceinline__ Q4<float> ldq4(float4 q) { Q4<float> r; r.w = q.x; r.x = q.y; r.y = q.z; r.z = q.w; return r; }
+
+__device__ __forceinline__ RowCtx row_ctx(const Ws& w, int a, int b) {
+  RowCtx c;
+  c.a = a; c.b = b;
+  c.ima = a >= 0 ? w.bx[a].w : 0.f;
+  c.imb = b >= 0 ? w.bx[b].w : 0.f;
+  c.sa = a >= 0 ? w.bd[a].w : 1.f;
+  c.sb = b >= 0 ? w.bd[b].w : 1.f;
+  if (a >= 0) c.Ia = load_Iw(w, a);
+  if (b >= 0) c.Ib = load_Iw(w, b);
+  return c;
+}
+
+__device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k) {
+  const JointDesc& j = p.joints[e.j0 + k];
+  const float h = p.h, beta = p.jbeta / h;
+  const float* tgt = p.targets ? p.targets + (size_t)e.env * p.max_dof : nullptr;
+  int A = j.parent, B = j.child;
+  RowCtx ctx = row_ctx(w, A, B);
+  V3<float> pa_l = v3<float>(j.pa[0], j.pa[1], j.pa[2]);
+  V3<float> pb_l = v3<float>(j.pb[0], j.pb[1], j.pb[2]);
+  V3<float> xa, ra, pa_w;
+  Q4<float> qFA;
+  if (A >= 0) {
+    xa = f3(w.bx[A]);
+    Q4<float> qa = ldq4(w.bq[A]);
+    ra = mul(qmat(qa), pa_l);
+    pa_w = xa + ra;
+    qFA = qmul(qa, ldq(j.qa));
+  } else {
+    xa = pa_l; ra = v3<float>(0.f, 0.f, 0.f); pa_w = pa_l; qFA = ldq(j.qa);
+  }
+  Q4<float> qb = ldq4(w.bq[B]);
+  V3<float> rb = mul(qmat(qb), pb_l);
+  V3<float> pb_w = f3(w.bx[B]) + rb;
+  Q4<float> qFB = qmul(qb, ldq(j.qb));
+  M3<float> MF = qmat(qFA);
+  V3<float> ux = col(MF, 0), uy = col(MF, 1), uz = col(MF, 2);
+  V3<float> dp = pb_w - pa_w;
+  Q4<float> qr = qmul(qconj(qFA), qFB);
+  if (qr.w < 0.f) { qr.w = -qr.w; qr.x = -qr.x; qr.y = -qr.y; qr.z = -qr.z; }
+  V3<float> raB = A >= 0 ? pb_w - xa : v3<float>(0.f, 0.f, 0.f);
+  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * 6;
+  int n = 0;
+  bool drive = j.k > 0.f || j.d > 0.f;
+  if (j.type == JT_REVOLUTE) {
+    for (int c = 0; c < 3; ++c) {
+      JRow r = lin_row(unit<float>(c), ra, rb);
+      r.bias = beta * comp(dp, c);
+      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+    }
+    V3<float> cr = cross(ux, col(qmat(qFB), 0));
+    JRow r1 = ang_row(uy); r1.bias = beta * dot(cr, uy); finish_row(r1, ctx, false); put_row(rows + 6 * n++, r1);
+    JRow r2 = ang_row(uz); r2.bias = beta * dot(cr, uz); finish_row(r2, ctx, false); put_row(rows + 6 * n++, r2);
+    if (drive) {
+      JRow r = ang_row(ux);
+      float theta = 2.f * atan2f(qr.x, qr.w);
+      soft_row(r, h, theta - (tgt ? tgt[j.dof] : 0.f), j.k, j.d, j.fmax);
+      finish_row(r, ctx, true); put_row(rows + 6 * n++, r);
+    }
+  } else if (j.type == JT_PRISMATIC) {
+    V3<float> us[2] = {uy, uz};
+    for (int c = 0; c < 2; ++c) {
+      JRow r = lin_row(us[c], raB, rb);
+      r.bias = beta * dot(dp, us[c]);
+      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+    }
+    V3<float> ua[3] = {ux, uy, uz};
+    float qv[3] = {qr.x, qr.y, qr.z};
+    for (int c = 0; c < 3; ++c) {
+      JRow r = ang_row(ua[c]);
+      r.bias = beta * (2.f * qv[c]);
+      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+    }
+    float dd = dot(dp, ux);
+    if (drive) {
+      JRow r = lin_row(ux, raB, rb);
+      soft_row(r, h, dd - (tgt ? tgt[j.dof] : 0.f), j.k, j.d, j.fmax);
+      finish_row(r, ctx, true); put_row(rows + 6 * n++, r);
+    }
+    for (int c = 0; c < 2; ++c) {
+      JRow r = lin_row(c == 0 ? ux : -ux, raB, rb);
+      float C = c == 0 ? dd - j.lo : j.hi - dd;
+      r.bias = C > 0.f ? C / h : beta * C;
+      r.lo = 0.f; r.hi = INFINITY;
+      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+    }
+  } else {
+    {
+      JRow r = lin_row(uz, raB, rb);
+      r.bias = beta * dot(dp, uz);
+      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+    }
+    V3<float> cr = cross(uz, col(qmat(qFB), 2));
+    V3<float> us[2] = {ux, uy};
+    for (int c = 0; c < 2; ++c) {
+      JRow r = ang_row(us[c]);
+      r.bias = beta * dot(cr, us[c]);
+      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+    }
+    if (drive) {
+      for (int c = 0; c < 2; ++c) {
+        JRow r = lin_row(us[c], raB, rb);
+        soft_row(r, h, dot(dp, us[c]) - (tgt ? tgt[j.dof + c] : 0.f), j.k, j.d, j.fmax);
+        finish_row(r, ctx, true); put_row(rows + 6 * n++, r);
+      }
+      JRow r = ang_row(uz);
+      float theta = 2.f * atan2f(qr.z, qr.w);
+      soft_row(r, h, theta - (tgt ? tgt[j.dof + 2] : 0.f), j.k, j.d, j.fmax);
+      finish_row(r, ctx, true); put_row(rows + 6 * n++, r);
+    }
+  }
+}
+
+__device__ __forceinline__ int joint_row_count(int type, bool drive) {
+  if (type == JT_REVOLUTE) return drive ? 6 : 5;
+  if (type == JT_PRISMATIC) return drive ? 8 : 7;
+  return drive ? 6 : 3;
+}
+
+// Duff et al. (2017) orthonormal basis from a unit normal.
+__device__ __forceinline__ void onb(const V3<float>& n, V3<float>& t1, V3<float>& t2) {
+  float sg = n.z >= 0.f ? 1.f : -1.f;
+  float a = -1.f / (sg + n.z);
+  float b = n.x * n.y * a;
+  t1 = v3<float>(1.f + sg * n.x * n.x * a, sg * b, -sg * n.x);
+  t2 = v3<float>(b, sg + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float eff_mass(const RowCtx& c, const V3<float>& d, const V3<float>& ra, const V3<float>& rb) {
+  float K = 0.f;
+  if (c.a >= 0) { V3<float> x = cross(ra, d); K = K + c.sa * (c.ima * dot(d, d) + dot(x, smul(c.Ia, x))); }
+  if (c.b >= 0) { V3<float> x = cross(rb, d); K = K + c.sb * (c.imb * dot(d, d) + dot(x, smul(c.Ib, x))); }
+  return K > 0.f ? 1.f / K : 0.f;
+}
+
+__device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int ci) {
+  int ids = w.cid[ci];
+  int a = ids & 0xffff, bc = ids >> 16;
+  int b = bc < e.D ? bc : -1;
+  RowCtx ctx = row_ctx(w, a, b);
+  float4 cn = w.cn[ci];
+  V3<float> n = f3(cn);
+  V3<float> ra = mul(qmat(ldq4(w.bq[a])), f3(w.cra[ci]));
+  V3<float> pa_w = f3(w.bx[a]) + ra;
+  V3<float> rb, pb_w;
+  if (b >= 0) { rb = mul(qmat(ldq4(w.bq[b])), f3(w.crb[ci])); pb_w = f3(w.bx[b]) + rb; }
+  else { pb_w = f3(w.crb[ci]); rb = v3<float>(0.f, 0.f, 0.f); }
+  float s = dot(n, pb_w - pa_w);
+  float bias = s > 0.f ? s / p.h : -(p.beta / p.h) * fmaxf(0.f, -s - p.slop);
+  if (p.rest > 0.f) {
+    V3<float> va = f3(w.bv[a]), wa = f3(w.bw[a]);
+    V3<float> dv = v3<float>(0.f, 0.f, 0.f) - (va + cross(wa, ra));
+    if (b >= 0) dv = dv + (f3(w.bv[b]) + cross(f3(w.bw[b]), rb));
+    float vn = dot(n, dv);
+    if (vn < -1.f) bias = fminf(bias, p.rest * vn);
+  }
+  V3<float> t1, t2;
+  onb(n, t1, t2);
+  w.kra[ci] = f4(ra, eff_mass(ctx, n, ra, rb));
+  w.krb[ci] = f4(rb, bias);
+  w.kt1[ci] = f4(t1, eff_mass(ctx, t1, ra, rb));
+  w.kt2[ci] = f4(t2, eff_mass(ctx, t2, ra, rb));
+  w.klam[ci] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
+  const int nc = w.misc[MC_CONTACTS];
+  for (int t = threadIdx.x; t < e.J + nc; t += blockDim.x) {
+    if (t < e.J) joint_rows(p, e, w, t);
+    else contact_rows(p, e, w, t - e.J);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6: solver
+// ---------------------------------------------------------------------------
+struct BodyVel { V3<float> va, wa, vb, wb; };
+
+__device__ __forceinline__ void apply_lin(V3<float>& v, V3<float>& wv, const V3<float>& P, const V3<float>& r,
+                                          float im, const Sym3& I, float sgn) {
+  v = v + P * (sgn * im);
+  wv = wv + smul(I, cross(r, P)) * sgn;
+}
+
+// Joint rows on velocities (va, wa, vb, wb); `sa`/`sb` scale the inverse
+// masses applied to the local copies (Jacobi mass splitting, 1 in PGS); the
+// true-mass change is accumulated in `dacc` when non-null.
+__device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, const Ws& w, int k, BodyVel& bv,
+                                            BodyVel* dacc) {
+  const JointDesc& j = p.joints[e.j0 + k];
+  const int A = j.parent;
+  const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = w.bx[j.child].w;
+  const float sa = A >= 0 ? w.bd[A].w : 1.f, sb = w.bd[j.child].w;
+  const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
+  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * 6;
+  for (int r = 0; r < nr; ++r) {
+    float4* R = rows + 6 * r;
+    float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4], r5 = R[5];
+    V3<float> la = f3(r0), aa = f3(r1), lb = f3(r2), ab = f3(r3), Ia = f3(r4), Ib = f3(r5);
+    float jv = dot(lb, bv.vb) + dot(ab, bv.wb);
+    if (A >= 0) jv = jv + dot(la, bv.va) + dot(aa, bv.wa);
+    float lam = r3.w;
+    float dl = -r0.w * (jv + r1.w + r2.w * lam);
+    float nl = fminf(fmaxf(lam + dl, r4.w), r5.w);
+    dl = nl - lam;
+    R[3].w = nl;
+    if (A >= 0) {
+      bv.va = bv.va + la * (sa * ima * dl);
+      bv.wa = bv.wa + Ia * (sa * dl);
+      if (dacc) { dacc->va = dacc->va + la * (ima * dl); dacc->wa = dacc->wa + Ia * dl; }
+    }
+    bv.vb = bv.vb + lb * (sb * imb * dl);
+    bv.wb = bv.wb + Ib * (sb * dl);
+    if (dacc) { dacc->vb = dacc->vb + lb * (imb * dl); dacc->wb = dacc->wb + Ib * dl; }
+  }
+}
+
+__device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e, const Ws& w, int m, BodyVel& bv,
+                                               BodyVel* dacc) {
+  int4 mf = w.man[m];
+  const int a = mf.x, b = mf.y;
+  const float ima = w.bx[a].w, imb = b >= 0 ? w.bx[b].w : 0.f;
+  const float sa = w.bd[a].w, sb = b >= 0 ? w.bd[b].w : 1.f;
+  Sym3 Ia = load_Iw(w, a), Ib;
+  if (b >= 0) Ib = load_Iw(w, b);
+  for (int c = mf.z; c < mf.z + mf.w; ++c) {
+    float4 kra = w.kra[c], krb = w.krb[c], kt1 = w.kt1[c], kt2 = w.kt2[c], lam = w.klam[c];
+    V3<float> n = f3(w.cn[c]);
+    V3<float> ra = f3(kra), rb = f3(krb);
+    V3<float> dirs[3] = {n, f3(kt1), f3(kt2)};
+    float ms[3] = {kra.w, kt1.w, kt2.w};
+    float ls[3] = {lam.x, lam.y, lam.z};
+    for (int r = 0; r < 3; ++r) {
+      V3<float> dv = bv.vb + cross(bv.wb, rb) - (bv.va + cross(bv.wa, ra));   // static b: vb = wb = 0
+      float vn = dot(dirs[r], dv);
+      float dl, nl;
+      if (r == 0) {
+        dl = -ms[0] * (vn + krb.w);
+        nl = fmaxf(ls[0] + dl, 0.f);
+      } else {
+        dl = -ms[r] * vn;
+        float lim = p.mu * ls[0];
+        nl = fminf(fmaxf(ls[r] + dl, -lim), lim);
+      }
+      dl = nl - ls[r];
+      ls[r] = nl;
+      V3<float> P = dirs[r] * dl;
+      apply_lin(bv.va, bv.wa, P, ra, ima, Ia, -sa);
+      if (dacc) { dacc->va = dacc->va - P * ima; dacc->wa = dacc->wa - smul(Ia, cross(ra, P)); }
+      if (b >= 0) {
+        apply_lin(bv.vb, bv.wb, P, rb, imb, Ib, sb);
+        if (dacc) { dacc->vb = dacc->vb + P * imb; dacc->wb = dacc->wb + smul(Ib, cross(rb, P)); }
+      }
+    }
+    w.klam[c] = make_float4(ls[0], ls[1], ls[2], 0.f);
+  }
+}
+
+__device__ __forceinline__ void con_bodies(const Params& p, const EnvInfo& e, const Ws& w, int k, int J, int& a, int& b) {
+  if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
+  else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
+}
+
+__device__ __forceinline__ BodyVel load_vel(const Ws& w, int a, int b) {
+  BodyVel v;
+  V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  v.va = a >= 0 ? f3(w.bv[a]) : z; v.wa = a >= 0 ? f3(w.bw[a]) : z;
+  v.vb = b >= 0 ? f3(w.bv[b]) : z; v.wb = b >= 0 ? f3(w.bw[b]) : z;
+  return v;
+}
+
+// One solver iteration over every constraint of the env.
+__device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w) {
+  const int J = e.J;
+  if (p.mode == MODE_COLOURED) {
+    const int ncol = w.misc[MC_COLOURS];
+    for (int c = 0; c < ncol; ++c) {
+      const int c0 = w.coff[c], c1 = w.coff[c + 1];
+      for (int idx = c0 + threadIdx.x; idx < c1; idx += blockDim.x) {
+        int k = w.corder[idx];
+        int a, b;
+        con_bodies(p, e, w, k, J, a, b);
+        BodyVel bv = load_vel(w, a, b);
+        if (k < J) solve_joint(p, e, w, k, bv, nullptr);
+        else solve_manifold(p, e, w, k - J, bv, nullptr);
+        if (a >= 0) { w.bv[a] = f4(bv.va, 0.f); w.bw[a] = f4(bv.wa, 0.f); }
+        if (b >= 0) { w.bv[b] = f4(bv.vb, 0.f); w.bw[b] = f4(bv.wb, 0.f); }
+      }
+      __syncthreads();
+    }
+  } else {
+    const int K = J + w.misc[MC_MANIFOLDS];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      int a, b;
+      con_bodies(p, e, w, k, J, a, b);
+      BodyVel bv = load_vel(w, a, b);
+      BodyVel d;
+      V3<float> z = v3<float>(0.f, 0.f, 0.f);
+      d.va = z; d.wa = z; d.vb = z; d.wb = z;
+      if (k < J) solve_joint(p, e, w, k, bv, &d);
+      else solve_manifold(p, e, w, k - J, bv, &d);
+      w.jdv[4 * k + 0] = f4(d.va, 0.f); w.jdv[4 * k + 1] = f4(d.wa, 0.f);
+      w.jdv[4 * k + 2] = f4(d.vb, 0.f); w.jdv[4 * k + 3] = f4(d.wb, 0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+      V3<float> dv = v3<float>(0.f, 0.f, 0.f), dw = dv;
+      for (int q = w.inc_off[i]; q < w.inc_off[i + 1]; ++q) {
+        int t = w.inc[q];
+        int k = t >> 1, side = t & 1;
+        dv = dv + f3(w.jdv[4 * k + 2 * side]);
+        dw = dw + f3(w.jdv[4 * k + 2 * side + 1]);
+      }
+      w.bv[i] = f4(f3(w.bv[i]) + dv, 0.f);
+      w.bw[i] = f4(f3(w.bw[i]) + dw, 0.f);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a7: positions
+// ---------------------------------------------------------------------------
+__device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws& w) {
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    float4 x = w.bx[i], v = w.bv[i], wv = w.bw[i], q = w.bq[i];
+    x.x = x.x + v.x * p.h; x.y = x.y + v.y * p.h; x.z = x.z + v.z * p.h;
+    Q4<float> wq; wq.w = 0.f; wq.x = wv.x; wq.y = wv.y; wq.z = wv.z;
+    Q4<float> dq = qmul(wq, ldq4(q));
+    float hh = p.h * 0.5f;
+    float qw = q.x + dq.w * hh, qx = q.y + dq.x * hh, qy = q.z + dq.y * hh, qz = q.w + dq.z * hh;
+    float nrm = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    w.bx[i] = x;
+    w.bq[i] = make_float4(qw / nrm, qx / nrm, qy / nrm, qz / nrm);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a8: write back, status
+// ---------------------------------------------------------------------------
+__device__ void stage_store(const Params& p, const EnvInfo& e, const Ws& w) {
+  int bad = 0;
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    int g = e.b0 + i;
+    float4 x = w.bx[i], q = w.bq[i], v = w.bv[i], wv = w.bw[i];
+    p.pos[3 * g] = x.x; p.pos[3 * g + 1] = x.y; p.pos[3 * g + 2] = x.z;
+    p.quat[4 * g] = q.x; p.quat[4 * g + 1] = q.y; p.quat[4 * g + 2] = q.z; p.quat[4 * g + 3] = q.w;
+    p.lv[3 * g] = v.x; p.lv[3 * g + 1] = v.y; p.lv[3 * g + 2] = v.z;
+    p.av[3 * g] = wv.x; p.av[3 * g + 1] = wv.y; p.av[3 * g + 2] = wv.z;
+    float s = x.x + x.y + x.z + q.x + q.y + q.z + q.w + v.x + v.y + v.z + wv.x + wv.y + wv.z;
+    if (!isfinite(s)) bad = 1;
+  }
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    int st = w.misc[MC_STATUS] | (bad ? ST_NONFINITE : 0);
+    if (st) p.status[e.env] |= st;
+  }
+}
+
+}  // namespace msh

@@ -1,0 +1,210 @@
+"""Thin PyTorch front end of the C ABI: device memory and streams only.
+
+Every stage of the step runs in libmsh.so; this module marshals arrays into
+the descriptor structs and passes tensor data pointers and the current CUDA
+stream. There is no CPU fallback: constructing a simulator without a CUDA
+device or without the library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import EXEC_FUSED, EXEC_PLAIN, SceneDesc, SolverCfg, State, check
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def make_desc(scene):
+    """Scene descriptor struct plus the host arrays it points to (keep both alive)."""
+    keep = dict(
+        body_off=_c(scene.body_off, np.int32), static_off=_c(scene.static_off, np.int32),
+        joint_off=_c(scene.joint_off, np.int32), body_shape=_c(scene.body_shape, np.int32),
+        body_dims=_c(scene.body_dims, np.float32), body_mass=_c(scene.body_mass, np.float32),
+        static_pose=_c(scene.static_pose, np.float32), static_half=_c(scene.static_half, np.float32),
+        joint_type=_c(scene.joint_type, np.int32), joint_parent=_c(scene.joint_parent, np.int32),
+        joint_child=_c(scene.joint_child, np.int32), joint_dof=_c(scene.joint_dof, np.int32),
+        joint_frame_a=_c(scene.joint_frame_a, np.float32), joint_frame_b=_c(scene.joint_frame_b, np.float32),
+        joint_gains=_c(scene.joint_gains, np.float32), joint_limits=_c(scene.joint_limits, np.float32))
+    d = SceneDesc()
+    d.num_envs = scene.num_envs
+    d.max_dof = scene.max_dof
+    for k, v in keep.items():
+        setattr(d, k, v.ctypes.data if v.size else None)
+    return d, keep
+
+
+def make_cfg(cfg) -> SolverCfg:
+    c = SolverCfg()
+    c.dt = cfg.dt
+    c.substeps = cfg.substeps
+    c.iterations = cfg.iterations
+    c.mode = cfg.mode
+    for i in range(3):
+        c.gravity[i] = cfg.gravity[i]
+    c.friction = cfg.friction
+    c.restitution = cfg.restitution
+    c.contact_offset = cfg.contact_offset
+    c.baumgarte = cfg.baumgarte
+    c.joint_baumgarte = cfg.joint_baumgarte
+    c.slop = cfg.slop
+    c.max_contacts = cfg.max_contacts
+    c.max_pairs = cfg.max_pairs
+    return c
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class MshSim:
+    """A batch of environments resident on one GPU.
+
+    state: pos [B,3], quat [B,4], linvel [B,3], angvel [B,3] float32 CUDA
+    tensors, updated in place by `step`."""
+
+    def __init__(self, scene, cfg, device="cuda", exec_form: str = "fused", threads_per_env: int = 128,
+                 use_graph: bool = False):
+        if not torch.cuda.is_available():
+            raise RuntimeError("MshSim needs a CUDA device; the step has no CPU implementation")
+        self.lib = _lib.load()
+        self.scene, self.cfg = scene, cfg
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            desc, keep = make_desc(scene)
+            self._cfg = make_cfg(cfg)
+            h = C.c_void_p()
+            check(self.lib.msh_create(C.byref(desc), C.byref(self._cfg), C.byref(h)), "msh_create")
+            self.handle = h
+        del keep
+        dev = self.device
+        self.pos = torch.from_numpy(_c(scene.pos, np.float32)).to(dev)
+        self.quat = torch.from_numpy(_c(scene.quat, np.float32)).to(dev)
+        self.linvel = torch.from_numpy(_c(scene.linvel, np.float32)).to(dev)
+        self.angvel = torch.from_numpy(_c(scene.angvel, np.float32)).to(dev)
+        self.max_dof = scene.max_dof
+        self.targets = torch.zeros((scene.num_envs, max(scene.max_dof, 1)), dtype=torch.float32, device=dev)
+        self.set_exec(exec_form, threads_per_env, use_graph)
+
+    # -- configuration ------------------------------------------------------
+    def set_exec(self, exec_form: str = "fused", threads_per_env: int = 128, use_graph: bool = False):
+        form = {"plain": EXEC_PLAIN, "fused": EXEC_FUSED}[exec_form]
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_set_exec(self.handle, form, int(threads_per_env), int(bool(use_graph))),
+                  "msh_set_exec")
+        self.exec_form, self.threads_per_env, self.use_graph = exec_form, threads_per_env, use_graph
+
+    @property
+    def launches_per_step(self) -> int:
+        return int(self.lib.msh_launches_per_step(self.handle))
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(self.lib.msh_scratch_bytes(self.handle))
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.lib.msh_workspace_bytes(self.handle))
+
+    # -- state ----------------------------------------------------------------
+    def _state(self):
+        st = State()
+        st.pos, st.quat = self.pos.data_ptr(), self.quat.data_ptr()
+        st.linvel, st.angvel = self.linvel.data_ptr(), self.angvel.data_ptr()
+        return st
+
+    def set_state(self, pos, quat, linvel, angvel):
+        for dst, src in ((self.pos, pos), (self.quat, quat), (self.linvel, linvel), (self.angvel, angvel)):
+            dst.copy_(torch.as_tensor(np.asarray(src, np.float32)).to(self.device))
+
+    def state_numpy(self):
+        torch.cuda.synchronize(self.device)
+        return tuple(t.detach().cpu().numpy().copy() for t in (self.pos, self.quat, self.linvel, self.angvel))
+
+    # -- stepping -------------------------------------------------------------
+    def step(self, targets=None, dt: float = 0.0, substeps: int = 0, stream=None):
+        """One step of every env; `targets` [E, max_dof] CUDA tensor or array (absolute PD targets)."""
+        if targets is not None and self.max_dof > 0:
+            if not (isinstance(targets, torch.Tensor) and targets.is_cuda and targets.dtype == torch.float32
+                    and targets.is_contiguous()):
+                self.targets.copy_(torch.as_tensor(np.asarray(targets, np.float32)).reshape(self.targets.shape))
+                targets = self.targets
+        else:
+            targets = self.targets
+        st = self._state()
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_step(self.handle, C.byref(st), _ptr(targets), float(dt), int(substeps),
+                                    _stream(stream)), "msh_step")
+
+    def step_host(self, pos, quat, linvel, angvel, targets, dt: float = 0.0, substeps: int = 0, stream=None):
+        """Step with HOST arrays (pinned tensors or contiguous numpy); copies in and out."""
+        def hp(a):
+            if isinstance(a, torch.Tensor):
+                assert not a.is_cuda and a.is_contiguous() and a.dtype == torch.float32
+                return C.c_void_p(a.data_ptr())
+            assert a.dtype == np.float32 and a.flags.c_contiguous
+            return a.ctypes.data_as(C.c_void_p)
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_step_host(self.handle, hp(pos), hp(quat), hp(linvel), hp(angvel),
+                                         hp(targets) if targets is not None else None, float(dt), int(substeps),
+                                         _stream(stream)), "msh_step_host")
+
+    def detect(self, stream=None):
+        """Collision stage at the current poses: AABBs, pairs, contacts, colours (numpy)."""
+        sc, cfg = self.scene, self.cfg
+        E, P, K = sc.num_envs, cfg.max_pairs, cfg.max_contacts
+        dev = self.device
+        out = dict(
+            aabb_body=torch.zeros((max(sc.num_bodies, 1), 6), device=dev),
+            aabb_static=torch.zeros((max(sc.num_statics, 1), 6), device=dev),
+            pair_count=torch.zeros(E, dtype=torch.int32, device=dev),
+            pairs=torch.full((E, P, 2), -1, dtype=torch.int32, device=dev),
+            contact_count=torch.zeros(E, dtype=torch.int32, device=dev),
+            contact_ids=torch.full((E, K, 2), -1, dtype=torch.int32, device=dev),
+            contact_geom=torch.zeros((E, K, 10), device=dev),
+            manifold_count=torch.zeros(E, dtype=torch.int32, device=dev),
+            colours=torch.full((sc.num_joints + E * P,), -1, dtype=torch.int32, device=dev),
+            ncolours=torch.zeros(E, dtype=torch.int32, device=dev))
+        st = self._state()
+        with torch.cuda.device(dev):
+            check(self.lib.msh_detect(self.handle, C.byref(st), *[_ptr(out[k]) for k in (
+                "aabb_body", "aabb_static", "pair_count", "pairs", "contact_count", "contact_ids",
+                "contact_geom", "manifold_count", "colours", "ncolours")], _stream(stream)), "msh_detect")
+            torch.cuda.synchronize(dev)
+        res = {k: v.cpu().numpy() for k, v in out.items()}
+        res["aabb_body"] = res["aabb_body"][:sc.num_bodies]
+        res["aabb_static"] = res["aabb_static"][:sc.num_statics]
+        return res
+
+    def status(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.scene.num_envs, np.int32)
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_get_status(self.handle, out.ctypes.data_as(C.c_void_p), _stream(stream)),
+                  "msh_get_status")
+        return out
+
+    def clear_status(self, stream=None):
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_clear_status(self.handle, _stream(stream)), "msh_clear_status")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            with torch.cuda.device(self.device):
+                self.lib.msh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

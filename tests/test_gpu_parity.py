@@ -1,0 +1,242 @@
+"""Parity of the CUDA step (through the C ABI) with the CPU oracle.
+
+Tolerances: the collision stage (AABBs, pairs, contacts, colours) is bit-exact
+against the FP32 oracle from identical poses; body states agree within 1e-5 m
+and 1e-4 m/s after one step and within 1e-3 m after 100 steps on envs that
+are not chaotic (a 1e-7 m FP64 perturbation grows by less than 1e-4 m over
+the horizon). The forms of the step (plain per-stage launches, fused
+persistent launch, CUDA graph, threads per env) agree bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_13211_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+SMALL = {1: 16, 2: 8, 3: 16, 4: 8, 5: 6}
+TOL_X, TOL_V = 1e-5, 1e-4
+
+_cache = {}
+
+
+def scene(idx, n=None, **cfg_over):
+    key = (idx, n)
+    if key not in _cache:
+        _cache[key] = S.make_config(idx, num_envs=n if n is not None else SMALL[idx])
+    sc, cfg = _cache[key]
+    cfg = S.SolverCfg(**{**cfg.__dict__, **cfg_over})
+    return sc, cfg
+
+
+def make_sim(sc, cfg, **kw):
+    from paper_2412_13211_b300.sim import MshSim
+    return MshSim(sc, cfg, **kw)
+
+
+def bits(a):
+    return np.ascontiguousarray(a, np.float32).view(np.int32)
+
+
+def oracle_states(sc, cfg, steps):
+    """Poses reached by the FP32 oracle after 0, steps/2, steps steps."""
+    st = sc.state()
+    out = [st]
+    tg = sc.target_walk(steps)
+    half = steps // 2
+    a, _ = oracle.step(sc, cfg, st, tg[:half], half, "f32")
+    b, _ = oracle.step(sc, cfg, a, tg[half:], steps - half, "f32")
+    return out + [a, b]
+
+
+@pytest.mark.parametrize("idx", [1, 2, 3, 4, 5])
+def test_collision_stage_bit_exact(idx):
+    sc, cfg = scene(idx)
+    sim = make_sim(sc, cfg)
+    for st in oracle_states(sc, cfg, 20):
+        sim.set_state(*st)
+        g = sim.detect()
+        o = oracle.detect(sc, cfg, st[0], st[1], "f32")
+        assert np.array_equal(bits(g["aabb_body"]), bits(o.aabb_body))
+        assert np.array_equal(bits(g["aabb_static"]), bits(o.aabb_static))
+        assert np.array_equal(g["pair_count"], o.pair_count)
+        assert np.array_equal(g["contact_count"], o.contact_count)
+        assert np.array_equal(g["manifold_count"], o.manifold_count)
+        assert np.array_equal(g["ncolours"], o.ncolours)
+        for e in range(sc.num_envs):
+            npair, nc = o.pair_count[e], o.contact_count[e]
+            assert np.array_equal(g["pairs"][e, :npair], o.pairs[e, :npair])
+            assert np.array_equal(g["contact_ids"][e, :nc], o.contact_ids[e, :nc])
+            assert np.array_equal(bits(g["contact_geom"][e, :nc]), bits(o.contact_geom[e, :nc]))
+        J = sc.num_joints
+        assert np.array_equal(g["colours"][:J], o.colours[:J])
+        for e in range(sc.num_envs):
+            m = o.manifold_count[e]
+            sl = slice(J + e * cfg.max_pairs, J + e * cfg.max_pairs + m)
+            assert np.array_equal(g["colours"][sl], o.colours[sl])
+    assert (o.contact_count > 0).any()
+
+
+def _step_both(sc, cfg, nsteps, seed=0, **kw):
+    tg = sc.target_walk(nsteps, seed)
+    sim = make_sim(sc, cfg, **kw)
+    import torch
+    for t in range(nsteps):
+        sim.step(torch.as_tensor(tg[t]).cuda())
+    gpu = sim.state_numpy()
+    status = sim.status()
+    o32, st32 = oracle.step(sc, cfg, sc.state(), tg, nsteps, "f32")
+    o64, _ = oracle.step(sc, cfg, sc.state(), tg, nsteps, "f64")
+    return gpu, o32, o64, status, st32
+
+
+def _err(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).max()) if np.size(a) else 0.0
+
+
+@pytest.mark.parametrize("mode", [S.MODE_COLOURED, S.MODE_JACOBI])
+@pytest.mark.parametrize("idx", [1, 2, 3, 4, 5])
+def test_one_step_parity(idx, mode, record_property):
+    sc, cfg = scene(idx, mode=mode)
+    gpu, o32, o64, status, st32 = _step_both(sc, cfg, 1)
+    assert np.array_equal(status, st32)
+    ex, eq, ev, ew = (_err(gpu[k], o32[k]) for k in range(4))
+    record_property("err_vs_fp32", [ex, eq, ev, ew])
+    record_property("err_vs_fp64", [_err(gpu[k], o64[k]) for k in range(4)])
+    assert ex <= TOL_X and eq <= TOL_X
+    assert ev <= TOL_V and ew <= TOL_V
+
+
+def _non_chaotic(sc, cfg, tg, steps):
+    a, _ = oracle.step(sc, cfg, sc.state(), tg, steps, "f64")
+    st = sc.state()
+    pert = (st[0].astype(np.float64) + 1e-7, st[1], st[2], st[3])
+    b, _ = oracle.step(sc, cfg, pert, tg, steps, "f64")
+    d = np.abs(a[0] - b[0]).max(axis=1)
+    return np.array([d[sc.body_off[e]:sc.body_off[e + 1]].max() < 1e-4 for e in range(sc.num_envs)])
+
+
+@pytest.mark.parametrize("idx", [1, 2, 4])
+def test_hundred_steps_non_chaotic(idx, record_property):
+    sc, cfg = scene(idx)
+    steps = 100
+    tg = sc.target_walk(steps)
+    calm = _non_chaotic(sc, cfg, tg, steps)
+    record_property("non_chaotic_envs", int(calm.sum()))
+    assert calm.sum() >= 1
+    gpu, o32, o64, status, _ = _step_both(sc, cfg, steps)
+    for e in np.nonzero(calm)[0]:
+        sl = slice(sc.body_off[e], sc.body_off[e + 1])
+        assert _err(gpu[0][sl], o32[0][sl]) <= 1e-3, e
+    assert not (status & 8).any()
+
+
+@pytest.mark.parametrize("idx", [2, 3])
+def test_plain_fused_graph_and_block_sizes_bitwise_equal(idx):
+    sc, cfg = scene(idx)
+    import torch
+    tg = sc.target_walk(3)
+    results = []
+    for kw in (dict(exec_form="fused"), dict(exec_form="plain"), dict(exec_form="fused", use_graph=True),
+               dict(exec_form="plain", use_graph=True), dict(exec_form="fused", threads_per_env=32),
+               dict(exec_form="fused", threads_per_env=64), dict(exec_form="fused", threads_per_env=256)):
+        sim = make_sim(sc, cfg, **kw)
+        for t in range(3):
+            sim.step(torch.as_tensor(tg[t]).cuda())
+        results.append(sim.state_numpy())
+        sim.close()
+    for r in results[1:]:
+        for a, b in zip(results[0], r):
+            assert np.array_equal(bits(a), bits(b))
+
+
+def test_host_buffer_step_equals_device_step():
+    sc, cfg = scene(3)
+    import torch
+    tg = sc.target_walk(2)
+    sim = make_sim(sc, cfg)
+    for t in range(2):
+        sim.step(torch.as_tensor(tg[t]).cuda())
+    dev = sim.state_numpy()
+    host = [np.ascontiguousarray(a, np.float32).copy() for a in sc.state()]
+    sim2 = make_sim(sc, cfg)
+    for t in range(2):
+        sim2.step_host(*host, np.ascontiguousarray(tg[t]))
+    for a, b in zip(dev, host):
+        assert np.array_equal(bits(a), bits(b))
+
+
+def test_full_size_apartment_batch_sampled():
+    """4096 envs of uneven size (the benchmark workload) in one fused launch;
+    sampled envs against the oracle, and the whole batch status-clean."""
+    sc, cfg = scene(3, 4096)
+    import torch
+    tg = sc.target_walk(1)
+    sim = make_sim(sc, cfg, use_graph=True)
+    sim.step(torch.as_tensor(tg[0]).cuda())
+    gpu = sim.state_numpy()
+    assert not sim.status().any()
+    assert all(np.isfinite(a).all() for a in gpu)
+    rng = np.random.default_rng(0)
+    counts = np.diff(sc.body_off)
+    sample = np.unique(np.concatenate([rng.choice(sc.num_envs, 24, replace=False),
+                                       [int(np.argmax(counts)), int(np.argmin(counts))]]))
+    sub = sc.subset(sample)
+    o32, _ = oracle.step(sub, cfg, sub.state(), tg[:, sample], 1, "f32")
+    for k, e in enumerate(sample):
+        g = slice(sc.body_off[e], sc.body_off[e + 1])
+        o = slice(sub.body_off[k], sub.body_off[k + 1])
+        assert _err(gpu[0][g], o32[0][o]) <= TOL_X
+        assert _err(gpu[2][g], o32[2][o]) <= TOL_V
+        assert _err(gpu[3][g], o32[3][o]) <= TOL_V
+
+
+def test_capacity_overflow_sets_status_and_truncates_like_oracle():
+    sc, cfg = scene(2, max_contacts=12, max_pairs=10)
+    sim = make_sim(sc, cfg)
+    g = sim.detect()
+    o = oracle.detect(sc, cfg, sc.pos, sc.quat, "f32")
+    assert np.array_equal(g["pair_count"], o.pair_count)
+    assert np.array_equal(g["contact_count"], o.contact_count)
+    assert (o.status & 1).any()
+    import torch
+    sim.step(torch.zeros((sc.num_envs, sc.max_dof)).cuda())
+    st = sim.status()
+    _, ost = oracle.step(sc, cfg, sc.state(), None, 1, "f32")
+    assert np.array_equal(st, ost)
+    assert (st & 1).any()
+
+
+def test_nonfinite_state_sets_status_without_trap():
+    sc, cfg = scene(1)
+    sim = make_sim(sc, cfg)
+    pos = sc.pos.copy()
+    pos[sc.body_off[3]] = np.nan
+    sim.set_state(pos, sc.quat, sc.linvel, sc.angvel)
+    sim.step()
+    st = sim.status()
+    assert st[3] & 8
+    assert not (np.delete(st, 3) & 8).any()
+    sim.clear_status()
+    assert not sim.status().any()
+
+
+def test_degenerate_envs():
+    """Env with one body and nothing else, env with no contacts (free flight),
+    env with only statics nearby, joint-only env."""
+    from helpers import env, scene_from_envs
+    envs = []
+    e = env(); e.body(S.SPHERE, (0.05,), 1.0, (0.0, 0.0, 3.0)); envs.append(e)
+    e = env(); e.body(S.BOX, (0.1, 0.1, 0.1), 1.0, (0.0, 0.0, 0.1)); e.static((0.5, 0.0, 0.2), (0.2, 0.2, 0.2))
+    envs.append(e)
+    e = env()
+    e.body(S.CAPSULE, (0.03, 0.1), 1.0, (0.0, 0.0, 1.0 + 0.1), S.Q_LINK)
+    e.joint(S.REVOLUTE, -1, 0, (0.0, 0.0, 1.0) + S.QW_AXIS_Z, (-0.1, 0.0, 0.0) + S.QL_AXIS_Z, S.ARM_GAINS,
+            (0.0, 0.0), [(0.0, 0.0, -3, 3)])
+    envs.append(e)
+    sc = scene_from_envs(envs)
+    cfg = S.SolverCfg(substeps=4, iterations=8)
+    gpu, o32, _, status, st32 = _step_both(sc, cfg, 3)
+    assert np.array_equal(status, st32)
+    assert _err(gpu[0], o32[0]) <= TOL_X and _err(gpu[2], o32[2]) <= TOL_V
