@@ -181,6 +181,24 @@ int msh_detect(msh_handle* h, const msh_state* st, float* aabb_body, float* aabb
                int32_t* contact_ids, float* contact_geom, int32_t* manifold_count,
                int32_t* colours, int32_t* ncolours, void* stream);
 
+/*
+ * The step without any device allocation. The paper has no counterpart;
+ * this entry point exists for callers that cannot call cudaMalloc when they
+ * step -- for example code running while a framework's caching allocator
+ * holds the device memory, or a real-time loop that must not block in the
+ * allocator. The handle still comes from msh_create (at start-up); this call
+ * itself allocates nothing. It runs the persistent step with its per-CTA
+ * workspace in a static device array of 32 MiB that every GPU loading this
+ * library holds until the process exits; workspaces larger than that are
+ * rejected (MSH_ERR_INVALID_ARG). The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. All calls share the
+ * array: calls that overlap on the GPU (other streams, other handles) race
+ * and must be serialised by the caller. Results equal msh_step's.
+ */
+int msh_step_static_scratch(msh_handle* h, const msh_state* st, const float* joint_targets, float dt,
+                            int32_t substeps, void* stream);
+
 /* Copies the per-env status words to host memory [num_envs] (synchronises
  * `stream`). */
 int msh_get_status(msh_handle* h, int32_t* status_host, void* stream);

@@ -16,7 +16,7 @@ EXEC_PLAIN, EXEC_FUSED = 0, 1
 
 EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_step", "msh_step_host",
            "msh_detect", "msh_get_status", "msh_clear_status", "msh_scratch_bytes", "msh_workspace_bytes",
-           "msh_launches_per_step")
+           "msh_launches_per_step", "msh_step_static_scratch")
 
 
 class SceneDesc(C.Structure):
@@ -61,6 +61,7 @@ def load(build_if_missing: bool = True):
     lib.msh_set_exec.argtypes = [P, I32, I32, I32]
     lib.msh_step.argtypes = [P, P, P, F, I32, P]
     lib.msh_step_host.argtypes = [P, P, P, P, P, P, F, I32, P]
+    lib.msh_step_static_scratch.argtypes = [P, P, P, F, I32, P]
     lib.msh_detect.argtypes = [P] * 12 + [P]
     lib.msh_get_status.argtypes = [P, P, P]
     lib.msh_clear_status.argtypes = [P, P]

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/msh.h"
@@ -661,3 +662,73 @@ int32_t msh_launches_per_step(const msh_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Step that allocates nothing: static scratch
+// ---------------------------------------------------------------------------
+// Some callers cannot call cudaMalloc at the time they step: code running
+// while a framework's caching allocator has reserved the device memory, a
+// real-time control loop that must not block in the driver's allocator, or a
+// host that hands this library a pre-sized device and forbids growth. For
+// them msh_step_static_scratch runs the persistent step kernel with its
+// per-CTA workspace slabs in the file-scope array below instead of in memory
+// from cudaMalloc. The array is part of the module, so every GPU that loads
+// this library holds MSH_STATIC_SCRATCH_BYTES until the process exits.
+#define MSH_STATIC_SCRATCH_BYTES (32 << 20)
+static __device__ __align__(256) char g_static_scratch[MSH_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+char* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device (the host-side name is only a stand-in for the device address).
+int static_scratch_address(char** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(MSH_ERR_UNSUPPORTED, "device ordinal beyond 63");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(MSH_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    g_scratch_ptr[dev] = (char*)p;
+  }
+  *out = g_scratch_ptr[dev];
+  return MSH_OK;
+}
+}  // namespace
+
+extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const float* joint_targets, float dt,
+                                       int32_t substeps, void* stream) {
+  if (!h || !st || !st->pos || !st->quat || !st->linvel || !st->angvel)
+    return fail(MSH_ERR_INVALID_ARG, "handle or state pointer is NULL");
+  if (h->max_dof > 0 && !joint_targets) return fail(MSH_ERR_INVALID_ARG, "joint_targets is NULL but max_dof > 0");
+  if (!(dt > 0.f)) dt = h->cfg.dt;
+  if (substeps < 1) substeps = h->cfg.substeps;
+  // layout: [0, 256) the env-queue counter, then one 256-aligned slab per CTA
+  const long long slab = ((long long)h->L.bytes + 255) & ~255LL;
+  if (256 + slab > MSH_STATIC_SCRATCH_BYTES)
+    return fail(MSH_ERR_INVALID_ARG, "per-env workspace of " + std::to_string(h->L.bytes) +
+                                         " bytes exceeds the static scratch of " +
+                                         std::to_string(MSH_STATIC_SCRATCH_BYTES - 256) + " bytes");
+  char* base = nullptr;
+  int rc = static_scratch_address(&base);
+  if (rc) return rc;
+  int blocks = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused, h->tpe, 0));
+  if (blocks < 1) return fail(MSH_ERR_UNSUPPORTED, "step kernel cannot be resident with this block size");
+  const long long fit = (MSH_STATIC_SCRATCH_BYTES - 256) / slab;
+  const int grid = (int)std::min<long long>(std::min<long long>(h->E, (long long)blocks * h->num_sms), fit);
+  Params p = make_params(h, st, joint_targets, dt, substeps);
+  p.ws = base + 256;
+  p.ws_stride = slab;
+  p.queue = (int*)base;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(base, 0, sizeof(int), s));   // the queue counter must start at zero
+  k_fused<<<grid, h->tpe, 0, s>>>(p, 0);
+  CK(cudaGetLastError());
+  return MSH_OK;
+}
