@@ -63,8 +63,9 @@ enum {
 
 /* Execution forms of the step (msh_set_exec). */
 enum {
-  MSH_EXEC_PLAIN = 0,  /* one launch per stage, workspace in HBM, S x N solver launches */
-  MSH_EXEC_FUSED = 1   /* one persistent launch per step: env work queue, workspace in shared memory */
+  MSH_EXEC_PLAIN = 0,    /* one launch per stage, workspace in HBM, S x N solver launches */
+  MSH_EXEC_FUSED = 1,    /* one persistent launch per step: env work queue, workspace in shared memory */
+  MSH_EXEC_SUBSTEP = 2   /* collision launches, then one launch per substep, workspace in HBM */
 };
 
 /* Solver modes. */
@@ -141,8 +142,10 @@ void msh_destroy(msh_handle* h);
 const char* msh_last_error(void);
 
 /*
- * Chooses the execution form: MSH_EXEC_PLAIN or MSH_EXEC_FUSED;
- * threads_per_env in {32, 64, 128, 256, 512} (0 = library default);
+ * Chooses the execution form: MSH_EXEC_PLAIN, MSH_EXEC_FUSED or
+ * MSH_EXEC_SUBSTEP; threads_per_env in {32, 64, 128, 256, 512} (0 = the
+ * form's default: 32 fused, 128 otherwise). All forms give bitwise identical
+ * results;
  * use_graph != 0 captures the step's launches in a CUDA graph on first use
  * (re-captured when the state pointers, dt or substeps change).
  * Returns MSH_ERR_UNSUPPORTED if the fused form cannot hold the workspace.

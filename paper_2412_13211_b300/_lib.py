@@ -12,7 +12,7 @@ MSH_ERR_CUDA = -2
 MSH_ERR_OOM = -3
 MSH_ERR_TIMEOUT = -4
 MSH_ERR_UNSUPPORTED = -5
-EXEC_PLAIN, EXEC_FUSED = 0, 1
+EXEC_PLAIN, EXEC_FUSED, EXEC_SUBSTEP = 0, 1, 2
 
 EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_step", "msh_step_host",
            "msh_detect", "msh_get_status", "msh_clear_status", "msh_scratch_bytes", "msh_workspace_bytes",

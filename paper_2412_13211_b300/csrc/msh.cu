@@ -71,6 +71,18 @@ __global__ void k_store(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
   stage_store(p, e, plain_ws(p, blockIdx.x));
 }
+// One whole substep per env (substep-fused form): gravity, rows, N sweeps,
+// positions, on the env's HBM workspace.
+__global__ void k_substep(Params p) {
+  EnvInfo e = env_info(p, blockIdx.x);
+  Ws w = plain_ws(p, blockIdx.x);
+  stage_integrate_vel(p, e, w);
+  __syncthreads();
+  stage_prep(p, e, w);
+  __syncthreads();
+  for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w);
+  stage_integrate_pos(p, e, w);
+}
 
 // One whole step per env; persistent CTAs pull envs from an atomic queue.
 __global__ void k_fused(Params p, int smem_ws) {
@@ -215,22 +227,27 @@ Layout make_layout(int Dm, int Sm, int Jm, int P, int C, bool jacobi) {
   auto take = [&](int bytes) { int r = o; o = align16(o + bytes); return r; };
   const int f4 = 16;
   L.bx = take(Dm * f4); L.bq = take(Dm * f4); L.bv = take(Dm * f4); L.bw = take(Dm * f4);
-  L.bI = take(Dm * f4); L.bd = take(Dm * f4); L.bIw0 = take(Dm * f4); L.bIw1 = take(Dm * f4);
-  L.sc = take(Sm * f4); L.sM = take(3 * Sm * f4);
-  L.alo = take((Dm + Sm) * f4); L.ahi = take((Dm + Sm) * f4);
-  L.pairs = take(P * 4);
+  L.bIw0 = take(Dm * f4); L.bIw1 = take(Dm * f4);
   L.cn = take(C * f4); L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4);
-  L.kra = take(C * f4); L.krb = take(C * f4); L.kt1 = take(C * f4); L.kt2 = take(C * f4); L.klam = take(C * f4);
   L.man = take(P * 16);
-  L.jr = take(L.R * 6 * f4);
+  L.jr = take(L.R * ROW_F4 * f4);
   L.ccol = take(L.K * 4); L.corder = take(L.K * 4); L.coff = take((MAX_COLOURS + 1) * 4);
-  L.masks = take(Dm * 8);
   if (jacobi) {
     L.jdv = take(L.K * 4 * f4); L.inc_off = take((Dm + 1) * 4); L.inc = take(2 * L.K * 4);
   } else {
     L.jdv = L.inc_off = L.inc = 0;
   }
   L.misc = take(MC_N * 4);
+  // shared region: collision-only arrays | per-substep contact rows
+  const int region = o;
+  L.sc = take(Sm * f4); L.sM = take(3 * Sm * f4);
+  L.alo = take((Dm + Sm) * f4); L.ahi = take((Dm + Sm) * f4);
+  L.pairs = take(P * 4);
+  L.masks = take(Dm * 8);
+  const int end_x = o;
+  o = region;
+  L.kra = take(C * f4); L.krb = take(C * f4); L.klam = take(C * f4);
+  o = std::max(o, end_x);
   L.bytes = o;
   return L;
 }
@@ -332,12 +349,16 @@ int launch_collision_plain(msh_handle* h, Params p, cudaStream_t s) {
 int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
   Params p = p0;
   const int T = h->tpe;
-  if (h->exec == MSH_EXEC_PLAIN) {
+  if (h->exec == MSH_EXEC_PLAIN || h->exec == MSH_EXEC_SUBSTEP) {
     int rc = launch_collision_plain(h, p, s);
     if (rc) return rc;
     p.ws = h->d_ws_plain;
     p.ws_stride = h->L.bytes;
     for (int sub = 0; sub < p.S; ++sub) {
+      if (h->exec == MSH_EXEC_SUBSTEP) {
+        k_substep<<<h->E, T, 0, s>>>(p);
+        continue;
+      }
       k_intvel<<<h->E, T, 0, s>>>(p);
       k_prep<<<h->E, T, 0, s>>>(p);
       for (int it = 0; it < p.N; ++it) k_solve<<<h->E, T, 0, s>>>(p);
@@ -515,7 +536,7 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
   }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(MSH_ERR_CUDA, "stream create"));
-  h->tpe = 128;
+  h->tpe = 32;
   h->exec = MSH_EXEC_FUSED;
   if ((rc = configure_fused(h))) return bail(rc);
   *out = h;
@@ -537,8 +558,9 @@ void msh_destroy(msh_handle* h) {
 
 int msh_set_exec(msh_handle* h, int32_t exec, int32_t tpe, int32_t use_graph) {
   if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
-  if (exec != MSH_EXEC_PLAIN && exec != MSH_EXEC_FUSED) return fail(MSH_ERR_INVALID_ARG, "exec must be 0 or 1");
-  if (tpe == 0) tpe = 128;
+  if (exec != MSH_EXEC_PLAIN && exec != MSH_EXEC_FUSED && exec != MSH_EXEC_SUBSTEP)
+    return fail(MSH_ERR_INVALID_ARG, "exec must be MSH_EXEC_PLAIN, MSH_EXEC_FUSED or MSH_EXEC_SUBSTEP");
+  if (tpe == 0) tpe = exec == MSH_EXEC_FUSED ? 32 : 128;
   if (tpe != 32 && tpe != 64 && tpe != 128 && tpe != 256 && tpe != 512)
     return fail(MSH_ERR_INVALID_ARG, "threads_per_env must be 32, 64, 128, 256 or 512");
   cudaDeviceSynchronize();
@@ -566,7 +588,7 @@ static int step_impl(msh_handle* h, const msh_state* st, const float* targets, f
              h->gkey_tpe == h->tpe;
   if (!hit) {
     drop_graph(h);
-    if (h->exec == MSH_EXEC_PLAIN) { int rc = ensure_plain_ws(h); if (rc) return rc; }
+    if (h->exec != MSH_EXEC_FUSED) { int rc = ensure_plain_ws(h); if (rc) return rc; }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue_step(h, make_params(h, st, h->d_targets, dt, substeps), h->cap_stream);
@@ -658,6 +680,7 @@ int64_t msh_workspace_bytes(const msh_handle* h) { return h ? h->L.bytes : 0; }
 int32_t msh_launches_per_step(const msh_handle* h) {
   if (!h) return 0;
   if (h->exec == MSH_EXEC_FUSED) return 1;
+  if (h->exec == MSH_EXEC_SUBSTEP) return 6 + h->cfg.substeps;
   return 6 + h->cfg.substeps * (3 + h->cfg.iterations);
 }
 

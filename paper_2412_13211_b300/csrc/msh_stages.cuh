@@ -23,12 +23,15 @@ struct JointDesc {     // 96 bytes
 };
 
 // Byte offsets of the per-env workspace arrays (16-byte aligned).
+// The collision-only arrays (static boxes, AABBs, pairs, colouring masks) and
+// the per-substep contact rows are never live at the same time and share
+// one region.
 struct Layout {
   int Dm, Sm, Jm, P, C, K, R;
-  int bx, bq, bv, bw, bI, bd, bIw0, bIw1;
+  int bx, bq, bv, bw, bIw0, bIw1;
   int sc, sM, alo, ahi;
   int pairs, cn, cra, crb, cid;
-  int kra, krb, kt1, kt2, klam;
+  int kra, krb, klam;
   int man, jr, ccol, corder, coff, masks;
   int jdv, inc_off, inc, misc;
   int bytes;
@@ -66,12 +69,12 @@ struct Params {
 };
 
 struct Ws {
-  float4 *bx, *bq, *bv, *bw, *bI, *bd, *bIw0, *bIw1;
+  float4 *bx, *bq, *bv, *bw, *bIw0, *bIw1;
   float4 *sc, *sM, *alo, *ahi;
   int* pairs;
   float4 *cn, *cra, *crb;
   int* cid;
-  float4 *kra, *krb, *kt1, *kt2, *klam;
+  float4 *kra, *krb, *klam;
   int4* man;
   float4* jr;
   int *ccol, *corder, *coff;
@@ -83,12 +86,11 @@ struct Ws {
 __device__ __forceinline__ Ws make_ws(char* b, const Layout& L) {
   Ws w;
   w.bx = (float4*)(b + L.bx); w.bq = (float4*)(b + L.bq); w.bv = (float4*)(b + L.bv); w.bw = (float4*)(b + L.bw);
-  w.bI = (float4*)(b + L.bI); w.bd = (float4*)(b + L.bd); w.bIw0 = (float4*)(b + L.bIw0); w.bIw1 = (float4*)(b + L.bIw1);
+  w.bIw0 = (float4*)(b + L.bIw0); w.bIw1 = (float4*)(b + L.bIw1);
   w.sc = (float4*)(b + L.sc); w.sM = (float4*)(b + L.sM); w.alo = (float4*)(b + L.alo); w.ahi = (float4*)(b + L.ahi);
   w.pairs = (int*)(b + L.pairs);
   w.cn = (float4*)(b + L.cn); w.cra = (float4*)(b + L.cra); w.crb = (float4*)(b + L.crb); w.cid = (int*)(b + L.cid);
-  w.kra = (float4*)(b + L.kra); w.krb = (float4*)(b + L.krb); w.kt1 = (float4*)(b + L.kt1); w.kt2 = (float4*)(b + L.kt2);
-  w.klam = (float4*)(b + L.klam);
+  w.kra = (float4*)(b + L.kra); w.krb = (float4*)(b + L.krb); w.klam = (float4*)(b + L.klam);
   w.man = (int4*)(b + L.man); w.jr = (float4*)(b + L.jr);
   w.ccol = (int*)(b + L.ccol); w.corder = (int*)(b + L.corder); w.coff = (int*)(b + L.coff);
   w.masks = (unsigned long long*)(b + L.masks);
@@ -143,13 +145,11 @@ __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
   for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
     int g = e.b0 + i;
     float4 inv = p.binv[g];
-    float4 dm = p.bdims[g];
     w.bx[i] = make_float4(p.pos[3 * g], p.pos[3 * g + 1], p.pos[3 * g + 2], inv.x);
     w.bq[i] = make_float4(p.quat[4 * g], p.quat[4 * g + 1], p.quat[4 * g + 2], p.quat[4 * g + 3]);
     w.bv[i] = make_float4(p.lv[3 * g], p.lv[3 * g + 1], p.lv[3 * g + 2], 0.f);
     w.bw[i] = make_float4(p.av[3 * g], p.av[3 * g + 1], p.av[3 * g + 2], 0.f);
-    w.bI[i] = make_float4(inv.y, inv.z, inv.w, dm.w);
-    w.bd[i] = make_float4(dm.x, dm.y, dm.z, 1.f);
+    w.bIw1[i] = make_float4(0.f, 0.f, 1.f, 0.f);   // .z: Jacobi split count (1 unless set by the colouring)
   }
   for (int k = threadIdx.x; k < e.S; k += blockDim.x) {
     const float* sp = p.static_pose + 7 * (e.s0 + k);
@@ -162,15 +162,13 @@ __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
   if (threadIdx.x < MC_N) w.misc[threadIdx.x] = 0;
 }
 
-__device__ __forceinline__ int body_shape_type(const Ws& w, int i) { return __float_as_int(w.bI[i].w); }
-
 // Collision shape of index i: dynamic body, static box or the plane.
-__device__ __forceinline__ Shape<nf> coll_shape(const Ws& w, const EnvInfo& e, int i) {
+__device__ __forceinline__ Shape<nf> coll_shape(const Params& p, const Ws& w, const EnvInfo& e, int i) {
   Shape<nf> s;
   if (i < e.D) {
-    float4 x = w.bx[i], q4 = w.bq[i], d = w.bd[i];
+    float4 x = w.bx[i], q4 = w.bq[i], d = __ldg(&p.bdims[e.b0 + i]);
     Q4<nf> q; q.w = nf(q4.x); q.x = nf(q4.y); q.y = nf(q4.z); q.z = nf(q4.w);
-    s.type = body_shape_type(w, i);
+    s.type = __float_as_int(d.w);
     s.c = v3<nf>(nf(x.x), nf(x.y), nf(x.z));
     s.M = qmat(q);
     s.d0 = nf(d.x); s.d1 = nf(d.y); s.d2 = nf(d.z);
@@ -197,7 +195,7 @@ __device__ __forceinline__ Shape<nf> coll_shape(const Ws& w, const EnvInfo& e, i
 // ---------------------------------------------------------------------------
 __device__ void stage_aabb(const Params& p, const EnvInfo& e, const Ws& w) {
   for (int i = threadIdx.x; i < e.D + e.S; i += blockDim.x) {
-    Shape<nf> s = coll_shape(w, e, i);
+    Shape<nf> s = coll_shape(p, w, e, i);
     AABBt<nf> b = shape_aabb(s, nf(p.off));
     w.alo[i] = make_float4(b.lo.x.v, b.lo.y.v, b.lo.z.v, 0.f);
     w.ahi[i] = make_float4(b.hi.x.v, b.hi.y.v, b.hi.z.v, 0.f);
@@ -276,8 +274,8 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
       int pr = w.pairs[idx];
       pi = pr & 0xffff;
       pj = pr >> 16;
-      Si = coll_shape(w, e, pi);
-      Sj = coll_shape(w, e, pj);
+      Si = coll_shape(p, w, e, pi);
+      Sj = coll_shape(p, w, e, pj);
       n = collide(Si, Sj, nf(p.off), pts);
     }
     int tot;
@@ -361,7 +359,7 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
       }
       for (int i = 0; i < e.D; ++i) {
         int n = w.inc_off[i + 1];
-        w.bd[i].w = (float)(n > 0 ? n : 1);
+        w.bIw1[i].z = (float)(n > 0 ? n : 1);
         w.inc_off[i + 1] += w.inc_off[i];
       }
       for (int i = 0; i < e.D; ++i) w.masks[i] = (unsigned long long)w.inc_off[i];   // fill cursor
@@ -385,10 +383,11 @@ __device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws&
     float4 v = w.bv[i];
     v.x = v.x + p.gx * p.h; v.y = v.y + p.gy * p.h; v.z = v.z + p.gz * p.h;
     w.bv[i] = v;
-    float4 q4 = w.bq[i], I = w.bI[i];
+    float4 q4 = w.bq[i], I = __ldg(&p.binv[e.b0 + i]);
+    const float split = w.bIw1[i].z;
     Q4<float> q; q.w = q4.x; q.x = q4.y; q.y = q4.z; q.z = q4.w;
     M3<float> R = qmat(q);
-    float d[3] = {I.x, I.y, I.z};
+    float d[3] = {I.y, I.z, I.w};
     float W[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -396,7 +395,7 @@ __device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws&
       for (int b = 0; b < 3; ++b)
         W[a][b] = R.m[a][0] * d[0] * R.m[b][0] + R.m[a][1] * d[1] * R.m[b][1] + R.m[a][2] * d[2] * R.m[b][2];
     w.bIw0[i] = make_float4(W[0][0], W[0][1], W[0][2], W[1][1]);
-    w.bIw1[i] = make_float4(W[1][2], W[2][2], 0.f, 0.f);
+    w.bIw1[i] = make_float4(W[1][2], W[2][2], split, 0.f);
   }
 }
 
@@ -409,12 +408,20 @@ __device__ __forceinline__ Sym3 load_Iw(const Ws& w, int i) {
 // ---------------------------------------------------------------------------
 // a5 (per substep): rows
 // ---------------------------------------------------------------------------
-// Generic joint row: 6 float4 = la|m, aa|bias, lb|gamma, ab|lam, Ia|lo, Ib|hi.
+// Generic joint row. Every joint row has lb = -la (linear rows: -u, u;
+// angular rows: 0, 0), so a row is stored as 5 float4: la|m, aa|bias,
+// ab|gamma, Ia|lam, Ib|clamp, where clamp >= 0 means lambda in [-clamp,
+// clamp] (soft drive), CLAMP_UNI means lambda >= 0 and CLAMP_FREE no clamp.
+enum { ROW_F4 = 5 };
+#define CLAMP_UNI (-1.f)
+#define CLAMP_FREE (-2.f)
 struct JRow { V3<float> la, aa, lb, ab, Ia, Ib; float m, bias, gamma, lam, lo, hi; };
 
 __device__ __forceinline__ void put_row(float4* r, const JRow& x) {
-  r[0] = f4(x.la, x.m); r[1] = f4(x.aa, x.bias); r[2] = f4(x.lb, x.gamma);
-  r[3] = f4(x.ab, x.lam); r[4] = f4(x.Ia, x.lo); r[5] = f4(x.Ib, x.hi);
+  // only soft rows have a finite upper clamp
+  float clamp = x.hi != INFINITY ? x.hi : (x.lo == 0.f ? CLAMP_UNI : CLAMP_FREE);
+  r[0] = f4(x.la, x.m); r[1] = f4(x.aa, x.bias); r[2] = f4(x.ab, x.gamma);
+  r[3] = f4(x.Ia, x.lam); r[4] = f4(x.Ib, clamp);
 }
 
 __device__ __forceinline__ JRow blank_row() {
@@ -461,8 +468,8 @@ __device__ __forceinline__ RowCtx row_ctx(const Ws& w, int a, int b) {
   c.a = a; c.b = b;
   c.ima = a >= 0 ? w.bx[a].w : 0.f;
   c.imb = b >= 0 ? w.bx[b].w : 0.f;
-  c.sa = a >= 0 ? w.bd[a].w : 1.f;
-  c.sb = b >= 0 ? w.bd[b].w : 1.f;
+  c.sa = a >= 0 ? w.bIw1[a].z : 1.f;
+  c.sb = b >= 0 ? w.bIw1[b].z : 1.f;
   if (a >= 0) c.Ia = load_Iw(w, a);
   if (b >= 0) c.Ib = load_Iw(w, b);
   return c;
@@ -497,74 +504,74 @@ __device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k
   Q4<float> qr = qmul(qconj(qFA), qFB);
   if (qr.w < 0.f) { qr.w = -qr.w; qr.x = -qr.x; qr.y = -qr.y; qr.z = -qr.z; }
   V3<float> raB = A >= 0 ? pb_w - xa : v3<float>(0.f, 0.f, 0.f);
-  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * 6;
+  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * ROW_F4;
   int n = 0;
   bool drive = j.k > 0.f || j.d > 0.f;
   if (j.type == JT_REVOLUTE) {
     for (int c = 0; c < 3; ++c) {
       JRow r = lin_row(unit<float>(c), ra, rb);
       r.bias = beta * comp(dp, c);
-      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
     }
     V3<float> cr = cross(ux, col(qmat(qFB), 0));
-    JRow r1 = ang_row(uy); r1.bias = beta * dot(cr, uy); finish_row(r1, ctx, false); put_row(rows + 6 * n++, r1);
-    JRow r2 = ang_row(uz); r2.bias = beta * dot(cr, uz); finish_row(r2, ctx, false); put_row(rows + 6 * n++, r2);
+    JRow r1 = ang_row(uy); r1.bias = beta * dot(cr, uy); finish_row(r1, ctx, false); put_row(rows + ROW_F4 * n++, r1);
+    JRow r2 = ang_row(uz); r2.bias = beta * dot(cr, uz); finish_row(r2, ctx, false); put_row(rows + ROW_F4 * n++, r2);
     if (drive) {
       JRow r = ang_row(ux);
       float theta = 2.f * atan2f(qr.x, qr.w);
       soft_row(r, h, theta - (tgt ? tgt[j.dof] : 0.f), j.k, j.d, j.fmax);
-      finish_row(r, ctx, true); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, true); put_row(rows + ROW_F4 * n++, r);
     }
   } else if (j.type == JT_PRISMATIC) {
     V3<float> us[2] = {uy, uz};
     for (int c = 0; c < 2; ++c) {
       JRow r = lin_row(us[c], raB, rb);
       r.bias = beta * dot(dp, us[c]);
-      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
     }
     V3<float> ua[3] = {ux, uy, uz};
     float qv[3] = {qr.x, qr.y, qr.z};
     for (int c = 0; c < 3; ++c) {
       JRow r = ang_row(ua[c]);
       r.bias = beta * (2.f * qv[c]);
-      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
     }
     float dd = dot(dp, ux);
     if (drive) {
       JRow r = lin_row(ux, raB, rb);
       soft_row(r, h, dd - (tgt ? tgt[j.dof] : 0.f), j.k, j.d, j.fmax);
-      finish_row(r, ctx, true); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, true); put_row(rows + ROW_F4 * n++, r);
     }
     for (int c = 0; c < 2; ++c) {
       JRow r = lin_row(c == 0 ? ux : -ux, raB, rb);
       float C = c == 0 ? dd - j.lo : j.hi - dd;
       r.bias = C > 0.f ? C / h : beta * C;
       r.lo = 0.f; r.hi = INFINITY;
-      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
     }
   } else {
     {
       JRow r = lin_row(uz, raB, rb);
       r.bias = beta * dot(dp, uz);
-      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
     }
     V3<float> cr = cross(uz, col(qmat(qFB), 2));
     V3<float> us[2] = {ux, uy};
     for (int c = 0; c < 2; ++c) {
       JRow r = ang_row(us[c]);
       r.bias = beta * dot(cr, us[c]);
-      finish_row(r, ctx, false); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
     }
     if (drive) {
       for (int c = 0; c < 2; ++c) {
         JRow r = lin_row(us[c], raB, rb);
         soft_row(r, h, dot(dp, us[c]) - (tgt ? tgt[j.dof + c] : 0.f), j.k, j.d, j.fmax);
-        finish_row(r, ctx, true); put_row(rows + 6 * n++, r);
+        finish_row(r, ctx, true); put_row(rows + ROW_F4 * n++, r);
       }
       JRow r = ang_row(uz);
       float theta = 2.f * atan2f(qr.z, qr.w);
       soft_row(r, h, theta - (tgt ? tgt[j.dof + 2] : 0.f), j.k, j.d, j.fmax);
-      finish_row(r, ctx, true); put_row(rows + 6 * n++, r);
+      finish_row(r, ctx, true); put_row(rows + ROW_F4 * n++, r);
     }
   }
 }
@@ -616,9 +623,8 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
   onb(n, t1, t2);
   w.kra[ci] = f4(ra, eff_mass(ctx, n, ra, rb));
   w.krb[ci] = f4(rb, bias);
-  w.kt1[ci] = f4(t1, eff_mass(ctx, t1, ra, rb));
-  w.kt2[ci] = f4(t2, eff_mass(ctx, t2, ra, rb));
-  w.klam[ci] = make_float4(0.f, 0.f, 0.f, 0.f);
+  w.klam[ci] = make_float4(0.f, 0.f, 0.f, eff_mass(ctx, t1, ra, rb));
+  w.cra[ci].w = eff_mass(ctx, t2, ra, rb);
 }
 
 __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
@@ -648,18 +654,21 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
   const JointDesc& j = p.joints[e.j0 + k];
   const int A = j.parent;
   const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = w.bx[j.child].w;
-  const float sa = A >= 0 ? w.bd[A].w : 1.f, sb = w.bd[j.child].w;
+  const float sa = A >= 0 ? w.bIw1[A].z : 1.f, sb = w.bIw1[j.child].z;
   const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
-  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * 6;
+  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * ROW_F4;
   for (int r = 0; r < nr; ++r) {
-    float4* R = rows + 6 * r;
-    float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4], r5 = R[5];
-    V3<float> la = f3(r0), aa = f3(r1), lb = f3(r2), ab = f3(r3), Ia = f3(r4), Ib = f3(r5);
-    float jv = dot(lb, bv.vb) + dot(ab, bv.wb);
+    float4* R = rows + ROW_F4 * r;
+    float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4];
+    V3<float> la = f3(r0), aa = f3(r1), ab = f3(r2), Ia = f3(r3), Ib = f3(r4);
+    float jv = dot(ab, bv.wb) - dot(la, bv.vb);
     if (A >= 0) jv = jv + dot(la, bv.va) + dot(aa, bv.wa);
     float lam = r3.w;
     float dl = -r0.w * (jv + r1.w + r2.w * lam);
-    float nl = fminf(fmaxf(lam + dl, r4.w), r5.w);
+    float nl = lam + dl;
+    const float cl = r4.w;
+    if (cl >= 0.f) nl = fminf(fmaxf(nl, -cl), cl);
+    else if (cl == CLAMP_UNI) nl = fmaxf(nl, 0.f);
     dl = nl - lam;
     R[3].w = nl;
     if (A >= 0) {
@@ -667,9 +676,9 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
       bv.wa = bv.wa + Ia * (sa * dl);
       if (dacc) { dacc->va = dacc->va + la * (ima * dl); dacc->wa = dacc->wa + Ia * dl; }
     }
-    bv.vb = bv.vb + lb * (sb * imb * dl);
+    bv.vb = bv.vb - la * (sb * imb * dl);
     bv.wb = bv.wb + Ib * (sb * dl);
-    if (dacc) { dacc->vb = dacc->vb + lb * (imb * dl); dacc->wb = dacc->wb + Ib * dl; }
+    if (dacc) { dacc->vb = dacc->vb - la * (imb * dl); dacc->wb = dacc->wb + Ib * dl; }
   }
 }
 
@@ -678,15 +687,17 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
   int4 mf = w.man[m];
   const int a = mf.x, b = mf.y;
   const float ima = w.bx[a].w, imb = b >= 0 ? w.bx[b].w : 0.f;
-  const float sa = w.bd[a].w, sb = b >= 0 ? w.bd[b].w : 1.f;
+  const float sa = w.bIw1[a].z, sb = b >= 0 ? w.bIw1[b].z : 1.f;
   Sym3 Ia = load_Iw(w, a), Ib;
   if (b >= 0) Ib = load_Iw(w, b);
   for (int c = mf.z; c < mf.z + mf.w; ++c) {
-    float4 kra = w.kra[c], krb = w.krb[c], kt1 = w.kt1[c], kt2 = w.kt2[c], lam = w.klam[c];
+    float4 kra = w.kra[c], krb = w.krb[c], lam = w.klam[c];
     V3<float> n = f3(w.cn[c]);
     V3<float> ra = f3(kra), rb = f3(krb);
-    V3<float> dirs[3] = {n, f3(kt1), f3(kt2)};
-    float ms[3] = {kra.w, kt1.w, kt2.w};
+    V3<float> t1, t2;
+    onb(n, t1, t2);
+    V3<float> dirs[3] = {n, t1, t2};
+    float ms[3] = {kra.w, lam.w, w.cra[c].w};
     float ls[3] = {lam.x, lam.y, lam.z};
     for (int r = 0; r < 3; ++r) {
       V3<float> dv = bv.vb + cross(bv.wb, rb) - (bv.va + cross(bv.wa, ra));   // static b: vb = wb = 0
@@ -710,7 +721,7 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
         if (dacc) { dacc->vb = dacc->vb + P * imb; dacc->wb = dacc->wb + smul(Ib, cross(rb, P)); }
       }
     }
-    w.klam[c] = make_float4(ls[0], ls[1], ls[2], 0.f);
+    w.klam[c] = make_float4(ls[0], ls[1], ls[2], lam.w);
   }
 }
 

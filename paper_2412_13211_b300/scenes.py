@@ -633,11 +633,12 @@ def make_config(idx: int, num_envs: int | None = None, seed: int = 0, env_start:
             raise ValueError(idx)
     scene = _pack(f"config{idx}", envs, seed, meta={"config": idx})
     cfg = {
-        1: SolverCfg(dt=0.01, substeps=1, iterations=10, friction=0.5, max_contacts=64, max_pairs=128),
-        2: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=192, max_pairs=512),
-        3: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=320, max_pairs=1024),
-        4: SolverCfg(dt=0.01, substeps=4, iterations=16, max_contacts=128, max_pairs=256),
-        5: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=320, max_pairs=1024),
+        # capacities: about 1.2-1.6x the largest per-env count seen over the first steps
+        1: SolverCfg(dt=0.01, substeps=1, iterations=10, friction=0.5, max_contacts=64, max_pairs=64),
+        2: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=112, max_pairs=48),
+        3: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=160, max_pairs=96),
+        4: SolverCfg(dt=0.01, substeps=4, iterations=16, max_contacts=48, max_pairs=24),
+        5: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=128, max_pairs=64),
     }[idx]
     steps = {1: 100, 2: 200, 3: 500, 4: 64, 5: 500}[idx]
     scene.meta["steps"] = steps

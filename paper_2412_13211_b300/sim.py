@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import EXEC_FUSED, EXEC_PLAIN, SceneDesc, SolverCfg, State, check
+from ._lib import EXEC_FUSED, EXEC_PLAIN, EXEC_SUBSTEP, SceneDesc, SolverCfg, State, check
 
 
 def _c(a, dt):
@@ -73,7 +73,7 @@ class MshSim:
     state: pos [B,3], quat [B,4], linvel [B,3], angvel [B,3] float32 CUDA
     tensors, updated in place by `step`."""
 
-    def __init__(self, scene, cfg, device="cuda", exec_form: str = "fused", threads_per_env: int = 128,
+    def __init__(self, scene, cfg, device="cuda", exec_form: str = "fused", threads_per_env: int = 0,
                  use_graph: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("MshSim needs a CUDA device; the step has no CPU implementation")
@@ -97,8 +97,10 @@ class MshSim:
         self.set_exec(exec_form, threads_per_env, use_graph)
 
     # -- configuration ------------------------------------------------------
-    def set_exec(self, exec_form: str = "fused", threads_per_env: int = 128, use_graph: bool = False):
-        form = {"plain": EXEC_PLAIN, "fused": EXEC_FUSED}[exec_form]
+    def set_exec(self, exec_form: str = "fused", threads_per_env: int = 0, use_graph: bool = False):
+        """exec_form: "fused" (one persistent launch per step), "substep" (one launch
+        per substep) or "plain" (one launch per stage); threads_per_env 0 = default."""
+        form = {"plain": EXEC_PLAIN, "fused": EXEC_FUSED, "substep": EXEC_SUBSTEP}[exec_form]
         with torch.cuda.device(self.device):
             check(self.lib.msh_set_exec(self.handle, form, int(threads_per_env), int(bool(use_graph))),
                   "msh_set_exec")

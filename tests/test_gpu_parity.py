@@ -139,8 +139,10 @@ def test_plain_fused_graph_and_block_sizes_bitwise_equal(idx):
     tg = sc.target_walk(3)
     results = []
     for kw in (dict(exec_form="fused"), dict(exec_form="plain"), dict(exec_form="fused", use_graph=True),
-               dict(exec_form="plain", use_graph=True), dict(exec_form="fused", threads_per_env=32),
-               dict(exec_form="fused", threads_per_env=64), dict(exec_form="fused", threads_per_env=256)):
+               dict(exec_form="plain", use_graph=True), dict(exec_form="substep"),
+               dict(exec_form="substep", use_graph=True, threads_per_env=64),
+               dict(exec_form="fused", threads_per_env=64), dict(exec_form="fused", threads_per_env=128),
+               dict(exec_form="fused", threads_per_env=256)):
         sim = make_sim(sc, cfg, **kw)
         for t in range(3):
             sim.step(torch.as_tensor(tg[t]).cuda())
@@ -240,3 +242,19 @@ def test_degenerate_envs():
     gpu, o32, _, status, st32 = _step_both(sc, cfg, 3)
     assert np.array_equal(status, st32)
     assert _err(gpu[0], o32[0]) <= TOL_X and _err(gpu[2], o32[2]) <= TOL_V
+
+
+def test_autotuner_picks_a_form_and_keeps_state():
+    import torch
+    from paper_2412_13211_b300 import autotune
+    sc, cfg = scene(3)
+    sim = make_sim(sc, cfg)
+    before = sim.state_numpy()
+    res = autotune.tune(sim, steps=2, warmup=1)
+    after = sim.state_numpy()
+    for a, b in zip(before, after):
+        assert np.array_equal(bits(a), bits(b))
+    assert res["best"][0] in ("fused", "substep", "plain") and len(res["ms"]) >= 3
+    assert (sim.exec_form, sim.threads_per_env) == tuple(res["best"])
+    sim.step(torch.zeros((sc.num_envs, sc.max_dof)).cuda())
+    assert not sim.status().any()
