@@ -1221,8 +1221,9 @@ template <class R, class T> void store_env(const OracleScene& sc, int e, const E
   }
 }
 
-template <class R> int step_batch(const OracleScene* sc, const OracleCfg* cfg, R* pos, R* quat, R* lv, R* av,
-                                  const float* targets, int nsteps, int32_t* status, int nthreads) {
+template <class R, class TT = float>
+int step_batch(const OracleScene* sc, const OracleCfg* cfg, R* pos, R* quat, R* lv, R* av, const TT* targets,
+               int nsteps, int32_t* status, int nthreads, const double* mass64 = nullptr) {
   int E = sc->num_envs;
   int md = sc->max_dof > 0 ? sc->max_dof : 1;
 #ifdef _OPENMP
@@ -1231,11 +1232,16 @@ template <class R> int step_batch(const OracleScene* sc, const OracleCfg* cfg, R
 #endif
   for (int e = 0; e < E; ++e) {
     EnvState<R> S;
-    load_env<R, R>(*sc, e, pos, quat, lv, av, nullptr, S);
+    std::vector<R> mass;
+    if (mass64) {
+      mass.resize(sc->body_off[E]);
+      for (int g = sc->body_off[e]; g < sc->body_off[e + 1]; ++g) mass[g] = R(mass64[g]);
+    }
+    load_env<R, R>(*sc, e, pos, quat, lv, av, mass64 ? mass.data() : nullptr, S);
     int st = 0;
     std::vector<R> tg(md);
     for (int t = 0; t < nsteps; ++t) {
-      const float* tt = targets ? targets + ((size_t)t * E + e) * md : nullptr;
+      const TT* tt = targets ? targets + ((size_t)t * E + e) * md : nullptr;
       for (int k = 0; k < md; ++k) tg[k] = tt ? R(tt[k]) : R(0);
       st |= step_env(S, *cfg, tg.data(), (Detect<R>*)nullptr);
     }
@@ -1291,6 +1297,71 @@ template <class R> int detect_batch(const OracleScene* sc, const OracleCfg* cfg,
   return 0;
 }
 
+
+// Reference gradients by forward-mode dual numbers: the rollout is run with
+// every scalar carrying NDIR tangents seeded on the initial velocities, the
+// per-step joint targets and the body masses; the loss of env e is the
+// squared distance of its goal body to its goal position after the last step.
+// Branch decisions (contact set, clamps) follow the primal values, so the
+// result is the derivative of the piecewise-smooth rollout at this point.
+constexpr int NDIR = 4;
+typedef Dual<NDIR> DR;
+
+int grad_batch(const OracleScene* sc, const OracleCfg* cfg, const double* pos, const double* quat, const double* lv,
+               const double* av, const float* targets, int nsteps, const int32_t* goal_body, const double* goal_pos,
+               int ndir, const double* dvel, const double* dtg, const double* dmass, double* loss, double* dloss,
+               int32_t* status, int nthreads) {
+  int E = sc->num_envs;
+  int B = sc->body_off[E];
+  int md = sc->max_dof > 0 ? sc->max_dof : 1;
+  if (ndir < 1 || ndir > NDIR) return -1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int e = 0; e < E; ++e) {
+    int b0 = sc->body_off[e], D = sc->body_off[e + 1] - b0;
+    std::vector<DR> mass(B);
+    for (int i = 0; i < D; ++i) {
+      int g = b0 + i;
+      mass[g] = DR(sc->body_mass[g]);
+      for (int k = 0; k < ndir; ++k) mass[g].d[k] = dmass ? dmass[(size_t)k * B + g] : 0.0;
+    }
+    EnvState<DR> S;
+    load_env<DR, double>(*sc, e, pos, quat, lv, av, mass.data(), S);
+    for (int i = 0; i < D; ++i) {
+      int g = b0 + i;
+      for (int k = 0; k < ndir; ++k) {
+        const double* dv = dvel ? dvel + ((size_t)k * B + g) * 6 : nullptr;
+        if (!dv) continue;
+        S.body[i].v.x.d[k] = dv[0]; S.body[i].v.y.d[k] = dv[1]; S.body[i].v.z.d[k] = dv[2];
+        S.body[i].w.x.d[k] = dv[3]; S.body[i].w.y.d[k] = dv[4]; S.body[i].w.z.d[k] = dv[5];
+      }
+    }
+    int st = 0;
+    std::vector<DR> tg(md);
+    for (int t = 0; t < nsteps; ++t) {
+      for (int j = 0; j < md; ++j) {
+        size_t idx = ((size_t)t * E + e) * md + j;
+        tg[j] = DR(targets ? (double)targets[idx] : 0.0);
+        for (int k = 0; k < ndir; ++k)
+          tg[j].d[k] = dtg ? dtg[(size_t)k * nsteps * E * md + idx] : 0.0;
+      }
+      st |= step_env(S, *cfg, tg.data(), (Detect<DR>*)nullptr);
+    }
+    DR L = DR(0.0);
+    int gb = goal_body ? goal_body[e] : -1;
+    if (gb >= 0 && gb < D) {
+      V3<DR> d = S.body[gb].x - v3<DR>(DR(goal_pos[3 * e]), DR(goal_pos[3 * e + 1]), DR(goal_pos[3 * e + 2]));
+      L = dot(d, d);
+    }
+    loss[e] = L.v;
+    for (int k = 0; k < ndir; ++k) dloss[(size_t)k * E + e] = L.d[k];
+    if (status) status[e] = st;
+  }
+  return 0;
+}
+
 }  // namespace orc
 
 extern "C" {
@@ -1302,6 +1373,13 @@ int oracle_step_f32(const OracleScene* sc, const OracleCfg* cfg, float* pos, flo
 int oracle_step_f64(const OracleScene* sc, const OracleCfg* cfg, double* pos, double* quat, double* lv,
                     double* av, const float* targets, int nsteps, int32_t* status, int nthreads) {
   return orc::step_batch<double>(sc, cfg, pos, quat, lv, av, targets, nsteps, status, nthreads);
+}
+// FP64 rollout whose joint targets [nsteps][E][max_dof] and body masses [B]
+// are given in double (so finite differences can use exact perturbations).
+int oracle_step_f64x(const OracleScene* sc, const OracleCfg* cfg, double* pos, double* quat, double* lv,
+                     double* av, const double* targets, const double* mass, int nsteps, int32_t* status,
+                     int nthreads) {
+  return orc::step_batch<double, double>(sc, cfg, pos, quat, lv, av, targets, nsteps, status, nthreads, mass);
 }
 int oracle_detect_f32(const OracleScene* sc, const OracleCfg* cfg, const float* pos, const float* quat,
                       float* aabb_body, float* aabb_static, int32_t* pair_count, int32_t* pairs,
@@ -1316,6 +1394,16 @@ int oracle_detect_f64(const OracleScene* sc, const OracleCfg* cfg, const double*
                       int32_t* manifold_count, int32_t* colours, int32_t* ncolours, int32_t* status) {
   return orc::detect_batch<double>(sc, cfg, pos, quat, aabb_body, aabb_static, pair_count, pairs, contact_count,
                                    contact_ids, contact_geom, manifold_count, colours, ncolours, status);
+}
+// Loss and NDIR (<= 4) directional derivatives of the rollout (see grad_batch).
+// dvel [ndir][B][6] (linear, angular), dtg [ndir][nsteps][E][max_dof],
+// dmass [ndir][B]; any may be NULL. Outputs loss [E], dloss [ndir][E].
+int oracle_grad_f64(const OracleScene* sc, const OracleCfg* cfg, const double* pos, const double* quat,
+                    const double* lv, const double* av, const float* targets, int nsteps, const int32_t* goal_body,
+                    const double* goal_pos, int ndir, const double* dvel, const double* dtg, const double* dmass,
+                    double* loss, double* dloss, int32_t* status, int nthreads) {
+  return orc::grad_batch(sc, cfg, pos, quat, lv, av, targets, nsteps, goal_body, goal_pos, ndir, dvel, dtg, dmass,
+                         loss, dloss, status, nthreads);
 }
 int oracle_max_threads(void) {
 #ifdef _OPENMP

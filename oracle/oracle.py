@@ -65,6 +65,10 @@ def load():
             fn = getattr(lib, name)
             fn.argtypes = [P] * 15
             fn.restype = C.c_int
+        lib.oracle_step_f64x.argtypes = [P, P, P, P, P, P, P, P, C.c_int, P, C.c_int]
+        lib.oracle_step_f64x.restype = C.c_int
+        lib.oracle_grad_f64.argtypes = [P, P, P, P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, C.c_int]
+        lib.oracle_grad_f64.restype = C.c_int
         lib.oracle_max_threads.restype = C.c_int
         _lib = lib
     return _lib
@@ -185,3 +189,59 @@ def detect(scene, cfg, pos, quat, precision: str = "f32") -> OracleDetect:
     if rc != 0:
         raise RuntimeError(f"oracle detect failed: {rc}")
     return out
+
+
+def loss_and_directional(scene, cfg, state, targets, nsteps, goal_body, goal_pos, dvel=None, dtargets=None,
+                         dmass=None, threads: int = 0):
+    """FP64 rollout loss sum_e |x_goal - goal|^2 per env and its directional
+    derivatives by forward-mode dual numbers (at most 4 directions).
+
+    dvel [K,B,6] (linear then angular velocity), dtargets [K,nsteps,E,max_dof],
+    dmass [K,B]. Returns (loss [E], dloss [K,E], status [E])."""
+    lib = load()
+    E, B = scene.num_envs, scene.num_bodies
+    md = max(scene.max_dof, 1)
+    K = max(len(x) for x in (dvel, dtargets, dmass) if x is not None)
+    assert 1 <= K <= 4
+    st = [np.ascontiguousarray(a, dtype=np.float64) for a in state]
+    tg = np.ascontiguousarray(targets, dtype=np.float32).reshape(-1, E, md)
+    f64 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+    dvel, dtargets, dmass = f64(dvel), f64(dtargets), f64(dmass)
+    loss = np.zeros(E)
+    dloss = np.zeros((K, E))
+    status = np.zeros(E, np.int32)
+    keep = _Keep(scene)
+    c = _cfg(cfg)
+    gb = np.ascontiguousarray(goal_body, dtype=np.int32)
+    gp = np.ascontiguousarray(goal_pos, dtype=np.float64)
+    rc = lib.oracle_grad_f64(C.byref(keep.struct), C.byref(c), _ptr(st[0]), _ptr(st[1]), _ptr(st[2]), _ptr(st[3]),
+                             _ptr(tg), int(nsteps), _ptr(gb), _ptr(gp), int(K), _ptr(dvel), _ptr(dtargets),
+                             _ptr(dmass), _ptr(loss), _ptr(dloss), _ptr(status), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle grad failed: {rc}")
+    return loss, dloss, status
+
+
+def loss_value(scene, cfg, state, targets, nsteps, goal_body, goal_pos, mass=None, threads: int = 0):
+    """FP64 loss per env after `nsteps` steps; targets [nsteps,E,max_dof] and
+    optional masses [B] are taken in double (for finite differences)."""
+    lib = load()
+    E = scene.num_envs
+    md = max(scene.max_dof, 1)
+    st = [np.ascontiguousarray(a, dtype=np.float64).copy() for a in state]
+    tg = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, E, md)
+    m = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
+    status = np.zeros(E, np.int32)
+    keep = _Keep(scene)
+    c = _cfg(cfg)
+    rc = lib.oracle_step_f64x(C.byref(keep.struct), C.byref(c), _ptr(st[0]), _ptr(st[1]), _ptr(st[2]),
+                              _ptr(st[3]), _ptr(tg), _ptr(m), int(nsteps), _ptr(status), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle step failed: {rc}")
+    L = np.zeros(E)
+    for e in range(E):
+        g = goal_body[e]
+        if g >= 0:
+            d = st[0][scene.body_off[e] + g] - np.asarray(goal_pos[e], np.float64)
+            L[e] = d @ d
+    return L, status

@@ -46,6 +46,23 @@ QL_AXIS_Z = (1.0, 0.0, 0.0, 0.0)
 QL_AXIS_Y = (0.5, 0.5, 0.5, 0.5)
 QL_AXIS_NY = (0.5, -0.5, 0.5, -0.5)
 
+# A hanging link: its local x axis points along world -z.
+Q_HANG = (_S2, 0.0, _S2, 0.0)
+
+
+def _qmul(a, b):
+    """Hamilton product, used only to express constant world frames in a
+    link's initial local frame when building a scene."""
+    aw, ax, ay, az = a
+    bw, bx, by, bz = b
+    return (aw * bw - ax * bx - ay * by - az * bz, aw * bx + ax * bw + ay * bz - az * by,
+            aw * by - ax * bz + ay * bw + az * bx, aw * bz + ax * by - ay * bx + az * bw)
+
+
+def _local_frame(q_body, q_world):
+    return _qmul((q_body[0], -q_body[1], -q_body[2], -q_body[3]), q_world)
+
+
 # Default drive gains (stiffness, damping, force limit) per DoF kind.
 ARM_GAINS = (1000.0, 100.0, 200.0)
 FINGER_GAINS = (1000.0, 100.0, 200.0)
@@ -268,6 +285,37 @@ def _pack(name, envs, seed, meta=None) -> Scene:
 # Robot: 7 revolute capsule links + 2 prismatic box fingers, optionally on a
 # planar (x, y, yaw) mobile base.
 # --------------------------------------------------------------------------
+def _add_hanging_robot(env: _Env, rng, anchor):
+    """Adds the arm hanging from world point `anchor` (links point down, joint
+    axes alternate world z / world y) with the two fingers at its lower end.
+    Returns (link lengths, z of the finger bottoms)."""
+    walk_rad, walk_fing = 0.02, 0.001
+    ax, ay, az = anchor
+    parent, prev_len = -1, None
+    z = az
+    lengths = [float(rng.uniform(0.1, 0.4)) for _ in range(7)]
+    for i, L in enumerate(lengths):
+        m = float(rng.uniform(1.0, 3.0))
+        link = env.body(CAPSULE, (LINK_RADIUS, 0.5 * L), m, (ax, ay, z - 0.5 * L), Q_HANG)
+        qw = QW_AXIS_Z if i % 2 == 0 else QW_AXIS_Y
+        ql = _local_frame(Q_HANG, qw)
+        fa = (ax, ay, az) + qw if parent == -1 else (0.5 * prev_len, 0.0, 0.0) + ql
+        env.joint(REVOLUTE, parent, link, fa, (-0.5 * L, 0.0, 0.0) + ql, ARM_GAINS, (0.0, 0.0),
+                  [(0.0, walk_rad, -np.pi, np.pi)])
+        parent, prev_len = link, L
+        z -= L
+    hand_bottom = z
+    fz = hand_bottom - LINK_RADIUS - FINGER_HALF[2] - 0.01
+    dz = fz - (hand_bottom + 0.5 * prev_len)     # world offset from the hand centre
+    for side, qw in ((+1.0, QW_AXIS_Y), (-1.0, QW_AXIS_NY)):
+        dy = side * 0.015
+        f = env.body(BOX, FINGER_HALF, 0.1, (ax, ay + dy, fz))
+        # world offset (0, dy, dz) in the hanging link's frame is (-dz, dy, 0)
+        env.joint(PRISMATIC, parent, f, (-dz, dy, 0.0) + _local_frame(Q_HANG, qw), (0.0, 0.0, 0.0) + qw,
+                  FINGER_GAINS, FINGER_LIMITS, [(0.0, walk_fing, FINGER_LIMITS[0], FINGER_LIMITS[1])])
+    return lengths, fz - FINGER_HALF[2]
+
+
 def _add_robot(env: _Env, rng, anchor, mobile_base: bool):
     """Adds the robot with its first joint at world point `anchor` (fixed base)
     or on a base box whose centre is at `anchor` (mobile base). The arm stands
@@ -448,16 +496,29 @@ def _cfg2_env(rng):
 
 
 def _cfg4_env(rng):
+    """Arm hanging over a table with its fingers 3 cm above the top, the goal
+    box 5 mm beside the fingers (so the target walk pushes it), five more
+    boxes elsewhere on the table, and a goal near the goal box."""
     env = _Env()
     top = 0.8
     env.static((0.0, 0.0, 0.5 * top), (0.6, 0.4, 0.5 * top))
-    base = (0.0, -0.25, top + 0.06)
-    _add_robot(env, rng, base, mobile_base=False)
+    # lengths are drawn inside the builder; the anchor height follows from them,
+    # so draw them first with the same generator state and rebuild
+    state = rng.bit_generator.state
+    lengths = [float(rng.uniform(0.1, 0.4)) for _ in range(7)]
+    rng.bit_generator.state = state
+    drop = sum(lengths) + LINK_RADIUS + 0.01 + 2 * FINGER_HALF[2]
+    anchor = (0.0, 0.0, top + 0.03 + drop)
+    _, finger_bottom = _add_hanging_robot(env, rng, anchor)
+    first = len(env.bodies)
+    h = tuple(float(v) for v in rng.uniform(0.02, 0.05, 3))
+    h = (h[0], h[1], max(h[2], 0.035))        # tall enough to reach the fingers
+    gx = FINGER_HALF[0] + 0.005 + h[0]
+    env.body(BOX, h, float(rng.uniform(0.05, 0.5)), (gx, 0.0, top + h[2]))
     surf = _Surfaces()
     surf.add(-0.58, 0.58, -0.38, 0.38, top)
-    first = len(env.bodies)
-    _place_objects(env, rng, surf, 6, (BOX,), 0.04, 0.10,
-                   lambda: rng.uniform(0.05, 0.5), keep_out=[(base[0], base[1], 0.2)])
+    _place_objects(env, rng, surf, 5, (BOX,), 0.04, 0.10,
+                   lambda: rng.uniform(0.05, 0.5), keep_out=[(0.0, 0.0, 0.25)])
     env.goal_body = first
     g = env.bodies[first][3]
     env.goal_pos = (g[0] + float(rng.uniform(-0.1, 0.1)), g[1] + float(rng.uniform(-0.1, 0.1)), g[2])
@@ -606,7 +667,8 @@ def make_config(idx: int, num_envs: int | None = None, seed: int = 0, env_start:
        counter of 6 static boxes, 4x20.
     3: 4096 envs, apartment rooms with U{10..60} static boxes, U{4..48}
        objects and a mobile manipulator (planar base), 4x20.
-    4: 512 envs, fixed-base arm + 6 boxes on a table, 4x16, goal box.
+    4: 512 envs, arm hanging over a table pushing a goal box + 5 more boxes,
+       4x16, goal position per env.
     5: 16384 envs, apartment rooms with 50 static boxes, 32 objects
        (spheres, capsules, boxes; log-uniform mass), mobile manipulator, 4x20.
     """

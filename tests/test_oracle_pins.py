@@ -865,3 +865,13 @@ def test_sphere_capsule_end_cap_and_mirrored_edge():
     assert d.contact_count[0] == 1
     g = d.contact_geom[0, 0]
     assert g[2] < -0.999999 and abs(g[9] + 0.002) < 1e-6
+
+
+def test_hanging_link_frames():
+    """Scene construction for the hanging arm: its local joint frames turn
+    the link axis onto the world joint axes (conj(Q_HANG) * world frame)."""
+    from paper_2412_13211_b300.scenes import Q_HANG, QW_AXIS_Y, QW_AXIS_Z, _local_frame
+    np.testing.assert_allclose(quat_rotate(Q_HANG, (1, 0, 0)), (0, 0, -1), atol=1e-15)
+    for qw in (QW_AXIS_Y, QW_AXIS_Z):
+        ql = _local_frame(Q_HANG, qw)
+        np.testing.assert_allclose(quat_mul(Q_HANG, ql), qw, atol=1e-15)
