@@ -202,6 +202,28 @@ int msh_detect(msh_handle* h, const msh_state* st, float* aabb_body, float* aabb
 int msh_step_static_scratch(msh_handle* h, const msh_state* st, const float* joint_targets, float dt,
                             int32_t substeps, void* stream);
 
+/*
+ * Differentiation (reverse mode). msh_set_tape(h, n) reserves a tape for n
+ * steps (0 frees it; coloured solver and zero restitution only). While a tape
+ * is set, every msh_step records the step (start state, per-substep poses and
+ * velocities, the lambdas after every sweep, the targets) into the next slot;
+ * graphs are not used for recorded steps. msh_backward reverses the most
+ * recently recorded step and pops it: given adj_out, the adjoint of the state
+ * after that step (DEVICE, same layout as msh_state), it writes adj_in, the
+ * adjoint of the state before it (may alias adj_out), the adjoint of that
+ * step's joint targets into adj_targets [num_envs, max_dof] (may be NULL), and
+ * ADDS the adjoint of the body masses into adj_mass [B] (may be NULL). The
+ * step is differentiated with its discrete decisions frozen: contact set and
+ * features, colouring, and the clamp states of every row update.
+ * msh_tape_reset drops every recorded step; msh_tape_count returns how many
+ * are recorded.
+ */
+int msh_set_tape(msh_handle* h, int32_t max_steps);
+int msh_tape_reset(msh_handle* h);
+int32_t msh_tape_count(const msh_handle* h);
+int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, float* adj_targets,
+                 float* adj_mass, void* stream);
+
 /* Copies the per-env status words to host memory [num_envs] (synchronises
  * `stream`). */
 int msh_get_status(msh_handle* h, int32_t* status_host, void* stream);

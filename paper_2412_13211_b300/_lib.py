@@ -16,7 +16,8 @@ EXEC_PLAIN, EXEC_FUSED, EXEC_SUBSTEP = 0, 1, 2
 
 EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_step", "msh_step_host",
            "msh_detect", "msh_get_status", "msh_clear_status", "msh_scratch_bytes", "msh_workspace_bytes",
-           "msh_launches_per_step", "msh_step_static_scratch")
+           "msh_launches_per_step", "msh_step_static_scratch", "msh_set_tape", "msh_tape_reset",
+           "msh_tape_count", "msh_backward")
 
 
 class SceneDesc(C.Structure):
@@ -62,6 +63,11 @@ def load(build_if_missing: bool = True):
     lib.msh_step.argtypes = [P, P, P, F, I32, P]
     lib.msh_step_host.argtypes = [P, P, P, P, P, P, F, I32, P]
     lib.msh_step_static_scratch.argtypes = [P, P, P, F, I32, P]
+    lib.msh_set_tape.argtypes = [P, I32]
+    lib.msh_tape_reset.argtypes = [P]
+    lib.msh_tape_count.argtypes = [P]
+    lib.msh_tape_count.restype = C.c_int32
+    lib.msh_backward.argtypes = [P, P, P, P, P, P]
     lib.msh_detect.argtypes = [P] * 12 + [P]
     lib.msh_get_status.argtypes = [P, P, P]
     lib.msh_clear_status.argtypes = [P, P]
@@ -74,7 +80,7 @@ def load(build_if_missing: bool = True):
     for name in EXPORTS:
         getattr(lib, name)
         if name not in ("msh_destroy", "msh_last_error", "msh_scratch_bytes", "msh_workspace_bytes",
-                        "msh_launches_per_step"):
+                        "msh_launches_per_step", "msh_tape_count"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

@@ -18,7 +18,10 @@ SOURCES = [os.path.join(HERE, "csrc", "msh.cu")]
 DEPS = (glob.glob(os.path.join(HERE, "csrc", "*.cu")) + glob.glob(os.path.join(HERE, "csrc", "*.cuh"))
         + [os.path.join(ROOT, "include", "msh.h")])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
+# -fmad=false: the only fused multiply-adds are explicit fmaf calls, so every
+# execution form of the step computes bitwise identical results.
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-shared",
+         "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:

@@ -18,7 +18,7 @@
 #include <vector>
 
 #include "../../include/msh.h"
-#include "msh_stages.cuh"
+#include "msh_adjoint.cuh"
 
 using namespace msh;
 
@@ -53,7 +53,7 @@ __global__ void k_colour(Params p) {
 }
 __global__ void k_intvel(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
-  stage_integrate_vel(p, e, plain_ws(p, blockIdx.x));
+  stage_integrate_vel(p, e, plain_ws(p, blockIdx.x), p.sub);
 }
 __global__ void k_prep(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
@@ -61,11 +61,11 @@ __global__ void k_prep(Params p) {
 }
 __global__ void k_solve(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
-  stage_solve_iter(p, e, plain_ws(p, blockIdx.x));
+  stage_solve_iter(p, e, plain_ws(p, blockIdx.x), p.sub, p.it);
 }
 __global__ void k_intpos(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
-  stage_integrate_pos(p, e, plain_ws(p, blockIdx.x));
+  stage_integrate_pos(p, e, plain_ws(p, blockIdx.x), p.sub);
 }
 __global__ void k_store(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
@@ -76,12 +76,12 @@ __global__ void k_store(Params p) {
 __global__ void k_substep(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
   Ws w = plain_ws(p, blockIdx.x);
-  stage_integrate_vel(p, e, w);
+  stage_integrate_vel(p, e, w, p.sub);
   __syncthreads();
   stage_prep(p, e, w);
   __syncthreads();
-  for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w);
-  stage_integrate_pos(p, e, w);
+  for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w, p.sub, it);
+  stage_integrate_pos(p, e, w, p.sub);
 }
 
 // One whole step per env; persistent CTAs pull envs from an atomic queue.
@@ -105,17 +105,106 @@ __global__ void k_fused(Params p, int smem_ws) {
     stage_narrowphase(p, e, w, scr);
     stage_colour(p, e, w);
     for (int s = 0; s < p.S; ++s) {
-      stage_integrate_vel(p, e, w);
+      stage_integrate_vel(p, e, w, s);
       __syncthreads();
       stage_prep(p, e, w);
       __syncthreads();
-      for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w);
-      stage_integrate_pos(p, e, w);
+      for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w, s, it);
+      stage_integrate_pos(p, e, w, s);
       __syncthreads();
     }
     stage_store(p, e, w);
     __syncthreads();
   }
+}
+
+// Adjoint of the recorded step in tape slot q.slot, one CTA per env (see
+// msh_adjoint.cuh). Replays the step's collision stage from the recorded
+// start state, then reverses the substeps and finally the narrowphase.
+__global__ void k_backward(Params p, AdjParams q) {
+  __shared__ int scr[33];
+  const int env = blockIdx.x;
+  EnvInfo e = env_info(p, env);
+  Ws w = plain_ws(p, env);
+  AWs a = make_aws(q.aws + (long long)env * q.aws_stride, q.A);
+  const TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+  const float* tape = p.tape + ((long long)q.slot * p.E + env) * p.tape_slab;
+  const float* tg = tape + tl.t3;
+  load_from_tape(p, e, w, tape);
+  __syncthreads();
+  stage_aabb(p, e, w);
+  __syncthreads();
+  stage_broadphase(p, e, w, scr);
+  stage_narrowphase(p, e, w, scr);
+  stage_colour(p, e, w);
+  build_incidence(p, e, w, a);
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    const int g = e.b0 + i;
+    a.bx[i] = make_float4(q.ax[3 * g], q.ax[3 * g + 1], q.ax[3 * g + 2], 0.f);
+    a.bq[i] = make_float4(q.aq[4 * g], q.aq[4 * g + 1], q.aq[4 * g + 2], q.aq[4 * g + 3]);
+    a.bv[i] = make_float4(q.av[3 * g], q.av[3 * g + 1], q.av[3 * g + 2], 0.f);
+    a.bw[i] = make_float4(q.aw[3 * g], q.aw[3 * g + 1], q.aw[3 * g + 2], 0.f);
+    a.bm[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const int nc = w.misc[MC_CONTACTS];
+  for (int c = threadIdx.x; c < 3 * nc; c += blockDim.x) a.cg[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = threadIdx.x; k < p.max_dof; k += blockDim.x) a.tg[k] = 0.f;
+  __syncthreads();
+  for (int s = p.S - 1; s >= 0; --s) {
+    const float* st = tape + tl.t1 + 19LL * s * p.L.Dm;
+    for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+      const float* t = st + 19 * i;
+      const float4 inv = p.binv[e.b0 + i];
+      w.bx[i] = make_float4(t[0], t[1], t[2], inv.x);
+      w.bq[i] = make_float4(t[3], t[4], t[5], t[6]);
+      w.bv[i] = make_float4(t[13], t[14], t[15], 0.f);
+      w.bw[i] = make_float4(t[16], t[17], t[18], 0.f);
+      Q4<float> qq; qq.w = t[3]; qq.x = t[4]; qq.y = t[5]; qq.z = t[6];
+      float dI[3] = {inv.y, inv.z, inv.w}, W6[6];
+      world_inv_inertia<float>(qq, dI, W6);
+      w.bIw0[i] = make_float4(W6[0], W6[1], W6[2], W6[3]);
+      w.bIw1[i] = make_float4(W6[4], W6[5], 1.f, 0.f);
+    }
+    reverse_integrate(p, e, a, st);
+    __syncthreads();
+    build_rows(p, e, w, a, tg);
+    __syncthreads();
+    const float* lam0 = tape + tl.t2 + (long long)s * p.N * p.tape_Rm;
+    for (int it = p.N - 1; it >= 0; --it)
+      reverse_sweep(p, e, w, a, lam0 + (long long)it * p.tape_Rm, it > 0 ? lam0 + (long long)(it - 1) * p.tape_Rm : nullptr);
+    reverse_setup(p, e, w, a, tg);
+    __syncthreads();
+    gather_bodies(e, a, true);
+    __syncthreads();
+    reverse_inertia(p, e, w, a);
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    const float* t = tape + 13 * i;
+    w.bx[i] = make_float4(t[0], t[1], t[2], w.bx[i].w);
+    w.bq[i] = make_float4(t[3], t[4], t[5], t[6]);
+  }
+  __syncthreads();
+  reverse_detection(p, e, w, a);
+  __syncthreads();
+  gather_bodies(e, a, false);
+  __syncthreads();
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    const int g = e.b0 + i;
+    float4 gx = a.bx[i], gq = a.bq[i], gv = a.bv[i], gw = a.bw[i], gm = a.bm[i];
+    q.ox[3 * g] = gx.x; q.ox[3 * g + 1] = gx.y; q.ox[3 * g + 2] = gx.z;
+    q.oq[4 * g] = gq.x; q.oq[4 * g + 1] = gq.y; q.oq[4 * g + 2] = gq.z; q.oq[4 * g + 3] = gq.w;
+    q.ov[3 * g] = gv.x; q.ov[3 * g + 1] = gv.y; q.ov[3 * g + 2] = gv.z;
+    q.ow[3 * g] = gw.x; q.ow[3 * g + 1] = gw.y; q.ow[3 * g + 2] = gw.z;
+    if (q.omass) {
+      // 1/m and the principal inverse inertias are both proportional to 1/m
+      const float4 inv = p.binv[g];
+      const float dm = -inv.x * inv.x * gm.x - inv.x * (inv.y * gm.y + inv.z * gm.z + inv.w * gm.w);
+      q.omass[g] += dm;
+    }
+  }
+  if (q.otg)
+    for (int k = threadIdx.x; k < p.max_dof; k += blockDim.x) q.otg[(long long)env * p.max_dof + k] = a.tg[k];
 }
 
 // Inverse mass and principal inverse inertia from mass and shape (solid
@@ -252,6 +341,26 @@ Layout make_layout(int Dm, int Sm, int Jm, int P, int C, bool jacobi) {
   return L;
 }
 
+AdjLayout make_adj_layout(const Layout& L, int md) {
+  AdjLayout A;
+  std::memset(&A, 0, sizeof(A));
+  A.Rm = ROWS_PER_JOINT * L.Jm + 3 * L.C;
+  A.Km = L.K;
+  int o = 0;
+  auto take = [&](long long bytes) { int r = o; o = align16((int)(o + bytes)); return r; };
+  const int f4 = 16;
+  A.bx = take(L.Dm * f4); A.bq = take(L.Dm * f4); A.bv = take(L.Dm * f4); A.bw = take(L.Dm * f4);
+  A.bI0 = take(L.Dm * f4); A.bI1 = take(L.Dm * f4); A.bm = take(L.Dm * f4);
+  A.rows = take((long long)A.Rm * ROW_F4 * f4); A.radj = take((long long)A.Rm * ROW_F4 * f4);
+  A.rkind = take((long long)A.Rm * 4);
+  A.gat = take((long long)A.Km * 8 * f4);
+  A.cg = take((long long)L.C * 3 * f4);
+  A.inc_off = take((L.Dm + 1) * 4); A.inc = take(2LL * A.Km * 4);
+  A.tg = take((long long)(md > 0 ? md : 1) * 4);
+  A.bytes = o;
+  return A;
+}
+
 }  // namespace
 
 struct msh_handle {
@@ -270,6 +379,12 @@ struct msh_handle {
   float *d_pos = nullptr, *d_quat = nullptr, *d_lv = nullptr, *d_av = nullptr;   // host-path state
   char* d_ws_plain = nullptr;   // E slabs
   char* d_ws_fused = nullptr;   // per-CTA slabs when SMEM cannot hold the workspace
+  // adjoint
+  float* d_tape = nullptr;      // tape_max recorded steps x E env slabs
+  long long tape_slab = 0;
+  int tape_max = 0, tape_count = 0, tape_Rm = 0;
+  char* d_aws = nullptr;        // adjoint workspace slabs (E)
+  AdjLayout A;
   int64_t bytes = 0;
   // execution
   int exec = MSH_EXEC_FUSED, tpe = 128, use_graph = 0;
@@ -323,6 +438,9 @@ Params make_params(const msh_handle* h, const msh_state* st, const float* target
   p.status = h->d_status;
   p.L = h->L;
   p.queue = h->d_queue;
+  p.tape = nullptr;
+  p.tape_slab = h->tape_slab;
+  p.tape_Rm = h->tape_Rm;
   return p;
 }
 
@@ -355,13 +473,17 @@ int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
     p.ws = h->d_ws_plain;
     p.ws_stride = h->L.bytes;
     for (int sub = 0; sub < p.S; ++sub) {
+      p.sub = sub;
       if (h->exec == MSH_EXEC_SUBSTEP) {
         k_substep<<<h->E, T, 0, s>>>(p);
         continue;
       }
       k_intvel<<<h->E, T, 0, s>>>(p);
       k_prep<<<h->E, T, 0, s>>>(p);
-      for (int it = 0; it < p.N; ++it) k_solve<<<h->E, T, 0, s>>>(p);
+      for (int it = 0; it < p.N; ++it) {
+        p.it = it;
+        k_solve<<<h->E, T, 0, s>>>(p);
+      }
       k_intpos<<<h->E, T, 0, s>>>(p);
     }
     k_store<<<h->E, T, 0, s>>>(p);
@@ -550,7 +672,7 @@ void msh_destroy(msh_handle* h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->d_body_off, h->d_static_off, h->d_joint_off, h->d_env_order, h->d_bdims, h->d_binv,
                   h->d_static_pose, h->d_static_half, h->d_joints, h->d_status, h->d_queue, h->d_targets,
-                  h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused};
+                  h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused, h->d_tape, h->d_aws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -579,6 +701,17 @@ static int step_impl(msh_handle* h, const msh_state* st, const float* targets, f
   if (h->max_dof > 0 && !targets) return fail(MSH_ERR_INVALID_ARG, "joint_targets is NULL but max_dof > 0");
   if (!(dt > 0.f)) dt = h->cfg.dt;
   if (substeps < 1) substeps = h->cfg.substeps;
+  if (h->tape_max > 0) {
+    // recording for the adjoint: direct launches, one tape slot per step
+    if (h->tape_count >= h->tape_max) return fail(MSH_ERR_INVALID_ARG, "tape full: call msh_backward or msh_tape_reset");
+    if (substeps != h->cfg.substeps) return fail(MSH_ERR_INVALID_ARG, "recorded steps must use the configured substeps");
+    Params p = make_params(h, st, targets, dt, substeps);
+    p.tape = h->d_tape + (long long)h->tape_count * h->E * h->tape_slab;
+    int rc = enqueue_step(h, p, s);
+    if (rc) return rc;
+    h->tape_count++;
+    return MSH_OK;
+  }
   if (!h->use_graph) return enqueue_step(h, make_params(h, st, targets, dt, substeps), s);
   // graph path: targets go through the library buffer so one graph serves every call
   if (h->max_dof > 0)
@@ -657,6 +790,67 @@ int msh_detect(msh_handle* h, const msh_state* st, float* aabb_body, float* aabb
   k_export<<<h->E, 128, 0, s>>>(p, aabb_body, aabb_static, pair_count, pairs, contact_count, contact_ids,
                                 contact_geom, manifold_count, colours, ncolours, h->J);
   CK(cudaGetLastError());
+  return MSH_OK;
+}
+
+int msh_set_tape(msh_handle* h, int32_t max_steps) {
+  if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
+  if (max_steps < 0) return fail(MSH_ERR_INVALID_ARG, "max_steps must be >= 0");
+  if (max_steps > 0 && h->cfg.mode != MSH_MODE_COLOURED)
+    return fail(MSH_ERR_UNSUPPORTED, "the adjoint supports the coloured solver only");
+  if (max_steps > 0 && h->cfg.restitution > 0.f)
+    return fail(MSH_ERR_UNSUPPORTED, "the adjoint supports restitution 0 only");
+  cudaDeviceSynchronize();
+  drop_graph(h);
+  if (h->d_tape) { cudaFree(h->d_tape); h->bytes -= (int64_t)h->tape_max * h->E * h->tape_slab * 4; h->d_tape = nullptr; }
+  h->tape_max = 0;
+  h->tape_count = 0;
+  if (max_steps == 0) return MSH_OK;
+  const TapeLayout tl = tape_layout(h->L.Dm, h->L.Jm, h->L.C, h->cfg.substeps, h->cfg.iterations, h->max_dof);
+  h->tape_slab = tl.slab;
+  h->tape_Rm = ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C;
+  int rc = dalloc(h, &h->d_tape, (size_t)max_steps * h->E * tl.slab);
+  if (rc) return rc;
+  if (!h->d_aws) {
+    h->A = make_adj_layout(h->L, h->max_dof);
+    if ((rc = dalloc(h, &h->d_aws, (size_t)h->E * h->A.bytes))) return rc;
+  }
+  if ((rc = ensure_plain_ws(h))) return rc;
+  h->tape_max = max_steps;
+  return MSH_OK;
+}
+
+int msh_tape_reset(msh_handle* h) {
+  if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
+  h->tape_count = 0;
+  return MSH_OK;
+}
+
+int32_t msh_tape_count(const msh_handle* h) { return h ? h->tape_count : 0; }
+
+int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, float* adj_targets, float* adj_mass,
+                 void* stream) {
+  if (!h || !adj_out || !adj_in || !adj_out->pos || !adj_out->quat || !adj_out->linvel || !adj_out->angvel ||
+      !adj_in->pos || !adj_in->quat || !adj_in->linvel || !adj_in->angvel)
+    return fail(MSH_ERR_INVALID_ARG, "handle or adjoint state pointer is NULL");
+  if (h->tape_count < 1) return fail(MSH_ERR_INVALID_ARG, "no recorded step to reverse (msh_set_tape, then msh_step)");
+  Params p = make_params(h, nullptr, nullptr, h->cfg.dt, h->cfg.substeps);
+  p.ws = h->d_ws_plain;
+  p.ws_stride = h->L.bytes;
+  p.tape = h->d_tape;
+  AdjParams q;
+  std::memset(&q, 0, sizeof(q));
+  q.A = h->A;
+  q.aws = h->d_aws;
+  q.aws_stride = h->A.bytes;
+  q.slot = h->tape_count - 1;
+  q.ax = adj_out->pos; q.aq = adj_out->quat; q.av = adj_out->linvel; q.aw = adj_out->angvel;
+  q.ox = adj_in->pos; q.oq = adj_in->quat; q.ov = adj_in->linvel; q.ow = adj_in->angvel;
+  q.otg = h->max_dof > 0 ? adj_targets : nullptr;
+  q.omass = adj_mass;
+  k_backward<<<h->E, 64, 0, (cudaStream_t)stream>>>(p, q);
+  CK(cudaGetLastError());
+  h->tape_count--;
   return MSH_OK;
 }
 

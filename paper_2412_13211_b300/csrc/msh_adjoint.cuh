@@ -1,0 +1,634 @@
+// Adjoint of one recorded step (reverse mode), per env.
+//
+// Given the adjoint of the state after a recorded step, computes the adjoint
+// of the state before it, of that step's joint targets and (accumulated) of
+// the body masses. The step is differentiated as the forward computes it,
+// with its discrete decisions frozen: the contact set and features found by
+// the narrowphase, the colouring, and every clamp of the projected
+// Gauss-Seidel sweeps.
+//   * integration: hand-written reverse of x += h v and of the normalised
+//     quaternion update;
+//   * coloured PGS: the sweeps run backwards (iterations, then colours in
+//     reverse order, rows of a constraint in reverse order); velocities before
+//     each row update are rebuilt from the velocities after it and the
+//     recorded lambdas (v_before = v_after - M^-1 J^T (lambda_after -
+//     lambda_before)); clamp states come from the recorded lambdas;
+//   * row set-up (lever arms, Jacobians, biases, drives) and the narrowphase:
+//     local Jacobians by single-tangent dual numbers, one input direction at a
+//     time, contracted with the row/contact adjoints;
+//   * effective masses and world inverse inertias: hand-written reverse.
+// Per-body sums are gathered in constraint order, so results are
+// deterministic (checkpointed and plain backward passes agree bitwise).
+#pragma once
+#include "msh_stages.cuh"
+
+namespace msh {
+
+#define CLAMP_FRIC (-3.f)
+
+// Per-env adjoint workspace (HBM), byte offsets.
+struct AdjLayout {
+  int Rm, Km;
+  int bx, bq, bv, bw, bI0, bI1, bm;   // per body: x, q, v, w adjoints; Iw adjoint (6) + 1/m adjoint; mass accum
+  int rows, radj, rkind;              // per row: 5 float4 params, 5 float4 adjoints, kind
+  int gat;                            // per constraint: 8 float4 (xa, qa, xb, qb, Iwa0, Iwa1|ima, Iwb0, Iwb1|imb)
+  int cg;                             // per contact point: 3 float4 (n, ra, rb adjoints)
+  int inc_off, inc, tg, bytes;
+};
+
+struct AdjParams {
+  AdjLayout A;
+  char* aws;             // per-env adjoint workspace slabs
+  long long aws_stride;
+  int slot;              // tape slot being reversed
+  const float* ax; const float* aq; const float* av; const float* aw;   // adjoint of the state after the step
+  float* ox; float* oq; float* ov; float* ow;                           // adjoint of the state before the step
+  float* otg;            // [E, max_dof] adjoint of this step's targets
+  float* omass;          // [B] accumulated mass adjoint
+};
+
+struct AWs {
+  float4 *bx, *bq, *bv, *bw, *bI0, *bI1, *bm;
+  float4 *rows, *radj;
+  int* rkind;
+  float4* gat;
+  float4* cg;
+  int *inc_off, *inc;
+  float* tg;
+};
+
+__device__ __forceinline__ AWs make_aws(char* b, const AdjLayout& A) {
+  AWs a;
+  a.bx = (float4*)(b + A.bx); a.bq = (float4*)(b + A.bq); a.bv = (float4*)(b + A.bv); a.bw = (float4*)(b + A.bw);
+  a.bI0 = (float4*)(b + A.bI0); a.bI1 = (float4*)(b + A.bI1); a.bm = (float4*)(b + A.bm);
+  a.rows = (float4*)(b + A.rows); a.radj = (float4*)(b + A.radj); a.rkind = (int*)(b + A.rkind);
+  a.gat = (float4*)(b + A.gat); a.cg = (float4*)(b + A.cg);
+  a.inc_off = (int*)(b + A.inc_off); a.inc = (int*)(b + A.inc); a.tg = (float*)(b + A.tg);
+  return a;
+}
+
+__device__ __forceinline__ void add4(float4& a, const V3<float>& v) { a.x += v.x; a.y += v.y; a.z += v.z; }
+__device__ __forceinline__ V3<float> sym_outer_diag(const V3<float>& g, const V3<float>& a) { return v3<float>(g.x * a.x, g.y * a.y, g.z * a.z); }
+
+// Row index of joint k row r, or of contact point c row i.
+__device__ __forceinline__ int jrow(int k, int r) { return k * ROWS_PER_JOINT + r; }
+__device__ __forceinline__ int crow(const Layout& L, int c, int i) { return ROWS_PER_JOINT * L.Jm + 3 * c + i; }
+
+// ---------------------------------------------------------------------------
+// replay helpers
+// ---------------------------------------------------------------------------
+// Loads the recorded step-start state into the workspace (as stage_load does
+// from the state arrays).
+__device__ void load_from_tape(const Params& p, const EnvInfo& e, const Ws& w, const float* tape) {
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    const float* t = tape + 13 * i;
+    float4 inv = p.binv[e.b0 + i];
+    w.bx[i] = make_float4(t[0], t[1], t[2], inv.x);
+    w.bq[i] = make_float4(t[3], t[4], t[5], t[6]);
+    w.bv[i] = make_float4(t[7], t[8], t[9], 0.f);
+    w.bw[i] = make_float4(t[10], t[11], t[12], 0.f);
+    w.bIw1[i] = make_float4(0.f, 0.f, 1.f, 0.f);
+  }
+  for (int k = threadIdx.x; k < e.S; k += blockDim.x) {
+    const float* sp = p.static_pose + 7 * (e.s0 + k);
+    const float* sh = p.static_half + 3 * (e.s0 + k);
+    Q4<nf> q; q.w = nf(sp[3]); q.x = nf(sp[4]); q.y = nf(sp[5]); q.z = nf(sp[6]);
+    M3<nf> M = qmat(q);
+    w.sc[k] = make_float4(sp[0], sp[1], sp[2], 0.f);
+    for (int r = 0; r < 3; ++r) w.sM[3 * k + r] = make_float4(M.m[r][0].v, M.m[r][1].v, M.m[r][2].v, sh[r]);
+  }
+  if (threadIdx.x < MC_N) w.misc[threadIdx.x] = 0;
+}
+
+// World inverse inertia from an orientation and principal inverse inertia.
+template <class T> __device__ __forceinline__ void world_inv_inertia(const Q4<T>& q, const T* d, T* W6) {
+  M3<T> R = qmat(q);
+  T W[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      W[a][b] = R.m[a][0] * d[0] * R.m[b][0] + R.m[a][1] * d[1] * R.m[b][1] + R.m[a][2] * d[2] * R.m[b][2];
+  W6[0] = W[0][0]; W6[1] = W[0][1]; W6[2] = W[0][2]; W6[3] = W[1][1]; W6[4] = W[1][2]; W6[5] = W[2][2];
+}
+
+// Constraint -> body incidence lists in constraint order (for deterministic gathers).
+__device__ void build_incidence(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
+  if (threadIdx.x == 0) {
+    const int K = e.J + w.misc[MC_MANIFOLDS];
+    for (int i = 0; i <= e.D; ++i) a.inc_off[i] = 0;
+    for (int k = 0; k < K; ++k) {
+      int x, y;
+      con_bodies(p, e, w, k, e.J, x, y);
+      if (x >= 0) a.inc_off[x + 1]++;
+      if (y >= 0) a.inc_off[y + 1]++;
+    }
+    for (int i = 0; i < e.D; ++i) a.inc_off[i + 1] += a.inc_off[i];
+    for (int i = 0; i < e.D; ++i) w.masks[i] = (unsigned long long)a.inc_off[i];
+    for (int k = 0; k < K; ++k) {
+      int x, y;
+      con_bodies(p, e, w, k, e.J, x, y);
+      if (x >= 0) a.inc[w.masks[x]++] = 2 * k;
+      if (y >= 0) a.inc[w.masks[y]++] = 2 * k + 1;
+    }
+  }
+  __syncthreads();
+}
+
+// Generic rows of every constraint at the workspace poses (for the reverse
+// sweeps): la|m, aa|bias, ab|gamma, Ia|0, Ib|clamp, plus a kind code.
+__device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
+  const int nc = w.misc[MC_CONTACTS];
+  for (int t = threadIdx.x; t < e.J + nc; t += blockDim.x) {
+    if (t < e.J) {
+      const JointDesc& j = p.joints[e.j0 + t];
+      const int A = j.parent, B = j.child;
+      RowCtx ctx = row_ctx(w, A, B);
+      float tgl[3] = {0.f, 0.f, 0.f};
+      if (j.k > 0.f || j.d > 0.f)
+        for (int c = 0; c < joint_ndof(j.type); ++c) tgl[c] = tg[j.dof + c];
+      V3<float> xa = A >= 0 ? f3(w.bx[A]) : v3<float>(0.f, 0.f, 0.f);
+      Q4<float> qa = A >= 0 ? ldq4(w.bq[A]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
+      GRow<float> g[ROWS_PER_JOINT];
+      int n = joint_geom<float>(j, A >= 0, xa, qa, f3(w.bx[B]), ldq4(w.bq[B]), tgl, p.h, p.jbeta, g);
+      for (int r = 0; r < n; ++r) {
+        JRow x = blank_row();
+        x.la = g[r].la; x.lb = -g[r].la; x.aa = g[r].aa; x.ab = g[r].ab;
+        x.bias = g[r].bias; x.gamma = g[r].gamma;
+        const bool soft = g[r].clamp >= 0.f;
+        finish_row(x, ctx, soft);
+        float4* R = a.rows + ROW_F4 * jrow(t, r);
+        R[0] = f4(x.la, x.m); R[1] = f4(x.aa, x.bias); R[2] = f4(x.ab, x.gamma);
+        R[3] = f4(x.Ia, 0.f); R[4] = f4(x.Ib, g[r].clamp);
+        a.rkind[jrow(t, r)] = 0;
+        float4* G = a.radj + ROW_F4 * jrow(t, r);
+        for (int q = 0; q < ROW_F4; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+      const int ci = t - e.J;
+      int ids = w.cid[ci];
+      int ia = ids & 0xffff, bc = ids >> 16;
+      int ib = bc < e.D ? bc : -1;
+      RowCtx ctx = row_ctx(w, ia, ib);
+      V3<float> n = f3(w.cn[ci]);
+      V3<float> ra, rb;
+      float bias;
+      V3<float> xb = ib >= 0 ? f3(w.bx[ib]) : v3<float>(0.f, 0.f, 0.f);
+      Q4<float> qb = ib >= 0 ? ldq4(w.bq[ib]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
+      contact_geom<float>(f3(w.bx[ia]), ldq4(w.bq[ia]), xb, qb, ib >= 0, n, f3(w.cra[ci]), f3(w.crb[ci]), p.h,
+                          p.beta, p.slop, ra, rb, bias);
+      V3<float> t1, t2;
+      onb(n, t1, t2);
+      V3<float> dirs[3] = {n, t1, t2};
+      for (int r = 0; r < 3; ++r) {
+        JRow x = blank_row();
+        x.la = -dirs[r]; x.lb = dirs[r]; x.aa = -cross(ra, dirs[r]); x.ab = cross(rb, dirs[r]);
+        x.bias = r == 0 ? bias : 0.f;
+        finish_row(x, ctx, false);
+        float4* R = a.rows + ROW_F4 * crow(p.L, ci, r);
+        R[0] = f4(x.la, x.m); R[1] = f4(x.aa, x.bias); R[2] = f4(x.ab, 0.f);
+        R[3] = f4(x.Ia, 0.f); R[4] = f4(x.Ib, r == 0 ? CLAMP_UNI : CLAMP_FRIC);
+        a.rkind[crow(p.L, ci, r)] = r;
+        float4* G = a.radj + ROW_F4 * crow(p.L, ci, r);
+        for (int q = 0; q < ROW_F4; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reverse of the projected Gauss-Seidel sweeps
+// ---------------------------------------------------------------------------
+struct BodyAdj { V3<float> va, wa, vb, wb; };
+
+// Reverse of one row update. `r` is the row index; la..Ib its parameters;
+// lam_after / lam_before its recorded lambdas around this update; lam_n_after
+// the normal row's lambda in this sweep (friction rows).
+__device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, float ima, float imb, BodyVel& v,
+                                            BodyAdj& g, float lam_after, float lam_before, float mu, int nrow,
+                                            float lam_n_after) {
+  float4* R = a.rows + ROW_F4 * r;
+  float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4];
+  V3<float> la = f3(r0), aa = f3(r1), ab = f3(r2), Ia = f3(r3), Ib = f3(r4);
+  const float m = r0.w, bias = r1.w, gamma = r2.w, clamp = r4.w;
+  const float D = lam_after - lam_before;
+  // velocities before the update
+  if (A >= 0) { v.va = v.va - la * (ima * D); v.wa = v.wa - Ia * D; }
+  if (B >= 0) { v.vb = v.vb + la * (imb * D); v.wb = v.wb - Ib * D; }
+  float4* G = a.radj + ROW_F4 * r;
+  float4 g0 = G[0], g1 = G[1], g2 = G[2], g3 = G[3], g4 = G[4];
+  V3<float> gla = f3(g0), gaa = f3(g1), gab = f3(g2), gIa = f3(g3), gIb = f3(g4);
+  float gm = g0.w, gbias = g1.w, glam = g2.w;
+  // adjoint of D through the velocity update
+  float gD = 0.f;
+  if (A >= 0) {
+    gD += ima * dot(la, g.va) + dot(Ia, g.wa);
+    gla = gla + g.va * (ima * D);
+    gIa = gIa + g.wa * D;
+    g3.w += dot(la, g.va) * D;        // adjoint of 1/m_a (kept in the row, moved to the body later)
+  }
+  if (B >= 0) {
+    gD += -imb * dot(la, g.vb) + dot(Ib, g.wb);
+    gla = gla - g.vb * (imb * D);
+    gIb = gIb + g.wb * D;
+    g4.w += -dot(la, g.vb) * D;       // adjoint of 1/m_b
+  }
+  const float a_after = glam + gD;
+  float glam_before = -gD;
+  // pre-clamp value
+  float jv = 0.f;
+  if (B >= 0) jv = dotf(ab, v.wb) - dotf(la, v.vb);
+  if (A >= 0) jv = jv + dotf(la, v.va) + dotf(aa, v.wa);
+  const float u = jv + bias + gamma * lam_before;
+  bool clamped;
+  float fric_sign = 0.f;
+  if (clamp >= 0.f) clamped = lam_after == clamp || lam_after == -clamp;
+  else if (clamp == CLAMP_UNI) clamped = lam_after == 0.f;
+  else if (clamp == CLAMP_FRIC) {
+    float lim = mu * lam_n_after;
+    clamped = lam_after == lim || lam_after == -lim;
+    fric_sign = lam_after == lim ? 1.f : -1.f;
+  } else clamped = false;
+  float gpre = clamped ? 0.f : a_after;
+  if (clamped && clamp == CLAMP_FRIC) {
+    float4* Gn = a.radj + ROW_F4 * nrow;
+    Gn[2].w += fric_sign * mu * a_after;
+  }
+  glam_before += gpre;
+  const float gu = -m * gpre;
+  gm += -u * gpre;
+  if (A >= 0) { g.va = g.va + la * gu; g.wa = g.wa + aa * gu; gaa = gaa + v.wa * gu; }
+  if (B >= 0) { g.vb = g.vb - la * gu; g.wb = g.wb + ab * gu; gab = gab + v.wb * gu; }
+  gla = gla + (v.va - v.vb) * gu;
+  gbias += gu;
+  glam_before += gamma * gu;
+  G[0] = f4(gla, gm); G[1] = f4(gaa, gbias); G[2] = f4(gab, glam_before); G[3] = f4(gIa, g3.w); G[4] = f4(gIb, g4.w);
+}
+
+__device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* lam_it,
+                              const float* lam_prev) {
+  const int J = e.J;
+  const int ncol = w.misc[MC_COLOURS];
+  for (int c = ncol - 1; c >= 0; --c) {
+    const int c0 = w.coff[c], c1 = w.coff[c + 1];
+    for (int idx = c0 + threadIdx.x; idx < c1; idx += blockDim.x) {
+      const int k = w.corder[idx];
+      int A, B;
+      con_bodies(p, e, w, k, J, A, B);
+      BodyVel v = load_vel(w, A, B);
+      BodyAdj g;
+      V3<float> z = v3<float>(0.f, 0.f, 0.f);
+      g.va = A >= 0 ? f3(a.bv[A]) : z; g.wa = A >= 0 ? f3(a.bw[A]) : z;
+      g.vb = B >= 0 ? f3(a.bv[B]) : z; g.wb = B >= 0 ? f3(a.bw[B]) : z;
+      const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
+      if (k < J) {
+        const JointDesc& j = p.joints[e.j0 + k];
+        const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
+        for (int r = nr - 1; r >= 0; --r) {
+          const int ri = jrow(k, r);
+          reverse_row(a, ri, A, B, ima, imb, v, g, lam_it[ri], lam_prev ? lam_prev[ri] : 0.f, 0.f, -1, 0.f);
+        }
+      } else {
+        int4 mf = w.man[k - J];
+        for (int ci = mf.z + mf.w - 1; ci >= mf.z; --ci) {
+          const int rn = crow(p.L, ci, 0);
+          for (int i = 2; i >= 0; --i) {
+            const int ri = rn + i;
+            reverse_row(a, ri, A, B, ima, imb, v, g, lam_it[ri], lam_prev ? lam_prev[ri] : 0.f, p.mu, rn,
+                        lam_it[rn]);
+          }
+        }
+      }
+      if (A >= 0) { w.bv[A] = f4(v.va, 0.f); w.bw[A] = f4(v.wa, 0.f); a.bv[A] = f4(g.va, 0.f); a.bw[A] = f4(g.wa, 0.f); }
+      if (B >= 0) { w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f); }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reverse of the row set-up
+// ---------------------------------------------------------------------------
+// Effective-mass and inertia terms of one row (K = ima la.la + aa.Ia + imb
+// la.la + ab.Ib, Ia = Iw_a aa, Ib = Iw_b ab, m = 1/(K + gamma)): moves the
+// adjoints of m, Ia, Ib and the row's 1/m adjoints onto la, aa, ab, the world
+// inverse inertias (gIwa/gIwb, unique entries xx xy xz yy yz zz) and 1/m.
+__device__ __forceinline__ void reverse_mass_part(const AWs& a, int r, int A, int B, float ima, float imb,
+                                                  const Sym3& Iwa, const Sym3& Iwb, float* gIwa, float* gIwb,
+                                                  float& gima, float& gimb) {
+  float4* R = a.rows + ROW_F4 * r;
+  float4* G = a.radj + ROW_F4 * r;
+  V3<float> la = f3(R[0]), aa = f3(R[1]), ab = f3(R[2]), Ia = f3(R[3]), Ib = f3(R[4]);
+  const float m = R[0].w;
+  V3<float> gla = f3(G[0]), gaa = f3(G[1]), gab = f3(G[2]), gIa = f3(G[3]), gIb = f3(G[4]);
+  const float gm = G[0].w;
+  gima += G[3].w;
+  gimb += G[4].w;
+  const float gK = m > 0.f ? -m * m * gm : 0.f;
+  const float ll = dot(la, la);
+  if (A >= 0) {
+    gla = gla + la * (2.f * gK * ima);
+    gima += gK * ll;
+    gaa = gaa + Ia * gK;
+    gIa = gIa + aa * gK;
+    gaa = gaa + smul(Iwa, gIa);
+    gIwa[0] += gIa.x * aa.x; gIwa[1] += gIa.x * aa.y + gIa.y * aa.x; gIwa[2] += gIa.x * aa.z + gIa.z * aa.x;
+    gIwa[3] += gIa.y * aa.y; gIwa[4] += gIa.y * aa.z + gIa.z * aa.y; gIwa[5] += gIa.z * aa.z;
+  }
+  if (B >= 0) {
+    gla = gla + la * (2.f * gK * imb);
+    gimb += gK * ll;
+    gab = gab + Ib * gK;
+    gIb = gIb + ab * gK;
+    gab = gab + smul(Iwb, gIb);
+    gIwb[0] += gIb.x * ab.x; gIwb[1] += gIb.x * ab.y + gIb.y * ab.x; gIwb[2] += gIb.x * ab.z + gIb.z * ab.x;
+    gIwb[3] += gIb.y * ab.y; gIwb[4] += gIb.y * ab.z + gIb.z * ab.y; gIwb[5] += gIb.z * ab.z;
+  }
+  G[0] = f4(gla, 0.f); G[1] = f4(gaa, G[1].w); G[2] = f4(gab, G[2].w);
+}
+
+__device__ __forceinline__ d1 tan_of(int idx, int k, float v) { return d1(v, idx == k ? 1.f : 0.f); }
+
+// Adjoints of a joint's pose inputs and targets from its row adjoints, by
+// dual passes over (x_a, q_a)[if A], x_b, q_b, targets.
+__device__ void joint_geom_adjoint(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int k,
+                                   const float* tg, float* out /* xa3 qa4 xb3 qb4 tg3 */) {
+  const JointDesc& j = p.joints[e.j0 + k];
+  const int A = j.parent, B = j.child;
+  const bool drive = j.k > 0.f || j.d > 0.f;
+  const int nd = drive ? joint_ndof(j.type) : 0;
+  const int nr = joint_row_count(j.type, drive);
+  float4 xa4 = A >= 0 ? w.bx[A] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 qa4 = A >= 0 ? w.bq[A] : make_float4(1.f, 0.f, 0.f, 0.f);
+  float4 xb4 = w.bx[B], qb4 = w.bq[B];
+  for (int q = 0; q < 17; ++q) out[q] = 0.f;
+  for (int idx = 0; idx < 17; ++idx) {
+    if (idx < 7 && A < 0) continue;
+    if (idx >= 14 && idx - 14 >= nd) continue;
+    V3<d1> xa = v3<d1>(tan_of(idx, 0, xa4.x), tan_of(idx, 1, xa4.y), tan_of(idx, 2, xa4.z));
+    Q4<d1> qa; qa.w = tan_of(idx, 3, qa4.x); qa.x = tan_of(idx, 4, qa4.y); qa.y = tan_of(idx, 5, qa4.z); qa.z = tan_of(idx, 6, qa4.w);
+    V3<d1> xb = v3<d1>(tan_of(idx, 7, xb4.x), tan_of(idx, 8, xb4.y), tan_of(idx, 9, xb4.z));
+    Q4<d1> qb; qb.w = tan_of(idx, 10, qb4.x); qb.x = tan_of(idx, 11, qb4.y); qb.y = tan_of(idx, 12, qb4.z); qb.z = tan_of(idx, 13, qb4.w);
+    d1 t[3];
+    for (int c = 0; c < 3; ++c) t[c] = tan_of(idx, 14 + c, c < nd ? tg[j.dof + c] : 0.f);
+    GRow<d1> g[ROWS_PER_JOINT];
+    int n = joint_geom<d1>(j, A >= 0, xa, qa, xb, qb, t, p.h, p.jbeta, g);
+    float acc = 0.f;
+    for (int r = 0; r < n && r < nr; ++r) {
+      const float4* G = a.radj + ROW_F4 * jrow(k, r);
+      acc += G[0].x * g[r].la.x.d + G[0].y * g[r].la.y.d + G[0].z * g[r].la.z.d;
+      acc += G[1].x * g[r].aa.x.d + G[1].y * g[r].aa.y.d + G[1].z * g[r].aa.z.d;
+      acc += G[2].x * g[r].ab.x.d + G[2].y * g[r].ab.y.d + G[2].z * g[r].ab.z.d;
+      acc += G[1].w * g[r].bias.d;
+    }
+    out[idx] = acc;
+  }
+}
+
+// Adjoints of one contact point's inputs (x_a, q_a, x_b, q_b, n, ra_l, rb_l)
+// from its three rows' adjoints, by dual passes.
+__device__ void contact_geom_adjoint(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int ci, int ia,
+                                     int ib, float* out /* xa3 qa4 xb3 qb4 n3 ra3 rb3 */) {
+  float4 xa4 = w.bx[ia], qa4 = w.bq[ia];
+  float4 xb4 = ib >= 0 ? w.bx[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 qb4 = ib >= 0 ? w.bq[ib] : make_float4(1.f, 0.f, 0.f, 0.f);
+  float4 n4 = w.cn[ci], ra4 = w.cra[ci], rb4 = w.crb[ci];
+  for (int q = 0; q < 23; ++q) out[q] = 0.f;
+  const float4* G0 = a.radj + ROW_F4 * crow(p.L, ci, 0);
+  for (int idx = 0; idx < 23; ++idx) {
+    if (ib < 0 && idx >= 7 && idx < 14) continue;
+    V3<d1> xa = v3<d1>(tan_of(idx, 0, xa4.x), tan_of(idx, 1, xa4.y), tan_of(idx, 2, xa4.z));
+    Q4<d1> qa; qa.w = tan_of(idx, 3, qa4.x); qa.x = tan_of(idx, 4, qa4.y); qa.y = tan_of(idx, 5, qa4.z); qa.z = tan_of(idx, 6, qa4.w);
+    V3<d1> xb = v3<d1>(tan_of(idx, 7, xb4.x), tan_of(idx, 8, xb4.y), tan_of(idx, 9, xb4.z));
+    Q4<d1> qb; qb.w = tan_of(idx, 10, qb4.x); qb.x = tan_of(idx, 11, qb4.y); qb.y = tan_of(idx, 12, qb4.z); qb.z = tan_of(idx, 13, qb4.w);
+    V3<d1> n = v3<d1>(tan_of(idx, 14, n4.x), tan_of(idx, 15, n4.y), tan_of(idx, 16, n4.z));
+    V3<d1> ral = v3<d1>(tan_of(idx, 17, ra4.x), tan_of(idx, 18, ra4.y), tan_of(idx, 19, ra4.z));
+    V3<d1> rbl = v3<d1>(tan_of(idx, 20, rb4.x), tan_of(idx, 21, rb4.y), tan_of(idx, 22, rb4.z));
+    V3<d1> ra, rb;
+    d1 bias;
+    contact_geom<d1>(xa, qa, xb, qb, ib >= 0, n, ral, rbl, p.h, p.beta, p.slop, ra, rb, bias);
+    V3<d1> t1, t2;
+    onb(n, t1, t2);
+    V3<d1> dirs[3] = {n, t1, t2};
+    float acc = 0.f;
+    for (int r = 0; r < 3; ++r) {
+      const float4* G = G0 + ROW_F4 * r;
+      V3<d1> la = -dirs[r], aa = -cross(ra, dirs[r]), ab = cross(rb, dirs[r]);
+      acc += G[0].x * la.x.d + G[0].y * la.y.d + G[0].z * la.z.d;
+      acc += G[1].x * aa.x.d + G[1].y * aa.y.d + G[1].z * aa.z.d;
+      if (ib >= 0) acc += G[2].x * ab.x.d + G[2].y * ab.y.d + G[2].z * ab.z.d;
+      if (r == 0) acc += G[1].w * bias.d;
+    }
+    out[idx] = acc;
+  }
+}
+
+// Per constraint: effective-mass reverse, then the geometry reverse; writes
+// pose/inertia/mass adjoints to the constraint's gather slot, contact geometry
+// adjoints to the contact points, target adjoints to the joint's DoFs.
+__device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
+  const int J = e.J, K = J + w.misc[MC_MANIFOLDS];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    int A, B;
+    con_bodies(p, e, w, k, J, A, B);
+    const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
+    Sym3 Iwa, Iwb;
+    if (A >= 0) Iwa = load_Iw(w, A);
+    if (B >= 0) Iwb = load_Iw(w, B);
+    float gIwa[6] = {0, 0, 0, 0, 0, 0}, gIwb[6] = {0, 0, 0, 0, 0, 0};
+    float gima = 0.f, gimb = 0.f;
+    float pose[14];
+    for (int q = 0; q < 14; ++q) pose[q] = 0.f;
+    if (k < J) {
+      const JointDesc& j = p.joints[e.j0 + k];
+      const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
+      for (int r = 0; r < nr; ++r) reverse_mass_part(a, jrow(k, r), A, B, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
+      float out[17];
+      joint_geom_adjoint(p, e, w, a, k, tg, out);
+      for (int q = 0; q < 14; ++q) pose[q] = out[q];
+      const int nd = (j.k > 0.f || j.d > 0.f) ? joint_ndof(j.type) : 0;
+      for (int c = 0; c < nd; ++c) a.tg[j.dof + c] += out[14 + c];
+    } else {
+      int4 mf = w.man[k - J];
+      for (int ci = mf.z; ci < mf.z + mf.w; ++ci) {
+        for (int r = 0; r < 3; ++r)
+          reverse_mass_part(a, crow(p.L, ci, r), A, B, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
+        float out[23];
+        contact_geom_adjoint(p, e, w, a, ci, A, B, out);
+        for (int q = 0; q < 14; ++q) pose[q] += out[q];
+        add4(a.cg[3 * ci + 0], v3<float>(out[14], out[15], out[16]));
+        add4(a.cg[3 * ci + 1], v3<float>(out[17], out[18], out[19]));
+        add4(a.cg[3 * ci + 2], v3<float>(out[20], out[21], out[22]));
+      }
+    }
+    float4* S = a.gat + 8 * k;
+    S[0] = make_float4(pose[0], pose[1], pose[2], 0.f);
+    S[1] = make_float4(pose[3], pose[4], pose[5], pose[6]);
+    S[2] = make_float4(pose[7], pose[8], pose[9], 0.f);
+    S[3] = make_float4(pose[10], pose[11], pose[12], pose[13]);
+    S[4] = make_float4(gIwa[0], gIwa[1], gIwa[2], gIwa[3]);
+    S[5] = make_float4(gIwa[4], gIwa[5], gima, 0.f);
+    S[6] = make_float4(gIwb[0], gIwb[1], gIwb[2], gIwb[3]);
+    S[7] = make_float4(gIwb[4], gIwb[5], gimb, 0.f);
+  }
+}
+
+// Per body: sums the constraint gather slots in constraint order into the
+// pose adjoints (and, when `inertia`, the world-inverse-inertia and 1/m
+// adjoints into bI0/bI1).
+__device__ void gather_bodies(const EnvInfo& e, const AWs& a, bool inertia) {
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    float4 gx = a.bx[i], gq = a.bq[i];
+    float4 I0 = make_float4(0.f, 0.f, 0.f, 0.f), I1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = a.inc_off[i]; q < a.inc_off[i + 1]; ++q) {
+      const int t = a.inc[q], k = t >> 1, side = t & 1;
+      const float4* S = a.gat + 8 * k;
+      float4 px = S[2 * side], pq = S[2 * side + 1];
+      gx.x += px.x; gx.y += px.y; gx.z += px.z;
+      gq.x += pq.x; gq.y += pq.y; gq.z += pq.z; gq.w += pq.w;
+      if (inertia) {
+        float4 s0 = S[4 + 2 * side], s1 = S[5 + 2 * side];
+        I0.x += s0.x; I0.y += s0.y; I0.z += s0.z; I0.w += s0.w;
+        I1.x += s1.x; I1.y += s1.y; I1.z += s1.z;
+      }
+    }
+    a.bx[i] = gx;
+    a.bq[i] = gq;
+    if (inertia) { a.bI0[i] = I0; a.bI1[i] = I1; }
+  }
+}
+
+// World inverse inertia adjoints -> orientation adjoint and principal inverse
+// inertia adjoint (dual passes over q and the 3 principal values); 1/m
+// adjoint into the mass accumulator.
+__device__ void reverse_inertia(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    float4 I0 = a.bI0[i], I1 = a.bI1[i];
+    const float gW[6] = {I0.x, I0.y, I0.z, I0.w, I1.x, I1.y};
+    float4 q4 = w.bq[i], inv = p.binv[e.b0 + i];
+    float res[7];
+    for (int idx = 0; idx < 7; ++idx) {
+      Q4<d1> q; q.w = tan_of(idx, 0, q4.x); q.x = tan_of(idx, 1, q4.y); q.y = tan_of(idx, 2, q4.z); q.z = tan_of(idx, 3, q4.w);
+      d1 dd[3] = {tan_of(idx, 4, inv.y), tan_of(idx, 5, inv.z), tan_of(idx, 6, inv.w)};
+      d1 W6[6];
+      world_inv_inertia<d1>(q, dd, W6);
+      float acc = 0.f;
+      for (int u = 0; u < 6; ++u) acc += gW[u] * W6[u].d;
+      res[idx] = acc;
+    }
+    float4 gq = a.bq[i];
+    gq.x += res[0]; gq.y += res[1]; gq.z += res[2]; gq.w += res[3];
+    a.bq[i] = gq;
+    float4 m = a.bm[i];
+    m.x += I1.z; m.y += res[4]; m.z += res[5]; m.w += res[6];
+    a.bm[i] = m;
+  }
+}
+
+// Reverse of x += h v and q <- normalise(q + h/2 (0,w) q) for one substep,
+// with x_s, q_s the substep-start pose and v_e, w_e the velocities it used.
+__device__ void reverse_integrate(const Params& p, const EnvInfo& e, const AWs& a, const float* sub_tape) {
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    const float* t = sub_tape + 19 * i;
+    const float qw = t[3], qx = t[4], qy = t[5], qz = t[6];
+    const float wx = t[16], wy = t[17], wz = t[18];
+    float4 gx = a.bx[i], gq = a.bq[i], gv = a.bv[i], gw = a.bw[i];
+    const float h = p.h, hh = h * 0.5f;
+    // x' = x + h v
+    gv.x += h * gx.x; gv.y += h * gx.y; gv.z += h * gx.z;
+    // p = q + hh (0,w) q ; q' = p / |p|
+    const float dqw = -(wx * qx + wy * qy + wz * qz);
+    const float dqx = qw * wx + (wy * qz - wz * qy);
+    const float dqy = qw * wy + (wz * qx - wx * qz);
+    const float dqz = qw * wz + (wx * qy - wy * qx);
+    const float pw = qw + hh * dqw, px = qx + hh * dqx, py = qy + hh * dqy, pz = qz + hh * dqz;
+    const float nrm = sqrtf(pw * pw + px * px + py * py + pz * pz);
+    const float ow = pw / nrm, ox = px / nrm, oy = py / nrm, oz = pz / nrm;
+    const float s = ow * gq.x + ox * gq.y + oy * gq.z + oz * gq.w;
+    const float gpw = (gq.x - ow * s) / nrm, gpx = (gq.y - ox * s) / nrm, gpy = (gq.z - oy * s) / nrm,
+                gpz = (gq.w - oz * s) / nrm;
+    float4 nq;
+    nq.x = gpw + hh * (gpx * wx + gpy * wy + gpz * wz);
+    nq.y = gpx + hh * (-gpw * wx + gpy * wz - gpz * wy);
+    nq.z = gpy + hh * (-gpw * wy - gpx * wz + gpz * wx);
+    nq.w = gpz + hh * (-gpw * wz + gpx * wy - gpy * wx);
+    gw.x += hh * (-gpw * qx + gpx * qw - gpy * qz + gpz * qy);
+    gw.y += hh * (-gpw * qy + gpx * qz + gpy * qw - gpz * qx);
+    gw.z += hh * (-gpw * qz - gpx * qy + gpy * qx + gpz * qw);
+    a.bq[i] = nq;
+    a.bv[i] = gv;
+    a.bw[i] = gw;
+  }
+}
+
+// Adjoints of the step-start poses from the contact-geometry adjoints: dual
+// passes of the narrowphase of each manifold's pair over the 14 pose inputs.
+__device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
+  const int J = e.J, M = w.misc[MC_MANIFOLDS];
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    int4 mf = w.man[m];
+    const int ia = mf.x, ib = mf.y;
+    const int pj = w.cid[mf.z] >> 16;
+    float res[14];
+    for (int q = 0; q < 14; ++q) res[q] = 0.f;
+    float4 xa4 = w.bx[ia], qa4 = w.bq[ia];
+    float4 xb4 = ib >= 0 ? w.bx[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 qb4 = ib >= 0 ? w.bq[ib] : make_float4(1.f, 0.f, 0.f, 0.f);
+    for (int idx = 0; idx < 14; ++idx) {
+      if (ib < 0 && idx >= 7) break;
+      Shape<d1> Si, Sj;
+      {
+        float4 d = p.bdims[e.b0 + ia];
+        Q4<d1> q; q.w = tan_of(idx, 3, qa4.x); q.x = tan_of(idx, 4, qa4.y); q.y = tan_of(idx, 5, qa4.z); q.z = tan_of(idx, 6, qa4.w);
+        Si.type = __float_as_int(d.w);
+        Si.c = v3<d1>(tan_of(idx, 0, xa4.x), tan_of(idx, 1, xa4.y), tan_of(idx, 2, xa4.z));
+        Si.M = qmat(q);
+        Si.d0 = d1(d.x); Si.d1 = d1(d.y); Si.d2 = d1(d.z);
+      }
+      if (ib >= 0) {
+        float4 d = p.bdims[e.b0 + ib];
+        Q4<d1> q; q.w = tan_of(idx, 10, qb4.x); q.x = tan_of(idx, 11, qb4.y); q.y = tan_of(idx, 12, qb4.z); q.z = tan_of(idx, 13, qb4.w);
+        Sj.type = __float_as_int(d.w);
+        Sj.c = v3<d1>(tan_of(idx, 7, xb4.x), tan_of(idx, 8, xb4.y), tan_of(idx, 9, xb4.z));
+        Sj.M = qmat(q);
+        Sj.d0 = d1(d.x); Sj.d1 = d1(d.y); Sj.d2 = d1(d.z);
+      } else if (pj < e.D + e.S) {
+        int k = pj - e.D;
+        float4 c = w.sc[k], r0 = w.sM[3 * k], r1 = w.sM[3 * k + 1], r2 = w.sM[3 * k + 2];
+        Sj.type = SH_BOX;
+        Sj.c = v3<d1>(d1(c.x), d1(c.y), d1(c.z));
+        Sj.M.m[0][0] = d1(r0.x); Sj.M.m[0][1] = d1(r0.y); Sj.M.m[0][2] = d1(r0.z);
+        Sj.M.m[1][0] = d1(r1.x); Sj.M.m[1][1] = d1(r1.y); Sj.M.m[1][2] = d1(r1.z);
+        Sj.M.m[2][0] = d1(r2.x); Sj.M.m[2][1] = d1(r2.y); Sj.M.m[2][2] = d1(r2.z);
+        Sj.d0 = d1(r0.w); Sj.d1 = d1(r1.w); Sj.d2 = d1(r2.w);
+      } else {
+        Sj.type = SH_PLANE;
+        Sj.c = v3<d1>(d1(0.f), d1(0.f), d1(0.f));
+        Sj.d0 = Sj.d1 = Sj.d2 = d1(0.f);
+      }
+      Pt<d1> pts[4];
+      int n = collide(Si, Sj, d1(p.off), pts);
+      float acc = 0.f;
+      for (int k = 0; k < n && k < mf.w; ++k) {
+        const int ci = mf.z + k;
+        V3<d1> ral = mulT(Si.M, pts[k].pa - Si.c);
+        V3<d1> rbl = ib >= 0 ? mulT(Sj.M, pts[k].pb - Sj.c) : pts[k].pb;
+        float4 gn = a.cg[3 * ci], gra = a.cg[3 * ci + 1], grb = a.cg[3 * ci + 2];
+        acc += gn.x * pts[k].n.x.d + gn.y * pts[k].n.y.d + gn.z * pts[k].n.z.d;
+        acc += gra.x * ral.x.d + gra.y * ral.y.d + gra.z * ral.z.d;
+        acc += grb.x * rbl.x.d + grb.y * rbl.y.d + grb.z * rbl.z.d;
+      }
+      res[idx] = acc;
+    }
+    float4* S = a.gat + 8 * (J + m);
+    S[0] = make_float4(res[0], res[1], res[2], 0.f);
+    S[1] = make_float4(res[3], res[4], res[5], res[6]);
+    S[2] = make_float4(res[7], res[8], res[9], 0.f);
+    S[3] = make_float4(res[10], res[11], res[12], res[13]);
+  }
+  // joints have no narrowphase inputs
+  for (int k = threadIdx.x; k < J; k += blockDim.x)
+    for (int q = 0; q < 4; ++q) a.gat[8 * k + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+}  // namespace msh

@@ -38,6 +38,36 @@ __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
 __device__ __forceinline__ float abs_(float a) { return fabsf(a); }
 __device__ __forceinline__ float fl(float a) { return a; }
 
+// Single-tangent forward-mode dual number (value v, derivative d). The
+// adjoint evaluates the row set-up and the narrowphase with it, one input
+// direction at a time, to get exact local Jacobians with the branch decisions
+// (clamps, contact features) of the primal values.
+struct d1 {
+  float v, d;
+  __device__ __forceinline__ d1() {}
+  __device__ __forceinline__ constexpr d1(float x) : v(x), d(0.f) {}
+  __device__ __forceinline__ constexpr d1(float x, float t) : v(x), d(t) {}
+};
+__device__ __forceinline__ d1 operator+(d1 a, d1 b) { return d1(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ d1 operator-(d1 a, d1 b) { return d1(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ d1 operator*(d1 a, d1 b) { return d1(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ d1 operator/(d1 a, d1 b) { float q = a.v / b.v; return d1(q, (a.d - q * b.d) / b.v); }
+__device__ __forceinline__ d1 operator-(d1 a) { return d1(-a.v, -a.d); }
+__device__ __forceinline__ bool operator<(d1 a, d1 b) { return a.v < b.v; }
+__device__ __forceinline__ bool operator>(d1 a, d1 b) { return a.v > b.v; }
+__device__ __forceinline__ bool operator<=(d1 a, d1 b) { return a.v <= b.v; }
+__device__ __forceinline__ bool operator>=(d1 a, d1 b) { return a.v >= b.v; }
+__device__ __forceinline__ bool operator==(d1 a, d1 b) { return a.v == b.v; }
+__device__ __forceinline__ bool operator!=(d1 a, d1 b) { return a.v != b.v; }
+__device__ __forceinline__ d1 sqrt_(d1 a) { float r = sqrtf(a.v); return d1(r, r > 0.f ? a.d / (2.f * r) : 0.f); }
+__device__ __forceinline__ d1 abs_(d1 a) { return a.v < 0.f ? -a : a; }
+__device__ __forceinline__ float fl(d1 a) { return a.v; }
+__device__ __forceinline__ d1 atan2_(d1 y, d1 x) {
+  float den = x.v * x.v + y.v * y.v;
+  return d1(atan2f(y.v, x.v), den > 0.f ? (x.v * y.d - y.v * x.d) / den : 0.f);
+}
+__device__ __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
+
 template <class T> __device__ __forceinline__ T clampv(T x, T lo, T hi) { return x < lo ? lo : (x > hi ? hi : x); }
 template <class T> __device__ __forceinline__ T maxv(T a, T b) { return a > b ? a : b; }
 template <class T> __device__ __forceinline__ T minv(T a, T b) { return a < b ? a : b; }
@@ -94,12 +124,28 @@ __device__ __forceinline__ V3<float> to_f(const V3<nf>& a) { return v3<float>(a.
 __device__ __forceinline__ V3<float> f3(float4 a) { return v3<float>(a.x, a.y, a.z); }
 __device__ __forceinline__ float4 f4(const V3<float>& a, float w) { return make_float4(a.x, a.y, a.z, w); }
 
+// Explicitly fused float helpers for the solver's hot loops. The library is
+// compiled with -fmad=false, so these are the only fused multiply-adds: one
+// correctly rounded fmaf does not depend on the surrounding code, which keeps
+// every execution form of the step bitwise identical.
+__device__ __forceinline__ float dotf(const V3<float>& a, const V3<float>& b) {
+  return fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)); }
+__device__ __forceinline__ V3<float> crossf(const V3<float>& a, const V3<float>& b) {
+  return v3<float>(fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)), fmaf(a.x, b.y, -(a.y * b.x))); }
+__device__ __forceinline__ V3<float> axpyf(const V3<float>& y, const V3<float>& x, float s) {
+  return v3<float>(fmaf(x.x, s, y.x), fmaf(x.y, s, y.y), fmaf(x.z, s, y.z)); }
+
 // symmetric 3x3 stored as (xx, xy, xz, yy) + (yz, zz)
 struct Sym3 { float xx, xy, xz, yy, yz, zz; };
 __device__ __forceinline__ V3<float> smul(const Sym3& S, const V3<float>& v) {
   return v3<float>(S.xx * v.x + S.xy * v.y + S.xz * v.z,
                    S.xy * v.x + S.yy * v.y + S.yz * v.z,
                    S.xz * v.x + S.yz * v.y + S.zz * v.z);
+}
+__device__ __forceinline__ V3<float> smulf(const Sym3& S, const V3<float>& v) {
+  return v3<float>(fmaf(S.xz, v.z, fmaf(S.xy, v.y, S.xx * v.x)),
+                   fmaf(S.yz, v.z, fmaf(S.yy, v.y, S.xy * v.x)),
+                   fmaf(S.zz, v.z, fmaf(S.yz, v.y, S.xz * v.x)));
 }
 
 }  // namespace msh

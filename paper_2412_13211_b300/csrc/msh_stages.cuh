@@ -66,7 +66,31 @@ struct Params {
   char* ws;              // HBM workspace base (plain form, or fused without room in SMEM)
   long long ws_stride;   // bytes between per-env (plain) or per-CTA (fused) slabs
   int* queue;
+  // tape (recorded for the adjoint when non-null): slab per env, see TapeLayout
+  float* tape;
+  long long tape_slab;   // floats per env slab of one recorded step
+  int tape_Rm;           // row slots per env: ROWS_PER_JOINT * Jm + 3 * C
+  // plain-form launch indices
+  int sub, it;
 };
+
+// Tape of one recorded step, per env (floats):
+//   state at the step start:       Dm x 13  (x, q, v, w)
+//   per substep s:                 Dm x 19  (x_s, q_s, v_s, w_s after gravity; v, w after the solve)
+//   lambda after every sweep:      S x N x Rm (joint k row r: k*8 + r; contact c row i: 8*Jm + 3c + i)
+//   joint targets of the step:     max_dof
+struct TapeLayout { long long t0, t1, t2, t3, slab; };
+__host__ __device__ __forceinline__ TapeLayout tape_layout(int Dm, int Jm, int C, int S, int N, int md) {
+  TapeLayout t;
+  const long long Rm = (long long)ROWS_PER_JOINT * Jm + 3LL * C;
+  t.t0 = 0;
+  t.t1 = t.t0 + 13LL * Dm;
+  t.t2 = t.t1 + 19LL * Dm * S;
+  t.t3 = t.t2 + (long long)S * N * Rm;
+  t.slab = (t.t3 + md + 3) & ~3LL;
+  return t;
+}
+__device__ __forceinline__ float* tape_env(const Params& p, int env) { return p.tape + (long long)env * p.tape_slab; }
 
 struct Ws {
   float4 *bx, *bq, *bv, *bw, *bIw0, *bIw1;
@@ -150,6 +174,18 @@ __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
     w.bv[i] = make_float4(p.lv[3 * g], p.lv[3 * g + 1], p.lv[3 * g + 2], 0.f);
     w.bw[i] = make_float4(p.av[3 * g], p.av[3 * g + 1], p.av[3 * g + 2], 0.f);
     w.bIw1[i] = make_float4(0.f, 0.f, 1.f, 0.f);   // .z: Jacobi split count (1 unless set by the colouring)
+    if (p.tape) {
+      float* t = tape_env(p, e.env) + 13 * i;
+      t[0] = p.pos[3 * g]; t[1] = p.pos[3 * g + 1]; t[2] = p.pos[3 * g + 2];
+      t[3] = p.quat[4 * g]; t[4] = p.quat[4 * g + 1]; t[5] = p.quat[4 * g + 2]; t[6] = p.quat[4 * g + 3];
+      t[7] = p.lv[3 * g]; t[8] = p.lv[3 * g + 1]; t[9] = p.lv[3 * g + 2];
+      t[10] = p.av[3 * g]; t[11] = p.av[3 * g + 1]; t[12] = p.av[3 * g + 2];
+    }
+  }
+  if (p.tape) {
+    TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+    for (int k = threadIdx.x; k < p.max_dof; k += blockDim.x)
+      tape_env(p, e.env)[tl.t3 + k] = p.targets ? p.targets[(size_t)e.env * p.max_dof + k] : 0.f;
   }
   for (int k = threadIdx.x; k < e.S; k += blockDim.x) {
     const float* sp = p.static_pose + 7 * (e.s0 + k);
@@ -378,11 +414,18 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
 // ---------------------------------------------------------------------------
 // a1: gravity; world inverse inertia
 // ---------------------------------------------------------------------------
-__device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws& w) {
+__device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
   for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
     float4 v = w.bv[i];
     v.x = v.x + p.gx * p.h; v.y = v.y + p.gy * p.h; v.z = v.z + p.gz * p.h;
     w.bv[i] = v;
+    if (p.tape) {
+      TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+      float* t = tape_env(p, e.env) + tl.t1 + 19LL * (sub * p.L.Dm + i);
+      float4 x = w.bx[i], q = w.bq[i], wv = w.bw[i];
+      t[0] = x.x; t[1] = x.y; t[2] = x.z; t[3] = q.x; t[4] = q.y; t[5] = q.z; t[6] = q.w;
+      t[7] = v.x; t[8] = v.y; t[9] = v.z; t[10] = wv.x; t[11] = wv.y; t[12] = wv.z;
+    }
     float4 q4 = w.bq[i], I = __ldg(&p.binv[e.b0 + i]);
     const float split = w.bIw1[i].z;
     Q4<float> q; q.w = q4.x; q.x = q4.y; q.y = q4.z; q.z = q4.w;
@@ -442,25 +485,6 @@ __device__ __forceinline__ void finish_row(JRow& r, const RowCtx& c, bool soft) 
   else r.m = K > 0.f ? 1.f / K : 0.f;
 }
 
-__device__ __forceinline__ JRow lin_row(const V3<float>& u, const V3<float>& ra, const V3<float>& rb) {
-  JRow r = blank_row();
-  r.la = -u; r.aa = -cross(ra, u); r.lb = u; r.ab = cross(rb, u);
-  return r;
-}
-__device__ __forceinline__ JRow ang_row(const V3<float>& u) {
-  JRow r = blank_row();
-  r.aa = -u; r.ab = u;
-  return r;
-}
-__device__ __forceinline__ void soft_row(JRow& r, float h, float C, float k, float d, float fmax) {
-  float den = d + h * k;
-  r.gamma = 1.f / (h * den);
-  r.bias = (h * k / den) / h * C;
-  r.lo = -fmax * h;
-  r.hi = fmax * h;
-}
-
-__device__ __forceinline__ Q4<float> ldq(const float* q) { Q4<float> r; r.w = q[0]; r.x = q[1]; r.y = q[2]; r.z = q[3]; return r; }
 __device__ __forceinline__ Q4<float> ldq4(float4 q) { Q4<float> r; r.w = q.x; r.x = q.y; r.y = q.z; r.z = q.w; return r; }
 
 __device__ __forceinline__ RowCtx row_ctx(const Ws& w, int a, int b) {
@@ -475,105 +499,130 @@ __device__ __forceinline__ RowCtx row_ctx(const Ws& w, int a, int b) {
   return c;
 }
 
-__device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k) {
-  const JointDesc& j = p.joints[e.j0 + k];
-  const float h = p.h, beta = p.jbeta / h;
-  const float* tgt = p.targets ? p.targets + (size_t)e.env * p.max_dof : nullptr;
-  int A = j.parent, B = j.child;
-  RowCtx ctx = row_ctx(w, A, B);
-  V3<float> pa_l = v3<float>(j.pa[0], j.pa[1], j.pa[2]);
-  V3<float> pb_l = v3<float>(j.pb[0], j.pb[1], j.pb[2]);
-  V3<float> xa, ra, pa_w;
-  Q4<float> qFA;
-  if (A >= 0) {
-    xa = f3(w.bx[A]);
-    Q4<float> qa = ldq4(w.bq[A]);
+// Row geometry before the mass terms: la (lb = -la), aa, ab, bias, the soft
+// constraint's gamma and the clamp code. Templated on the scalar so that the
+// adjoint can differentiate it with dual numbers.
+template <class T> struct GRow { V3<T> la, aa, ab; T bias; float gamma; float clamp; };
+
+template <class T> __device__ __forceinline__ GRow<T> g_lin(const V3<T>& u, const V3<T>& ra, const V3<T>& rb) {
+  GRow<T> r;
+  r.la = -u; r.aa = -cross(ra, u); r.ab = cross(rb, u);
+  r.bias = T(0.f); r.gamma = 0.f; r.clamp = CLAMP_FREE;
+  return r;
+}
+template <class T> __device__ __forceinline__ GRow<T> g_ang(const V3<T>& u) {
+  GRow<T> r;
+  r.la = v3<T>(T(0.f), T(0.f), T(0.f)); r.aa = -u; r.ab = u;
+  r.bias = T(0.f); r.gamma = 0.f; r.clamp = CLAMP_FREE;
+  return r;
+}
+// Catto (2011) soft constraint: gamma = 1/(h(d + h k)), bias = (h k/(d + h k))/h * C.
+template <class T> __device__ __forceinline__ void g_soft(GRow<T>& r, float h, T C, float k, float d, float fmax) {
+  float den = d + h * k;
+  r.gamma = 1.f / (h * den);
+  r.bias = T((h * k / den) / h) * C;
+  r.clamp = fmax * h;
+}
+template <class T> __device__ __forceinline__ Q4<T> tq(const float* q) { Q4<T> r; r.w = T(q[0]); r.x = T(q[1]); r.y = T(q[2]); r.z = T(q[3]); return r; }
+template <class T> __device__ __forceinline__ V3<T> tv(const float* v) { return v3<T>(T(v[0]), T(v[1]), T(v[2])); }
+
+// Joint rows from the poses of the parent (when hasA) and the child and the
+// joint's targets tgt[0..ndof). Returns the row count.
+template <class T>
+__device__ int joint_geom(const JointDesc& j, bool hasA, const V3<T>& xa, const Q4<T>& qa, const V3<T>& xb,
+                          const Q4<T>& qb, const T* tgt, float h, float jbeta, GRow<T>* rows) {
+  const float beta = jbeta / h;
+  V3<T> pa_l = tv<T>(j.pa), pb_l = tv<T>(j.pb);
+  V3<T> ra, pa_w, xA;
+  Q4<T> qFA;
+  if (hasA) {
+    xA = xa;
     ra = mul(qmat(qa), pa_l);
     pa_w = xa + ra;
-    qFA = qmul(qa, ldq(j.qa));
+    qFA = qmul(qa, tq<T>(j.qa));
   } else {
-    xa = pa_l; ra = v3<float>(0.f, 0.f, 0.f); pa_w = pa_l; qFA = ldq(j.qa);
+    xA = pa_l; ra = v3<T>(T(0.f), T(0.f), T(0.f)); pa_w = pa_l; qFA = tq<T>(j.qa);
   }
-  Q4<float> qb = ldq4(w.bq[B]);
-  V3<float> rb = mul(qmat(qb), pb_l);
-  V3<float> pb_w = f3(w.bx[B]) + rb;
-  Q4<float> qFB = qmul(qb, ldq(j.qb));
-  M3<float> MF = qmat(qFA);
-  V3<float> ux = col(MF, 0), uy = col(MF, 1), uz = col(MF, 2);
-  V3<float> dp = pb_w - pa_w;
-  Q4<float> qr = qmul(qconj(qFA), qFB);
-  if (qr.w < 0.f) { qr.w = -qr.w; qr.x = -qr.x; qr.y = -qr.y; qr.z = -qr.z; }
-  V3<float> raB = A >= 0 ? pb_w - xa : v3<float>(0.f, 0.f, 0.f);
-  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * ROW_F4;
+  V3<T> rb = mul(qmat(qb), pb_l);
+  V3<T> pb_w = xb + rb;
+  Q4<T> qFB = qmul(qb, tq<T>(j.qb));
+  M3<T> MF = qmat(qFA);
+  V3<T> ux = col(MF, 0), uy = col(MF, 1), uz = col(MF, 2);
+  V3<T> dp = pb_w - pa_w;
+  Q4<T> qr = qmul(qconj(qFA), qFB);
+  if (qr.w < T(0.f)) { qr.w = -qr.w; qr.x = -qr.x; qr.y = -qr.y; qr.z = -qr.z; }
+  V3<T> raB = hasA ? pb_w - xA : v3<T>(T(0.f), T(0.f), T(0.f));
   int n = 0;
-  bool drive = j.k > 0.f || j.d > 0.f;
+  const bool drive = j.k > 0.f || j.d > 0.f;
+  const T tb = T(beta);
   if (j.type == JT_REVOLUTE) {
     for (int c = 0; c < 3; ++c) {
-      JRow r = lin_row(unit<float>(c), ra, rb);
-      r.bias = beta * comp(dp, c);
-      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_lin(unit<T>(c), ra, rb);
+      r.bias = tb * comp(dp, c);
+      rows[n++] = r;
     }
-    V3<float> cr = cross(ux, col(qmat(qFB), 0));
-    JRow r1 = ang_row(uy); r1.bias = beta * dot(cr, uy); finish_row(r1, ctx, false); put_row(rows + ROW_F4 * n++, r1);
-    JRow r2 = ang_row(uz); r2.bias = beta * dot(cr, uz); finish_row(r2, ctx, false); put_row(rows + ROW_F4 * n++, r2);
+    V3<T> cr = cross(ux, col(qmat(qFB), 0));
+    GRow<T> r1 = g_ang(uy); r1.bias = tb * dot(cr, uy); rows[n++] = r1;
+    GRow<T> r2 = g_ang(uz); r2.bias = tb * dot(cr, uz); rows[n++] = r2;
     if (drive) {
-      JRow r = ang_row(ux);
-      float theta = 2.f * atan2f(qr.x, qr.w);
-      soft_row(r, h, theta - (tgt ? tgt[j.dof] : 0.f), j.k, j.d, j.fmax);
-      finish_row(r, ctx, true); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_ang(ux);
+      T theta = T(2.f) * atan2_(qr.x, qr.w);
+      g_soft(r, h, theta - tgt[0], j.k, j.d, j.fmax);
+      rows[n++] = r;
     }
   } else if (j.type == JT_PRISMATIC) {
-    V3<float> us[2] = {uy, uz};
+    V3<T> us[2] = {uy, uz};
     for (int c = 0; c < 2; ++c) {
-      JRow r = lin_row(us[c], raB, rb);
-      r.bias = beta * dot(dp, us[c]);
-      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_lin(us[c], raB, rb);
+      r.bias = tb * dot(dp, us[c]);
+      rows[n++] = r;
     }
-    V3<float> ua[3] = {ux, uy, uz};
-    float qv[3] = {qr.x, qr.y, qr.z};
+    V3<T> ua[3] = {ux, uy, uz};
+    T qv[3] = {qr.x, qr.y, qr.z};
     for (int c = 0; c < 3; ++c) {
-      JRow r = ang_row(ua[c]);
-      r.bias = beta * (2.f * qv[c]);
-      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_ang(ua[c]);
+      r.bias = tb * (T(2.f) * qv[c]);
+      rows[n++] = r;
     }
-    float dd = dot(dp, ux);
+    T dd = dot(dp, ux);
     if (drive) {
-      JRow r = lin_row(ux, raB, rb);
-      soft_row(r, h, dd - (tgt ? tgt[j.dof] : 0.f), j.k, j.d, j.fmax);
-      finish_row(r, ctx, true); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_lin(ux, raB, rb);
+      g_soft(r, h, dd - tgt[0], j.k, j.d, j.fmax);
+      rows[n++] = r;
     }
     for (int c = 0; c < 2; ++c) {
-      JRow r = lin_row(c == 0 ? ux : -ux, raB, rb);
-      float C = c == 0 ? dd - j.lo : j.hi - dd;
-      r.bias = C > 0.f ? C / h : beta * C;
-      r.lo = 0.f; r.hi = INFINITY;
-      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_lin(c == 0 ? ux : -ux, raB, rb);
+      T C = c == 0 ? dd - T(j.lo) : T(j.hi) - dd;
+      r.bias = C > T(0.f) ? C / T(h) : tb * C;
+      r.clamp = CLAMP_UNI;
+      rows[n++] = r;
     }
   } else {
     {
-      JRow r = lin_row(uz, raB, rb);
-      r.bias = beta * dot(dp, uz);
-      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_lin(uz, raB, rb);
+      r.bias = tb * dot(dp, uz);
+      rows[n++] = r;
     }
-    V3<float> cr = cross(uz, col(qmat(qFB), 2));
-    V3<float> us[2] = {ux, uy};
+    V3<T> cr = cross(uz, col(qmat(qFB), 2));
+    V3<T> us[2] = {ux, uy};
     for (int c = 0; c < 2; ++c) {
-      JRow r = ang_row(us[c]);
-      r.bias = beta * dot(cr, us[c]);
-      finish_row(r, ctx, false); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_ang(us[c]);
+      r.bias = tb * dot(cr, us[c]);
+      rows[n++] = r;
     }
     if (drive) {
       for (int c = 0; c < 2; ++c) {
-        JRow r = lin_row(us[c], raB, rb);
-        soft_row(r, h, dot(dp, us[c]) - (tgt ? tgt[j.dof + c] : 0.f), j.k, j.d, j.fmax);
-        finish_row(r, ctx, true); put_row(rows + ROW_F4 * n++, r);
+        GRow<T> r = g_lin(us[c], raB, rb);
+        g_soft(r, h, dot(dp, us[c]) - tgt[c], j.k, j.d, j.fmax);
+        rows[n++] = r;
       }
-      JRow r = ang_row(uz);
-      float theta = 2.f * atan2f(qr.z, qr.w);
-      soft_row(r, h, theta - (tgt ? tgt[j.dof + 2] : 0.f), j.k, j.d, j.fmax);
-      finish_row(r, ctx, true); put_row(rows + ROW_F4 * n++, r);
+      GRow<T> r = g_ang(uz);
+      T theta = T(2.f) * atan2_(qr.z, qr.w);
+      g_soft(r, h, theta - tgt[2], j.k, j.d, j.fmax);
+      rows[n++] = r;
     }
   }
+  return n;
 }
 
 __device__ __forceinline__ int joint_row_count(int type, bool drive) {
@@ -581,14 +630,54 @@ __device__ __forceinline__ int joint_row_count(int type, bool drive) {
   if (type == JT_PRISMATIC) return drive ? 8 : 7;
   return drive ? 6 : 3;
 }
+__device__ __forceinline__ int joint_ndof(int type) { return type == JT_PLANAR ? 3 : 1; }
+
+__device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k) {
+  const JointDesc& j = p.joints[e.j0 + k];
+  const int A = j.parent, B = j.child;
+  RowCtx ctx = row_ctx(w, A, B);
+  float tg[3] = {0.f, 0.f, 0.f};
+  if (p.targets && (j.k > 0.f || j.d > 0.f))
+    for (int c = 0; c < joint_ndof(j.type); ++c) tg[c] = p.targets[(size_t)e.env * p.max_dof + j.dof + c];
+  V3<float> xa = A >= 0 ? f3(w.bx[A]) : v3<float>(0.f, 0.f, 0.f);
+  Q4<float> qa = A >= 0 ? ldq4(w.bq[A]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
+  GRow<float> g[ROWS_PER_JOINT];
+  int n = joint_geom<float>(j, A >= 0, xa, qa, f3(w.bx[B]), ldq4(w.bq[B]), tg, p.h, p.jbeta, g);
+  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * ROW_F4;
+  for (int r = 0; r < n; ++r) {
+    JRow x = blank_row();
+    x.la = g[r].la; x.lb = -g[r].la; x.aa = g[r].aa; x.ab = g[r].ab;
+    x.bias = g[r].bias; x.gamma = g[r].gamma;
+    const bool soft = g[r].clamp >= 0.f;
+    if (soft) { x.lo = -g[r].clamp; x.hi = g[r].clamp; }
+    else if (g[r].clamp == CLAMP_UNI) { x.lo = 0.f; x.hi = INFINITY; }
+    finish_row(x, ctx, soft);
+    put_row(rows + ROW_F4 * r, x);
+  }
+}
 
 // Duff et al. (2017) orthonormal basis from a unit normal.
-__device__ __forceinline__ void onb(const V3<float>& n, V3<float>& t1, V3<float>& t2) {
-  float sg = n.z >= 0.f ? 1.f : -1.f;
-  float a = -1.f / (sg + n.z);
-  float b = n.x * n.y * a;
-  t1 = v3<float>(1.f + sg * n.x * n.x * a, sg * b, -sg * n.x);
-  t2 = v3<float>(b, sg + n.y * n.y * a, -n.y);
+template <class T> __device__ __forceinline__ void onb(const V3<T>& n, V3<T>& t1, V3<T>& t2) {
+  T sg = n.z >= T(0.f) ? T(1.f) : T(-1.f);
+  T a = T(-1.f) / (sg + n.z);
+  T b = n.x * n.y * a;
+  t1 = v3<T>(T(1.f) + sg * n.x * n.x * a, sg * b, -sg * n.x);
+  t2 = v3<T>(b, sg + n.y * n.y * a, -n.y);
+}
+
+// World lever arms and speculative bias of one contact point from the body
+// poses and the point's normal and anchors (rb_l is world space for a static b).
+template <class T>
+__device__ __forceinline__ void contact_geom(const V3<T>& xa, const Q4<T>& qa, const V3<T>& xb, const Q4<T>& qb,
+                                             bool bdyn, const V3<T>& n, const V3<T>& ra_l, const V3<T>& rb_l, float h,
+                                             float beta, float slop, V3<T>& ra, V3<T>& rb, T& bias) {
+  ra = mul(qmat(qa), ra_l);
+  V3<T> pa_w = xa + ra;
+  V3<T> pb_w;
+  if (bdyn) { rb = mul(qmat(qb), rb_l); pb_w = xb + rb; }
+  else { pb_w = rb_l; rb = v3<T>(T(0.f), T(0.f), T(0.f)); }
+  T s = dot(n, pb_w - pa_w);
+  bias = s > T(0.f) ? s / T(h) : -T(beta / h) * maxv(T(0.f), -s - T(slop));
 }
 
 __device__ __forceinline__ float eff_mass(const RowCtx& c, const V3<float>& d, const V3<float>& ra, const V3<float>& rb) {
@@ -603,15 +692,13 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
   int a = ids & 0xffff, bc = ids >> 16;
   int b = bc < e.D ? bc : -1;
   RowCtx ctx = row_ctx(w, a, b);
-  float4 cn = w.cn[ci];
-  V3<float> n = f3(cn);
-  V3<float> ra = mul(qmat(ldq4(w.bq[a])), f3(w.cra[ci]));
-  V3<float> pa_w = f3(w.bx[a]) + ra;
-  V3<float> rb, pb_w;
-  if (b >= 0) { rb = mul(qmat(ldq4(w.bq[b])), f3(w.crb[ci])); pb_w = f3(w.bx[b]) + rb; }
-  else { pb_w = f3(w.crb[ci]); rb = v3<float>(0.f, 0.f, 0.f); }
-  float s = dot(n, pb_w - pa_w);
-  float bias = s > 0.f ? s / p.h : -(p.beta / p.h) * fmaxf(0.f, -s - p.slop);
+  V3<float> n = f3(w.cn[ci]);
+  V3<float> ra, rb;
+  float bias;
+  V3<float> xb = b >= 0 ? f3(w.bx[b]) : v3<float>(0.f, 0.f, 0.f);
+  Q4<float> qb = b >= 0 ? ldq4(w.bq[b]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
+  contact_geom<float>(f3(w.bx[a]), ldq4(w.bq[a]), xb, qb, b >= 0, n, f3(w.cra[ci]), f3(w.crb[ci]), p.h, p.beta,
+                      p.slop, ra, rb, bias);
   if (p.rest > 0.f) {
     V3<float> va = f3(w.bv[a]), wa = f3(w.bw[a]);
     V3<float> dv = v3<float>(0.f, 0.f, 0.f) - (va + cross(wa, ra));
@@ -642,8 +729,8 @@ struct BodyVel { V3<float> va, wa, vb, wb; };
 
 __device__ __forceinline__ void apply_lin(V3<float>& v, V3<float>& wv, const V3<float>& P, const V3<float>& r,
                                           float im, const Sym3& I, float sgn) {
-  v = v + P * (sgn * im);
-  wv = wv + smul(I, cross(r, P)) * sgn;
+  v = axpyf(v, P, sgn * im);
+  wv = axpyf(wv, smulf(I, crossf(r, P)), sgn);
 }
 
 // Joint rows on velocities (va, wa, vb, wb); `sa`/`sb` scale the inverse
@@ -661,10 +748,10 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
     float4* R = rows + ROW_F4 * r;
     float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4];
     V3<float> la = f3(r0), aa = f3(r1), ab = f3(r2), Ia = f3(r3), Ib = f3(r4);
-    float jv = dot(ab, bv.wb) - dot(la, bv.vb);
-    if (A >= 0) jv = jv + dot(la, bv.va) + dot(aa, bv.wa);
+    float jv = dotf(ab, bv.wb) - dotf(la, bv.vb);
+    if (A >= 0) jv = jv + dotf(la, bv.va) + dotf(aa, bv.wa);
     float lam = r3.w;
-    float dl = -r0.w * (jv + r1.w + r2.w * lam);
+    float dl = -r0.w * fmaf(r2.w, lam, jv + r1.w);
     float nl = lam + dl;
     const float cl = r4.w;
     if (cl >= 0.f) nl = fminf(fmaxf(nl, -cl), cl);
@@ -672,13 +759,13 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
     dl = nl - lam;
     R[3].w = nl;
     if (A >= 0) {
-      bv.va = bv.va + la * (sa * ima * dl);
-      bv.wa = bv.wa + Ia * (sa * dl);
-      if (dacc) { dacc->va = dacc->va + la * (ima * dl); dacc->wa = dacc->wa + Ia * dl; }
+      bv.va = axpyf(bv.va, la, sa * ima * dl);
+      bv.wa = axpyf(bv.wa, Ia, sa * dl);
+      if (dacc) { dacc->va = axpyf(dacc->va, la, ima * dl); dacc->wa = axpyf(dacc->wa, Ia, dl); }
     }
-    bv.vb = bv.vb - la * (sb * imb * dl);
-    bv.wb = bv.wb + Ib * (sb * dl);
-    if (dacc) { dacc->vb = dacc->vb - la * (imb * dl); dacc->wb = dacc->wb + Ib * dl; }
+    bv.vb = axpyf(bv.vb, la, -(sb * imb * dl));
+    bv.wb = axpyf(bv.wb, Ib, sb * dl);
+    if (dacc) { dacc->vb = axpyf(dacc->vb, la, -(imb * dl)); dacc->wb = axpyf(dacc->wb, Ib, dl); }
   }
 }
 
@@ -700,8 +787,8 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
     float ms[3] = {kra.w, lam.w, w.cra[c].w};
     float ls[3] = {lam.x, lam.y, lam.z};
     for (int r = 0; r < 3; ++r) {
-      V3<float> dv = bv.vb + cross(bv.wb, rb) - (bv.va + cross(bv.wa, ra));   // static b: vb = wb = 0
-      float vn = dot(dirs[r], dv);
+      V3<float> dv = (bv.vb + crossf(bv.wb, rb)) - (bv.va + crossf(bv.wa, ra));   // static b: vb = wb = 0
+      float vn = dotf(dirs[r], dv);
       float dl, nl;
       if (r == 0) {
         dl = -ms[0] * (vn + krb.w);
@@ -715,10 +802,10 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
       ls[r] = nl;
       V3<float> P = dirs[r] * dl;
       apply_lin(bv.va, bv.wa, P, ra, ima, Ia, -sa);
-      if (dacc) { dacc->va = dacc->va - P * ima; dacc->wa = dacc->wa - smul(Ia, cross(ra, P)); }
+      if (dacc) { dacc->va = axpyf(dacc->va, P, -ima); dacc->wa = dacc->wa - smulf(Ia, crossf(ra, P)); }
       if (b >= 0) {
         apply_lin(bv.vb, bv.wb, P, rb, imb, Ib, sb);
-        if (dacc) { dacc->vb = dacc->vb + P * imb; dacc->wb = dacc->wb + smul(Ib, cross(rb, P)); }
+        if (dacc) { dacc->vb = axpyf(dacc->vb, P, imb); dacc->wb = dacc->wb + smulf(Ib, crossf(rb, P)); }
       }
     }
     w.klam[c] = make_float4(ls[0], ls[1], ls[2], lam.w);
@@ -738,8 +825,27 @@ __device__ __forceinline__ BodyVel load_vel(const Ws& w, int a, int b) {
   return v;
 }
 
+// Records the lambdas of constraint k after its update in sweep `it`.
+__device__ __forceinline__ void tape_lambdas(const Params& p, const EnvInfo& e, const Ws& w, int k, int sub, int it) {
+  TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+  float* t = tape_env(p, e.env) + tl.t2 + (long long)(sub * p.N + it) * p.tape_Rm;
+  if (k < e.J) {
+    const JointDesc& j = p.joints[e.j0 + k];
+    const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
+    const float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * ROW_F4;
+    for (int r = 0; r < nr; ++r) t[k * ROWS_PER_JOINT + r] = rows[ROW_F4 * r + 3].w;
+  } else {
+    int4 mf = w.man[k - e.J];
+    for (int c = mf.z; c < mf.z + mf.w; ++c) {
+      float4 l = w.klam[c];
+      float* q = t + ROWS_PER_JOINT * p.L.Jm + 3 * c;
+      q[0] = l.x; q[1] = l.y; q[2] = l.z;
+    }
+  }
+}
+
 // One solver iteration over every constraint of the env.
-__device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w) {
+__device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w, int sub, int it) {
   const int J = e.J;
   if (p.mode == MODE_COLOURED) {
     const int ncol = w.misc[MC_COLOURS];
@@ -754,6 +860,7 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w)
         else solve_manifold(p, e, w, k - J, bv, nullptr);
         if (a >= 0) { w.bv[a] = f4(bv.va, 0.f); w.bw[a] = f4(bv.wa, 0.f); }
         if (b >= 0) { w.bv[b] = f4(bv.vb, 0.f); w.bw[b] = f4(bv.wb, 0.f); }
+        if (p.tape) tape_lambdas(p, e, w, k, sub, it);
       }
       __syncthreads();
     }
@@ -790,9 +897,14 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w)
 // ---------------------------------------------------------------------------
 // a7: positions
 // ---------------------------------------------------------------------------
-__device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws& w) {
+__device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
   for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
     float4 x = w.bx[i], v = w.bv[i], wv = w.bw[i], q = w.bq[i];
+    if (p.tape) {
+      TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+      float* t = tape_env(p, e.env) + tl.t1 + 19LL * (sub * p.L.Dm + i) + 13;
+      t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = wv.x; t[4] = wv.y; t[5] = wv.z;
+    }
     x.x = x.x + v.x * p.h; x.y = x.y + v.y * p.h; x.z = x.z + v.z * p.h;
     Q4<float> wq; wq.w = 0.f; wq.x = wv.x; wq.y = wv.y; wq.z = wv.z;
     Q4<float> dq = qmul(wq, ldq4(q));

@@ -188,6 +188,36 @@ class MshSim:
         res["aabb_static"] = res["aabb_static"][:sc.num_statics]
         return res
 
+    # -- adjoint --------------------------------------------------------------
+    def set_tape(self, max_steps: int):
+        """Reserves a tape for `max_steps` recorded steps (0 frees it)."""
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_set_tape(self.handle, int(max_steps)), "msh_set_tape")
+
+    def tape_reset(self):
+        check(self.lib.msh_tape_reset(self.handle), "msh_tape_reset")
+
+    @property
+    def tape_count(self) -> int:
+        return int(self.lib.msh_tape_count(self.handle))
+
+    def backward(self, adj_out, adj_targets=None, adj_mass=None, stream=None):
+        """Reverses the last recorded step. adj_out: adjoints (pos, quat, linvel,
+        angvel) of the state after it; returns the adjoints of the state before
+        it. adj_targets [E, max_dof] receives that step's target adjoint;
+        adj_mass [B] accumulates."""
+        def st(ts):
+            x = State()
+            x.pos, x.quat, x.linvel, x.angvel = (t.data_ptr() for t in ts)
+            return x
+        ins = [t.contiguous() for t in adj_out]
+        outs = [torch.empty_like(t) for t in ins]
+        a, b = st(ins), st(outs)
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_backward(self.handle, C.byref(a), C.byref(b), _ptr(adj_targets), _ptr(adj_mass),
+                                        _stream(stream)), "msh_backward")
+        return tuple(outs)
+
     def status(self, stream=None) -> np.ndarray:
         out = np.zeros(self.scene.num_envs, np.int32)
         with torch.cuda.device(self.device):
