@@ -170,6 +170,50 @@ def cpu_baseline(scene, cfg, budget_s=12.0):
                       f"{dt:.1f} s of CPU time"}
 
 
+def time_fwd_bwd(sim, scene, tg, horizon, k, stream, reps=2):
+    """env-steps/s of forward + backward through a differentiable rollout of
+    `horizon` steps (step checkpointing every k): CUDA events around the whole
+    forward and backward pass, after one untimed warm-up pass."""
+    import torch
+    from paper_2412_13211_b300.autograd import rollout
+    dev = sim.device
+    goal_body = np.where(scene.goal_body >= 0, scene.goal_body, np.diff(scene.body_off) - 1)
+    idx = torch.as_tensor(scene.body_off[:-1] + goal_body, device=dev, dtype=torch.long)
+    own = scene.goal_body >= 0
+    goal_np = scene.pos[scene.body_off[:-1] + goal_body] + np.array([0.1, 0.0, 0.0], np.float32)
+    goal_np[own] = scene.goal_pos[own]
+    goal = torch.as_tensor(goal_np, device=dev)
+    init = [torch.as_tensor(np.asarray(a, np.float32), device=dev) for a in scene.state()]
+    mass0 = torch.as_tensor(np.asarray(scene.body_mass, np.float32), device=dev)
+    targets0 = tg[:horizon].contiguous()
+
+    def once():
+        st = [x.clone().requires_grad_(True) for x in init]
+        mass = mass0.clone().requires_grad_(True)
+        targets = targets0.clone().requires_grad_(True)
+        out = rollout(sim, st, targets, mass, k)
+        d = out[0][idx] - goal
+        (d * d).sum().backward()
+        return st[2].grad
+
+    with torch.cuda.stream(stream):
+        sim.set_exec("fused", 32, False)
+        once()
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            g = once()
+        b.record(stream)
+        stream.synchronize()
+    ms = a.elapsed_time(b) / reps
+    tape_bytes = sim.scratch_bytes
+    return {"value": scene.num_envs * horizon / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms,
+            "horizon": horizon, "checkpoint_every": k, "finite": bool(torch.isfinite(g).all().item()),
+            "library_device_bytes": int(tape_bytes),
+            "note": "forward (fused) + recorded re-run of each checkpoint segment + msh_backward per step"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,6 +226,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--bwd-horizon", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -268,6 +314,19 @@ def main():
                  "launches_per_step": sim.launches_per_step, "steps": n_plain, "graph": True}
         sim.set_exec(form, tpe, True)
 
+    # forward + backward: a differentiable rollout (checkpoint every 8 steps) of
+    # the same batch, loss = squared goal distance of one object per env
+    fwd_bwd = None
+    if not args.no_backward:
+        fwd_bwd = time_fwd_bwd(sim, scene, tg, horizon=args.bwd_horizon, k=8, stream=stream)
+        sim.set_exec(form, tpe, True)
+        # the differentiation workload: 512 envs, arm pushing a goal box, 64-step horizon
+        sc4, cfg4 = scenes.make_config(4, num_envs=512, env_start=rank * 512)
+        sim4 = MshSim(sc4, cfg4, device=dev)
+        tg4 = torch.as_tensor(sc4.target_walk(64)).to(dev)
+        fwd_bwd["differentiation_workload"] = time_fwd_bwd(sim4, sc4, tg4, horizon=64, k=8, stream=stream, reps=1)
+        sim4.close()
+
     # end to end through the C ABI with pinned host buffers
     host = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory() for a in scene.state()]
     htg = torch.from_numpy(np.ascontiguousarray(scene.target_walk(total), np.float32)).pin_memory()
@@ -307,7 +366,7 @@ def main():
                          "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": bytes_step},
         "plain_step": plain,
-        "fwd_bwd": None,
+        "fwd_bwd": fwd_bwd,
         "e2e": {"value": scene.num_envs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": n_e2e},
         "gpu_launches": args.steps * sim.launches_per_step,

@@ -203,9 +203,11 @@ int msh_step_static_scratch(msh_handle* h, const msh_state* st, const float* joi
                             int32_t substeps, void* stream);
 
 /*
- * Differentiation (reverse mode). msh_set_tape(h, n) reserves a tape for n
- * steps (0 frees it; coloured solver and zero restitution only). While a tape
- * is set, every msh_step records the step (start state, per-substep poses and
+ * Differentiation (reverse mode). msh_set_tape(h, n), n > 0, makes room for
+ * n recorded steps (reusing a large enough tape) and starts recording
+ * (coloured solver and zero restitution only); n = 0 stops recording and
+ * keeps the memory, n = -1 stops and frees it. Setting the tape drops any
+ * recorded steps. While recording, every msh_step records the step (start state, per-substep poses and
  * velocities, the lambdas after every sweep, the targets) into the next slot;
  * graphs are not used for recorded steps. msh_backward reverses the most
  * recently recorded step and pops it: given adj_out, the adjoint of the state

@@ -52,7 +52,7 @@ class _Rollout(torch.autograd.Function):
                 sim.step(targets[t])
             for t in reversed(range(t0, t1)):
                 adj = sim.backward(adj, adj_targets[t], adj_mass)
-        sim.tape_reset()
+        sim.set_tape(0)        # stop recording; the tape memory is kept for the next backward pass
         return (None, adj_targets, None) + adj + (adj_mass,)
 
 

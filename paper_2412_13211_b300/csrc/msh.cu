@@ -382,7 +382,7 @@ struct msh_handle {
   // adjoint
   float* d_tape = nullptr;      // tape_max recorded steps x E env slabs
   long long tape_slab = 0;
-  int tape_max = 0, tape_count = 0, tape_Rm = 0;
+  int tape_max = 0, tape_count = 0, tape_Rm = 0, tape_cap = 0;   // recording capacity, recorded, rows, allocated
   char* d_aws = nullptr;        // adjoint workspace slabs (E)
   AdjLayout A;
   int64_t bytes = 0;
@@ -506,10 +506,13 @@ int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
 
 int configure_fused(msh_handle* h) {
   const int bytes = h->L.bytes;
-  h->fused_smem = bytes + 1024 <= h->smem_optin;
+  // the attribute belongs to the kernel, not to a handle: raise it once to the
+  // device limit (occupancy still follows each launch's actual size)
+  const int max_dyn = h->smem_optin - 2048;
+  h->fused_smem = bytes <= max_dyn;
   int blocks = 0;
   if (h->fused_smem) {
-    CK(cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    CK(cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused, h->tpe, bytes));
   } else {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused, h->tpe, 0));
@@ -795,22 +798,35 @@ int msh_detect(msh_handle* h, const msh_state* st, float* aabb_body, float* aabb
 
 int msh_set_tape(msh_handle* h, int32_t max_steps) {
   if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
-  if (max_steps < 0) return fail(MSH_ERR_INVALID_ARG, "max_steps must be >= 0");
+  if (max_steps < -1) return fail(MSH_ERR_INVALID_ARG, "max_steps must be >= -1");
   if (max_steps > 0 && h->cfg.mode != MSH_MODE_COLOURED)
     return fail(MSH_ERR_UNSUPPORTED, "the adjoint supports the coloured solver only");
   if (max_steps > 0 && h->cfg.restitution > 0.f)
     return fail(MSH_ERR_UNSUPPORTED, "the adjoint supports restitution 0 only");
-  cudaDeviceSynchronize();
-  drop_graph(h);
-  if (h->d_tape) { cudaFree(h->d_tape); h->bytes -= (int64_t)h->tape_max * h->E * h->tape_slab * 4; h->d_tape = nullptr; }
-  h->tape_max = 0;
   h->tape_count = 0;
-  if (max_steps == 0) return MSH_OK;
+  if (max_steps <= 0) {
+    h->tape_max = 0;                       // stop recording
+    if (max_steps == -1 && h->d_tape) {    // and free the tape
+      cudaDeviceSynchronize();
+      cudaFree(h->d_tape);
+      h->bytes -= (int64_t)h->tape_cap * h->E * h->tape_slab * 4;
+      h->d_tape = nullptr;
+      h->tape_cap = 0;
+    }
+    return MSH_OK;
+  }
+  drop_graph(h);
   const TapeLayout tl = tape_layout(h->L.Dm, h->L.Jm, h->L.C, h->cfg.substeps, h->cfg.iterations, h->max_dof);
   h->tape_slab = tl.slab;
   h->tape_Rm = ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C;
-  int rc = dalloc(h, &h->d_tape, (size_t)max_steps * h->E * tl.slab);
-  if (rc) return rc;
+  int rc;
+  if (max_steps > h->tape_cap) {
+    cudaDeviceSynchronize();
+    if (h->d_tape) { cudaFree(h->d_tape); h->bytes -= (int64_t)h->tape_cap * h->E * h->tape_slab * 4; h->d_tape = nullptr; }
+    h->tape_cap = 0;
+    if ((rc = dalloc(h, &h->d_tape, (size_t)max_steps * h->E * tl.slab))) return rc;
+    h->tape_cap = max_steps;
+  }
   if (!h->d_aws) {
     h->A = make_adj_layout(h->L, h->max_dof);
     if ((rc = dalloc(h, &h->d_aws, (size_t)h->E * h->A.bytes))) return rc;

@@ -190,7 +190,8 @@ class MshSim:
 
     # -- adjoint --------------------------------------------------------------
     def set_tape(self, max_steps: int):
-        """Reserves a tape for `max_steps` recorded steps (0 frees it)."""
+        """max_steps > 0: record the next steps (room for max_steps); 0: stop
+        recording (memory kept); -1: stop and free the tape."""
         with torch.cuda.device(self.device):
             check(self.lib.msh_set_tape(self.handle, int(max_steps)), "msh_set_tape")
 

@@ -135,3 +135,20 @@ def test_backward_through_c_abi_directly():
     lhs = sum(float((s.cpu().numpy().astype(np.float64) * o).sum()) for s, o in zip(seed, dout))
     rhs = float((adj[2].cpu().numpy().astype(np.float64) * d).sum())
     assert abs(lhs - rhs) <= 1e-3 * abs(lhs) + 1e-4
+
+
+def test_steps_after_backward_do_not_record():
+    import torch
+    from paper_2412_13211_b300.autograd import goal_loss, rollout
+    from paper_2412_13211_b300.sim import MshSim
+    sc, cfg = S.make_config(4, num_envs=4)
+    sim = MshSim(sc, cfg)
+    st = [torch.tensor(np.asarray(a, np.float32), device="cuda", requires_grad=True) for a in sc.state()]
+    mass = torch.tensor(np.asarray(sc.body_mass, np.float32), device="cuda", requires_grad=True)
+    tg = torch.tensor(sc.target_walk(4), device="cuda", requires_grad=True)
+    out = rollout(sim, st, tg, mass, 2)
+    goal_loss(sim, out[0]).sum().backward()
+    for _ in range(20):
+        sim.step(tg[0].detach())
+    assert sim.tape_count == 0
+    sim.set_tape(-1)

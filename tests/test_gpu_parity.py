@@ -258,3 +258,19 @@ def test_autotuner_picks_a_form_and_keeps_state():
     assert (sim.exec_form, sim.threads_per_env) == tuple(res["best"])
     sim.step(torch.zeros((sc.num_envs, sc.max_dof)).cuda())
     assert not sim.status().any()
+
+
+def test_handles_with_different_workspaces_coexist():
+    """A second handle with a smaller workspace must not break the first one's
+    fused launches (kernel attributes are shared by all handles)."""
+    import torch
+    big_sc, big_cfg = scene(3)
+    small_sc, small_cfg = scene(4)
+    big = make_sim(big_sc, big_cfg)
+    small = make_sim(small_sc, small_cfg)
+    assert small.workspace_bytes < big.workspace_bytes
+    big.step(torch.zeros((big_sc.num_envs, big_sc.max_dof)).cuda())
+    small.step(torch.zeros((small_sc.num_envs, small_sc.max_dof)).cuda())
+    small.close()
+    big.step(torch.zeros((big_sc.num_envs, big_sc.max_dof)).cuda())
+    assert not big.status().any()
