@@ -228,6 +228,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--bwd-horizon", type=int, default=16)
+    ap.add_argument("--profile-backward", action="store_true",
+                    help="only a short fwd+bwd rollout of the 512-env differentiation workload (small case for ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -240,12 +242,21 @@ def main():
     from paper_2412_13211_b300.sim import MshSim
 
     torch.cuda.set_device(local)
+    if args.profile_backward:
+        sc4, cfg4 = scenes.make_config(4, num_envs=512)
+        sim4 = MshSim(sc4, cfg4, device=torch.device("cuda", local))
+        tg4 = torch.as_tensor(sc4.target_walk(8)).cuda()
+        r = time_fwd_bwd(sim4, sc4, tg4, horizon=8, k=8, stream=torch.cuda.Stream(), reps=1)
+        print(json.dumps({"profile_backward": r}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    scene, cfg = scenes.make_config(args.config, num_envs=args.envs, env_start=rank * args.envs)
+    from paper_2412_13211_b300 import replicas
+    start, _ = replicas.env_range(args.envs, rank)
+    scene, cfg = scenes.make_config(args.config, num_envs=args.envs, env_start=start)
     from paper_2412_13211_b300 import autotune
     sim = MshSim(scene, cfg, device=dev, exec_form="fused", use_graph=True)
     total = args.warmup + args.steps
@@ -290,12 +301,8 @@ def main():
     if dist:
         dist.barrier()
     t_step = float(np.mean(ms))
-    t_tot = float(np.sum(ms))
-    if dist:
-        tt = torch.tensor([t_tot], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_tot = float(tt.item())
-    value = world * scene.num_envs * args.steps / (t_tot / 1e3)
+    t_tot = replicas.slowest(float(np.sum(ms)) / 1e3, device=dev)
+    value = replicas.job_throughput(scene.num_envs, args.steps, t_tot, world)
     status = sim.status()
 
     # plain form (one launch per stage), same inputs
