@@ -236,7 +236,9 @@ int msh_clear_status(msh_handle* h, void* stream);
 /* Bytes of device memory owned by the handle. */
 int64_t msh_scratch_bytes(const msh_handle* h);
 
-/* Per-env workspace bytes (shared memory in the fused form). */
+/* Per-env shared-memory workspace bytes of the fused form (the hot part: body
+   state, contact normals, solver rows, colouring). Contact anchors and ids
+   (read once per substep) live in device memory beside it. */
 int64_t msh_workspace_bytes(const msh_handle* h);
 
 /* Number of kernel launches one msh_step issues in the current form. */

@@ -26,7 +26,8 @@ using namespace msh;
 // kernels
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ Ws plain_ws(const Params& p, int env) {
-  return make_ws(p.ws + (long long)env * p.ws_stride, p.L);
+  char* b = p.ws + (long long)env * p.ws_stride;
+  return make_ws(b, b + p.L.hot_bytes, p.L);
 }
 
 __global__ void k_load(Params p) {
@@ -85,12 +86,13 @@ __global__ void k_substep(Params p) {
 }
 
 // One whole step per env; persistent CTAs pull envs from an atomic queue.
-__global__ void k_fused(Params p, int smem_ws) {
+__device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int scr[33];
   __shared__ int s_next;
-  char* base = smem_ws ? smem : p.ws + (long long)blockIdx.x * p.ws_stride;
-  Ws w = make_ws(base, p.L);
+  char* slab = p.ws + (long long)blockIdx.x * p.ws_stride;   // per-CTA HBM slab (cold part, or all)
+  char* base = smem_ws ? smem : slab;
+  Ws w = make_ws(base, slab + p.L.hot_bytes, p.L);
   for (;;) {
     if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
     __syncthreads();
@@ -117,6 +119,16 @@ __global__ void k_fused(Params p, int smem_ws) {
     __syncthreads();
   }
 }
+
+// Up to 256 threads per CTA the compiler's own register choice is kept
+// (measured: capping registers to fit more one-warp CTAs per SM made every
+// stage slower); 512-thread CTAs need a 128-register budget.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT) k_fused(Params p, int smem_ws) { fused_body(p, smem_ws); }
+
+using FusedKernel = void (*)(Params, int);
+
+static FusedKernel fused_kernel(int tpe) { return tpe <= 256 ? k_fused<256> : k_fused<512>; }
 
 // Adjoint of the recorded step in tape slot q.slot, one CTA per env (see
 // msh_adjoint.cuh). Replays the step's collision stage from the recorded
@@ -242,6 +254,12 @@ __global__ void k_params(int B, const float* mass, const int* shape, const float
   bdims[g] = make_float4(d0.v, d1.v, d2.v, __int_as_float(sh));
 }
 
+// World frames and AABBs of the static boxes (once per scene).
+__global__ void k_static(int S, const float* pose, const float* half, float off, float4* sworld) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < S) static_world(pose + 7 * g, half + 3 * g, off, sworld + (size_t)SW_N * g);
+}
+
 // Copies the collision stage results of every env out of the plain workspace.
 __global__ void k_export(Params p, float* aabb_body, float* aabb_static, int* pair_count, int* pairs,
                          int* contact_count, int* contact_ids, float* contact_geom, int* manifold_count,
@@ -254,7 +272,7 @@ __global__ void k_export(Params p, float* aabb_body, float* aabb_static, int* pa
     float* o = i < e.D ? (aabb_body ? aabb_body + 6 * (e.b0 + i) : nullptr)
                        : (aabb_static ? aabb_static + 6 * (e.s0 + i - e.D) : nullptr);
     if (!o) continue;
-    float4 lo = w.alo[i], hi = w.ahi[i];
+    float4 lo = aabb_lo(p, w, e, i), hi = aabb_hi(p, w, e, i);
     o[0] = lo.x; o[1] = lo.y; o[2] = lo.z; o[3] = hi.x; o[4] = hi.y; o[5] = hi.z;
   }
   for (int k = threadIdx.x; k < np; k += blockDim.x) {
@@ -308,18 +326,19 @@ int fail(int code, const std::string& msg) {
 
 int align16(int x) { return (x + 15) & ~15; }
 
-Layout make_layout(int Dm, int Sm, int Jm, int P, int C, bool jacobi) {
+Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
-  L.Dm = Dm; L.Sm = Sm; L.Jm = Jm; L.P = P; L.C = C; L.K = Jm + P; L.R = Jm * ROWS_PER_JOINT;
+  L.Dm = Dm; L.Sm = Sm; L.Jm = Jm; L.P = P; L.C = C; L.K = Jm + P; L.R = std::max(Rm, 1);
   int o = 0;
   auto take = [&](int bytes) { int r = o; o = align16(o + bytes); return r; };
   const int f4 = 16;
   L.bx = take(Dm * f4); L.bq = take(Dm * f4); L.bv = take(Dm * f4); L.bw = take(Dm * f4);
   L.bIw0 = take(Dm * f4); L.bIw1 = take(Dm * f4);
-  L.cn = take(C * f4); L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4);
+  L.cn = take(C * f4);
   L.man = take(P * 16);
   L.jr = take(L.R * ROW_F4 * f4);
+  L.jinfo = take(Jm * 16);
   L.ccol = take(L.K * 4); L.corder = take(L.K * 4); L.coff = take((MAX_COLOURS + 1) * 4);
   if (jacobi) {
     L.jdv = take(L.K * 4 * f4); L.inc_off = take((Dm + 1) * 4); L.inc = take(2 * L.K * 4);
@@ -329,15 +348,20 @@ Layout make_layout(int Dm, int Sm, int Jm, int P, int C, bool jacobi) {
   L.misc = take(MC_N * 4);
   // shared region: collision-only arrays | per-substep contact rows
   const int region = o;
-  L.sc = take(Sm * f4); L.sM = take(3 * Sm * f4);
-  L.alo = take((Dm + Sm) * f4); L.ahi = take((Dm + Sm) * f4);
+  L.sw = take(SW_N * Sm * f4);
+  L.alo = take(Dm * f4); L.ahi = take(Dm * f4);
   L.pairs = take(P * 4);
   L.masks = take(Dm * 8);
   const int end_x = o;
   o = region;
   L.kra = take(C * f4); L.krb = take(C * f4); L.klam = take(C * f4);
   o = std::max(o, end_x);
-  L.bytes = o;
+  L.hot_bytes = align16(o);
+  // cold part: offsets relative to the cold base
+  o = 0;
+  L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4);
+  L.cold_bytes = align16(o);
+  L.bytes = L.hot_bytes + L.cold_bytes;
   return L;
 }
 
@@ -372,13 +396,17 @@ struct msh_handle {
   int *d_body_off = nullptr, *d_static_off = nullptr, *d_joint_off = nullptr, *d_env_order = nullptr;
   float4 *d_bdims = nullptr, *d_binv = nullptr;
   float *d_static_pose = nullptr, *d_static_half = nullptr;
+  float4* d_sworld = nullptr;
   JointDesc* d_joints = nullptr;
   int* d_status = nullptr;
   int* d_queue = nullptr;
   float* d_targets = nullptr;   // library copy of the targets (graphs, host path)
   float *d_pos = nullptr, *d_quat = nullptr, *d_lv = nullptr, *d_av = nullptr;   // host-path state
   char* d_ws_plain = nullptr;   // E slabs
-  char* d_ws_fused = nullptr;   // per-CTA slabs when SMEM cannot hold the workspace
+  char* d_ws_fused = nullptr;   // per-CTA HBM slabs (cold part, or the whole workspace without room in SMEM)
+  int64_t fused_slab_bytes = 0;
+  FusedKernel fused_fn = nullptr;  // instantiation chosen for the block size and workspace
+  int fused_blocks_per_sm = 0;
   // adjoint
   float* d_tape = nullptr;      // tape_max recorded steps x E env slabs
   long long tape_slab = 0;
@@ -426,7 +454,7 @@ Params make_params(const msh_handle* h, const msh_state* st, const float* target
   p.E = h->E; p.max_dof = h->max_dof;
   p.body_off = h->d_body_off; p.static_off = h->d_static_off; p.joint_off = h->d_joint_off;
   p.bdims = h->d_bdims; p.binv = h->d_binv;
-  p.static_pose = h->d_static_pose; p.static_half = h->d_static_half;
+  p.static_pose = h->d_static_pose; p.static_half = h->d_static_half; p.sworld = h->d_sworld;
   p.joints = h->d_joints; p.env_order = h->d_env_order;
   p.dt = dt; p.S = S; p.h = dt / (float)S; p.N = h->cfg.iterations; p.mode = h->cfg.mode;
   p.gx = h->cfg.gravity[0]; p.gy = h->cfg.gravity[1]; p.gz = h->cfg.gravity[2];
@@ -492,38 +520,40 @@ int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
   }
   CK(cudaMemsetAsync(h->d_queue, 0, sizeof(int), s));
   if (h->fused_smem) {
-    p.ws = nullptr;
-    p.ws_stride = 0;
-    k_fused<<<h->fused_grid, T, h->L.bytes, s>>>(p, 1);
+    p.ws = h->d_ws_fused;                  // cold parts (the hot part lives in shared memory)
+    p.ws_stride = h->L.bytes;
+    h->fused_fn<<<h->fused_grid, T, h->L.hot_bytes, s>>>(p, 1);
   } else {
     p.ws = h->d_ws_fused;
     p.ws_stride = h->L.bytes;
-    k_fused<<<h->fused_grid, T, 0, s>>>(p, 0);
+    h->fused_fn<<<h->fused_grid, T, 0, s>>>(p, 0);
   }
   CK(cudaGetLastError());
   return MSH_OK;
 }
 
 int configure_fused(msh_handle* h) {
-  const int bytes = h->L.bytes;
+  const int bytes = h->L.hot_bytes;
   // the attribute belongs to the kernel, not to a handle: raise it once to the
   // device limit (occupancy still follows each launch's actual size)
   const int max_dyn = h->smem_optin - 2048;
   h->fused_smem = bytes <= max_dyn;
+  h->fused_fn = fused_kernel(h->tpe);
   int blocks = 0;
   if (h->fused_smem) {
-    CK(cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused, h->tpe, bytes));
+    CK(cudaFuncSetAttribute(h->fused_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, h->tpe, bytes));
   } else {
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused, h->tpe, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, h->tpe, 0));
   }
+  h->fused_blocks_per_sm = blocks;
   if (blocks < 1) return fail(MSH_ERR_UNSUPPORTED, "fused kernel cannot be resident with this block size");
   h->fused_grid = std::min(h->E, blocks * h->num_sms);
-  if (!h->fused_smem) {
-    if (h->d_ws_fused) { cudaFree(h->d_ws_fused); h->d_ws_fused = nullptr; }
-    int rc = dalloc(h, &h->d_ws_fused, (size_t)h->fused_grid * bytes);
-    if (rc) return rc;
-  }
+  // per-CTA HBM slabs: the cold part (shared-memory form) or the whole workspace
+  if (h->d_ws_fused) { cudaFree(h->d_ws_fused); h->bytes -= h->fused_slab_bytes; h->d_ws_fused = nullptr; }
+  h->fused_slab_bytes = (int64_t)h->fused_grid * h->L.bytes;
+  int rc = dalloc(h, &h->d_ws_fused, (size_t)h->fused_slab_bytes);
+  if (rc) return rc;
   return MSH_OK;
 }
 
@@ -588,8 +618,10 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
     for (int c = 0; c < 3; ++c)
       if (!(d->static_half[3 * k + c] >= 0.f)) return fail(MSH_ERR_INVALID_ARG, "static half extents must be >= 0");
   std::vector<JointDesc> jd(J);
+  int Rm = 0;   // joint solver rows of the largest env
   for (int e = 0; e < E; ++e) {
     int D = d->body_off[e + 1] - d->body_off[e];
+    int roff = 0;
     for (int g = d->joint_off[e]; g < d->joint_off[e + 1]; ++g) {
       JointDesc& j = jd[g];
       std::memset(&j, 0, sizeof(j));
@@ -608,12 +640,15 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
       std::memcpy(j.pb, d->joint_frame_b + 7 * g, 3 * 4); std::memcpy(j.qb, d->joint_frame_b + 7 * g + 3, 4 * 4);
       j.k = gn[0]; j.d = gn[1]; j.fmax = gn[2];
       j.lo = d->joint_limits[2 * g]; j.hi = d->joint_limits[2 * g + 1];
+      j.roff = roff;
+      roff += joint_row_count(j.type, drive);
     }
+    Rm = std::max(Rm, roff);
   }
   msh_handle* h = new msh_handle();
   h->E = E; h->B = B; h->S = S; h->J = J; h->max_dof = d->max_dof; h->cfg = *cfg;
   h->Dm = std::max(Dm, 1); h->Sm = std::max(Sm, 1); h->Jm = std::max(Jm, 1);
-  h->L = make_layout(h->Dm, h->Sm, h->Jm, cfg->max_pairs, cfg->max_contacts, cfg->mode == MSH_MODE_JACOBI);
+  h->L = make_layout(h->Dm, h->Sm, h->Jm, Rm, cfg->max_pairs, cfg->max_contacts, cfg->mode == MSH_MODE_JACOBI);
   auto bail = [&](int code) { msh_destroy(h); return code; };
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(MSH_ERR_CUDA, "no CUDA device"));
@@ -636,6 +671,12 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
   if ((rc = upload(h, &h->d_static_pose, d->static_pose, (size_t)7 * S))) return bail(rc);
   if ((rc = upload(h, &h->d_static_half, d->static_half, (size_t)3 * S))) return bail(rc);
   if ((rc = upload(h, &h->d_joints, jd.data(), J))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_sworld, (size_t)SW_N * std::max(S, 1)))) return bail(rc);
+  if (S) {
+    k_static<<<(S + 255) / 256, 256>>>(S, h->d_static_pose, h->d_static_half, cfg->contact_offset, h->d_sworld);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return bail(fail(MSH_ERR_CUDA, std::string("k_static: ") + cudaGetErrorString(e)));
+  }
   if ((rc = dalloc(h, &h->d_bdims, B))) return bail(rc);
   if ((rc = dalloc(h, &h->d_binv, B))) return bail(rc);
   if ((rc = dalloc(h, &h->d_status, E))) return bail(rc);
@@ -674,7 +715,7 @@ void msh_destroy(msh_handle* h) {
   drop_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->d_body_off, h->d_static_off, h->d_joint_off, h->d_env_order, h->d_bdims, h->d_binv,
-                  h->d_static_pose, h->d_static_half, h->d_joints, h->d_status, h->d_queue, h->d_targets,
+                  h->d_static_pose, h->d_static_half, h->d_sworld, h->d_joints, h->d_status, h->d_queue, h->d_targets,
                   h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused, h->d_tape, h->d_aws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -885,7 +926,7 @@ int msh_clear_status(msh_handle* h, void* stream) {
 }
 
 int64_t msh_scratch_bytes(const msh_handle* h) { return h ? h->bytes : 0; }
-int64_t msh_workspace_bytes(const msh_handle* h) { return h ? h->L.bytes : 0; }
+int64_t msh_workspace_bytes(const msh_handle* h) { return h ? h->L.hot_bytes : 0; }
 
 int32_t msh_launches_per_step(const msh_handle* h) {
   if (!h) return 0;
@@ -950,8 +991,9 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   char* base = nullptr;
   int rc = static_scratch_address(&base);
   if (rc) return rc;
+  FusedKernel fn = fused_kernel(h->tpe);
   int blocks = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fused, h->tpe, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, h->tpe, 0));
   if (blocks < 1) return fail(MSH_ERR_UNSUPPORTED, "step kernel cannot be resident with this block size");
   const long long fit = (MSH_STATIC_SCRATCH_BYTES - 256) / slab;
   const int grid = (int)std::min<long long>(std::min<long long>(h->E, (long long)blocks * h->num_sms), fit);
@@ -961,7 +1003,7 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   p.queue = (int*)base;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemsetAsync(base, 0, sizeof(int), s));   // the queue counter must start at zero
-  k_fused<<<grid, h->tpe, 0, s>>>(p, 0);
+  fn<<<grid, h->tpe, 0, s>>>(p, 0);
   CK(cudaGetLastError());
   return MSH_OK;
 }

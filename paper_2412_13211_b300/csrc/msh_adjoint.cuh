@@ -89,14 +89,8 @@ __device__ void load_from_tape(const Params& p, const EnvInfo& e, const Ws& w, c
     w.bw[i] = make_float4(t[10], t[11], t[12], 0.f);
     w.bIw1[i] = make_float4(0.f, 0.f, 1.f, 0.f);
   }
-  for (int k = threadIdx.x; k < e.S; k += blockDim.x) {
-    const float* sp = p.static_pose + 7 * (e.s0 + k);
-    const float* sh = p.static_half + 3 * (e.s0 + k);
-    Q4<nf> q; q.w = nf(sp[3]); q.x = nf(sp[4]); q.y = nf(sp[5]); q.z = nf(sp[6]);
-    M3<nf> M = qmat(q);
-    w.sc[k] = make_float4(sp[0], sp[1], sp[2], 0.f);
-    for (int r = 0; r < 3; ++r) w.sM[3 * k + r] = make_float4(M.m[r][0].v, M.m[r][1].v, M.m[r][2].v, sh[r]);
-  }
+  load_jinfo(p, e, w);
+  load_statics(p, e, w);
   if (threadIdx.x < MC_N) w.misc[threadIdx.x] = 0;
 }
 
@@ -593,14 +587,7 @@ __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w
         Sj.M = qmat(q);
         Sj.d0 = d1(d.x); Sj.d1 = d1(d.y); Sj.d2 = d1(d.z);
       } else if (pj < e.D + e.S) {
-        int k = pj - e.D;
-        float4 c = w.sc[k], r0 = w.sM[3 * k], r1 = w.sM[3 * k + 1], r2 = w.sM[3 * k + 2];
-        Sj.type = SH_BOX;
-        Sj.c = v3<d1>(d1(c.x), d1(c.y), d1(c.z));
-        Sj.M.m[0][0] = d1(r0.x); Sj.M.m[0][1] = d1(r0.y); Sj.M.m[0][2] = d1(r0.z);
-        Sj.M.m[1][0] = d1(r1.x); Sj.M.m[1][1] = d1(r1.y); Sj.M.m[1][2] = d1(r1.z);
-        Sj.M.m[2][0] = d1(r2.x); Sj.M.m[2][1] = d1(r2.y); Sj.M.m[2][2] = d1(r2.z);
-        Sj.d0 = d1(r0.w); Sj.d1 = d1(r1.w); Sj.d2 = d1(r2.w);
+        Sj = static_shape<d1>(p.sworld + (size_t)SW_N * (e.s0 + pj - e.D));   // the region is reused by then
       } else {
         Sj.type = SH_PLANE;
         Sj.c = v3<d1>(d1(0.f), d1(0.f), d1(0.f));

@@ -19,22 +19,34 @@ enum { MC_PAIRS = 0, MC_CONTACTS = 1, MC_MANIFOLDS = 2, MC_COLOURS = 3, MC_STATU
 struct JointDesc {     // 96 bytes
   int type, parent, child, dof;
   float pa[3], qa[4], pb[3], qb[4];
-  float k, d, fmax, lo, hi, pad;
+  float k, d, fmax, lo, hi;
+  int roff;            // first solver row of this joint within its env's joint rows
 };
 
+// Solver rows of a joint: revolute 3 linear + 2 angular + limit (+ drive),
+// prismatic 3 angular + 2 linear + 2 limits (+ drive), planar 3 (+ 3 drives).
+__host__ __device__ __forceinline__ int joint_row_count(int type, bool drive) {
+  if (type == JT_REVOLUTE) return drive ? 6 : 5;
+  if (type == JT_PRISMATIC) return drive ? 8 : 7;
+  return drive ? 6 : 3;
+}
+
 // Byte offsets of the per-env workspace arrays (16-byte aligned).
-// The collision-only arrays (static boxes, AABBs, pairs, colouring masks) and
-// the per-substep contact rows are never live at the same time and share
-// one region.
+// The collision-only arrays (body AABBs, pairs, colouring masks) and the
+// per-substep contact rows are never live at the same time and share one
+// region. Static boxes never move: their world frames and AABBs are computed
+// once per scene (StaticWorld) and copied into the collision region per step.
 struct Layout {
-  int Dm, Sm, Jm, P, C, K, R;
+  int Dm, Sm, Jm, P, C, K, R;   // R: joint solver rows of the largest env
   int bx, bq, bv, bw, bIw0, bIw1;
-  int sc, sM, alo, ahi;
+  int sw, alo, ahi;
   int pairs, cn, cra, crb, cid;
   int kra, krb, klam;
-  int man, jr, ccol, corder, coff, masks;
+  int man, jr, jinfo, ccol, corder, coff, masks;
   int jdv, inc_off, inc, misc;
-  int bytes;
+  int hot_bytes;    // shared memory in the fused form
+  int cold_bytes;   // contact anchors and ids (read once per substep), always in HBM
+  int bytes;        // hot + cold: one HBM slab in the plain form
 };
 
 struct Params {
@@ -47,6 +59,7 @@ struct Params {
   const float4* binv;    // (invm, invIx, invIy, invIz)
   const float* static_pose;
   const float* static_half;
+  const float4* sworld;  // per static box: StaticWorld
   const JointDesc* joints;
   const int* env_order;
   // solver
@@ -92,30 +105,39 @@ __host__ __device__ __forceinline__ TapeLayout tape_layout(int Dm, int Jm, int C
 }
 __device__ __forceinline__ float* tape_env(const Params& p, int env) { return p.tape + (long long)env * p.tape_slab; }
 
+// World data of a static box, 6 float4: centre, the three rows of its
+// rotation matrix (half extent in .w), AABB low and high corners (widened by
+// the contact offset).
+enum { SW_C = 0, SW_M = 1, SW_LO = 4, SW_HI = 5, SW_N = 6 };
+
 struct Ws {
   float4 *bx, *bq, *bv, *bw, *bIw0, *bIw1;
-  float4 *sc, *sM, *alo, *ahi;
+  float4 *sw;         // static boxes' StaticWorld records (collision stages only)
+  float4 *alo, *ahi;  // body AABBs
   int* pairs;
   float4 *cn, *cra, *crb;
   int* cid;
   float4 *kra, *krb, *klam;
   int4* man;
   float4* jr;
+  int4* jinfo;      // per joint: parent, child, first solver row, row count
   int *ccol, *corder, *coff;
   unsigned long long* masks;
   float4* jdv;
   int *inc_off, *inc, *misc;
 };
 
-__device__ __forceinline__ Ws make_ws(char* b, const Layout& L) {
+// hot: the first L.hot_bytes of a slab or shared memory; cold: HBM.
+__device__ __forceinline__ Ws make_ws(char* b, char* cold, const Layout& L) {
   Ws w;
   w.bx = (float4*)(b + L.bx); w.bq = (float4*)(b + L.bq); w.bv = (float4*)(b + L.bv); w.bw = (float4*)(b + L.bw);
   w.bIw0 = (float4*)(b + L.bIw0); w.bIw1 = (float4*)(b + L.bIw1);
-  w.sc = (float4*)(b + L.sc); w.sM = (float4*)(b + L.sM); w.alo = (float4*)(b + L.alo); w.ahi = (float4*)(b + L.ahi);
+  w.sw = (float4*)(b + L.sw); w.alo = (float4*)(b + L.alo); w.ahi = (float4*)(b + L.ahi);
   w.pairs = (int*)(b + L.pairs);
-  w.cn = (float4*)(b + L.cn); w.cra = (float4*)(b + L.cra); w.crb = (float4*)(b + L.crb); w.cid = (int*)(b + L.cid);
+  w.cn = (float4*)(b + L.cn);
+  w.cra = (float4*)(cold + L.cra); w.crb = (float4*)(cold + L.crb); w.cid = (int*)(cold + L.cid);
   w.kra = (float4*)(b + L.kra); w.krb = (float4*)(b + L.krb); w.klam = (float4*)(b + L.klam);
-  w.man = (int4*)(b + L.man); w.jr = (float4*)(b + L.jr);
+  w.man = (int4*)(b + L.man); w.jr = (float4*)(b + L.jr); w.jinfo = (int4*)(b + L.jinfo);
   w.ccol = (int*)(b + L.ccol); w.corder = (int*)(b + L.corder); w.coff = (int*)(b + L.coff);
   w.masks = (unsigned long long*)(b + L.masks);
   w.jdv = (float4*)(b + L.jdv); w.inc_off = (int*)(b + L.inc_off); w.inc = (int*)(b + L.inc);
@@ -165,6 +187,20 @@ __device__ __forceinline__ int block_exscan(int v, int* scr, int* total) {
 // ---------------------------------------------------------------------------
 // a0: stage the env's bodies and statics
 // ---------------------------------------------------------------------------
+// The env's static boxes (StaticWorld records) into the collision region.
+__device__ __forceinline__ void load_statics(const Params& p, const EnvInfo& e, const Ws& w) {
+  const float4* src = p.sworld + (size_t)SW_N * e.s0;
+  for (int k = threadIdx.x; k < SW_N * e.S; k += blockDim.x) w.sw[k] = __ldg(src + k);
+}
+
+// Per-joint solver bookkeeping into the workspace (read by every sweep).
+__device__ __forceinline__ void load_jinfo(const Params& p, const EnvInfo& e, const Ws& w) {
+  for (int k = threadIdx.x; k < e.J; k += blockDim.x) {
+    const JointDesc& j = p.joints[e.j0 + k];
+    w.jinfo[k] = make_int4(j.parent, j.child, j.roff, joint_row_count(j.type, j.k > 0.f || j.d > 0.f));
+  }
+}
+
 __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
   for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
     int g = e.b0 + i;
@@ -187,15 +223,47 @@ __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
     for (int k = threadIdx.x; k < p.max_dof; k += blockDim.x)
       tape_env(p, e.env)[tl.t3 + k] = p.targets ? p.targets[(size_t)e.env * p.max_dof + k] : 0.f;
   }
-  for (int k = threadIdx.x; k < e.S; k += blockDim.x) {
-    const float* sp = p.static_pose + 7 * (e.s0 + k);
-    const float* sh = p.static_half + 3 * (e.s0 + k);
-    Q4<nf> q; q.w = nf(sp[3]); q.x = nf(sp[4]); q.y = nf(sp[5]); q.z = nf(sp[6]);
-    M3<nf> M = qmat(q);
-    w.sc[k] = make_float4(sp[0], sp[1], sp[2], 0.f);
-    for (int r = 0; r < 3; ++r) w.sM[3 * k + r] = make_float4(M.m[r][0].v, M.m[r][1].v, M.m[r][2].v, sh[r]);
-  }
+  load_jinfo(p, e, w);
+  load_statics(p, e, w);
   if (threadIdx.x < MC_N) w.misc[threadIdx.x] = 0;
+}
+
+// Collision shape of a static box from its StaticWorld record.
+template <class T> __device__ __forceinline__ Shape<T> static_shape(const float4* sw) {
+  float4 c = sw[SW_C], r0 = sw[SW_M], r1 = sw[SW_M + 1], r2 = sw[SW_M + 2];
+  Shape<T> s;
+  s.type = SH_BOX;
+  s.c = v3<T>(T(c.x), T(c.y), T(c.z));
+  s.M.m[0][0] = T(r0.x); s.M.m[0][1] = T(r0.y); s.M.m[0][2] = T(r0.z);
+  s.M.m[1][0] = T(r1.x); s.M.m[1][1] = T(r1.y); s.M.m[1][2] = T(r1.z);
+  s.M.m[2][0] = T(r2.x); s.M.m[2][1] = T(r2.y); s.M.m[2][2] = T(r2.z);
+  s.d0 = T(r0.w); s.d1 = T(r1.w); s.d2 = T(r2.w);
+  return s;
+}
+
+// World frame and AABB of each static box: the same FP32 arithmetic as the
+// per-step shapes, done once per scene.
+__device__ __forceinline__ void static_world(const float* sp, const float* sh, float off, float4* out) {
+  Q4<nf> q; q.w = nf(sp[3]); q.x = nf(sp[4]); q.y = nf(sp[5]); q.z = nf(sp[6]);
+  M3<nf> M = qmat(q);
+  out[SW_C] = make_float4(sp[0], sp[1], sp[2], 0.f);
+  for (int r = 0; r < 3; ++r) out[SW_M + r] = make_float4(M.m[r][0].v, M.m[r][1].v, M.m[r][2].v, sh[r]);
+  Shape<nf> s;
+  s.type = SH_BOX;
+  s.c = v3<nf>(nf(sp[0]), nf(sp[1]), nf(sp[2]));
+  s.M = M;
+  s.d0 = nf(sh[0]); s.d1 = nf(sh[1]); s.d2 = nf(sh[2]);
+  AABBt<nf> b = shape_aabb(s, nf(off));
+  out[SW_LO] = make_float4(b.lo.x.v, b.lo.y.v, b.lo.z.v, 0.f);
+  out[SW_HI] = make_float4(b.hi.x.v, b.hi.y.v, b.hi.z.v, 0.f);
+}
+
+// AABB corners of collision index i < D + S (body or static box).
+__device__ __forceinline__ float4 aabb_lo(const Params& p, const Ws& w, const EnvInfo& e, int i) {
+  return i < e.D ? w.alo[i] : w.sw[SW_N * (i - e.D) + SW_LO];
+}
+__device__ __forceinline__ float4 aabb_hi(const Params& p, const Ws& w, const EnvInfo& e, int i) {
+  return i < e.D ? w.ahi[i] : w.sw[SW_N * (i - e.D) + SW_HI];
 }
 
 // Collision shape of index i: dynamic body, static box or the plane.
@@ -209,15 +277,7 @@ __device__ __forceinline__ Shape<nf> coll_shape(const Params& p, const Ws& w, co
     s.M = qmat(q);
     s.d0 = nf(d.x); s.d1 = nf(d.y); s.d2 = nf(d.z);
   } else if (i < e.D + e.S) {
-    int k = i - e.D;
-    float4 c = w.sc[k];
-    float4 r0 = w.sM[3 * k], r1 = w.sM[3 * k + 1], r2 = w.sM[3 * k + 2];
-    s.type = SH_BOX;
-    s.c = v3<nf>(nf(c.x), nf(c.y), nf(c.z));
-    s.M.m[0][0] = nf(r0.x); s.M.m[0][1] = nf(r0.y); s.M.m[0][2] = nf(r0.z);
-    s.M.m[1][0] = nf(r1.x); s.M.m[1][1] = nf(r1.y); s.M.m[1][2] = nf(r1.z);
-    s.M.m[2][0] = nf(r2.x); s.M.m[2][1] = nf(r2.y); s.M.m[2][2] = nf(r2.z);
-    s.d0 = nf(r0.w); s.d1 = nf(r1.w); s.d2 = nf(r2.w);
+    s = static_shape<nf>(w.sw + SW_N * (i - e.D));
   } else {
     s.type = SH_PLANE;
     s.c = v3<nf>(nf(0.f), nf(0.f), nf(0.f));
@@ -227,10 +287,10 @@ __device__ __forceinline__ Shape<nf> coll_shape(const Params& p, const Ws& w, co
 }
 
 // ---------------------------------------------------------------------------
-// a2: AABBs of bodies and static boxes
+// a2: AABBs of the bodies (static boxes: StaticWorld)
 // ---------------------------------------------------------------------------
 __device__ void stage_aabb(const Params& p, const EnvInfo& e, const Ws& w) {
-  for (int i = threadIdx.x; i < e.D + e.S; i += blockDim.x) {
+  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
     Shape<nf> s = coll_shape(p, w, e, i);
     AABBt<nf> b = shape_aabb(s, nf(p.off));
     w.alo[i] = make_float4(b.lo.x.v, b.lo.y.v, b.lo.z.v, 0.f);
@@ -273,7 +333,7 @@ __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w,
       if (pj == W) {
         flag = al.z <= 0.f;
       } else {
-        float4 ah = w.ahi[pi], bl = w.alo[pj], bh = w.ahi[pj];
+        float4 ah = w.ahi[pi], bl = aabb_lo(p, w, e, pj), bh = aabb_hi(p, w, e, pj);
         flag = al.x <= bh.x && bl.x <= ah.x && al.y <= bh.y && bl.y <= ah.y && al.z <= bh.z && bl.z <= ah.z;
         if (flag && pj < D && jointed(p, e, pi, pj)) flag = 0;
       }
@@ -479,8 +539,8 @@ struct RowCtx { int a, b; float ima, imb, sa, sb; Sym3 Ia, Ib; };
 
 __device__ __forceinline__ void finish_row(JRow& r, const RowCtx& c, bool soft) {
   float K = 0.f;
-  if (c.a >= 0) { r.Ia = smul(c.Ia, r.aa); K = K + c.sa * (c.ima * dot(r.la, r.la) + dot(r.aa, r.Ia)); }
-  if (c.b >= 0) { r.Ib = smul(c.Ib, r.ab); K = K + c.sb * (c.imb * dot(r.lb, r.lb) + dot(r.ab, r.Ib)); }
+  if (c.a >= 0) { r.Ia = smulf(c.Ia, r.aa); K = fmaf(c.sa, fmaf(c.ima, dotf(r.la, r.la), dotf(r.aa, r.Ia)), K); }
+  if (c.b >= 0) { r.Ib = smulf(c.Ib, r.ab); K = fmaf(c.sb, fmaf(c.imb, dotf(r.lb, r.lb), dotf(r.ab, r.Ib)), K); }
   if (soft) r.m = 1.f / (K + r.gamma);
   else r.m = K > 0.f ? 1.f / K : 0.f;
 }
@@ -625,11 +685,6 @@ __device__ int joint_geom(const JointDesc& j, bool hasA, const V3<T>& xa, const 
   return n;
 }
 
-__device__ __forceinline__ int joint_row_count(int type, bool drive) {
-  if (type == JT_REVOLUTE) return drive ? 6 : 5;
-  if (type == JT_PRISMATIC) return drive ? 8 : 7;
-  return drive ? 6 : 3;
-}
 __device__ __forceinline__ int joint_ndof(int type) { return type == JT_PLANAR ? 3 : 1; }
 
 __device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k) {
@@ -643,7 +698,7 @@ __device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k
   Q4<float> qa = A >= 0 ? ldq4(w.bq[A]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
   GRow<float> g[ROWS_PER_JOINT];
   int n = joint_geom<float>(j, A >= 0, xa, qa, f3(w.bx[B]), ldq4(w.bq[B]), tg, p.h, p.jbeta, g);
-  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * ROW_F4;
+  float4* rows = w.jr + (size_t)j.roff * ROW_F4;
   for (int r = 0; r < n; ++r) {
     JRow x = blank_row();
     x.la = g[r].la; x.lb = -g[r].la; x.aa = g[r].aa; x.ab = g[r].ab;
@@ -682,8 +737,8 @@ __device__ __forceinline__ void contact_geom(const V3<T>& xa, const Q4<T>& qa, c
 
 __device__ __forceinline__ float eff_mass(const RowCtx& c, const V3<float>& d, const V3<float>& ra, const V3<float>& rb) {
   float K = 0.f;
-  if (c.a >= 0) { V3<float> x = cross(ra, d); K = K + c.sa * (c.ima * dot(d, d) + dot(x, smul(c.Ia, x))); }
-  if (c.b >= 0) { V3<float> x = cross(rb, d); K = K + c.sb * (c.imb * dot(d, d) + dot(x, smul(c.Ib, x))); }
+  if (c.a >= 0) { V3<float> x = crossf(ra, d); K = fmaf(c.sa, fmaf(c.ima, dotf(d, d), dotf(x, smulf(c.Ia, x))), K); }
+  if (c.b >= 0) { V3<float> x = crossf(rb, d); K = fmaf(c.sb, fmaf(c.imb, dotf(d, d), dotf(x, smulf(c.Ib, x))), K); }
   return K > 0.f ? 1.f / K : 0.f;
 }
 
@@ -711,7 +766,7 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
   w.kra[ci] = f4(ra, eff_mass(ctx, n, ra, rb));
   w.krb[ci] = f4(rb, bias);
   w.klam[ci] = make_float4(0.f, 0.f, 0.f, eff_mass(ctx, t1, ra, rb));
-  w.cra[ci].w = eff_mass(ctx, t2, ra, rb);
+  w.cn[ci].w = eff_mass(ctx, t2, ra, rb);   // the separation s0 is not needed after the narrowphase
 }
 
 __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
@@ -727,29 +782,28 @@ __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
 // ---------------------------------------------------------------------------
 struct BodyVel { V3<float> va, wa, vb, wb; };
 
-__device__ __forceinline__ void apply_lin(V3<float>& v, V3<float>& wv, const V3<float>& P, const V3<float>& r,
-                                          float im, const Sym3& I, float sgn) {
-  v = axpyf(v, P, sgn * im);
-  wv = axpyf(wv, smulf(I, crossf(r, P)), sgn);
-}
-
 // Joint rows on velocities (va, wa, vb, wb); `sa`/`sb` scale the inverse
 // masses applied to the local copies (Jacobi mass splitting, 1 in PGS); the
-// true-mass change is accumulated in `dacc` when non-null.
+// true-mass change is accumulated in `dacc` when non-null. The relative
+// velocity along a row is three independent dot products, so the chain from
+// one row's impulse to the next row's velocities stays short.
 __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, const Ws& w, int k, BodyVel& bv,
                                             BodyVel* dacc) {
-  const JointDesc& j = p.joints[e.j0 + k];
-  const int A = j.parent;
-  const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = w.bx[j.child].w;
-  const float sa = A >= 0 ? w.bIw1[A].z : 1.f, sb = w.bIw1[j.child].z;
-  const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
-  float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * ROW_F4;
+  const int4 ji = w.jinfo[k];   // parent, child, first row, row count
+  const int A = ji.x;
+  const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = w.bx[ji.y].w;
+  const float sa = A >= 0 ? w.bIw1[A].z : 1.f, sb = w.bIw1[ji.y].z;
+  const float ka = sa * ima, kb = sb * imb;
+  const int nr = ji.w;
+  float4* rows = w.jr + (size_t)ji.z * ROW_F4;
+  float4 r0 = rows[0], r1 = rows[1], r2 = rows[2], r3 = rows[3], r4 = rows[4];
   for (int r = 0; r < nr; ++r) {
     float4* R = rows + ROW_F4 * r;
-    float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4];
+    float4 n0 = r0, n1 = r1, n2 = r2, n3 = r3, n4 = r4;
+    if (r + 1 < nr) { n0 = R[5]; n1 = R[6]; n2 = R[7]; n3 = R[8]; n4 = R[9]; }   // next row, loaded early
     V3<float> la = f3(r0), aa = f3(r1), ab = f3(r2), Ia = f3(r3), Ib = f3(r4);
-    float jv = dotf(ab, bv.wb) - dotf(la, bv.vb);
-    if (A >= 0) jv = jv + dotf(la, bv.va) + dotf(aa, bv.wa);
+    // J v = la.(va - vb) + aa.wa + ab.wb  (a static parent has va = wa = 0)
+    float jv = dotf(la, bv.va - bv.vb) + dotf(ab, bv.wb) + dotf(aa, bv.wa);
     float lam = r3.w;
     float dl = -r0.w * fmaf(r2.w, lam, jv + r1.w);
     float nl = lam + dl;
@@ -759,36 +813,50 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
     dl = nl - lam;
     R[3].w = nl;
     if (A >= 0) {
-      bv.va = axpyf(bv.va, la, sa * ima * dl);
+      bv.va = axpyf(bv.va, la, ka * dl);
       bv.wa = axpyf(bv.wa, Ia, sa * dl);
       if (dacc) { dacc->va = axpyf(dacc->va, la, ima * dl); dacc->wa = axpyf(dacc->wa, Ia, dl); }
     }
-    bv.vb = axpyf(bv.vb, la, -(sb * imb * dl));
+    bv.vb = axpyf(bv.vb, la, -(kb * dl));
     bv.wb = axpyf(bv.wb, Ib, sb * dl);
     if (dacc) { dacc->vb = axpyf(dacc->vb, la, -(imb * dl)); dacc->wb = axpyf(dacc->wb, Ib, dl); }
+    r0 = n0; r1 = n1; r2 = n2; r3 = n3; r4 = n4;
   }
 }
 
+// One manifold's points in order, each as a normal row then two friction
+// rows (Gauss-Seidel). For a row along d: the lever terms ra x d, rb x d and
+// their images under the inverse inertias do not depend on the velocities and
+// are formed off the row-to-row dependency chain.
 __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e, const Ws& w, int m, BodyVel& bv,
                                                BodyVel* dacc) {
   int4 mf = w.man[m];
   const int a = mf.x, b = mf.y;
   const float ima = w.bx[a].w, imb = b >= 0 ? w.bx[b].w : 0.f;
   const float sa = w.bIw1[a].z, sb = b >= 0 ? w.bIw1[b].z : 1.f;
+  const float ka = sa * ima, kb = sb * imb;
   Sym3 Ia = load_Iw(w, a), Ib;
   if (b >= 0) Ib = load_Iw(w, b);
-  for (int c = mf.z; c < mf.z + mf.w; ++c) {
-    float4 kra = w.kra[c], krb = w.krb[c], lam = w.klam[c];
-    V3<float> n = f3(w.cn[c]);
+  const int c1 = mf.z + mf.w;
+  // software pipelining: the next point's data is loaded while this point's rows run
+  float4 cn = w.cn[mf.z], kra = w.kra[mf.z], krb = w.krb[mf.z], lam = w.klam[mf.z];
+  for (int c = mf.z; c < c1; ++c) {
+    float4 ncn = cn, nkra = kra, nkrb = krb, nlam = lam;
+    if (c + 1 < c1) { ncn = w.cn[c + 1]; nkra = w.kra[c + 1]; nkrb = w.krb[c + 1]; nlam = w.klam[c + 1]; }
+    V3<float> n = f3(cn);
     V3<float> ra = f3(kra), rb = f3(krb);
     V3<float> t1, t2;
     onb(n, t1, t2);
     V3<float> dirs[3] = {n, t1, t2};
-    float ms[3] = {kra.w, lam.w, w.cra[c].w};
+    float ms[3] = {kra.w, lam.w, cn.w};
     float ls[3] = {lam.x, lam.y, lam.z};
+#pragma unroll
     for (int r = 0; r < 3; ++r) {
-      V3<float> dv = (bv.vb + crossf(bv.wb, rb)) - (bv.va + crossf(bv.wa, ra));   // static b: vb = wb = 0
-      float vn = dotf(dirs[r], dv);
+      const V3<float> d = dirs[r];
+      const V3<float> ca = crossf(ra, d), cb = crossf(rb, d);
+      const V3<float> ia = smulf(Ia, ca);
+      // v_rel . d = d.(vb - va) + (rb x d).wb - (ra x d).wa   (static b: vb = wb = 0)
+      float vn = dotf(d, bv.vb - bv.va) + dotf(cb, bv.wb) - dotf(ca, bv.wa);
       float dl, nl;
       if (r == 0) {
         dl = -ms[0] * (vn + krb.w);
@@ -800,20 +868,23 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
       }
       dl = nl - ls[r];
       ls[r] = nl;
-      V3<float> P = dirs[r] * dl;
-      apply_lin(bv.va, bv.wa, P, ra, ima, Ia, -sa);
-      if (dacc) { dacc->va = axpyf(dacc->va, P, -ima); dacc->wa = dacc->wa - smulf(Ia, crossf(ra, P)); }
+      bv.va = axpyf(bv.va, d, -(ka * dl));
+      bv.wa = axpyf(bv.wa, ia, -(sa * dl));
+      if (dacc) { dacc->va = axpyf(dacc->va, d, -(ima * dl)); dacc->wa = axpyf(dacc->wa, ia, -dl); }
       if (b >= 0) {
-        apply_lin(bv.vb, bv.wb, P, rb, imb, Ib, sb);
-        if (dacc) { dacc->vb = axpyf(dacc->vb, P, imb); dacc->wb = dacc->wb + smulf(Ib, crossf(rb, P)); }
+        const V3<float> ib = smulf(Ib, cb);
+        bv.vb = axpyf(bv.vb, d, kb * dl);
+        bv.wb = axpyf(bv.wb, ib, sb * dl);
+        if (dacc) { dacc->vb = axpyf(dacc->vb, d, imb * dl); dacc->wb = axpyf(dacc->wb, ib, dl); }
       }
     }
     w.klam[c] = make_float4(ls[0], ls[1], ls[2], lam.w);
+    cn = ncn; kra = nkra; krb = nkrb; lam = nlam;
   }
 }
 
 __device__ __forceinline__ void con_bodies(const Params& p, const EnvInfo& e, const Ws& w, int k, int J, int& a, int& b) {
-  if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
+  if (k < J) { int4 ji = w.jinfo[k]; a = ji.x; b = ji.y; }
   else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
 }
 
@@ -832,7 +903,7 @@ __device__ __forceinline__ void tape_lambdas(const Params& p, const EnvInfo& e, 
   if (k < e.J) {
     const JointDesc& j = p.joints[e.j0 + k];
     const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
-    const float4* rows = w.jr + (size_t)k * ROWS_PER_JOINT * ROW_F4;
+    const float4* rows = w.jr + (size_t)j.roff * ROW_F4;
     for (int r = 0; r < nr; ++r) t[k * ROWS_PER_JOINT + r] = rows[ROW_F4 * r + 3].w;
   } else {
     int4 mf = w.man[k - e.J];
@@ -905,12 +976,12 @@ __device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws&
       float* t = tape_env(p, e.env) + tl.t1 + 19LL * (sub * p.L.Dm + i) + 13;
       t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = wv.x; t[4] = wv.y; t[5] = wv.z;
     }
-    x.x = x.x + v.x * p.h; x.y = x.y + v.y * p.h; x.z = x.z + v.z * p.h;
+    x.x = fmaf(v.x, p.h, x.x); x.y = fmaf(v.y, p.h, x.y); x.z = fmaf(v.z, p.h, x.z);
     Q4<float> wq; wq.w = 0.f; wq.x = wv.x; wq.y = wv.y; wq.z = wv.z;
     Q4<float> dq = qmul(wq, ldq4(q));
     float hh = p.h * 0.5f;
-    float qw = q.x + dq.w * hh, qx = q.y + dq.x * hh, qy = q.z + dq.y * hh, qz = q.w + dq.z * hh;
-    float nrm = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    float qw = fmaf(dq.w, hh, q.x), qx = fmaf(dq.x, hh, q.y), qy = fmaf(dq.y, hh, q.z), qz = fmaf(dq.z, hh, q.w);
+    float nrm = sqrtf(fmaf(qw, qw, fmaf(qx, qx, fmaf(qy, qy, qz * qz))));
     w.bx[i] = x;
     w.bq[i] = make_float4(qw / nrm, qx / nrm, qy / nrm, qz / nrm);
   }
