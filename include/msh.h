@@ -143,9 +143,10 @@ const char* msh_last_error(void);
 
 /*
  * Chooses the execution form: MSH_EXEC_PLAIN, MSH_EXEC_FUSED or
- * MSH_EXEC_SUBSTEP; threads_per_env in {32, 64, 128, 256, 512} (0 = the
- * form's default: 32 fused, 128 otherwise). All forms give bitwise identical
- * results;
+ * MSH_EXEC_SUBSTEP; threads_per_env in {32, 64, 128, 256, 512}, and for the
+ * fused form also 8 or 16 (4 or 2 envs share one warp, each with its own
+ * workspace and group-local barriers); 0 = the form's default: 32 fused,
+ * 128 otherwise. All forms give bitwise identical results;
  * use_graph != 0 captures the step's launches in a CUDA graph on first use
  * (re-captured when the state pointers, dt or substeps change).
  * Returns MSH_ERR_UNSUPPORTED if the fused form cannot hold the workspace.

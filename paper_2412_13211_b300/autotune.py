@@ -13,8 +13,8 @@ import os
 import numpy as np
 import torch
 
-CANDIDATES = [("fused", 32), ("fused", 64), ("fused", 128), ("substep", 64), ("substep", 128),
-              ("plain", 128)]
+CANDIDATES = [("fused", 8), ("fused", 16), ("fused", 32), ("fused", 64), ("fused", 128), ("substep", 64),
+              ("substep", 128), ("plain", 128)]
 _cache: dict = {}
 
 

@@ -86,43 +86,57 @@ __global__ void k_substep(Params p) {
 }
 
 // One whole step per env; persistent CTAs pull envs from an atomic queue.
+// With p.G < 32 a warp holds 32 / p.G env groups, each with its own
+// workspace slice, queue entries and group-local barriers.
 __device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int scr[33];
   __shared__ int s_next;
-  char* slab = p.ws + (long long)blockIdx.x * p.ws_stride;   // per-CTA HBM slab (cold part, or all)
-  char* base = smem_ws ? smem : slab;
+  const int G = p.G > 0 && p.G < (int)blockDim.x ? p.G : (int)blockDim.x;   // threads per env
+  const int gi = threadIdx.x / G, lane = threadIdx.x % G;
+  const unsigned mask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+  const long long slot = (long long)blockIdx.x * (blockDim.x / G) + gi;   // workspace slot of this group
+  char* slab = p.ws + slot * p.ws_stride;   // per-slot HBM slab (cold part, or all)
+  char* base = smem_ws ? smem + (size_t)gi * p.L.hot_bytes : slab;
   Ws w = make_ws(base, slab + p.L.hot_bytes, p.L);
   for (;;) {
-    if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
-    __syncthreads();
-    const int idx = s_next;
+    int idx;
+    if (G < 32) {
+      int v = 0;
+      if (lane == 0) v = atomicAdd(p.queue, 1);
+      idx = __shfl_sync(mask, v, 0, G);
+    } else {
+      if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
+      __syncthreads();
+      idx = s_next;
+    }
     if (idx >= p.E) break;
-    EnvInfo e = env_info(p, p.env_order[idx]);
+    EnvInfo e = env_info(p, p.env_order[idx], lane, G, mask);
     stage_load(p, e, w);
-    __syncthreads();
+    gsync(e);
     stage_aabb(p, e, w);
-    __syncthreads();
+    gsync(e);
     stage_broadphase(p, e, w, scr);
     stage_narrowphase(p, e, w, scr);
     stage_colour(p, e, w);
     for (int s = 0; s < p.S; ++s) {
       stage_integrate_vel(p, e, w, s);
-      __syncthreads();
+      gsync(e);
       stage_prep(p, e, w);
-      __syncthreads();
+      gsync(e);
       for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w, s, it);
       stage_integrate_pos(p, e, w, s);
-      __syncthreads();
+      gsync(e);
     }
     stage_store(p, e, w);
-    __syncthreads();
+    gsync(e);
   }
 }
 
 // Up to 256 threads per CTA the compiler's own register choice is kept
-// (measured: capping registers to fit more one-warp CTAs per SM made every
-// stage slower); 512-thread CTAs need a 128-register budget.
+// (measured on the 4096-env apartment batch: caps of 224, 200 or 168
+// registers, for 9, 10 or 12 one-warp CTAs per SM, were no faster or
+// slower); 512-thread CTAs need a 128-register budget.
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT) k_fused(Params p, int smem_ws) { fused_body(p, smem_ws); }
 
@@ -456,6 +470,7 @@ Params make_params(const msh_handle* h, const msh_state* st, const float* target
   p.bdims = h->d_bdims; p.binv = h->d_binv;
   p.static_pose = h->d_static_pose; p.static_half = h->d_static_half; p.sworld = h->d_sworld;
   p.joints = h->d_joints; p.env_order = h->d_env_order;
+  p.G = h->tpe;
   p.dt = dt; p.S = S; p.h = dt / (float)S; p.N = h->cfg.iterations; p.mode = h->cfg.mode;
   p.gx = h->cfg.gravity[0]; p.gy = h->cfg.gravity[1]; p.gz = h->cfg.gravity[2];
   p.mu = h->cfg.friction; p.rest = h->cfg.restitution; p.off = h->cfg.contact_offset;
@@ -492,6 +507,10 @@ int launch_collision_plain(msh_handle* h, Params p, cudaStream_t s) {
   return MSH_OK;
 }
 
+// Fused form: threads per CTA and env groups per CTA for `tpe` threads per env.
+int fused_block(int tpe) { return tpe < 32 ? 32 : tpe; }
+int fused_groups(int tpe) { return tpe < 32 ? 32 / tpe : 1; }
+
 int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
   Params p = p0;
   const int T = h->tpe;
@@ -519,39 +538,39 @@ int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
     return MSH_OK;
   }
   CK(cudaMemsetAsync(h->d_queue, 0, sizeof(int), s));
-  if (h->fused_smem) {
-    p.ws = h->d_ws_fused;                  // cold parts (the hot part lives in shared memory)
-    p.ws_stride = h->L.bytes;
-    h->fused_fn<<<h->fused_grid, T, h->L.hot_bytes, s>>>(p, 1);
-  } else {
-    p.ws = h->d_ws_fused;
-    p.ws_stride = h->L.bytes;
-    h->fused_fn<<<h->fused_grid, T, 0, s>>>(p, 0);
-  }
+  p.G = T;
+  p.ws = h->d_ws_fused;   // per-group slabs: the cold part (hot part in shared memory), or everything
+  p.ws_stride = h->L.bytes;
+  const int blk = fused_block(T);
+  if (h->fused_smem)
+    h->fused_fn<<<h->fused_grid, blk, (size_t)fused_groups(T) * h->L.hot_bytes, s>>>(p, 1);
+  else
+    h->fused_fn<<<h->fused_grid, blk, 0, s>>>(p, 0);
   CK(cudaGetLastError());
   return MSH_OK;
 }
 
 int configure_fused(msh_handle* h) {
-  const int bytes = h->L.hot_bytes;
+  const int ng = fused_groups(h->tpe), blk = fused_block(h->tpe);
+  const int bytes = ng * h->L.hot_bytes;
   // the attribute belongs to the kernel, not to a handle: raise it once to the
   // device limit (occupancy still follows each launch's actual size)
   const int max_dyn = h->smem_optin - 2048;
   h->fused_smem = bytes <= max_dyn;
-  h->fused_fn = fused_kernel(h->tpe);
+  h->fused_fn = fused_kernel(blk);
   int blocks = 0;
   if (h->fused_smem) {
     CK(cudaFuncSetAttribute(h->fused_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, h->tpe, bytes));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, blk, bytes));
   } else {
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, h->tpe, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, blk, 0));
   }
   h->fused_blocks_per_sm = blocks;
   if (blocks < 1) return fail(MSH_ERR_UNSUPPORTED, "fused kernel cannot be resident with this block size");
-  h->fused_grid = std::min(h->E, blocks * h->num_sms);
-  // per-CTA HBM slabs: the cold part (shared-memory form) or the whole workspace
+  h->fused_grid = std::min((h->E + ng - 1) / ng, blocks * h->num_sms);
+  // per-group HBM slabs: the cold part (shared-memory form) or the whole workspace
   if (h->d_ws_fused) { cudaFree(h->d_ws_fused); h->bytes -= h->fused_slab_bytes; h->d_ws_fused = nullptr; }
-  h->fused_slab_bytes = (int64_t)h->fused_grid * h->L.bytes;
+  h->fused_slab_bytes = (int64_t)h->fused_grid * ng * h->L.bytes;
   int rc = dalloc(h, &h->d_ws_fused, (size_t)h->fused_slab_bytes);
   if (rc) return rc;
   return MSH_OK;
@@ -727,8 +746,10 @@ int msh_set_exec(msh_handle* h, int32_t exec, int32_t tpe, int32_t use_graph) {
   if (exec != MSH_EXEC_PLAIN && exec != MSH_EXEC_FUSED && exec != MSH_EXEC_SUBSTEP)
     return fail(MSH_ERR_INVALID_ARG, "exec must be MSH_EXEC_PLAIN, MSH_EXEC_FUSED or MSH_EXEC_SUBSTEP");
   if (tpe == 0) tpe = exec == MSH_EXEC_FUSED ? 32 : 128;
-  if (tpe != 32 && tpe != 64 && tpe != 128 && tpe != 256 && tpe != 512)
-    return fail(MSH_ERR_INVALID_ARG, "threads_per_env must be 32, 64, 128, 256 or 512");
+  if (tpe != 8 && tpe != 16 && tpe != 32 && tpe != 64 && tpe != 128 && tpe != 256 && tpe != 512)
+    return fail(MSH_ERR_INVALID_ARG, "threads_per_env must be 8, 16, 32, 64, 128, 256 or 512");
+  if (tpe < 32 && exec != MSH_EXEC_FUSED)
+    return fail(MSH_ERR_INVALID_ARG, "threads_per_env 8 and 16 (several envs per warp) are for the fused form only");
   cudaDeviceSynchronize();
   drop_graph(h);
   h->exec = exec;
@@ -982,7 +1003,7 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   if (h->max_dof > 0 && !joint_targets) return fail(MSH_ERR_INVALID_ARG, "joint_targets is NULL but max_dof > 0");
   if (!(dt > 0.f)) dt = h->cfg.dt;
   if (substeps < 1) substeps = h->cfg.substeps;
-  // layout: [0, 256) the env-queue counter, then one 256-aligned slab per CTA
+  // layout: [0, 256) the env-queue counter, then one 256-aligned slab per env group
   const long long slab = ((long long)h->L.bytes + 255) & ~255LL;
   if (256 + slab > MSH_STATIC_SCRATCH_BYTES)
     return fail(MSH_ERR_INVALID_ARG, "per-env workspace of " + std::to_string(h->L.bytes) +
@@ -991,19 +1012,24 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   char* base = nullptr;
   int rc = static_scratch_address(&base);
   if (rc) return rc;
-  FusedKernel fn = fused_kernel(h->tpe);
+  const int ng = fused_groups(h->tpe), blk = fused_block(h->tpe);
+  FusedKernel fn = fused_kernel(blk);
   int blocks = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, h->tpe, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, blk, 0));
   if (blocks < 1) return fail(MSH_ERR_UNSUPPORTED, "step kernel cannot be resident with this block size");
-  const long long fit = (MSH_STATIC_SCRATCH_BYTES - 256) / slab;
-  const int grid = (int)std::min<long long>(std::min<long long>(h->E, (long long)blocks * h->num_sms), fit);
+  const long long fit = (MSH_STATIC_SCRATCH_BYTES - 256) / slab / ng;   // CTAs whose slabs fit
+  if (fit < 1)
+    return fail(MSH_ERR_INVALID_ARG, "the static scratch cannot hold one CTA's env groups at this threads_per_env");
+  const int grid = (int)std::min<long long>(
+      std::min<long long>((h->E + ng - 1) / ng, (long long)blocks * h->num_sms), fit);
   Params p = make_params(h, st, joint_targets, dt, substeps);
+  p.G = h->tpe;
   p.ws = base + 256;
   p.ws_stride = slab;
   p.queue = (int*)base;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemsetAsync(base, 0, sizeof(int), s));   // the queue counter must start at zero
-  fn<<<grid, h->tpe, 0, s>>>(p, 0);
+  fn<<<grid, blk, 0, s>>>(p, 0);
   CK(cudaGetLastError());
   return MSH_OK;
 }

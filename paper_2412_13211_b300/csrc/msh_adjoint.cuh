@@ -80,7 +80,7 @@ __device__ __forceinline__ int crow(const Layout& L, int c, int i) { return ROWS
 // Loads the recorded step-start state into the workspace (as stage_load does
 // from the state arrays).
 __device__ void load_from_tape(const Params& p, const EnvInfo& e, const Ws& w, const float* tape) {
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     const float* t = tape + 13 * i;
     float4 inv = p.binv[e.b0 + i];
     w.bx[i] = make_float4(t[0], t[1], t[2], inv.x);
@@ -91,7 +91,7 @@ __device__ void load_from_tape(const Params& p, const EnvInfo& e, const Ws& w, c
   }
   load_jinfo(p, e, w);
   load_statics(p, e, w);
-  if (threadIdx.x < MC_N) w.misc[threadIdx.x] = 0;
+  if (e.lane < MC_N) w.misc[e.lane] = 0;
 }
 
 // World inverse inertia from an orientation and principal inverse inertia.
@@ -108,7 +108,7 @@ template <class T> __device__ __forceinline__ void world_inv_inertia(const Q4<T>
 
 // Constraint -> body incidence lists in constraint order (for deterministic gathers).
 __device__ void build_incidence(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
-  if (threadIdx.x == 0) {
+  if (e.lane == 0) {
     const int K = e.J + w.misc[MC_MANIFOLDS];
     for (int i = 0; i <= e.D; ++i) a.inc_off[i] = 0;
     for (int k = 0; k < K; ++k) {
@@ -126,14 +126,14 @@ __device__ void build_incidence(const Params& p, const EnvInfo& e, const Ws& w, 
       if (y >= 0) a.inc[w.masks[y]++] = 2 * k + 1;
     }
   }
-  __syncthreads();
+  gsync(e);
 }
 
 // Generic rows of every constraint at the workspace poses (for the reverse
 // sweeps): la|m, aa|bias, ab|gamma, Ia|0, Ib|clamp, plus a kind code.
 __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
   const int nc = w.misc[MC_CONTACTS];
-  for (int t = threadIdx.x; t < e.J + nc; t += blockDim.x) {
+  for (int t = e.lane; t < e.J + nc; t += e.nthr) {
     if (t < e.J) {
       const JointDesc& j = p.joints[e.j0 + t];
       const int A = j.parent, B = j.child;
@@ -265,7 +265,7 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
   const int ncol = w.misc[MC_COLOURS];
   for (int c = ncol - 1; c >= 0; --c) {
     const int c0 = w.coff[c], c1 = w.coff[c + 1];
-    for (int idx = c0 + threadIdx.x; idx < c1; idx += blockDim.x) {
+    for (int idx = c0 + e.lane; idx < c1; idx += e.nthr) {
       const int k = w.corder[idx];
       int A, B;
       con_bodies(p, e, w, k, J, A, B);
@@ -296,7 +296,7 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
       if (A >= 0) { w.bv[A] = f4(v.va, 0.f); w.bw[A] = f4(v.wa, 0.f); a.bv[A] = f4(g.va, 0.f); a.bw[A] = f4(g.wa, 0.f); }
       if (B >= 0) { w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f); }
     }
-    __syncthreads();
+    gsync(e);
   }
 }
 
@@ -422,7 +422,7 @@ __device__ void contact_geom_adjoint(const Params& p, const EnvInfo& e, const Ws
 // adjoints to the contact points, target adjoints to the joint's DoFs.
 __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
   const int J = e.J, K = J + w.misc[MC_MANIFOLDS];
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+  for (int k = e.lane; k < K; k += e.nthr) {
     int A, B;
     con_bodies(p, e, w, k, J, A, B);
     const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
@@ -471,7 +471,7 @@ __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, co
 // pose adjoints (and, when `inertia`, the world-inverse-inertia and 1/m
 // adjoints into bI0/bI1).
 __device__ void gather_bodies(const EnvInfo& e, const AWs& a, bool inertia) {
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 gx = a.bx[i], gq = a.bq[i];
     float4 I0 = make_float4(0.f, 0.f, 0.f, 0.f), I1 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int q = a.inc_off[i]; q < a.inc_off[i + 1]; ++q) {
@@ -496,7 +496,7 @@ __device__ void gather_bodies(const EnvInfo& e, const AWs& a, bool inertia) {
 // inertia adjoint (dual passes over q and the 3 principal values); 1/m
 // adjoint into the mass accumulator.
 __device__ void reverse_inertia(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 I0 = a.bI0[i], I1 = a.bI1[i];
     const float gW[6] = {I0.x, I0.y, I0.z, I0.w, I1.x, I1.y};
     float4 q4 = w.bq[i], inv = p.binv[e.b0 + i];
@@ -522,7 +522,7 @@ __device__ void reverse_inertia(const Params& p, const EnvInfo& e, const Ws& w, 
 // Reverse of x += h v and q <- normalise(q + h/2 (0,w) q) for one substep,
 // with x_s, q_s the substep-start pose and v_e, w_e the velocities it used.
 __device__ void reverse_integrate(const Params& p, const EnvInfo& e, const AWs& a, const float* sub_tape) {
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     const float* t = sub_tape + 19 * i;
     const float qw = t[3], qx = t[4], qy = t[5], qz = t[6];
     const float wx = t[16], wy = t[17], wz = t[18];
@@ -559,7 +559,7 @@ __device__ void reverse_integrate(const Params& p, const EnvInfo& e, const AWs& 
 // passes of the narrowphase of each manifold's pair over the 14 pose inputs.
 __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS];
-  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+  for (int m = e.lane; m < M; m += e.nthr) {
     int4 mf = w.man[m];
     const int ia = mf.x, ib = mf.y;
     const int pj = w.cid[mf.z] >> 16;
@@ -614,7 +614,7 @@ __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w
     S[3] = make_float4(res[10], res[11], res[12], res[13]);
   }
   // joints have no narrowphase inputs
-  for (int k = threadIdx.x; k < J; k += blockDim.x)
+  for (int k = e.lane; k < J; k += e.nthr)
     for (int q = 0; q < 4; ++q) a.gat[8 * k + q] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 

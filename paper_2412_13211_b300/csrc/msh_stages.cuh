@@ -77,7 +77,8 @@ struct Params {
   // workspace
   Layout L;
   char* ws;              // HBM workspace base (plain form, or fused without room in SMEM)
-  long long ws_stride;   // bytes between per-env (plain) or per-CTA (fused) slabs
+  long long ws_stride;   // bytes between per-env (plain) or per-group (fused) slabs
+  int G;                 // fused form: threads per env (8 or 16: several envs per warp)
   int* queue;
   // tape (recorded for the adjoint when non-null): slab per env, see TapeLayout
   float* tape;
@@ -145,15 +146,36 @@ __device__ __forceinline__ Ws make_ws(char* b, char* cold, const Layout& L) {
   return w;
 }
 
-struct EnvInfo { int env, b0, D, s0, S, j0, J; };
+// One env and the threads that work on it: `nthr` threads with group-local
+// index `lane`. A group is a whole CTA (nthr >= 32) or an aligned slice of a
+// warp (nthr = 8 or 16, lanes `mask`), so several envs can share one warp.
+struct EnvInfo {
+  int env, b0, D, s0, S, j0, J;
+  int lane, nthr;
+  unsigned mask;
+};
 
-__device__ __forceinline__ EnvInfo env_info(const Params& p, int env) {
+__device__ __forceinline__ EnvInfo env_info(const Params& p, int env, int lane, int nthr, unsigned mask) {
   EnvInfo e;
   e.env = env;
   e.b0 = p.body_off[env]; e.D = p.body_off[env + 1] - e.b0;
   e.s0 = p.static_off[env]; e.S = p.static_off[env + 1] - e.s0;
   e.j0 = p.joint_off[env]; e.J = p.joint_off[env + 1] - e.j0;
+  e.lane = lane; e.nthr = nthr; e.mask = mask;
   return e;
+}
+// the whole CTA on one env
+__device__ __forceinline__ EnvInfo env_info(const Params& p, int env) {
+  return env_info(p, env, threadIdx.x, blockDim.x, 0xffffffffu);
+}
+
+// Barrier and vote over the env's threads.
+__device__ __forceinline__ void gsync(const EnvInfo& e) {
+  if (e.nthr < 32) __syncwarp(e.mask);
+  else __syncthreads();
+}
+__device__ __forceinline__ int gany(const EnvInfo& e, int v) {
+  return e.nthr < 32 ? __any_sync(e.mask, v) : __syncthreads_or(v);
 }
 
 // Exclusive block-wide prefix sum; every thread of the block must call it.
@@ -184,25 +206,38 @@ __device__ __forceinline__ int block_exscan(int v, int* scr, int* total) {
   return off + x - v;
 }
 
+// Exclusive prefix sum over the env's threads (all of them must call it);
+// warp shuffles within a group of at most 32 threads.
+__device__ __forceinline__ int group_exscan(const EnvInfo& e, int v, int* scr, int* total) {
+  if (e.nthr > 32) return block_exscan(v, scr, total);
+  int x = v;
+  for (int o = 1; o < e.nthr; o <<= 1) {
+    int y = __shfl_up_sync(e.mask, x, o, e.nthr);
+    if (e.lane >= o) x += y;
+  }
+  *total = __shfl_sync(e.mask, x, e.nthr - 1, e.nthr);
+  return x - v;
+}
+
 // ---------------------------------------------------------------------------
 // a0: stage the env's bodies and statics
 // ---------------------------------------------------------------------------
 // The env's static boxes (StaticWorld records) into the collision region.
 __device__ __forceinline__ void load_statics(const Params& p, const EnvInfo& e, const Ws& w) {
   const float4* src = p.sworld + (size_t)SW_N * e.s0;
-  for (int k = threadIdx.x; k < SW_N * e.S; k += blockDim.x) w.sw[k] = __ldg(src + k);
+  for (int k = e.lane; k < SW_N * e.S; k += e.nthr) w.sw[k] = __ldg(src + k);
 }
 
 // Per-joint solver bookkeeping into the workspace (read by every sweep).
 __device__ __forceinline__ void load_jinfo(const Params& p, const EnvInfo& e, const Ws& w) {
-  for (int k = threadIdx.x; k < e.J; k += blockDim.x) {
+  for (int k = e.lane; k < e.J; k += e.nthr) {
     const JointDesc& j = p.joints[e.j0 + k];
     w.jinfo[k] = make_int4(j.parent, j.child, j.roff, joint_row_count(j.type, j.k > 0.f || j.d > 0.f));
   }
 }
 
 __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     int g = e.b0 + i;
     float4 inv = p.binv[g];
     w.bx[i] = make_float4(p.pos[3 * g], p.pos[3 * g + 1], p.pos[3 * g + 2], inv.x);
@@ -220,12 +255,12 @@ __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
   }
   if (p.tape) {
     TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
-    for (int k = threadIdx.x; k < p.max_dof; k += blockDim.x)
+    for (int k = e.lane; k < p.max_dof; k += e.nthr)
       tape_env(p, e.env)[tl.t3 + k] = p.targets ? p.targets[(size_t)e.env * p.max_dof + k] : 0.f;
   }
   load_jinfo(p, e, w);
   load_statics(p, e, w);
-  if (threadIdx.x < MC_N) w.misc[threadIdx.x] = 0;
+  if (e.lane < MC_N) w.misc[e.lane] = 0;
 }
 
 // Collision shape of a static box from its StaticWorld record.
@@ -290,7 +325,7 @@ __device__ __forceinline__ Shape<nf> coll_shape(const Params& p, const Ws& w, co
 // a2: AABBs of the bodies (static boxes: StaticWorld)
 // ---------------------------------------------------------------------------
 __device__ void stage_aabb(const Params& p, const EnvInfo& e, const Ws& w) {
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     Shape<nf> s = coll_shape(p, w, e, i);
     AABBt<nf> b = shape_aabb(s, nf(p.off));
     w.alo[i] = make_float4(b.lo.x.v, b.lo.y.v, b.lo.z.v, 0.f);
@@ -316,8 +351,8 @@ __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w,
   const long long total = (long long)D * W - (long long)D * (D - 1) / 2;
   int count = 0;
   int status = 0;
-  for (long long base = 0; base < total; base += blockDim.x) {
-    long long k = base + threadIdx.x;
+  for (long long base = 0; base < total; base += e.nthr) {
+    long long k = base + e.lane;
     int flag = 0, pi = 0, pj = 0;
     if (k < total) {
       int lo = 0, hi = D - 1;
@@ -339,7 +374,7 @@ __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w,
       }
     }
     int tot;
-    int pre = block_exscan(flag, scr, &tot);
+    int pre = group_exscan(e, flag, scr, &tot);
     if (flag) {
       int slot = count + pre;
       if (slot < p.P) w.pairs[slot] = pi | (pj << 16);
@@ -347,11 +382,11 @@ __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w,
     count += tot;
   }
   if (count > p.P) { status |= ST_PAIR_OVERFLOW; count = p.P; }
-  if (threadIdx.x == 0) {
+  if (e.lane == 0) {
     w.misc[MC_PAIRS] = count;
     w.misc[MC_STATUS] |= status;
   }
-  __syncthreads();
+  gsync(e);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,8 +396,8 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
   const int npairs = w.misc[MC_PAIRS];
   int cbase = 0, mbase = 0;
   bool over = false;
-  for (int base = 0; base < npairs; base += blockDim.x) {
-    int idx = base + threadIdx.x;
+  for (int base = 0; base < npairs; base += e.nthr) {
+    int idx = base + e.lane;
     Pt<nf> pts[4];
     Shape<nf> Si, Sj;
     int n = 0, pi = 0, pj = 0;
@@ -375,7 +410,7 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
       n = collide(Si, Sj, nf(p.off), pts);
     }
     int tot;
-    int pre = block_exscan(n, scr, &tot);
+    int pre = group_exscan(e, n, scr, &tot);
     int start = cbase + pre;
     int kept = n;
     if (start + kept > p.C) kept = max(0, p.C - start);
@@ -391,19 +426,19 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
       }
     }
     int mt;
-    int mpre = block_exscan(kept > 0 ? 1 : 0, scr, &mt);
+    int mpre = group_exscan(e, kept > 0 ? 1 : 0, scr, &mt);
     if (idx < npairs && kept > 0)
       w.man[mbase + mpre] = make_int4(pi, pj < e.D ? pj : -1, start, kept);
     if (cbase + tot > p.C) over = true;
     cbase = min(cbase + tot, p.C);
     mbase += mt;
   }
-  if (threadIdx.x == 0) {
+  if (e.lane == 0) {
     w.misc[MC_CONTACTS] = cbase;
     w.misc[MC_MANIFOLDS] = mbase;
     if (over) w.misc[MC_STATUS] |= ST_CONTACT_OVERFLOW;
   }
-  __syncthreads();
+  gsync(e);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,7 +447,7 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
 // ---------------------------------------------------------------------------
 __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS], K = J + M;
-  if (threadIdx.x == 0) {
+  if (e.lane == 0) {
     for (int i = 0; i < e.D; ++i) w.masks[i] = 0ull;
     int ncol = 0, status = 0;
     int cnt[MAX_COLOURS + 1];
@@ -468,14 +503,14 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
       }
     }
   }
-  __syncthreads();
+  gsync(e);
 }
 
 // ---------------------------------------------------------------------------
 // a1: gravity; world inverse inertia
 // ---------------------------------------------------------------------------
 __device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 v = w.bv[i];
     v.x = v.x + p.gx * p.h; v.y = v.y + p.gy * p.h; v.z = v.z + p.gz * p.h;
     w.bv[i] = v;
@@ -771,7 +806,7 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
 
 __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
   const int nc = w.misc[MC_CONTACTS];
-  for (int t = threadIdx.x; t < e.J + nc; t += blockDim.x) {
+  for (int t = e.lane; t < e.J + nc; t += e.nthr) {
     if (t < e.J) joint_rows(p, e, w, t);
     else contact_rows(p, e, w, t - e.J);
   }
@@ -922,7 +957,7 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w,
     const int ncol = w.misc[MC_COLOURS];
     for (int c = 0; c < ncol; ++c) {
       const int c0 = w.coff[c], c1 = w.coff[c + 1];
-      for (int idx = c0 + threadIdx.x; idx < c1; idx += blockDim.x) {
+      for (int idx = c0 + e.lane; idx < c1; idx += e.nthr) {
         int k = w.corder[idx];
         int a, b;
         con_bodies(p, e, w, k, J, a, b);
@@ -933,11 +968,11 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w,
         if (b >= 0) { w.bv[b] = f4(bv.vb, 0.f); w.bw[b] = f4(bv.wb, 0.f); }
         if (p.tape) tape_lambdas(p, e, w, k, sub, it);
       }
-      __syncthreads();
+      gsync(e);
     }
   } else {
     const int K = J + w.misc[MC_MANIFOLDS];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    for (int k = e.lane; k < K; k += e.nthr) {
       int a, b;
       con_bodies(p, e, w, k, J, a, b);
       BodyVel bv = load_vel(w, a, b);
@@ -949,8 +984,8 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w,
       w.jdv[4 * k + 0] = f4(d.va, 0.f); w.jdv[4 * k + 1] = f4(d.wa, 0.f);
       w.jdv[4 * k + 2] = f4(d.vb, 0.f); w.jdv[4 * k + 3] = f4(d.wb, 0.f);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+    gsync(e);
+    for (int i = e.lane; i < e.D; i += e.nthr) {
       V3<float> dv = v3<float>(0.f, 0.f, 0.f), dw = dv;
       for (int q = w.inc_off[i]; q < w.inc_off[i + 1]; ++q) {
         int t = w.inc[q];
@@ -961,7 +996,7 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w,
       w.bv[i] = f4(f3(w.bv[i]) + dv, 0.f);
       w.bw[i] = f4(f3(w.bw[i]) + dw, 0.f);
     }
-    __syncthreads();
+    gsync(e);
   }
 }
 
@@ -969,7 +1004,7 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w,
 // a7: positions
 // ---------------------------------------------------------------------------
 __device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 x = w.bx[i], v = w.bv[i], wv = w.bw[i], q = w.bq[i];
     if (p.tape) {
       TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
@@ -992,7 +1027,7 @@ __device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws&
 // ---------------------------------------------------------------------------
 __device__ void stage_store(const Params& p, const EnvInfo& e, const Ws& w) {
   int bad = 0;
-  for (int i = threadIdx.x; i < e.D; i += blockDim.x) {
+  for (int i = e.lane; i < e.D; i += e.nthr) {
     int g = e.b0 + i;
     float4 x = w.bx[i], q = w.bq[i], v = w.bv[i], wv = w.bw[i];
     p.pos[3 * g] = x.x; p.pos[3 * g + 1] = x.y; p.pos[3 * g + 2] = x.z;
@@ -1002,8 +1037,8 @@ __device__ void stage_store(const Params& p, const EnvInfo& e, const Ws& w) {
     float s = x.x + x.y + x.z + q.x + q.y + q.z + q.w + v.x + v.y + v.z + wv.x + wv.y + wv.z;
     if (!isfinite(s)) bad = 1;
   }
-  bad = __syncthreads_or(bad);
-  if (threadIdx.x == 0) {
+  bad = gany(e, bad);
+  if (e.lane == 0) {
     int st = w.misc[MC_STATUS] | (bad ? ST_NONFINITE : 0);
     if (st) p.status[e.env] |= st;
   }

@@ -142,7 +142,8 @@ def test_plain_fused_graph_and_block_sizes_bitwise_equal(idx):
                dict(exec_form="plain", use_graph=True), dict(exec_form="substep"),
                dict(exec_form="substep", use_graph=True, threads_per_env=64),
                dict(exec_form="fused", threads_per_env=64), dict(exec_form="fused", threads_per_env=128),
-               dict(exec_form="fused", threads_per_env=256)):
+               dict(exec_form="fused", threads_per_env=256), dict(exec_form="fused", threads_per_env=16),
+               dict(exec_form="fused", threads_per_env=8, use_graph=True)):
         sim = make_sim(sc, cfg, **kw)
         for t in range(3):
             sim.step(torch.as_tensor(tg[t]).cuda())

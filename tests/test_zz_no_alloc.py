@@ -23,8 +23,8 @@ def _err(a, b):
     return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).max())
 
 
-@pytest.mark.parametrize("idx,envs", [(2, 8), (3, 16)])
-def test_static_scratch_step_matches_msh_step(idx, envs):
+@pytest.mark.parametrize("idx,envs,tpe", [(2, 8, 32), (3, 16, 32), (3, 16, 16)])
+def test_static_scratch_step_matches_msh_step(idx, envs, tpe):
     import torch
     from paper_2412_13211_b300 import _lib, scenes
     from paper_2412_13211_b300.sim import MshSim
@@ -32,7 +32,7 @@ def test_static_scratch_step_matches_msh_step(idx, envs):
     sc, cfg = scenes.make_config(idx, num_envs=envs)
     tg = torch.as_tensor(sc.target_walk(2)).cuda()
     ref = MshSim(sc, cfg)                      # regular step
-    nal = MshSim(sc, cfg)                      # same scene, stepped without allocation
+    nal = MshSim(sc, cfg, threads_per_env=tpe)   # same scene, stepped without allocation
     lib = _lib.load()
     stream = torch.cuda.current_stream()
     for t in range(2):
