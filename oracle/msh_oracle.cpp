@@ -1075,9 +1075,96 @@ template <class R> void detect(const EnvState<R>& E, const OracleCfg& cfg, Detec
   out.ncolours = nc;
 }
 
+// Contact report of one env for one step. The paper's event labels and
+// success conditions (Sec. 3.3, Appendix A.4-A.5) consume pairwise contact
+// forces F_{a,b,t} in N, the robot's cumulative collision force and a grasp
+// indicator "computed by the simulator"; it does not say how. Readings:
+//   * the force of contact c on its second body is its accumulated impulse
+//     over the step's substeps, sum_s (l_n n + l_t1 t1 + l_t2 t2), divided by
+//     the step's dt (the mean force over the step); the first body receives
+//     the opposite force;
+//   * the robot collision force of a step is the sum over robot links of the
+//     norm of each link's net force from contacts with static boxes and with
+//     dynamic bodies that are neither robot links nor the target (self
+//     contacts, the ground plane and the target itself do not count); the
+//     cumulative force adds it up step by step;
+//   * grasped(x): both fingers touch x with a force of at least f_min whose
+//     angle to the finger's opening direction (from the other finger towards
+//     it) is at most theta_max, tested as F.o >= cos(theta_max) |F|.
+template <class R> struct ReportEnv {
+  const int32_t* flags = nullptr;   // env-local body flags: bit 0 robot link, bit 1 end-effector link
+  int finger[2] = {-1, -1};
+  int target = -1;
+  double fmin = 0.0, cosmax = 1.0;
+  std::vector<V3<R>> body_force;    // net contact force per dynamic body
+  V3<R> target_force, finger_force[2];
+  R robot_inc = R(0);
+  int grasped = 0;
+};
+
+template <class R> R norm3(const V3<R>& a) { return sqrt_(a.x * a.x + a.y * a.y + a.z * a.z); }
+
+template <class R> void contact_report(const EnvState<R>& E, const OracleCfg& cfg, const Detect<R>& det,
+                                       const std::vector<V3<R>>& lam_sum, ReportEnv<R>& rp) {
+  const int D = E.D, S = E.S;
+  const V3<R> z = v3<R>(R(0), R(0), R(0));
+  const R dt = R(cfg.dt);
+  rp.body_force.assign(D, z);
+  rp.target_force = z;
+  rp.finger_force[0] = z;
+  rp.finger_force[1] = z;
+  std::vector<V3<R>> robot_net(D, z);
+  auto robot = [&](int i) { return i < D && (rp.flags[i] & 1); };
+  auto ee = [&](int i) { return i < D && (rp.flags[i] & 2); };
+  auto counts_against = [&](int other) {   // does a contact with `other` count as a robot collision?
+    if (other >= D) return other < D + S;   // static boxes count, the plane does not
+    return !robot(other) && other != rp.target;
+  };
+  for (size_t c = 0; c < det.contacts.size(); ++c) {
+    const Contact<R>& ct = det.contacts[c];
+    V3<R> t1, t2;
+    onb(ct.n, t1, t2);
+    const V3<R>& L = lam_sum[c];
+    V3<R> P = (ct.n * L.x + t1 * L.y) + t2 * L.z;
+    V3<R> F = v3<R>(P.x / dt, P.y / dt, P.z / dt);   // on b; -F on a
+    const int a = ct.a, b = ct.b;
+    rp.body_force[a] = rp.body_force[a] - F;
+    if (b < D) rp.body_force[b] = rp.body_force[b] + F;
+    if (robot(a) && counts_against(b)) robot_net[a] = robot_net[a] - F;
+    if (robot(b) && counts_against(a)) robot_net[b] = robot_net[b] + F;
+    if (rp.target >= 0) {
+      if (ee(a) && b == rp.target) rp.target_force = rp.target_force + F;
+      if (ee(b) && a == rp.target) rp.target_force = rp.target_force - F;
+      for (int f = 0; f < 2; ++f) {
+        const int fb = rp.finger[f];
+        if (fb < 0) continue;
+        if (a == fb && b == rp.target) rp.finger_force[f] = rp.finger_force[f] - F;
+        if (b == fb && a == rp.target) rp.finger_force[f] = rp.finger_force[f] + F;
+      }
+    }
+  }
+  rp.robot_inc = R(0);
+  for (int i = 0; i < D; ++i)
+    if (robot(i)) rp.robot_inc = rp.robot_inc + norm3(robot_net[i]);
+  rp.grasped = 0;
+  if (rp.target >= 0 && rp.finger[0] >= 0 && rp.finger[1] >= 0) {
+    int ok = 1;
+    for (int f = 0; f < 2; ++f) {
+      V3<R> o = E.body[rp.finger[f]].x - E.body[rp.finger[1 - f]].x;   // opening direction (unnormalised)
+      const V3<R>& Ff = rp.finger_force[f];
+      R fn = norm3(Ff);
+      R on = norm3(o);
+      if (!(fn >= R(rp.fmin)) || !(dot(Ff, o) >= R(rp.cosmax) * fn * on)) ok = 0;
+    }
+    rp.grasped = ok;
+  }
+}
+
 // One step of one env: detection at the step start, then per substep:
 // gravity, rows from the current poses, N solver iterations, position update.
-template <class R> int step_env(EnvState<R>& E, const OracleCfg& cfg, const R* tgt, Detect<R>* dbg) {
+// With `rp`, the contact report of the step is computed at its end.
+template <class R> int step_env(EnvState<R>& E, const OracleCfg& cfg, const R* tgt, Detect<R>* dbg,
+                                ReportEnv<R>* rp = nullptr) {
   Detect<R> det;
   detect(E, cfg, det);
   int D = E.D;
@@ -1090,6 +1177,7 @@ template <class R> int step_env(EnvState<R>& E, const OracleCfg& cfg, const R* t
   sv.Iw.resize(D);
   sv.split.assign(D, R(1));
   bool jacobi = cfg.mode == 1;
+  std::vector<V3<R>> lam_sum;
   if (jacobi) {
     std::vector<int> cnt(D, 0);
     for (int k = 0; k < E.J; ++k) {
@@ -1141,6 +1229,18 @@ template <class R> int step_env(EnvState<R>& E, const OracleCfg& cfg, const R* t
         for (int i = 0; i < D; ++i) { E.body[i].v = E.body[i].v + dv[i]; E.body[i].w = E.body[i].w + dw[i]; }
       }
     }
+    // accumulated impulse (normal, t1, t2) of every contact point over the substeps
+    if (rp) {
+      if (s == 0) lam_sum.assign(det.contacts.size(), v3<R>(R(0), R(0), R(0)));
+      for (size_t m = 0; m < det.manifolds.size(); ++m) {
+        const Con& cn = sv.cons[E.J + m];
+        for (int k = 0; k < det.manifolds[m].count; ++k) {
+          const int r = cn.first + 3 * k;
+          V3<R>& L = lam_sum[det.manifolds[m].first + k];
+          L = L + v3<R>(sv.rows[r].lam, sv.rows[r + 1].lam, sv.rows[r + 2].lam);
+        }
+      }
+    }
     // a7: x += h v; q <- normalise(q + h/2 (0,w) q)
     for (int i = 0; i < D; ++i) {
       Body<R>& b = E.body[i];
@@ -1152,6 +1252,10 @@ template <class R> int step_env(EnvState<R>& E, const OracleCfg& cfg, const R* t
       R nrm = sqrt_(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
       b.q.w = q.w / nrm; b.q.x = q.x / nrm; b.q.y = q.y / nrm; b.q.z = q.z / nrm;
     }
+  }
+  if (rp) {
+    if (S == 0) lam_sum.assign(det.contacts.size(), v3<R>(R(0), R(0), R(0)));
+    contact_report(E, cfg, det, lam_sum, *rp);
   }
   int st = det.status;
   for (int i = 0; i < D; ++i) {
@@ -1246,6 +1350,69 @@ int step_batch(const OracleScene* sc, const OracleCfg* cfg, R* pos, R* quat, R* 
       st |= step_env(S, *cfg, tg.data(), (Detect<R>*)nullptr);
     }
     store_env<R, R>(*sc, e, S, pos, quat, lv, av);
+    if (status) status[e] = st;
+  }
+  return 0;
+}
+
+}  // namespace orc
+
+extern "C" struct OracleReportSpec {
+  const int32_t* body_flags;   // [B]: bit 0 robot link, bit 1 end-effector link
+  const int32_t* fingers;      // [E][2] env-local ids (-1: none)
+  const int32_t* target;       // [E] env-local id (-1: none)
+  double grasp_min_force;      // N
+  double grasp_max_angle_deg;
+};
+
+namespace orc {
+
+// `nsteps` steps with the contact report of the last step written out and the
+// robot collision force of every step added to robot_force [E].
+template <class R>
+int step_report_batch(const OracleScene* sc, const OracleCfg* cfg, R* pos, R* quat, R* lv, R* av, const float* targets,
+                      int nsteps, int32_t* status, int nthreads, const OracleReportSpec* spec, R* body_force,
+                      R* target_force, R* finger_force, R* robot_force, int32_t* grasped) {
+  int E = sc->num_envs;
+  int md = sc->max_dof > 0 ? sc->max_dof : 1;
+  const double cosmax = std::cos(spec->grasp_max_angle_deg * 3.14159265358979323846 / 180.0);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int e = 0; e < E; ++e) {
+    EnvState<R> S;
+    load_env<R, R>(*sc, e, pos, quat, lv, av, nullptr, S);
+    const int b0 = sc->body_off[e];
+    ReportEnv<R> rp;
+    rp.flags = spec->body_flags + b0;
+    rp.finger[0] = spec->fingers ? spec->fingers[2 * e] : -1;
+    rp.finger[1] = spec->fingers ? spec->fingers[2 * e + 1] : -1;
+    rp.target = spec->target ? spec->target[e] : -1;
+    rp.fmin = spec->grasp_min_force;
+    rp.cosmax = cosmax;
+    int st = 0;
+    std::vector<R> tg(md);
+    for (int t = 0; t < nsteps; ++t) {
+      const float* tt = targets ? targets + ((size_t)t * E + e) * md : nullptr;
+      for (int k = 0; k < md; ++k) tg[k] = tt ? R(tt[k]) : R(0);
+      st |= step_env(S, *cfg, tg.data(), (Detect<R>*)nullptr, &rp);
+      robot_force[e] = robot_force[e] + rp.robot_inc;
+    }
+    store_env<R, R>(*sc, e, S, pos, quat, lv, av);
+    for (int i = 0; i < S.D; ++i) {
+      body_force[3 * (b0 + i)] = rp.body_force[i].x;
+      body_force[3 * (b0 + i) + 1] = rp.body_force[i].y;
+      body_force[3 * (b0 + i) + 2] = rp.body_force[i].z;
+    }
+    target_force[3 * e] = rp.target_force.x; target_force[3 * e + 1] = rp.target_force.y;
+    target_force[3 * e + 2] = rp.target_force.z;
+    for (int f = 0; f < 2; ++f) {
+      finger_force[6 * e + 3 * f] = rp.finger_force[f].x;
+      finger_force[6 * e + 3 * f + 1] = rp.finger_force[f].y;
+      finger_force[6 * e + 3 * f + 2] = rp.finger_force[f].z;
+    }
+    grasped[e] = rp.grasped;
     if (status) status[e] = st;
   }
   return 0;
@@ -1404,6 +1571,23 @@ int oracle_grad_f64(const OracleScene* sc, const OracleCfg* cfg, const double* p
                     double* loss, double* dloss, int32_t* status, int nthreads) {
   return orc::grad_batch(sc, cfg, pos, quat, lv, av, targets, nsteps, goal_body, goal_pos, ndir, dvel, dtg, dmass,
                          loss, dloss, status, nthreads);
+}
+// `nsteps` steps with the contact report (see contact_report): body_force [B][3],
+// target_force [E][3] and finger_force [E][2][3] of the last step, grasped [E];
+// robot_force [E] accumulates every step's robot collision force.
+int oracle_step_report_f32(const OracleScene* sc, const OracleCfg* cfg, float* pos, float* quat, float* lv, float* av,
+                           const float* targets, int nsteps, int32_t* status, int nthreads,
+                           const OracleReportSpec* spec, float* body_force, float* target_force, float* finger_force,
+                           float* robot_force, int32_t* grasped) {
+  return orc::step_report_batch<float>(sc, cfg, pos, quat, lv, av, targets, nsteps, status, nthreads, spec,
+                                       body_force, target_force, finger_force, robot_force, grasped);
+}
+int oracle_step_report_f64(const OracleScene* sc, const OracleCfg* cfg, double* pos, double* quat, double* lv,
+                           double* av, const float* targets, int nsteps, int32_t* status, int nthreads,
+                           const OracleReportSpec* spec, double* body_force, double* target_force,
+                           double* finger_force, double* robot_force, int32_t* grasped) {
+  return orc::step_report_batch<double>(sc, cfg, pos, quat, lv, av, targets, nsteps, status, nthreads, spec,
+                                        body_force, target_force, finger_force, robot_force, grasped);
 }
 int oracle_max_threads(void) {
 #ifdef _OPENMP

@@ -70,6 +70,9 @@ def load():
         lib.oracle_grad_f64.argtypes = [P, P, P, P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, C.c_int]
         lib.oracle_grad_f64.restype = C.c_int
         lib.oracle_max_threads.restype = C.c_int
+        for fn in (lib.oracle_step_report_f32, lib.oracle_step_report_f64):
+            fn.argtypes = [P, P, P, P, P, P, P, C.c_int, P, C.c_int, P, P, P, P, P, P]
+            fn.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -147,6 +150,53 @@ def step(scene, cfg, state, targets=None, nsteps: int = 1, precision: str = "f32
     if rc != 0:
         raise RuntimeError(f"oracle step failed: {rc}")
     return tuple(st), status
+
+
+class _ReportSpec(C.Structure):
+    _fields_ = [("body_flags", C.c_void_p), ("fingers", C.c_void_p), ("target", C.c_void_p),
+                ("grasp_min_force", C.c_double), ("grasp_max_angle_deg", C.c_double)]
+
+
+@dataclass
+class OracleReport:
+    body_force: np.ndarray     # [B,3] net contact force on each body, last step (N)
+    target_force: np.ndarray   # [E,3] force on the target from end-effector links
+    finger_force: np.ndarray   # [E,2,3] force on each finger from the target
+    robot_force: np.ndarray    # [E] cumulative robot collision force (N)
+    grasped: np.ndarray        # [E]
+
+
+def step_report(scene, cfg, state, targets, nsteps, body_flags, fingers, target, grasp_min_force=0.5,
+                grasp_max_angle_deg=85.0, robot_force=None, precision: str = "f32", threads: int = 0):
+    """`nsteps` steps with the contact report (forces of the last step; the robot
+    collision force of every step added to `robot_force`, zeros if None).
+    Returns (new_state, status[E], OracleReport)."""
+    lib = load()
+    dt = np.float32 if precision == "f32" else np.float64
+    st = [np.ascontiguousarray(a, dtype=dt).copy() for a in state]
+    E, B = scene.num_envs, scene.num_bodies
+    md = max(scene.max_dof, 1)
+    if targets is None:
+        targets = np.zeros((nsteps, E, md), np.float32)
+    targets = np.ascontiguousarray(targets, dtype=np.float32).reshape(-1, E, md)
+    flags = np.ascontiguousarray(body_flags, np.int32)
+    fing = np.ascontiguousarray(fingers, np.int32).reshape(E, 2)
+    tgt = np.ascontiguousarray(target, np.int32).reshape(E)
+    spec = _ReportSpec(flags.ctypes.data, fing.ctypes.data, tgt.ctypes.data, float(grasp_min_force),
+                       float(grasp_max_angle_deg))
+    rep = OracleReport(np.zeros((B, 3), dt), np.zeros((E, 3), dt), np.zeros((E, 2, 3), dt),
+                       np.zeros(E, dt) if robot_force is None else np.ascontiguousarray(robot_force, dt).copy(),
+                       np.zeros(E, np.int32))
+    status = np.zeros(E, np.int32)
+    keep = _Keep(scene)
+    c = _cfg(cfg)
+    fn = lib.oracle_step_report_f32 if precision == "f32" else lib.oracle_step_report_f64
+    rc = fn(C.byref(keep.struct), C.byref(c), _ptr(st[0]), _ptr(st[1]), _ptr(st[2]), _ptr(st[3]), _ptr(targets),
+            int(nsteps), _ptr(status), int(threads), C.byref(spec), _ptr(rep.body_force), _ptr(rep.target_force),
+            _ptr(rep.finger_force), _ptr(rep.robot_force), _ptr(rep.grasped))
+    if rc != 0:
+        raise RuntimeError(f"oracle step_report failed: {rc}")
+    return tuple(st), status, rep
 
 
 @dataclass
