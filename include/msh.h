@@ -204,6 +204,47 @@ int msh_step_static_scratch(msh_handle* h, const msh_state* st, const float* joi
                             int32_t substeps, void* stream);
 
 /*
+ * Contact report, written by every msh_step (and msh_step_static_scratch)
+ * while enabled; recorded steps (msh_set_tape) do not write it. It carries
+ * what the paper's subtask success conditions and event labels consume
+ * (Sec. 3.3, Appendix A.4-A.5): pairwise contact forces F_{a,b,t} in N, the
+ * robot's cumulative collision force, and whether the target is grasped.
+ *   - The force of a contact on its second body is its impulse
+ *     (l_n n + l_t1 t1 + l_t2 t2) summed over the step's substeps and divided
+ *     by dt; the first body receives the opposite force.
+ *   - body_force [num_bodies][3]: the net contact force on each body.
+ *   - target_force [num_envs][3]: the force on the target from the
+ *     end-effector links.
+ *   - finger_force [num_envs][2][3]: the force on each finger from the target.
+ *   - robot_force [num_envs]: each step ADDS the sum over robot links of the
+ *     norm of the link's net force from contacts with static boxes and with
+ *     bodies that are neither robot links nor the target (the caller zeroes it
+ *     at episode start).
+ *   - grasped [num_envs]: 1 when both fingers feel at least grasp_min_force
+ *     from the target, each within grasp_max_angle_deg of the finger's opening
+ *     direction (from the other finger towards it).
+ * body_flags, fingers and target are HOST arrays read during the call (not
+ * retained); fingers and target hold env-local body ids (-1: none; NULL: all
+ * -1). The outputs are caller-owned DEVICE pointers kept by the handle; any
+ * may be NULL (not written). msh_set_report(h, NULL) turns the report off.
+ * Returns MSH_ERR_INVALID_ARG on a NULL body_flags or out-of-range ids.
+ */
+typedef struct msh_report_desc {
+  const int32_t* body_flags;   /* [num_bodies]: bit 0 robot link, bit 1 end-effector link */
+  const int32_t* fingers;      /* [num_envs][2] */
+  const int32_t* target;       /* [num_envs] */
+  float grasp_min_force;       /* N (>= 0) */
+  float grasp_max_angle_deg;   /* [0, 180] */
+  float* body_force;
+  float* target_force;
+  float* finger_force;
+  float* robot_force;
+  int32_t* grasped;
+} msh_report_desc;
+
+int msh_set_report(msh_handle* h, const msh_report_desc* desc);
+
+/*
  * Differentiation (reverse mode). msh_set_tape(h, n), n > 0, makes room for
  * n recorded steps (reusing a large enough tape) and starts recording
  * (coloured solver and zero restitution only); n = 0 stops recording and

@@ -17,7 +17,7 @@ EXEC_PLAIN, EXEC_FUSED, EXEC_SUBSTEP = 0, 1, 2
 EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_step", "msh_step_host",
            "msh_detect", "msh_get_status", "msh_clear_status", "msh_scratch_bytes", "msh_workspace_bytes",
            "msh_launches_per_step", "msh_step_static_scratch", "msh_set_tape", "msh_tape_reset",
-           "msh_tape_count", "msh_backward")
+           "msh_tape_count", "msh_backward", "msh_set_report")
 
 
 class SceneDesc(C.Structure):
@@ -34,6 +34,13 @@ class SolverCfg(C.Structure):
                 ("gravity", C.c_float * 3), ("friction", C.c_float), ("restitution", C.c_float),
                 ("contact_offset", C.c_float), ("baumgarte", C.c_float), ("joint_baumgarte", C.c_float),
                 ("slop", C.c_float), ("max_contacts", C.c_int32), ("max_pairs", C.c_int32)]
+
+
+class ReportDesc(C.Structure):
+    _fields_ = [("body_flags", C.c_void_p), ("fingers", C.c_void_p), ("target", C.c_void_p),
+                ("grasp_min_force", C.c_float), ("grasp_max_angle_deg", C.c_float),
+                ("body_force", C.c_void_p), ("target_force", C.c_void_p), ("finger_force", C.c_void_p),
+                ("robot_force", C.c_void_p), ("grasped", C.c_void_p)]
 
 
 class State(C.Structure):
@@ -64,6 +71,7 @@ def load(build_if_missing: bool = True):
     lib.msh_step_host.argtypes = [P, P, P, P, P, P, F, I32, P]
     lib.msh_step_static_scratch.argtypes = [P, P, P, F, I32, P]
     lib.msh_set_tape.argtypes = [P, I32]
+    lib.msh_set_report.argtypes = [P, P]
     lib.msh_tape_reset.argtypes = [P]
     lib.msh_tape_count.argtypes = [P]
     lib.msh_tape_count.restype = C.c_int32

@@ -66,11 +66,15 @@ __global__ void k_solve(Params p) {
 }
 __global__ void k_intpos(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
-  stage_integrate_pos(p, e, plain_ws(p, blockIdx.x), p.sub);
+  Ws w = plain_ws(p, blockIdx.x);
+  stage_accum_impulse(p, e, w, p.sub);
+  stage_integrate_pos(p, e, w, p.sub);
 }
 __global__ void k_store(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
-  stage_store(p, e, plain_ws(p, blockIdx.x));
+  Ws w = plain_ws(p, blockIdx.x);
+  stage_report(p, e, w);
+  stage_store(p, e, w);
 }
 // One whole substep per env (substep-fused form): gravity, rows, N sweeps,
 // positions, on the env's HBM workspace.
@@ -82,6 +86,7 @@ __global__ void k_substep(Params p) {
   stage_prep(p, e, w);
   __syncthreads();
   for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w, p.sub, it);
+  stage_accum_impulse(p, e, w, p.sub);
   stage_integrate_pos(p, e, w, p.sub);
 }
 
@@ -125,9 +130,11 @@ __device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
       stage_prep(p, e, w);
       gsync(e);
       for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w, s, it);
+      stage_accum_impulse(p, e, w, s);
       stage_integrate_pos(p, e, w, s);
       gsync(e);
     }
+    stage_report(p, e, w);
     stage_store(p, e, w);
     gsync(e);
   }
@@ -373,7 +380,7 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi) {
   L.hot_bytes = align16(o);
   // cold part: offsets relative to the cold base
   o = 0;
-  L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4);
+  L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4); L.crep = take(C * f4);
   L.cold_bytes = align16(o);
   L.bytes = L.hot_bytes + L.cold_bytes;
   return L;
@@ -411,6 +418,12 @@ struct msh_handle {
   float4 *d_bdims = nullptr, *d_binv = nullptr;
   float *d_static_pose = nullptr, *d_static_half = nullptr;
   float4* d_sworld = nullptr;
+  std::vector<int> body_off_host;   // CSR body offsets (host copy, for argument checks)
+  // contact report (msh_set_report)
+  int rep_on = 0;
+  int *d_rep_flags = nullptr, *d_rep_fingers = nullptr, *d_rep_target = nullptr;
+  float rep_fmin = 0.f, rep_cosmax = 1.f;
+  msh_report_desc rep{};
   JointDesc* d_joints = nullptr;
   int* d_status = nullptr;
   int* d_queue = nullptr;
@@ -471,6 +484,11 @@ Params make_params(const msh_handle* h, const msh_state* st, const float* target
   p.static_pose = h->d_static_pose; p.static_half = h->d_static_half; p.sworld = h->d_sworld;
   p.joints = h->d_joints; p.env_order = h->d_env_order;
   p.G = h->tpe;
+  p.rep_on = h->rep_on;
+  p.rep_flags = h->d_rep_flags; p.rep_fingers = h->d_rep_fingers; p.rep_target = h->d_rep_target;
+  p.rep_fmin = h->rep_fmin; p.rep_cosmax = h->rep_cosmax;
+  p.rep_body_force = h->rep.body_force; p.rep_target_force = h->rep.target_force;
+  p.rep_finger_force = h->rep.finger_force; p.rep_robot_force = h->rep.robot_force; p.rep_grasped = h->rep.grasped;
   p.dt = dt; p.S = S; p.h = dt / (float)S; p.N = h->cfg.iterations; p.mode = h->cfg.mode;
   p.gx = h->cfg.gravity[0]; p.gy = h->cfg.gravity[1]; p.gz = h->cfg.gravity[2];
   p.mu = h->cfg.friction; p.rest = h->cfg.restitution; p.off = h->cfg.contact_offset;
@@ -665,7 +683,8 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
     Rm = std::max(Rm, roff);
   }
   msh_handle* h = new msh_handle();
-  h->E = E; h->B = B; h->S = S; h->J = J; h->max_dof = d->max_dof; h->cfg = *cfg;
+  h->E = E; h->B = B; h->S = S; h->J = J;
+  h->body_off_host.assign(d->body_off, d->body_off + E + 1); h->max_dof = d->max_dof; h->cfg = *cfg;
   h->Dm = std::max(Dm, 1); h->Sm = std::max(Sm, 1); h->Jm = std::max(Jm, 1);
   h->L = make_layout(h->Dm, h->Sm, h->Jm, Rm, cfg->max_pairs, cfg->max_contacts, cfg->mode == MSH_MODE_JACOBI);
   auto bail = [&](int code) { msh_destroy(h); return code; };
@@ -735,7 +754,8 @@ void msh_destroy(msh_handle* h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   void* ptrs[] = {h->d_body_off, h->d_static_off, h->d_joint_off, h->d_env_order, h->d_bdims, h->d_binv,
                   h->d_static_pose, h->d_static_half, h->d_sworld, h->d_joints, h->d_status, h->d_queue, h->d_targets,
-                  h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused, h->d_tape, h->d_aws};
+                  h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused, h->d_tape, h->d_aws,
+                  h->d_rep_flags, h->d_rep_fingers, h->d_rep_target};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -772,6 +792,7 @@ static int step_impl(msh_handle* h, const msh_state* st, const float* targets, f
     if (substeps != h->cfg.substeps) return fail(MSH_ERR_INVALID_ARG, "recorded steps must use the configured substeps");
     Params p = make_params(h, st, targets, dt, substeps);
     p.tape = h->d_tape + (long long)h->tape_count * h->E * h->tape_slab;
+    p.rep_on = 0;   // recorded re-runs of a rollout do not repeat the report
     int rc = enqueue_step(h, p, s);
     if (rc) return rc;
     h->tape_count++;
@@ -943,6 +964,49 @@ int msh_get_status(msh_handle* h, int32_t* status_host, void* stream) {
 int msh_clear_status(msh_handle* h, void* stream) {
   if (!h) return fail(MSH_ERR_INVALID_ARG, "NULL handle");
   CK(cudaMemsetAsync(h->d_status, 0, (size_t)h->E * 4, (cudaStream_t)stream));
+  return MSH_OK;
+}
+
+int msh_set_report(msh_handle* h, const msh_report_desc* d) {
+  if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
+  if (d) {
+    if (!d->body_flags) return fail(MSH_ERR_INVALID_ARG, "body_flags is NULL");
+    if (!(d->grasp_min_force >= 0.f) || !(d->grasp_max_angle_deg >= 0.f) || !(d->grasp_max_angle_deg <= 180.f))
+      return fail(MSH_ERR_INVALID_ARG, "grasp_min_force must be >= 0 and grasp_max_angle_deg in [0, 180]");
+    for (int e = 0; e < h->E; ++e) {
+      const int D = h->body_off_host[e + 1] - h->body_off_host[e];
+      for (int k = 0; k < 3; ++k) {
+        const int v = k < 2 ? (d->fingers ? d->fingers[2 * e + k] : -1) : (d->target ? d->target[e] : -1);
+        if (v < -1 || v >= D)
+          return fail(MSH_ERR_INVALID_ARG, "env " + std::to_string(e) + ": finger or target id out of range");
+      }
+    }
+  }
+  cudaDeviceSynchronize();
+  drop_graph(h);
+  int* old[] = {h->d_rep_flags, h->d_rep_fingers, h->d_rep_target};
+  const size_t sizes[] = {(size_t)std::max(h->B, 1), 2 * (size_t)h->E, (size_t)h->E};
+  for (int k = 0; k < 3; ++k)
+    if (old[k]) { cudaFree(old[k]); h->bytes -= (int64_t)sizes[k] * 4; }
+  h->d_rep_flags = h->d_rep_fingers = h->d_rep_target = nullptr;
+  h->rep_on = 0;
+  h->rep = msh_report_desc{};
+  if (!d) return MSH_OK;
+  std::vector<int> fing(2 * (size_t)h->E, -1), tgt(h->E, -1), flags(std::max(h->B, 1), 0);
+  for (int e = 0; e < h->E; ++e) {
+    for (int f = 0; f < 2; ++f) fing[2 * e + f] = d->fingers ? d->fingers[2 * e + f] : -1;
+    tgt[e] = d->target ? d->target[e] : -1;
+  }
+  for (int g = 0; g < h->B; ++g) flags[g] = d->body_flags[g];
+  int rc;
+  if ((rc = upload(h, &h->d_rep_flags, flags.data(), flags.size()))) return rc;
+  if ((rc = upload(h, &h->d_rep_fingers, fing.data(), fing.size()))) return rc;
+  if ((rc = upload(h, &h->d_rep_target, tgt.data(), tgt.size()))) return rc;
+  h->rep = *d;
+  h->rep.body_flags = h->rep.fingers = h->rep.target = nullptr;   // host arrays are not retained
+  h->rep_fmin = d->grasp_min_force;
+  h->rep_cosmax = (float)std::cos((double)d->grasp_max_angle_deg * 3.14159265358979323846 / 180.0);
+  h->rep_on = 1;
   return MSH_OK;
 }
 

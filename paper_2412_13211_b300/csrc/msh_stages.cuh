@@ -40,7 +40,7 @@ struct Layout {
   int Dm, Sm, Jm, P, C, K, R;   // R: joint solver rows of the largest env
   int bx, bq, bv, bw, bIw0, bIw1;
   int sw, alo, ahi;
-  int pairs, cn, cra, crb, cid;
+  int pairs, cn, cra, crb, cid, crep;
   int kra, krb, klam;
   int man, jr, jinfo, ccol, corder, coff, masks;
   int jdv, inc_off, inc, misc;
@@ -84,6 +84,17 @@ struct Params {
   float* tape;
   long long tape_slab;   // floats per env slab of one recorded step
   int tape_Rm;           // row slots per env: ROWS_PER_JOINT * Jm + 3 * C
+  // contact report (when rep_on; see stage_report)
+  int rep_on;
+  const int* rep_flags;      // per body: bit 0 robot link, bit 1 end-effector link
+  const int* rep_fingers;    // per env: two env-local finger ids (-1: none)
+  const int* rep_target;     // per env: env-local target id (-1: none)
+  float rep_fmin, rep_cosmax;
+  float* rep_body_force;     // [B][3]
+  float* rep_target_force;   // [E][3]
+  float* rep_finger_force;   // [E][2][3]
+  float* rep_robot_force;    // [E], accumulated
+  int* rep_grasped;          // [E]
   // plain-form launch indices
   int sub, it;
 };
@@ -117,6 +128,7 @@ struct Ws {
   float4 *alo, *ahi;  // body AABBs
   int* pairs;
   float4 *cn, *cra, *crb;
+  float4* crep;       // contact report: impulse sums over the substeps, then forces
   int* cid;
   float4 *kra, *krb, *klam;
   int4* man;
@@ -137,6 +149,7 @@ __device__ __forceinline__ Ws make_ws(char* b, char* cold, const Layout& L) {
   w.pairs = (int*)(b + L.pairs);
   w.cn = (float4*)(b + L.cn);
   w.cra = (float4*)(cold + L.cra); w.crb = (float4*)(cold + L.crb); w.cid = (int*)(cold + L.cid);
+  w.crep = (float4*)(cold + L.crep);
   w.kra = (float4*)(b + L.kra); w.krb = (float4*)(b + L.krb); w.klam = (float4*)(b + L.klam);
   w.man = (int4*)(b + L.man); w.jr = (float4*)(b + L.jr); w.jinfo = (int4*)(b + L.jinfo);
   w.ccol = (int*)(b + L.ccol); w.corder = (int*)(b + L.corder); w.coff = (int*)(b + L.coff);
@@ -1020,6 +1033,125 @@ __device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws&
     w.bx[i] = x;
     w.bq[i] = make_float4(qw / nrm, qx / nrm, qy / nrm, qz / nrm);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Contact report (optional, once per step). The paper's success conditions
+// and event labels (Sec. 3.3, Appendix A.4-A.5) use pairwise contact forces,
+// the robot's cumulative collision force and a grasp indicator; the readings
+// (identical in the oracle):
+//   * contact c's force on its second body is its impulse (l_n n + l_t1 t1 +
+//     l_t2 t2) summed over the step's substeps, divided by dt; the first body
+//     receives the opposite;
+//   * a step's robot collision force is the sum over robot links of the norm
+//     of each link's net force from contacts with static boxes and with bodies
+//     that are neither robot links nor the target;
+//   * grasped: both fingers feel a force of at least f_min from the target,
+//     within theta_max of the finger's opening direction (F.o >= cos |F||o|).
+// ---------------------------------------------------------------------------
+// After substep `sub`'s sweeps: add each contact's lambdas to its impulse sum.
+__device__ void stage_accum_impulse(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
+  if (!p.rep_on) return;
+  const int nc = w.misc[MC_CONTACTS];
+  for (int c = e.lane; c < nc; c += e.nthr) {
+    const float4 l = w.klam[c];
+    const float4 a = sub == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : w.crep[c];
+    w.crep[c] = make_float4(a.x + l.x, a.y + l.y, a.z + l.z, 0.f);
+  }
+}
+
+__device__ __forceinline__ float norm3f(float x, float y, float z) { return sqrtf(x * x + y * y + z * z); }
+
+__device__ __forceinline__ bool rep_counts(const Params& p, const EnvInfo& e, int other, int target) {
+  if (other >= e.D) return other < e.D + e.S;   // static boxes count, the plane does not
+  return !(p.rep_flags[e.b0 + other] & 1) && other != target;
+}
+
+// At the end of the step (final poses); plain float arithmetic in the
+// oracle's order (the library is built without FMA contraction).
+__device__ void stage_report(const Params& p, const EnvInfo& e, const Ws& w) {
+  if (!p.rep_on) return;
+  const int nc = w.misc[MC_CONTACTS];
+  const int D = e.D;
+  const int target = p.rep_target ? p.rep_target[e.env] : -1;
+  for (int c = e.lane; c < nc; c += e.nthr) {
+    const float4 n4 = w.cn[c], L = w.crep[c];
+    V3<float> n = f3(n4), t1, t2;
+    onb(n, t1, t2);
+    const float px = (n.x * L.x + t1.x * L.y) + t2.x * L.z;
+    const float py = (n.y * L.x + t1.y * L.y) + t2.y * L.z;
+    const float pz = (n.z * L.x + t1.z * L.y) + t2.z * L.z;
+    w.crep[c] = make_float4(px / p.dt, py / p.dt, pz / p.dt, 0.f);   // force on the second body
+  }
+  gsync(e);
+  for (int i = e.lane; i < D; i += e.nthr) {
+    const bool robot = p.rep_flags[e.b0 + i] & 1;
+    float fx = 0.f, fy = 0.f, fz = 0.f, rx = 0.f, ry = 0.f, rz = 0.f;
+    for (int c = 0; c < nc; ++c) {
+      const int id = w.cid[c], a = id & 0xffff, b = id >> 16;
+      if (a != i && b != i) continue;
+      const float4 F = w.crep[c];
+      if (a == i) {
+        fx = fx - F.x; fy = fy - F.y; fz = fz - F.z;
+        if (robot && rep_counts(p, e, b, target)) { rx = rx - F.x; ry = ry - F.y; rz = rz - F.z; }
+      } else {
+        fx = fx + F.x; fy = fy + F.y; fz = fz + F.z;
+        if (robot && rep_counts(p, e, a, target)) { rx = rx + F.x; ry = ry + F.y; rz = rz + F.z; }
+      }
+    }
+    if (p.rep_body_force) {
+      float* o = p.rep_body_force + 3 * (size_t)(e.b0 + i);
+      o[0] = fx; o[1] = fy; o[2] = fz;
+    }
+    w.bIw0[i] = make_float4(rx, ry, rz, 0.f);   // free after the last substep
+  }
+  gsync(e);
+  if (e.lane == 0) {
+    float inc = 0.f;
+    for (int i = 0; i < D; ++i)
+      if (p.rep_flags[e.b0 + i] & 1) { const float4 r = w.bIw0[i]; inc = inc + norm3f(r.x, r.y, r.z); }
+    if (p.rep_robot_force) p.rep_robot_force[e.env] = p.rep_robot_force[e.env] + inc;
+    const int f0 = p.rep_fingers ? p.rep_fingers[2 * e.env] : -1;
+    const int f1 = p.rep_fingers ? p.rep_fingers[2 * e.env + 1] : -1;
+    const int fing[2] = {f0, f1};
+    float T[3] = {0.f, 0.f, 0.f}, Fg[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    if (target >= 0) {
+      for (int c = 0; c < nc; ++c) {
+        const int id = w.cid[c], a = id & 0xffff, b = id >> 16;
+        const float4 F = w.crep[c];
+        const bool ee_a = a < D && (p.rep_flags[e.b0 + a] & 2), ee_b = b < D && (p.rep_flags[e.b0 + b] & 2);
+        if (ee_a && b == target) { T[0] = T[0] + F.x; T[1] = T[1] + F.y; T[2] = T[2] + F.z; }
+        if (ee_b && a == target) { T[0] = T[0] - F.x; T[1] = T[1] - F.y; T[2] = T[2] - F.z; }
+        for (int f = 0; f < 2; ++f) {
+          if (fing[f] < 0) continue;
+          if (a == fing[f] && b == target) { Fg[f][0] = Fg[f][0] - F.x; Fg[f][1] = Fg[f][1] - F.y; Fg[f][2] = Fg[f][2] - F.z; }
+          if (b == fing[f] && a == target) { Fg[f][0] = Fg[f][0] + F.x; Fg[f][1] = Fg[f][1] + F.y; Fg[f][2] = Fg[f][2] + F.z; }
+        }
+      }
+    }
+    int grasped = 0;
+    if (target >= 0 && f0 >= 0 && f1 >= 0) {
+      int ok = 1;
+      for (int f = 0; f < 2; ++f) {
+        const float4 xa = w.bx[fing[f]], xb = w.bx[fing[1 - f]];
+        const float ox = xa.x - xb.x, oy = xa.y - xb.y, oz = xa.z - xb.z;   // opening direction
+        const float fn = norm3f(Fg[f][0], Fg[f][1], Fg[f][2]), on = norm3f(ox, oy, oz);
+        const float d = Fg[f][0] * ox + Fg[f][1] * oy + Fg[f][2] * oz;
+        if (!(fn >= p.rep_fmin) || !(d >= p.rep_cosmax * fn * on)) ok = 0;
+      }
+      grasped = ok;
+    }
+    if (p.rep_target_force) {
+      float* o = p.rep_target_force + 3 * (size_t)e.env;
+      o[0] = T[0]; o[1] = T[1]; o[2] = T[2];
+    }
+    if (p.rep_finger_force) {
+      float* o = p.rep_finger_force + 6 * (size_t)e.env;
+      for (int f = 0; f < 2; ++f) { o[3 * f] = Fg[f][0]; o[3 * f + 1] = Fg[f][1]; o[3 * f + 2] = Fg[f][2]; }
+    }
+    if (p.rep_grasped) p.rep_grasped[e.env] = grasped;
+  }
+  gsync(e);
 }
 
 // ---------------------------------------------------------------------------

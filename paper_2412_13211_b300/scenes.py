@@ -141,6 +141,31 @@ class Scene:
         return (np.diff(self.body_off), np.diff(self.static_off),
                 np.diff(self.joint_off))
 
+    def report_spec(self):
+        """Inputs of the contact report from the joint structure: robot links
+        are the bodies that joints connect (bit 0), the fingers are the children
+        of each env's first two prismatic joints, the end-effector links are
+        the fingers and their parent (bit 1), the target is the goal body.
+        Returns (body_flags [B], fingers [E,2], target [E])."""
+        E = self.num_envs
+        flags = np.zeros(self.num_bodies, np.int32)
+        fingers = np.full((E, 2), -1, np.int32)
+        for e in range(E):
+            b0 = self.body_off[e]
+            fing = []
+            for g in range(self.joint_off[e], self.joint_off[e + 1]):
+                for b in (self.joint_parent[g], self.joint_child[g]):
+                    if b >= 0:
+                        flags[b0 + b] |= 1
+                if self.joint_type[g] == PRISMATIC and len(fing) < 2:
+                    fing.append(int(self.joint_child[g]))
+                    if self.joint_parent[g] >= 0:
+                        flags[b0 + self.joint_parent[g]] |= 2
+            for k, b in enumerate(fing):
+                fingers[e, k] = b
+                flags[b0 + b] |= 2
+        return flags, fingers, np.asarray(self.goal_body, np.int32).copy()
+
     def state(self):
         """Fresh copies of the initial state arrays (pos, quat, linvel, angvel)."""
         return (self.pos.copy(), self.quat.copy(), self.linvel.copy(),

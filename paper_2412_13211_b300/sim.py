@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import EXEC_FUSED, EXEC_PLAIN, EXEC_SUBSTEP, SceneDesc, SolverCfg, State, check
+from ._lib import EXEC_FUSED, EXEC_PLAIN, EXEC_SUBSTEP, ReportDesc, SceneDesc, SolverCfg, State, check
 
 
 def _c(a, dt):
@@ -186,6 +186,50 @@ class MshSim:
         res = {k: v.cpu().numpy() for k, v in out.items()}
         res["aabb_body"] = res["aabb_body"][:sc.num_bodies]
         res["aabb_static"] = res["aabb_static"][:sc.num_statics]
+        return res
+
+    # -- contact report ---------------------------------------------------------
+    def set_report(self, body_flags, fingers=None, target=None, grasp_min_force: float = 0.5,
+                   grasp_max_angle_deg: float = 85.0):
+        """Turns on the per-step contact report (msh_set_report) into device
+        tensors owned by this object: body_force [B,3], target_force [E,3],
+        finger_force [E,2,3], robot_force [E] (accumulated; zero it with
+        reset_robot_force) and grasped [E]. body_flags [B]: bit 0 robot link,
+        bit 1 end-effector link; fingers [E,2] and target [E] are env-local
+        body ids (-1: none). Returns the dict of output tensors."""
+        sc, dev = self.scene, self.device
+        E, B = sc.num_envs, sc.num_bodies
+        out = dict(body_force=torch.zeros((max(B, 1), 3), device=dev), target_force=torch.zeros((E, 3), device=dev),
+                   finger_force=torch.zeros((E, 2, 3), device=dev), robot_force=torch.zeros(E, device=dev),
+                   grasped=torch.zeros(E, dtype=torch.int32, device=dev))
+        flags = np.ascontiguousarray(body_flags, np.int32).reshape(B)
+        fing = None if fingers is None else np.ascontiguousarray(fingers, np.int32).reshape(E, 2)
+        tgt = None if target is None else np.ascontiguousarray(target, np.int32).reshape(E)
+        d = ReportDesc()
+        d.body_flags = flags.ctypes.data
+        d.fingers = fing.ctypes.data if fing is not None else None
+        d.target = tgt.ctypes.data if tgt is not None else None
+        d.grasp_min_force, d.grasp_max_angle_deg = float(grasp_min_force), float(grasp_max_angle_deg)
+        for k in ("body_force", "target_force", "finger_force", "robot_force", "grasped"):
+            setattr(d, k, out[k].data_ptr())
+        with torch.cuda.device(dev):
+            check(self.lib.msh_set_report(self.handle, C.byref(d)), "msh_set_report")
+        self.report_out = out
+        return out
+
+    def clear_report(self):
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_set_report(self.handle, None), "msh_set_report")
+        self.report_out = None
+
+    def reset_robot_force(self):
+        if getattr(self, "report_out", None) is not None:
+            self.report_out["robot_force"].zero_()
+
+    def report(self) -> dict:
+        """numpy copies of the report outputs (synchronises)."""
+        res = {k: v.cpu().numpy() for k, v in self.report_out.items()}
+        res["body_force"] = res["body_force"][:self.scene.num_bodies]
         return res
 
     # -- adjoint --------------------------------------------------------------
