@@ -227,6 +227,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-report", action="store_true")
     ap.add_argument("--bwd-horizon", type=int, default=16)
     ap.add_argument("--profile-backward", action="store_true",
                     help="only a short fwd+bwd rollout of the 512-env differentiation workload (small case for ncu)")
@@ -305,6 +306,21 @@ def main():
     value = replicas.job_throughput(scene.num_envs, args.steps, t_tot, world)
     status = sim.status()
 
+    # the same fused step with the contact report on (forces, robot collision
+    # force, grasp test written every step)
+    report = None
+    if not args.no_report:
+        sim.set_report(*scene.report_spec())
+        with torch.cuda.stream(stream):
+            for k in range(3):
+                fused_step(args.warmup + k)
+        stream.synchronize()
+        n_rep = max(3, min(args.steps, 20))
+        rms = timed(fused_step, args.warmup, n_rep)
+        sim.clear_report()
+        report = {"ms_per_step": float(np.mean(rms)), "overhead": float(np.mean(rms) / t_step - 1.0),
+                  "steps": n_rep}
+
     # plain form (one launch per stage), same inputs
     plain = None
     if not args.no_plain:
@@ -372,7 +388,7 @@ def main():
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": bytes_step},
-        "plain_step": plain,
+        "plain_step": plain, "contact_report": report,
         "fwd_bwd": fwd_bwd,
         "e2e": {"value": scene.num_envs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": n_e2e},
