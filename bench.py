@@ -214,6 +214,49 @@ def time_fwd_bwd(sim, scene, tg, horizon, k, stream, reps=2):
             "note": "forward (fused) + recorded re-run of each checkpoint segment + msh_backward per step"}
 
 
+def time_labels(dev, stream, hbm_peak, n_traj=262144, steps=200, reps=5, cpu=True):
+    """Event labeling (Appendix A.5) of a Pick batch: n_traj trajectories x steps
+    records (force, cumulative collision force: FP32; flags: u8), inputs in HBM
+    (larger than L2), CUDA events over `reps` launches; the oracle (Python) is
+    timed on a 1000-trajectory sample of the same batch."""
+    import torch
+    from paper_2412_13211_b300 import labels as GL, trajectories as TR
+    small = TR.make(GL.PICK, num=2048, steps=steps, seed=1)
+    reps_tile = n_traj // 2048
+    traj_np = {k: (np.tile(v, (1, reps_tile)) if v.ndim == 2 else np.tile(v, reps_tile)) for k, v in small.items()}
+    traj = GL.to_device(traj_np, dev)
+    rec = int(traj_np["length"].astype(np.int64).sum())            # records the scan reads (t >= 0 of each length)
+    in_bytes = 9 * rec                                              # 4 force + 4 cumcol + 1 flags per record
+    out_bytes = n_traj * (32 + 4 + 4 + 4)                          # events, count, label, length read
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            GL.label_events(GL.PICK, traj, stream=stream)
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            GL.label_events(GL.PICK, traj, stream=stream)
+        b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b) / reps
+    gbs = (in_bytes + out_bytes) / (ms / 1e3) / 1e9
+    res = {"metric": "trajectories labeled/s", "value": n_traj / (ms / 1e3), "ms_per_launch": ms,
+           "workload": f"Pick, {n_traj} trajectories x {steps} steps (lengths 60-100 %)",
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "algorithmic_bytes": in_bytes + out_bytes,
+                        "note": "9 B per record read (force, cumcol, flags) + 44 B per trajectory written"}}
+    if cpu:
+        import oracle.labels as OL
+        n_cpu = 1000
+        sub = {k: (v[:, :n_cpu] if v.ndim == 2 else v[:n_cpu]) for k, v in traj_np.items()}
+        t0 = time.perf_counter()
+        OL.label_batch(OL.PICK, sub)
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": n_cpu / dt, "unit": "trajectories/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{n_cpu} trajectories of the batch, Python oracle"}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,6 +271,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-report", action="store_true")
+    ap.add_argument("--no-labels", action="store_true")
     ap.add_argument("--bwd-horizon", type=int, default=16)
     ap.add_argument("--profile-backward", action="store_true",
                     help="only a short fwd+bwd rollout of the 512-env differentiation workload (small case for ncu)")
@@ -364,6 +408,7 @@ def main():
     d2h = 52 * scene.num_bodies
 
     hbm_peak, sm_max, peak_kind = peaks()
+    labels = None if args.no_labels else time_labels(dev, stream, hbm_peak, cpu=rank == 0 and not args.no_cpu_baseline)
     bytes_step = algorithmic(scene)
     flops_step = FLOP_ROW * rows * cfg.substeps * cfg.iterations
     alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x clock, TFLOP/s
@@ -388,7 +433,7 @@ def main():
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": bytes_step},
-        "plain_step": plain, "contact_report": report,
+        "plain_step": plain, "contact_report": report, "event_labeling": labels,
         "fwd_bwd": fwd_bwd,
         "e2e": {"value": scene.num_envs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": n_e2e},

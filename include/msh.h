@@ -286,6 +286,49 @@ int64_t msh_workspace_bytes(const msh_handle* h);
 /* Number of kernel launches one msh_step issues in the current form. */
 int32_t msh_launches_per_step(const msh_handle* h);
 
+/*
+ * Event labeling and trajectory categorization (Sec. 3.3, Appendix A.5): a
+ * batched scan over per-step records of N trajectories of one subtask. For
+ * t = 1..length-1 the subtask's events are evaluated in the appendix's order
+ * from the records at t-1 and t and appended to the trajectory's
+ * chronological list; the list then decides the success or failure mode.
+ *   Pick:  contact, grasped, dropped, success, excessive_collisions
+ *   Place: grasped, obj_at_goal, released_at_goal, released_outside_goal,
+ *          obj_left_goal, success, excessive_collisions
+ *   Open:  contact, opened, slightly_opened, closed, success, excessive_collisions
+ *   Close: contact, closed, slightly_closed, opened, success, excessive_collisions
+ * (event codes are the 0-based positions in these lists). Modes are the
+ * appendix's roman numerals (Pick 1-9, Place 1-12, Open and Close 1-9), tested
+ * in order; 0 when none holds. Readings: contact needs a nonzero force; an
+ * event's index is its last occurrence; Open/Close success mode iii requires
+ * excessive collisions in the list; thresholds are formed and compared in FP32.
+ * All arrays are DEVICE pointers; records are step-major [num_steps][num_traj].
+ */
+enum { MSH_TASK_PICK = 0, MSH_TASK_PLACE = 1, MSH_TASK_OPEN = 2, MSH_TASK_CLOSE = 3 };
+
+typedef struct msh_traj_batch {
+  int32_t num_traj, num_steps;
+  const float* force;        /* [T][N] |F_{ee,target}| in N (Pick, Open, Close) */
+  const float* cumcol;       /* [T][N] cumulative robot collision force in N */
+  const float* dist;         /* [T][N] target-to-goal distance in m (Place) */
+  const float* artq;         /* [T][N] articulation joint position (Open, Close) */
+  const uint8_t* flags;      /* [T][N] bit 0 grasped(target), bit 1 success */
+  const int32_t* length;     /* [N] valid records per trajectory (clipped to T); NULL: T */
+  const float* art_range;    /* [N][2] qmin, qmax (Open, Close) */
+  const uint8_t* art_fridge; /* [N] 1: fridge (opens at 0.75 of the range), 0: drawer (0.9); NULL: drawers */
+  float collision_limit;     /* N; <= 0: 5000 Pick, 7500 Place, 10000 Open/Close */
+  float goal_radius;         /* m; <= 0: 0.15 */
+} msh_traj_batch;
+
+/*
+ * Writes num_events [N] (the list's length), the first max_events (1..127)
+ * codes of each list into events [N][max_events] (int8, -1 padded) and the
+ * mode into label [N]; all DEVICE, asynchronous on `stream`. Returns
+ * MSH_ERR_INVALID_ARG for a bad task, NULL arrays the task needs or bad sizes.
+ */
+int msh_label_events(int32_t task, const msh_traj_batch* batch, int32_t max_events, int8_t* events,
+                     int32_t* num_events, int32_t* label, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

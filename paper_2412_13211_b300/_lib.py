@@ -17,7 +17,8 @@ EXEC_PLAIN, EXEC_FUSED, EXEC_SUBSTEP = 0, 1, 2
 EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_step", "msh_step_host",
            "msh_detect", "msh_get_status", "msh_clear_status", "msh_scratch_bytes", "msh_workspace_bytes",
            "msh_launches_per_step", "msh_step_static_scratch", "msh_set_tape", "msh_tape_reset",
-           "msh_tape_count", "msh_backward", "msh_set_report")
+           "msh_tape_count", "msh_backward", "msh_set_report", "msh_label_events")
+TASK_PICK, TASK_PLACE, TASK_OPEN, TASK_CLOSE = 0, 1, 2, 3
 
 
 class SceneDesc(C.Structure):
@@ -41,6 +42,13 @@ class ReportDesc(C.Structure):
                 ("grasp_min_force", C.c_float), ("grasp_max_angle_deg", C.c_float),
                 ("body_force", C.c_void_p), ("target_force", C.c_void_p), ("finger_force", C.c_void_p),
                 ("robot_force", C.c_void_p), ("grasped", C.c_void_p)]
+
+
+class TrajBatch(C.Structure):
+    _fields_ = [("num_traj", C.c_int32), ("num_steps", C.c_int32), ("force", C.c_void_p), ("cumcol", C.c_void_p),
+                ("dist", C.c_void_p), ("artq", C.c_void_p), ("flags", C.c_void_p), ("length", C.c_void_p),
+                ("art_range", C.c_void_p), ("art_fridge", C.c_void_p), ("collision_limit", C.c_float),
+                ("goal_radius", C.c_float)]
 
 
 class State(C.Structure):
@@ -72,6 +80,7 @@ def load(build_if_missing: bool = True):
     lib.msh_step_static_scratch.argtypes = [P, P, P, F, I32, P]
     lib.msh_set_tape.argtypes = [P, I32]
     lib.msh_set_report.argtypes = [P, P]
+    lib.msh_label_events.argtypes = [I32, P, I32, P, P, P, P]
     lib.msh_tape_reset.argtypes = [P]
     lib.msh_tape_count.argtypes = [P]
     lib.msh_tape_count.restype = C.c_int32

@@ -336,6 +336,15 @@ int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+}  // namespace
+
+// Error reporting for the library's other translation units (msh_last_error).
+int msh_fail(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+
+namespace {
 
 #define CK(call)                                                                          \
   do {                                                                                    \

@@ -98,3 +98,17 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.msh_scratch_bytes(None) == 0
     assert lib.msh_set_report(None, None) == _lib.MSH_ERR_INVALID_ARG
     lib.msh_destroy(None)
+
+
+def test_label_events_rejects_bad_arguments_before_any_launch():
+    lib = _lib.load()
+    b = _lib.TrajBatch()
+    assert lib.msh_label_events(0, None, 8, None, None, None, None) == _lib.MSH_ERR_INVALID_ARG
+    b.num_traj, b.num_steps = 4, 10
+    out = (C.c_int8 * 32)()
+    n = (C.c_int32 * 4)()
+    lab = (C.c_int32 * 4)()
+    assert lib.msh_label_events(7, C.byref(b), 8, out, n, lab, None) == _lib.MSH_ERR_INVALID_ARG   # unknown task
+    assert lib.msh_label_events(0, C.byref(b), 8, out, n, lab, None) == _lib.MSH_ERR_INVALID_ARG   # no records
+    assert lib.msh_label_events(0, C.byref(b), 0, out, n, lab, None) == _lib.MSH_ERR_INVALID_ARG   # max_events
+    assert b"records" in lib.msh_last_error() or b"max_events" in lib.msh_last_error()
