@@ -195,37 +195,53 @@ __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const
 // ---------------------------------------------------------------------------
 struct BodyAdj { V3<float> va, wa, vb, wb; };
 
-// Reverse of one row update. `r` is the row index; la..Ib its parameters;
-// lam_after / lam_before its recorded lambdas around this update; lam_n_after
-// the normal row's lambda in this sweep (friction rows).
+// The loaded state of one row for its reverse update: parameters, adjoint
+// accumulators and its recorded lambdas.
+struct RevRow {
+  float4 r0, r1, r2, r3, r4;   // la|m, aa|bias, ab|gamma, Ia|-, Ib|clamp
+  float4 g0, g1, g2, g3, g4;   // adjoints (gla|gm, gaa|gbias, gab|glam, gIa|g(1/m_a), gIb|g(1/m_b))
+  float lam_after, lam_before, lam_n_after;
+};
+
+__device__ __forceinline__ void load_rev_row(const AWs& a, int r, const float* lam_it, const float* lam_prev, int nrow,
+                                             RevRow& x) {
+  const float4* R = a.rows + ROW_F4 * r;
+  const float4* G = a.radj + ROW_F4 * r;
+  x.r0 = R[0]; x.r1 = R[1]; x.r2 = R[2]; x.r3 = R[3]; x.r4 = R[4];
+  x.g0 = G[0]; x.g1 = G[1]; x.g2 = G[2]; x.g3 = G[3]; x.g4 = G[4];
+  x.lam_after = lam_it[r];
+  x.lam_before = lam_prev ? lam_prev[r] : 0.f;
+  x.lam_n_after = nrow >= 0 ? lam_it[nrow] : 0.f;
+}
+
+// Reverse of one row update on the loaded row `x` (writes its adjoints back
+// to row r). `gfric` receives the adjoint this row (a friction row at its
+// limit) sends to its normal row's lambda; the caller adds it when it
+// reaches that row.
 __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, float ima, float imb, BodyVel& v,
-                                            BodyAdj& g, float lam_after, float lam_before, float mu, int nrow,
-                                            float lam_n_after) {
-  float4* R = a.rows + ROW_F4 * r;
-  float4 r0 = R[0], r1 = R[1], r2 = R[2], r3 = R[3], r4 = R[4];
-  V3<float> la = f3(r0), aa = f3(r1), ab = f3(r2), Ia = f3(r3), Ib = f3(r4);
-  const float m = r0.w, bias = r1.w, gamma = r2.w, clamp = r4.w;
+                                            BodyAdj& g, const RevRow& x, float mu, float& gfric) {
+  V3<float> la = f3(x.r0), aa = f3(x.r1), ab = f3(x.r2), Ia = f3(x.r3), Ib = f3(x.r4);
+  const float m = x.r0.w, bias = x.r1.w, gamma = x.r2.w, clamp = x.r4.w;
+  const float lam_after = x.lam_after, lam_before = x.lam_before;
   const float D = lam_after - lam_before;
   // velocities before the update
   if (A >= 0) { v.va = v.va - la * (ima * D); v.wa = v.wa - Ia * D; }
   if (B >= 0) { v.vb = v.vb + la * (imb * D); v.wb = v.wb - Ib * D; }
-  float4* G = a.radj + ROW_F4 * r;
-  float4 g0 = G[0], g1 = G[1], g2 = G[2], g3 = G[3], g4 = G[4];
-  V3<float> gla = f3(g0), gaa = f3(g1), gab = f3(g2), gIa = f3(g3), gIb = f3(g4);
-  float gm = g0.w, gbias = g1.w, glam = g2.w;
+  V3<float> gla = f3(x.g0), gaa = f3(x.g1), gab = f3(x.g2), gIa = f3(x.g3), gIb = f3(x.g4);
+  float gm = x.g0.w, gbias = x.g1.w, glam = x.g2.w, gima = x.g3.w, gimb = x.g4.w;
   // adjoint of D through the velocity update
   float gD = 0.f;
   if (A >= 0) {
     gD += ima * dot(la, g.va) + dot(Ia, g.wa);
     gla = gla + g.va * (ima * D);
     gIa = gIa + g.wa * D;
-    g3.w += dot(la, g.va) * D;        // adjoint of 1/m_a (kept in the row, moved to the body later)
+    gima += dot(la, g.va) * D;        // adjoint of 1/m_a (kept in the row, moved to the body later)
   }
   if (B >= 0) {
     gD += -imb * dot(la, g.vb) + dot(Ib, g.wb);
     gla = gla - g.vb * (imb * D);
     gIb = gIb + g.wb * D;
-    g4.w += -dot(la, g.vb) * D;       // adjoint of 1/m_b
+    gimb += -dot(la, g.vb) * D;       // adjoint of 1/m_b
   }
   const float a_after = glam + gD;
   float glam_before = -gD;
@@ -239,15 +255,12 @@ __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, f
   if (clamp >= 0.f) clamped = lam_after == clamp || lam_after == -clamp;
   else if (clamp == CLAMP_UNI) clamped = lam_after == 0.f;
   else if (clamp == CLAMP_FRIC) {
-    float lim = mu * lam_n_after;
+    float lim = mu * x.lam_n_after;
     clamped = lam_after == lim || lam_after == -lim;
     fric_sign = lam_after == lim ? 1.f : -1.f;
   } else clamped = false;
   float gpre = clamped ? 0.f : a_after;
-  if (clamped && clamp == CLAMP_FRIC) {
-    float4* Gn = a.radj + ROW_F4 * nrow;
-    Gn[2].w += fric_sign * mu * a_after;
-  }
+  gfric = clamped && clamp == CLAMP_FRIC ? fric_sign * mu * a_after : 0.f;
   glam_before += gpre;
   const float gu = -m * gpre;
   gm += -u * gpre;
@@ -256,7 +269,17 @@ __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, f
   gla = gla + (v.va - v.vb) * gu;
   gbias += gu;
   glam_before += gamma * gu;
-  G[0] = f4(gla, gm); G[1] = f4(gaa, gbias); G[2] = f4(gab, glam_before); G[3] = f4(gIa, g3.w); G[4] = f4(gIb, g4.w);
+  float4* G = a.radj + ROW_F4 * r;
+  G[0] = f4(gla, gm); G[1] = f4(gaa, gbias); G[2] = f4(gab, glam_before); G[3] = f4(gIa, gima); G[4] = f4(gIb, gimb);
+}
+
+// The i-th row of manifold mf in reverse update order (points last to
+// first, each t2, t1, normal); nrow receives the point's normal row.
+__device__ __forceinline__ int rev_contact_row(const Layout& L, int4 mf, int i, int& nrow) {
+  const int ci = mf.z + mf.w - 1 - i / 3;
+  const int rn = crow(L, ci, 0);
+  nrow = rn;
+  return rn + 2 - i % 3;
 }
 
 __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* lam_it,
@@ -275,23 +298,29 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
       g.va = A >= 0 ? f3(a.bv[A]) : z; g.wa = A >= 0 ? f3(a.bw[A]) : z;
       g.vb = B >= 0 ? f3(a.bv[B]) : z; g.wb = B >= 0 ? f3(a.bw[B]) : z;
       const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
-      if (k < J) {
-        const JointDesc& j = p.joints[e.j0 + k];
-        const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
-        for (int r = nr - 1; r >= 0; --r) {
-          const int ri = jrow(k, r);
-          reverse_row(a, ri, A, B, ima, imb, v, g, lam_it[ri], lam_prev ? lam_prev[ri] : 0.f, 0.f, -1, 0.f);
+      int nrows, jnr = 0;
+      int4 mf = make_int4(0, 0, 0, 0);
+      if (k < J) { jnr = w.jinfo[k].w; nrows = jnr; }
+      else { mf = w.man[k - J]; nrows = 3 * mf.w; }
+      const float mu = k < J ? 0.f : p.mu;
+      // software pipelining: the next row's parameters, adjoints and lambdas
+      // load while this row runs (rows of a constraint never alias)
+      int nr_cur = -1;
+      int r_cur = k < J ? jrow(k, jnr - 1) : rev_contact_row(p.L, mf, 0, nr_cur);
+      RevRow cur, nxt;
+      load_rev_row(a, r_cur, lam_it, lam_prev, k < J ? -1 : nr_cur, cur);
+      float pend = 0.f;   // friction adjoints owed to the current point's normal row
+      for (int i = 0; i < nrows; ++i) {
+        int r_nxt = -1, nr_nxt = -1;
+        if (i + 1 < nrows) {
+          r_nxt = k < J ? jrow(k, jnr - 2 - i) : rev_contact_row(p.L, mf, i + 1, nr_nxt);
+          load_rev_row(a, r_nxt, lam_it, lam_prev, k < J ? -1 : nr_nxt, nxt);
         }
-      } else {
-        int4 mf = w.man[k - J];
-        for (int ci = mf.z + mf.w - 1; ci >= mf.z; --ci) {
-          const int rn = crow(p.L, ci, 0);
-          for (int i = 2; i >= 0; --i) {
-            const int ri = rn + i;
-            reverse_row(a, ri, A, B, ima, imb, v, g, lam_it[ri], lam_prev ? lam_prev[ri] : 0.f, p.mu, rn,
-                        lam_it[rn]);
-          }
-        }
+        if (k >= J && r_cur == nr_cur) { cur.g2.w += pend; pend = 0.f; }   // the normal row: add what t1, t2 sent
+        float gfric;
+        reverse_row(a, r_cur, A, B, ima, imb, v, g, cur, mu, gfric);
+        pend += gfric;
+        if (i + 1 < nrows) { cur = nxt; r_cur = r_nxt; nr_cur = nr_nxt; }
       }
       if (A >= 0) { w.bv[A] = f4(v.va, 0.f); w.bw[A] = f4(v.wa, 0.f); a.bv[A] = f4(g.va, 0.f); a.bw[A] = f4(g.wa, 0.f); }
       if (B >= 0) { w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f); }
