@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "msh_oracle.cpp")
+_SOURCES = [_SRC, os.path.join(_HERE, "msh_raycast.cpp")]
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
@@ -24,12 +25,12 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compiles the oracle if the shared object is missing or older than its source."""
     if (not force and os.path.exists(_OUT)
-            and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_OUT) >= os.path.getmtime(f) for f in _SOURCES)):
         return _OUT
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     tmp = _OUT + f".{os.getpid()}.tmp"
     cmd = ["g++", "-O3", "-std=c++17", "-march=x86-64-v2", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-fPIC", "-shared", _SRC, "-o", tmp]
+           "-fno-fast-math", "-fPIC", "-shared"] + _SOURCES + ["-o", tmp]
     subprocess.check_call(cmd)
     os.replace(tmp, _OUT)
     return _OUT
@@ -70,6 +71,9 @@ def load():
         lib.oracle_grad_f64.argtypes = [P, P, P, P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, C.c_int]
         lib.oracle_grad_f64.restype = C.c_int
         lib.oracle_max_threads.restype = C.c_int
+        for fn in (lib.oracle_render_depth_f32, lib.oracle_render_depth_f64):
+            fn.argtypes = [P, P, P, P, P, C.c_int]
+            fn.restype = C.c_int
         for fn in (lib.oracle_step_report_f32, lib.oracle_step_report_f64):
             fn.argtypes = [P, P, P, P, P, P, P, C.c_int, P, C.c_int, P, P, P, P, P, P]
             fn.restype = C.c_int
@@ -197,6 +201,42 @@ def step_report(scene, cfg, state, targets, nsteps, body_flags, fingers, target,
     if rc != 0:
         raise RuntimeError(f"oracle step_report failed: {rc}")
     return tuple(st), status, rep
+
+
+class _RayScene(C.Structure):
+    _fields_ = [("num_envs", C.c_int32), ("body_off", C.c_void_p), ("static_off", C.c_void_p),
+                ("body_shape", C.c_void_p), ("body_dims", C.c_void_p), ("static_pose", C.c_void_p),
+                ("static_half", C.c_void_p)]
+
+
+class _Cams(C.Structure):
+    _fields_ = [("ncam", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("focal", C.c_float),
+                ("near_", C.c_float), ("far_", C.c_float), ("body", C.c_void_p), ("pose", C.c_void_p)]
+
+
+def render_depth(scene, pos, quat, cam_body, cam_pose, width, height, focal, near, far, precision="f32",
+                 threads: int = 0):
+    """Depth images [E, ncam, H, W] (z-depth in m, 0 = no hit) of every env's
+    cameras at poses (pos, quat); cam_body [E, ncam] env-local mount bodies
+    (-1: world), cam_pose [E, ncam, 7] mount-local poses; focal in pixels."""
+    lib = load()
+    dt = np.float32 if precision == "f32" else np.float64
+    E = scene.num_envs
+    body = np.ascontiguousarray(cam_body, np.int32).reshape(E, -1)
+    ncam = body.shape[1]
+    pose = np.ascontiguousarray(cam_pose, np.float32).reshape(E, ncam, 7)
+    keep = [np.ascontiguousarray(a) for a in (scene.body_off, scene.static_off, scene.body_shape, scene.body_dims,
+                                              scene.static_pose, scene.static_half)]
+    rs = _RayScene(E, *[_ptr(a) for a in keep])
+    cams = _Cams(ncam, int(width), int(height), float(focal), float(near), float(far), _ptr(body), _ptr(pose))
+    p = np.ascontiguousarray(pos, dt)
+    q = np.ascontiguousarray(quat, dt)
+    out = np.zeros((E, ncam, int(height), int(width)), dt)
+    fn = lib.oracle_render_depth_f32 if precision == "f32" else lib.oracle_render_depth_f64
+    rc = fn(C.byref(rs), _ptr(p), _ptr(q), C.byref(cams), _ptr(out), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle render failed: {rc}")
+    return out
 
 
 @dataclass
