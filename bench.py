@@ -257,6 +257,50 @@ def time_labels(dev, stream, hbm_peak, n_traj=262144, steps=200, reps=5, cpu=Tru
     return res
 
 
+def time_render(sim, scene, stream, hbm_peak, width=128, height=128, reps=10, cpu=True):
+    """Depth cameras: two cameras per env (scene.camera_mounts), 128x128, at the
+    batch's current state; CUDA events over `reps` renders; the oracle on 32 envs."""
+    import torch
+    body, pose = scene.camera_mounts()
+    fov, near, far = np.pi / 2, 0.01, 10.0
+    sim.set_cameras(body, pose, width, height, fov, near, far)
+    out = torch.empty((scene.num_envs, body.shape[1], height, width), dtype=torch.float32, device=sim.device)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            sim.render_depth(out, stream=stream)
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            sim.render_depth(out, stream=stream)
+        b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b) / reps
+    frames = scene.num_envs * body.shape[1]
+    out_bytes = out.numel() * 4
+    gbs = out_bytes / (ms / 1e3) / 1e9
+    hit = float((out > 0).float().mean().item())
+    res = {"metric": "depth images/s", "value": frames / (ms / 1e3), "ms_per_render": ms,
+           "workload": f"{scene.num_envs} envs x {body.shape[1]} cameras x {width}x{height}",
+           "pixels_hit": hit,
+           "roofline_hbm": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                            "note": "output writes only (4 B per pixel); the kernel is bound by FP32 "
+                                    "intersection arithmetic, see the profile summary"}}
+    if cpu:
+        import oracle
+        n = 32
+        sub = scene.subset(np.arange(n))
+        st = [t.detach().cpu().numpy() for t in (sim.pos, sim.quat)]
+        b0 = scene.body_off[n]
+        t0 = time.perf_counter()
+        oracle.render_depth(sub, st[0][:b0], st[1][:b0], body[:n], pose[:n], width, height,
+                            float(np.float32(height * 0.5 / np.tan(float(np.float32(fov)) * 0.5))), near, far, "f32")
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": n * body.shape[1] / dt, "unit": "depth images/s", "cores": oracle.cores(),
+                               "kind": "oracle", "sample": f"first {n} envs, brute force per pixel"}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,6 +316,7 @@ def main():
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-report", action="store_true")
     ap.add_argument("--no-labels", action="store_true")
+    ap.add_argument("--no-render", action="store_true")
     ap.add_argument("--bwd-horizon", type=int, default=16)
     ap.add_argument("--profile-backward", action="store_true",
                     help="only a short fwd+bwd rollout of the 512-env differentiation workload (small case for ncu)")
@@ -409,6 +454,8 @@ def main():
 
     hbm_peak, sm_max, peak_kind = peaks()
     labels = None if args.no_labels else time_labels(dev, stream, hbm_peak, cpu=rank == 0 and not args.no_cpu_baseline)
+    render = None if args.no_render else time_render(sim, scene, stream, hbm_peak,
+                                                     cpu=rank == 0 and not args.no_cpu_baseline)
     bytes_step = algorithmic(scene)
     flops_step = FLOP_ROW * rows * cfg.substeps * cfg.iterations
     alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x clock, TFLOP/s
@@ -433,7 +480,7 @@ def main():
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": bytes_step},
-        "plain_step": plain, "contact_report": report, "event_labeling": labels,
+        "plain_step": plain, "contact_report": report, "event_labeling": labels, "depth_cameras": render,
         "fwd_bwd": fwd_bwd,
         "e2e": {"value": scene.num_envs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": n_e2e},

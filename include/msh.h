@@ -245,6 +245,37 @@ typedef struct msh_report_desc {
 int msh_set_report(msh_handle* h, const msh_report_desc* desc);
 
 /*
+ * Depth cameras (the paper's per-env RGB-D cameras, Sec. 4.2; the depth
+ * channel, ray-cast against the env's primitives instead of rasterised).
+ * Pinhole camera looking along its frame's +x (image right = -y, image down
+ * = -z), pixel (row, col) centred at (col + 1/2, row + 1/2), focal length
+ * f = (height/2) / tan(fov_y/2) pixels. A camera is mounted on a body
+ * (env-local id; its pose is composed with the body's) or on the world (-1).
+ * The depth of a pixel is the z-depth (distance along the optical axis) of
+ * the nearest hit in [near, far] among spheres, capsules, boxes, static boxes
+ * and the ground plane, or 0 when nothing is hit. body and pose are HOST
+ * arrays read during msh_set_cameras (not retained). Envs may hold at most
+ * MSH_RENDER_MAX_PRIMS bodies plus static boxes. Returns MSH_ERR_INVALID_ARG
+ * on bad sizes, angles, clip distances or ids.
+ */
+enum { MSH_RENDER_MAX_PRIMS = 256 };
+
+typedef struct msh_camera_desc {
+  int32_t num_cameras;   /* per env, >= 1 */
+  int32_t width, height; /* pixels, 1..4096 */
+  float fov_y;           /* vertical field of view, radians, in (0, pi) */
+  float near_, far_;     /* clip distances along the optical axis, 0 < near < far */
+  const int32_t* body;   /* [num_envs][num_cameras] env-local mount body, -1 = world */
+  const float* pose;     /* [num_envs][num_cameras][7] mount-local position and quaternion (w,x,y,z) */
+} msh_camera_desc;
+
+int msh_set_cameras(msh_handle* h, const msh_camera_desc* desc);
+
+/* Renders every camera of every env at the state st (DEVICE) into depth,
+ * DEVICE float [num_envs][num_cameras][height][width]; asynchronous. */
+int msh_render_depth(msh_handle* h, const msh_state* st, float* depth, void* stream);
+
+/*
  * Differentiation (reverse mode). msh_set_tape(h, n), n > 0, makes room for
  * n recorded steps (reusing a large enough tape) and starts recording
  * (coloured solver and zero restitution only); n = 0 stops recording and

@@ -17,7 +17,8 @@ EXEC_PLAIN, EXEC_FUSED, EXEC_SUBSTEP = 0, 1, 2
 EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_step", "msh_step_host",
            "msh_detect", "msh_get_status", "msh_clear_status", "msh_scratch_bytes", "msh_workspace_bytes",
            "msh_launches_per_step", "msh_step_static_scratch", "msh_set_tape", "msh_tape_reset",
-           "msh_tape_count", "msh_backward", "msh_set_report", "msh_label_events")
+           "msh_tape_count", "msh_backward", "msh_set_report", "msh_label_events", "msh_set_cameras",
+           "msh_render_depth")
 TASK_PICK, TASK_PLACE, TASK_OPEN, TASK_CLOSE = 0, 1, 2, 3
 
 
@@ -42,6 +43,11 @@ class ReportDesc(C.Structure):
                 ("grasp_min_force", C.c_float), ("grasp_max_angle_deg", C.c_float),
                 ("body_force", C.c_void_p), ("target_force", C.c_void_p), ("finger_force", C.c_void_p),
                 ("robot_force", C.c_void_p), ("grasped", C.c_void_p)]
+
+
+class CameraDesc(C.Structure):
+    _fields_ = [("num_cameras", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("fov_y", C.c_float),
+                ("near_", C.c_float), ("far_", C.c_float), ("body", C.c_void_p), ("pose", C.c_void_p)]
 
 
 class TrajBatch(C.Structure):
@@ -80,6 +86,8 @@ def load(build_if_missing: bool = True):
     lib.msh_step_static_scratch.argtypes = [P, P, P, F, I32, P]
     lib.msh_set_tape.argtypes = [P, I32]
     lib.msh_set_report.argtypes = [P, P]
+    lib.msh_set_cameras.argtypes = [P, P]
+    lib.msh_render_depth.argtypes = [P, P, P, P]
     lib.msh_label_events.argtypes = [I32, P, I32, P, P, P, P]
     lib.msh_tape_reset.argtypes = [P]
     lib.msh_tape_count.argtypes = [P]

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/msh.h"
+#include "msh_render.h"
 #include "msh_adjoint.cuh"
 
 using namespace msh;
@@ -433,6 +434,12 @@ struct msh_handle {
   float *d_static_pose = nullptr, *d_static_half = nullptr;
   float4* d_sworld = nullptr;
   std::vector<int> body_off_host;   // CSR body offsets (host copy, for argument checks)
+  std::vector<int> static_off_host;
+  // depth cameras (msh_set_cameras)
+  int cam_n = 0, cam_w = 0, cam_h = 0;
+  float cam_focal = 0.f, cam_near = 0.f, cam_far = 0.f;
+  int* d_cam_body = nullptr;
+  float* d_cam_pose = nullptr;
   // contact report (msh_set_report)
   int rep_on = 0;
   int *d_rep_flags = nullptr, *d_rep_fingers = nullptr, *d_rep_target = nullptr;
@@ -699,7 +706,8 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
   }
   msh_handle* h = new msh_handle();
   h->E = E; h->B = B; h->S = S; h->J = J;
-  h->body_off_host.assign(d->body_off, d->body_off + E + 1); h->max_dof = d->max_dof; h->cfg = *cfg;
+  h->body_off_host.assign(d->body_off, d->body_off + E + 1);
+  h->static_off_host.assign(d->static_off, d->static_off + E + 1); h->max_dof = d->max_dof; h->cfg = *cfg;
   h->Dm = std::max(Dm, 1); h->Sm = std::max(Sm, 1); h->Jm = std::max(Jm, 1);
   h->L = make_layout(h->Dm, h->Sm, h->Jm, Rm, cfg->max_pairs, cfg->max_contacts, cfg->mode == MSH_MODE_JACOBI);
   auto bail = [&](int code) { msh_destroy(h); return code; };
@@ -770,7 +778,7 @@ void msh_destroy(msh_handle* h) {
   void* ptrs[] = {h->d_body_off, h->d_static_off, h->d_joint_off, h->d_env_order, h->d_bdims, h->d_binv,
                   h->d_static_pose, h->d_static_half, h->d_sworld, h->d_joints, h->d_status, h->d_queue, h->d_targets,
                   h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused, h->d_tape, h->d_aws,
-                  h->d_rep_flags, h->d_rep_fingers, h->d_rep_target};
+                  h->d_rep_flags, h->d_rep_fingers, h->d_rep_target, h->d_cam_body, h->d_cam_pose};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -1039,6 +1047,50 @@ int msh_set_report(msh_handle* h, const msh_report_desc* d) {
   h->rep_cosmax = (float)std::cos((double)d->grasp_max_angle_deg * 3.14159265358979323846 / 180.0);
   h->rep_on = 1;
   return MSH_OK;
+}
+
+
+int msh_set_cameras(msh_handle* h, const msh_camera_desc* d) {
+  if (!h || !d || !d->body || !d->pose) return fail(MSH_ERR_INVALID_ARG, "handle, descriptor or arrays are NULL");
+  if (d->num_cameras < 1 || d->num_cameras > 64 || d->width < 1 || d->width > 4096 || d->height < 1 ||
+      d->height > 4096)
+    return fail(MSH_ERR_INVALID_ARG, "num_cameras must be 1..64 and width, height 1..4096");
+  if (!(d->fov_y > 0.f) || !(d->fov_y < 3.14159265f) || !(d->near_ > 0.f) || !(d->far_ > d->near_))
+    return fail(MSH_ERR_INVALID_ARG, "fov_y must be in (0, pi) and 0 < near < far");
+  for (int e = 0; e < h->E; ++e) {
+    const int D = h->body_off_host[e + 1] - h->body_off_host[e];
+    const int S = h->static_off_host[e + 1] - h->static_off_host[e];
+    if (D + S > MSH_RENDER_MAX_PRIMS)
+      return fail(MSH_ERR_INVALID_ARG, "env " + std::to_string(e) + " has more than MSH_RENDER_MAX_PRIMS primitives");
+    for (int c = 0; c < d->num_cameras; ++c) {
+      const int b = d->body[e * d->num_cameras + c];
+      if (b < -1 || b >= D) return fail(MSH_ERR_INVALID_ARG, "env " + std::to_string(e) + ": mount body out of range");
+    }
+  }
+  cudaDeviceSynchronize();
+  if (h->d_cam_body) { cudaFree(h->d_cam_body); h->bytes -= (int64_t)h->E * h->cam_n * 4; h->d_cam_body = nullptr; }
+  if (h->d_cam_pose) { cudaFree(h->d_cam_pose); h->bytes -= (int64_t)h->E * h->cam_n * 28; h->d_cam_pose = nullptr; }
+  h->cam_n = 0;
+  int rc;
+  if ((rc = upload(h, &h->d_cam_body, d->body, (size_t)h->E * d->num_cameras))) return rc;
+  if ((rc = upload(h, &h->d_cam_pose, d->pose, (size_t)h->E * d->num_cameras * 7))) return rc;
+  h->cam_n = d->num_cameras; h->cam_w = d->width; h->cam_h = d->height;
+  h->cam_focal = (float)((double)d->height * 0.5 / std::tan((double)d->fov_y * 0.5));
+  h->cam_near = d->near_; h->cam_far = d->far_;
+  return MSH_OK;
+}
+
+int msh_render_depth(msh_handle* h, const msh_state* st, float* depth, void* stream) {
+  if (!h || !st || !st->pos || !st->quat || !depth) return fail(MSH_ERR_INVALID_ARG, "handle, state or output is NULL");
+  if (h->cam_n < 1) return fail(MSH_ERR_INVALID_ARG, "no cameras: call msh_set_cameras first");
+  RenderScene sc;
+  sc.E = h->E; sc.body_off = h->d_body_off; sc.static_off = h->d_static_off;
+  sc.bdims = h->d_bdims; sc.sworld = h->d_sworld; sc.pos = st->pos; sc.quat = st->quat;
+  RenderCams cm;
+  cm.ncam = h->cam_n; cm.width = h->cam_w; cm.height = h->cam_h;
+  cm.focal = h->cam_focal; cm.near_ = h->cam_near; cm.far_ = h->cam_far;
+  cm.body = h->d_cam_body; cm.pose = h->d_cam_pose;
+  return msh_render_launch(sc, cm, depth, (cudaStream_t)stream);
 }
 
 int64_t msh_scratch_bytes(const msh_handle* h) { return h ? h->bytes : 0; }

@@ -166,6 +166,50 @@ class Scene:
                 flags[b0 + b] |= 2
         return flags, fingers, np.asarray(self.goal_body, np.int32).copy()
 
+    def camera_mounts(self):
+        """Two depth cameras per env, standing in for the paper's head and arm
+        RGB-D cameras (Sec. 4.2). Camera frames look along +x. Head camera: on
+        the mobile base 1 m above its centre, or 0.6 m behind and 0.9 m above
+        a fixed arm's first joint, pitched down 0.6 rad; without a robot, in
+        the world at (-1.5, 0, 1.2) pitched down 0.5 rad. Arm camera: on the
+        hand (the fingers' parent link), 6 cm off its axis at the tip, looking
+        along the link; without a robot, at (0, -1.5, 1.2) facing +y.
+        Returns (body [E, 2] env-local or -1, pose [E, 2, 7])."""
+        E = self.num_envs
+        body = np.full((E, 2), -1, np.int32)
+        pose = np.zeros((E, 2, 7), np.float32)
+
+        def pitch(a):
+            return (np.cos(a / 2), 0.0, np.sin(a / 2), 0.0)
+        for e in range(E):
+            j0, j1 = self.joint_off[e], self.joint_off[e + 1]
+            hand = -1
+            for g in range(j0, j1):
+                if self.joint_type[g] == PRISMATIC and self.joint_parent[g] >= 0:
+                    hand = int(self.joint_parent[g])
+                    break
+            if j1 > j0 and self.joint_type[j0] == PLANAR:
+                body[e, 0] = int(self.joint_child[j0])
+                pose[e, 0] = (0.0, 0.0, 1.0) + pitch(0.6)
+            elif j1 > j0:
+                a = self.joint_frame_a[j0][:3]
+                pose[e, 0] = (a[0] - 0.6, a[1], a[2] + 0.9) + pitch(0.6)
+            else:
+                pose[e, 0] = (-1.5, 0.0, 1.2) + pitch(0.5)
+            if hand >= 0:
+                g = self.body_off[e] + hand
+                body[e, 1] = hand
+                pose[e, 1] = (float(self.body_dims[g][1]), 0.0, 0.06, 1.0, 0.0, 0.0, 0.0)
+            else:
+                yaw = (np.cos(np.pi / 4), 0.0, 0.0, np.sin(np.pi / 4))
+                p_ = pitch(0.5)
+                w0, x0, y0, z0 = yaw
+                w1, x1, y1, z1 = p_
+                q = (w0 * w1 - x0 * x1 - y0 * y1 - z0 * z1, w0 * x1 + x0 * w1 + y0 * z1 - z0 * y1,
+                     w0 * y1 - x0 * z1 + y0 * w1 + z0 * x1, w0 * z1 + x0 * y1 - y0 * x1 + z0 * w1)
+                pose[e, 1] = (0.0, -1.5, 1.2) + q
+        return body, pose
+
     def state(self):
         """Fresh copies of the initial state arrays (pos, quat, linvel, angvel)."""
         return (self.pos.copy(), self.quat.copy(), self.linvel.copy(),

@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import EXEC_FUSED, EXEC_PLAIN, EXEC_SUBSTEP, ReportDesc, SceneDesc, SolverCfg, State, check
+from ._lib import EXEC_FUSED, EXEC_PLAIN, EXEC_SUBSTEP, CameraDesc, ReportDesc, SceneDesc, SolverCfg, State, check
 
 
 def _c(a, dt):
@@ -187,6 +187,30 @@ class MshSim:
         res["aabb_body"] = res["aabb_body"][:sc.num_bodies]
         res["aabb_static"] = res["aabb_static"][:sc.num_statics]
         return res
+
+    # -- depth cameras ---------------------------------------------------------
+    def set_cameras(self, body, pose, width: int = 128, height: int = 128, fov_y: float = np.pi / 2,
+                    near: float = 0.01, far: float = 10.0):
+        """Depth cameras (msh_set_cameras): body [E, ncam] env-local mount bodies
+        (-1: world), pose [E, ncam, 7] mount-local poses (position, quaternion)."""
+        E = self.scene.num_envs
+        b = np.ascontiguousarray(body, np.int32).reshape(E, -1)
+        ps = np.ascontiguousarray(pose, np.float32).reshape(E, b.shape[1], 7)
+        d = CameraDesc(b.shape[1], int(width), int(height), float(fov_y), float(near), float(far),
+                       b.ctypes.data, ps.ctypes.data)
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_set_cameras(self.handle, C.byref(d)), "msh_set_cameras")
+        self.cam_shape = (E, b.shape[1], int(height), int(width))
+
+    def render_depth(self, out=None, stream=None):
+        """Depth images [E, ncam, H, W] (z-depth in m, 0 = no hit) at the current state."""
+        if out is None:
+            out = torch.empty(self.cam_shape, dtype=torch.float32, device=self.device)
+        st = self._state()
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_render_depth(self.handle, C.byref(st), C.c_void_p(out.data_ptr()), _stream(stream)),
+                  "msh_render_depth")
+        return out
 
     # -- contact report ---------------------------------------------------------
     def set_report(self, body_flags, fingers=None, target=None, grasp_min_force: float = 0.5,
