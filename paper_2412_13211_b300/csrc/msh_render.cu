@@ -14,10 +14,13 @@
 // IEEE FP32 without FMA contraction (the library is built with -fmad=false),
 // in a fixed operation order.
 //
-// Kernel: one CTA per 32x32 tile of one camera of one env. The CTA builds the
-// env's primitives in world space, keeps those whose bounding sphere meets
-// the tile's view frustum (a conservative test: a kept primitive only costs
-// time), and every thread then casts its 4 pixels against the kept list.
+// Kernel: one CTA (8 warps) per 32x32 tile of one camera of one env. The CTA
+// builds the env's primitives in world space with widened bounding spheres;
+// each warp then keeps those meeting the view frustum of its own 8x16 pixel
+// block and orders them by the smallest z-depth their bounding sphere allows.
+// A pixel walks that order and stops at the first primitive that cannot come
+// nearer than its current hit. Both tests are conservative (bounding spheres
+// widened by 1 % and 1 mm), so the result is the brute-force minimum.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -127,9 +130,32 @@ __device__ __forceinline__ void camera_pose(const RenderScene& p, const RenderCa
   qmat3(q[0], q[1], q[2], q[3], Mc);
 }
 
+// Inward unit normals of the four side planes of the view frustum through
+// pixel rectangle [u0, u1] x [v0, v1] (pixel-edge coordinates).
+__device__ __forceinline__ void frustum(const float Mc[3][3], float f, float cx, float cy, float u0, float u1,
+                                        float v0, float v1, float3 nrm[4]) {
+  const float3 cr[4] = {mul3(Mc, mk3(1.f, -((u0 - cx) / f), -((v0 - cy) / f))),
+                        mul3(Mc, mk3(1.f, -((u1 - cx) / f), -((v0 - cy) / f))),
+                        mul3(Mc, mk3(1.f, -((u1 - cx) / f), -((v1 - cy) / f))),
+                        mul3(Mc, mk3(1.f, -((u0 - cx) / f), -((v1 - cy) / f)))};
+  const float3 mid = mul3(Mc, mk3(1.f, -((0.5f * (u0 + u1) - cx) / f), -((0.5f * (v0 + v1) - cy) / f)));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float3 a = cr[k], b = cr[(k + 1) & 3];
+    float3 n = mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    if (dot3(n, mid) < 0.f) n = scl3(n, -1.f);
+    nrm[k] = scl3(n, 1.f / sqrtf(dot3(n, n)));
+  }
+}
+
+enum { WB_W = 8, WB_H = 16, WARPS = RT_THREADS / 32 };
+
 __global__ void __launch_bounds__(RT_THREADS) k_render(RenderScene p, RenderCams cm, float* depth) {
   __shared__ float s_prim[MSH_RENDER_MAX_PRIMS * PRIM_F];
-  __shared__ int s_n;
+  __shared__ float4 s_bs[MSH_RENDER_MAX_PRIMS];                // widened bounding sphere: centre - camera, radius
+  __shared__ float s_near[WARPS][MSH_RENDER_MAX_PRIMS];        // per warp: near bound of each kept primitive
+  __shared__ unsigned char s_keep[WARPS][MSH_RENDER_MAX_PRIMS];
+  __shared__ unsigned char s_order[WARPS][MSH_RENDER_MAX_PRIMS];
   const int env = blockIdx.z, c = blockIdx.y;
   const int tiles_x = (cm.width + TILE - 1) / TILE;
   const int tx0 = (blockIdx.x % tiles_x) * TILE, ty0 = (blockIdx.x / tiles_x) * TILE;
@@ -139,31 +165,8 @@ __global__ void __launch_bounds__(RT_THREADS) k_render(RenderScene p, RenderCams
   float Mc[3][3];
   camera_pose(p, cm, env, b0, c, o, Mc);
   const float f = cm.focal, cx = (float)cm.width * 0.5f, cy = (float)cm.height * 0.5f;
-  // the tile's view frustum: its four side planes through the camera centre,
-  // inward normals in world space (from the tile's corner rays)
-  float3 nrm[4];
-  {
-    const float u0 = (float)tx0, u1 = (float)min(tx0 + TILE, cm.width);
-    const float v0 = (float)ty0, v1 = (float)min(ty0 + TILE, cm.height);
-    const float3 r00 = mul3(Mc, mk3(1.f, -((u0 - cx) / f), -((v0 - cy) / f)));
-    const float3 r10 = mul3(Mc, mk3(1.f, -((u1 - cx) / f), -((v0 - cy) / f)));
-    const float3 r11 = mul3(Mc, mk3(1.f, -((u1 - cx) / f), -((v1 - cy) / f)));
-    const float3 r01 = mul3(Mc, mk3(1.f, -((u0 - cx) / f), -((v1 - cy) / f)));
-    const float3 cr[4] = {r00, r10, r11, r01};
-    const float3 mid = mul3(Mc, mk3(1.f, -((0.5f * (u0 + u1) - cx) / f), -((0.5f * (v0 + v1) - cy) / f)));
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float3 a = cr[k], b = cr[(k + 1) & 3];
-      float3 n = mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-      if (dot3(n, mid) < 0.f) n = scl3(n, -1.f);
-      const float len = sqrtf(dot3(n, n));
-      nrm[k] = scl3(n, 1.f / len);
-    }
-  }
   const float3 fwd = mk3(Mc[0][0], Mc[1][0], Mc[2][0]);
-  if (threadIdx.x == 0) s_n = 0;
-  __syncthreads();
-  // primitives of the env whose bounding sphere meets the tile's frustum
+  // the env's primitives in world space
   for (int i = threadIdx.x; i < D + S; i += blockDim.x) {
     float rec[PRIM_F];
     float3 cen;
@@ -205,29 +208,67 @@ __global__ void __launch_bounds__(RT_THREADS) k_render(RenderScene p, RenderCams
       rec[13] = m0.w; rec[14] = m1.w; rec[15] = m2.w;
       rho = sqrtf(m0.w * m0.w + m1.w * m1.w + m2.w * m2.w);
     }
-    // conservative: widened by 1 % and 1 mm so that rounding never drops a primitive that a ray hits
+    float* dst = s_prim + i * PRIM_F;
+#pragma unroll
+    for (int q = 0; q < PRIM_F; ++q) dst[q] = rec[q];
+    // widened by 1 % and 1 mm so that rounding never drops a primitive that a ray hits
     const float3 w = sub3(cen, o);
-    const float rr = rho * 1.01f + 1e-3f;
-    bool keep = dot3(w, fwd) >= cm.near_ - rr && dot3(w, fwd) <= cm.far_ + rr;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) keep = keep && dot3(nrm[k], w) >= -rr;
-    if (keep) {
-      const int slot = atomicAdd(&s_n, 1);
-      float* dst = s_prim + slot * PRIM_F;
-#pragma unroll
-      for (int q = 0; q < PRIM_F; ++q) dst[q] = rec[q];
-    }
+    s_bs[i] = make_float4(w.x, w.y, w.z, rho * 1.01f + 1e-3f);
   }
   __syncthreads();
-  const int n = s_n;
-  const int col = tx0 + (threadIdx.x & (TILE - 1));
-  for (int row = ty0 + (threadIdx.x >> 5); row < min(ty0 + TILE, cm.height); row += RT_THREADS / TILE) {
-    if (col >= cm.width) break;
+  // per warp: the primitives meeting its block's frustum, in near-bound order
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bx0 = tx0 + (warp % (TILE / WB_W)) * WB_W, by0 = ty0 + (warp / (TILE / WB_W)) * WB_H;
+  float3 nrm[4];
+  frustum(Mc, f, cx, cy, (float)bx0, (float)min(bx0 + WB_W, cm.width), (float)by0, (float)min(by0 + WB_H, cm.height),
+          nrm);
+  int n = 0;
+  for (int base = 0; base < D + S; base += 32) {
+    const int i = base + lane;
+    bool keep = false;
+    float nb = 0.f;
+    if (i < D + S) {
+      const float4 bs = s_bs[i];
+      const float3 w = mk3(bs.x, bs.y, bs.z);
+      const float zc = dot3(w, fwd);
+      keep = zc >= cm.near_ - bs.w && zc <= cm.far_ + bs.w;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) keep = keep && dot3(nrm[k], w) >= -bs.w;
+      nb = zc - bs.w;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int slot = n + __popc(m & ((1u << lane) - 1u));
+      s_keep[warp][slot] = (unsigned char)i;
+      s_near[warp][slot] = nb;
+    }
+    n += __popc(m);
+  }
+  __syncwarp();
+  for (int a = lane; a < n; a += 32) {   // rank sort, ties by position
+    const float key = s_near[warp][a];
+    int rank = 0;
+    for (int b = 0; b < n; ++b) {
+      const float kb = s_near[warp][b];
+      rank += (kb < key) || (kb == key && b < a);
+    }
+    s_order[warp][rank] = (unsigned char)a;
+  }
+  __syncwarp();
+  const int col = bx0 + (lane % WB_W);
+  for (int row = by0 + lane / WB_W; row < by0 + WB_H; row += 32 / WB_W) {
+    if (col >= cm.width || row >= cm.height) break;
     const float u = (float)col + 0.5f, v = (float)row + 0.5f;
     const float3 Dw = mul3(Mc, mk3(1.f, -((u - cx) / f), -((v - cy) / f)));
     float best = INFINITY;
+    if (Dw.z < 0.f) {   // ground plane z = 0
+      const float s = -o.z / Dw.z;
+      if (s >= cm.near_) best = s;
+    }
     for (int k = 0; k < n; ++k) {
-      const float* pr = s_prim + k * PRIM_F;
+      const int a = s_order[warp][k];
+      if (s_near[warp][a] > best) break;   // this and every later primitive lie beyond the current hit
+      const float* pr = s_prim + s_keep[warp][a] * PRIM_F;
       const int ty = __float_as_int(pr[0]);
       const float3 w = sub3(o, mk3(pr[1], pr[2], pr[3]));
       float s;
@@ -245,10 +286,6 @@ __global__ void __launch_bounds__(RT_THREADS) k_render(RenderScene p, RenderCams
         s = hit_box(ob, db, mk3(pr[13], pr[14], pr[15]), cm.near_);
       }
       if (s < best) best = s;
-    }
-    if (Dw.z < 0.f) {   // ground plane z = 0
-      const float s = -o.z / Dw.z;
-      if (s >= cm.near_ && s < best) best = s;
     }
     depth[(((size_t)env * cm.ncam + c) * cm.height + row) * cm.width + col] = best <= cm.far_ ? best : 0.f;
   }
