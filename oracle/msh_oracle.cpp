@@ -841,6 +841,15 @@ template <class R> struct Solver {
         soft(r, theta - tgt[j.dof], j.k, j.d, j.fmax);
         rows.push_back(r);
       }
+      if (j.lo < j.hi) {   // hinge angle limits lo <= theta <= hi, speculative unilateral rows
+        R theta = R(2) * atan2_(qr.x, qr.w);
+        for (int e = 0; e < 2; ++e) {
+          Row<R> r = ang_row(A, B, e == 0 ? ux : -ux, ROW_UNILATERAL);
+          R C = e == 0 ? theta - j.lo : j.hi - theta;
+          r.bias = C > R(0) ? C / h : beta * C;
+          rows.push_back(r);
+        }
+      }
     } else if (j.type == PRISMATIC) {
       V3<R> us[2] = {uy, uz};
       for (int k = 0; k < 2; ++k) {

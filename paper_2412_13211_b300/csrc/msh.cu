@@ -700,7 +700,7 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
       j.k = gn[0]; j.d = gn[1]; j.fmax = gn[2];
       j.lo = d->joint_limits[2 * g]; j.hi = d->joint_limits[2 * g + 1];
       j.roff = roff;
-      roff += joint_row_count(j.type, drive);
+      roff += joint_row_count(j);
     }
     Rm = std::max(Rm, roff);
   }

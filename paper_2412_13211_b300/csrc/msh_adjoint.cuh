@@ -380,7 +380,7 @@ __device__ void joint_geom_adjoint(const Params& p, const EnvInfo& e, const Ws& 
   const int A = j.parent, B = j.child;
   const bool drive = j.k > 0.f || j.d > 0.f;
   const int nd = drive ? joint_ndof(j.type) : 0;
-  const int nr = joint_row_count(j.type, drive);
+  const int nr = joint_row_count(j);
   float4 xa4 = A >= 0 ? w.bx[A] : make_float4(0.f, 0.f, 0.f, 0.f);
   float4 qa4 = A >= 0 ? w.bq[A] : make_float4(1.f, 0.f, 0.f, 0.f);
   float4 xb4 = w.bx[B], qb4 = w.bq[B];
@@ -464,7 +464,7 @@ __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, co
     for (int q = 0; q < 14; ++q) pose[q] = 0.f;
     if (k < J) {
       const JointDesc& j = p.joints[e.j0 + k];
-      const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
+      const int nr = joint_row_count(j);
       for (int r = 0; r < nr; ++r) reverse_mass_part(a, jrow(k, r), A, B, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
       float out[17];
       joint_geom_adjoint(p, e, w, a, k, tg, out);

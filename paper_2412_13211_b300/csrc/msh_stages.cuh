@@ -23,11 +23,13 @@ struct JointDesc {     // 96 bytes
   int roff;            // first solver row of this joint within its env's joint rows
 };
 
-// Solver rows of a joint: revolute 3 linear + 2 angular + limit (+ drive),
-// prismatic 3 angular + 2 linear + 2 limits (+ drive), planar 3 (+ 3 drives).
-__host__ __device__ __forceinline__ int joint_row_count(int type, bool drive) {
-  if (type == JT_REVOLUTE) return drive ? 6 : 5;
-  if (type == JT_PRISMATIC) return drive ? 8 : 7;
+// Solver rows of a joint: revolute 3 linear + 2 angular (+ drive) (+ 2 angle
+// limits when lo < hi), prismatic 2 linear + 3 angular (+ drive) + 2 limits,
+// planar 3 (+ 3 drives).
+__host__ __device__ __forceinline__ int joint_row_count(const JointDesc& j) {
+  const bool drive = j.k > 0.f || j.d > 0.f;
+  if (j.type == JT_REVOLUTE) return 5 + (drive ? 1 : 0) + (j.lo < j.hi ? 2 : 0);
+  if (j.type == JT_PRISMATIC) return drive ? 8 : 7;
   return drive ? 6 : 3;
 }
 
@@ -245,7 +247,7 @@ __device__ __forceinline__ void load_statics(const Params& p, const EnvInfo& e, 
 __device__ __forceinline__ void load_jinfo(const Params& p, const EnvInfo& e, const Ws& w) {
   for (int k = e.lane; k < e.J; k += e.nthr) {
     const JointDesc& j = p.joints[e.j0 + k];
-    w.jinfo[k] = make_int4(j.parent, j.child, j.roff, joint_row_count(j.type, j.k > 0.f || j.d > 0.f));
+    w.jinfo[k] = make_int4(j.parent, j.child, j.roff, joint_row_count(j));
   }
 }
 
@@ -678,6 +680,16 @@ __device__ int joint_geom(const JointDesc& j, bool hasA, const V3<T>& xa, const 
       g_soft(r, h, theta - tgt[0], j.k, j.d, j.fmax);
       rows[n++] = r;
     }
+    if (j.lo < j.hi) {   // hinge angle limits (unilateral, speculative like the prismatic limits)
+      T theta = T(2.f) * atan2_(qr.x, qr.w);
+      for (int c = 0; c < 2; ++c) {
+        GRow<T> r = g_ang(c == 0 ? ux : -ux);
+        T C = c == 0 ? theta - T(j.lo) : T(j.hi) - theta;
+        r.bias = C > T(0.f) ? C / T(h) : tb * C;
+        r.clamp = CLAMP_UNI;
+        rows[n++] = r;
+      }
+    }
   } else if (j.type == JT_PRISMATIC) {
     V3<T> us[2] = {uy, uz};
     for (int c = 0; c < 2; ++c) {
@@ -950,7 +962,7 @@ __device__ __forceinline__ void tape_lambdas(const Params& p, const EnvInfo& e, 
   float* t = tape_env(p, e.env) + tl.t2 + (long long)(sub * p.N + it) * p.tape_Rm;
   if (k < e.J) {
     const JointDesc& j = p.joints[e.j0 + k];
-    const int nr = joint_row_count(j.type, j.k > 0.f || j.d > 0.f);
+    const int nr = joint_row_count(j);
     const float4* rows = w.jr + (size_t)j.roff * ROW_F4;
     for (int r = 0; r < nr; ++r) t[k * ROWS_PER_JOINT + r] = rows[ROW_F4 * r + 3].w;
   } else {

@@ -875,3 +875,47 @@ def test_hanging_link_frames():
     for qw in (QW_AXIS_Y, QW_AXIS_Z):
         ql = _local_frame(Q_HANG, qw)
         np.testing.assert_allclose(quat_mul(Q_HANG, ql), qw, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# hinge limits (articulated receptacles: a fridge door)
+# --------------------------------------------------------------------------
+def _door(limits, w0):
+    """A door panel on a vertical hinge at its edge (hinge frame: local x = world z)."""
+    e = env()
+    q_up = axis_angle((0.0, 1.0, 0.0), -np.pi / 2)               # local x -> world z
+    # spinning about the hinge: centre velocity w x r, r = 0.3 m along world x
+    e.body(S.BOX, (0.3, 0.02, 0.4), 5.0, (0.3, 0.0, 1.0), linvel=(0.0, 0.3 * w0, 0.0), angvel=(0.0, 0.0, w0))
+    e.joint(S.REVOLUTE, -1, 0, (0.0, 0.0, 1.0) + tuple(q_up), (-0.3, 0.0, 0.0) + tuple(q_up),
+            (0.0, 0.0, 0.0), limits, [])
+    return e
+
+
+def _door_angle(q):
+    # the panel's local x axis in world
+    w, x, y, z = q
+    ax = np.array([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)])
+    return np.arctan2(ax[1], ax[0])
+
+
+@pytest.mark.parametrize("w0,bound", [(3.0, 1.2), (-3.0, 0.0)])
+def test_hinge_limits_stop_the_door(w0, bound):
+    sc = scene_from_envs([_door((0.0, 1.2), w0)])
+    c = cfg(substeps=4, iterations=20, gravity=(0.0, 0.0, 0.0))
+    st = sc.state()
+    angles = []
+    for _ in range(60):
+        st, status = oracle.step(sc, c, st, None, 1, "f64")
+        angles.append(_door_angle(st[1][0]))
+    angles = np.array(angles)
+    assert (angles <= 1.2 + 2e-3).all() and (angles >= -2e-3).all()
+    assert abs(angles[-1] - bound) < 2e-3                       # resting on the limit
+    assert abs(st[3][0][2]) < 5e-3                               # and stopped (no restitution; Baumgarte residue)
+
+
+def test_hinge_without_limits_keeps_turning():
+    sc = scene_from_envs([_door((0.0, 0.0), 3.0)])               # lo == hi: no limit rows
+    c = cfg(substeps=4, iterations=20, gravity=(0.0, 0.0, 0.0))
+    st, _ = oracle.step(sc, c, sc.state(), None, 50, "f64")
+    assert abs(st[3][0][2] - 3.0) < 2e-3                         # free spin about the hinge (solver drift)
+    assert abs(_door_angle(st[1][0]) - np.angle(np.exp(1j * 1.5))) < 1e-2   # 3 rad/s for 0.5 s
