@@ -594,10 +594,51 @@ def _cfg4_env(rng):
     return env
 
 
-def _apartment_env(rng, n_obj, n_static, kinds, size_lo, size_hi, mass_fn):
+DRAWER_GAINS = (0.0, 5.0, 100.0)   # a damper only (no spring): passive articulations
+DRAWER_LIMITS = (0.0, 0.35)
+DOOR_LIMITS = (0.0, 1.57)
+
+
+def _add_receptacles(env, W, D, foot):
+    """A kitchen cabinet with a drawer and a fridge with a door against the +y
+    wall (the paper's articulated receptacles, Sec. 3.1): the drawer slides out
+    of the cabinet's cavity on a prismatic joint (0-0.35 m), the door swings
+    into the room on a vertical hinge at its right edge (0-1.57 rad). Both are
+    passive (damped) joints. Uses 5 static boxes."""
+    yw = 0.5 * D
+    # cabinet x in [-1.2, -0.4], 0.6 deep, 0.8 high: side panels, top, bottom around a cavity
+    x0, x1, y0 = -1.2, -0.4, yw - 0.6
+    cx = 0.5 * (x0 + x1)
+    env.static((x0 + 0.02, yw - 0.3, 0.4), (0.02, 0.3, 0.4))
+    env.static((x1 - 0.02, yw - 0.3, 0.4), (0.02, 0.3, 0.4))
+    env.static((cx, yw - 0.3, 0.79), (0.5 * (x1 - x0), 0.3, 0.01))
+    env.static((cx, yw - 0.3, 0.35), (0.5 * (x1 - x0) - 0.04, 0.3, 0.02))
+    # the drawer: a box in the cavity, front flush with the cabinet front
+    dh = (0.5 * (x1 - x0) - 0.05, 0.28, 0.17)
+    dc = (cx, y0 + dh[1], 0.35 + 0.02 + dh[2] + 0.01)
+    drawer = env.body(BOX, dh, 2.0, dc)
+    q_out = (np.cos(-np.pi / 4), 0.0, 0.0, np.sin(-np.pi / 4))        # joint axis (local x) = world -y
+    env.joint(PRISMATIC, -1, drawer, dc + q_out, (0.0, 0.0, 0.0) + q_out, DRAWER_GAINS, DRAWER_LIMITS,
+              [(0.0, 0.0, DRAWER_LIMITS[0], DRAWER_LIMITS[1])])
+    foot.append((x0, x1, yw - 0.6 - 0.4, yw))                          # keep the drawer's path clear
+    # fridge x in [0.4, 1.1], 0.6 deep, 1.8 high; the door in front of it
+    fx0, fx1 = 0.4, 1.1
+    env.static((0.5 * (fx0 + fx1), yw - 0.3, 0.9), (0.5 * (fx1 - fx0), 0.3, 0.9))
+    hx = 0.5 * (fx1 - fx0)
+    door_c = (0.5 * (fx0 + fx1), yw - 0.6 - 0.025, 0.9)
+    door = env.body(BOX, (hx, 0.02, 0.85), 8.0, door_c)
+    q_up = (np.cos(-np.pi / 4), 0.0, np.sin(-np.pi / 4), 0.0)          # hinge frame: local x = world z
+    hinge = (fx1, door_c[1], door_c[2])
+    env.joint(REVOLUTE, -1, door, hinge + q_up, (hx, 0.0, 0.0) + q_up, DRAWER_GAINS, DOOR_LIMITS,
+              [(0.0, 0.0, DOOR_LIMITS[0], DOOR_LIMITS[1])])
+    foot.append((fx0 - 0.1, fx1 + 0.1, yw - 0.6 - 0.8, yw))           # the door's swing
+
+
+def _apartment_env(rng, n_obj, n_static, kinds, size_lo, size_hi, mass_fn, receptacles=False):
     """A rectangular room (3-6 m sides) with four walls, counters and shelves
     along the walls, island counters when the walls are full, objects resting on
-    furniture or the floor, and the mobile manipulator near the room centre."""
+    furniture or the floor, and the mobile manipulator near the room centre;
+    with `receptacles`, a cabinet drawer and a fridge door (5 of the statics)."""
     env = _Env()
     W, D = float(rng.uniform(3, 6)), float(rng.uniform(3, 6))
     t, H = 0.1, 2.5
@@ -610,6 +651,9 @@ def _apartment_env(rng, n_obj, n_static, kinds, size_lo, size_hi, mass_fn):
     keep = [(rb[0], rb[1], 0.6)]
     surf = _Surfaces()
     foot = []   # furniture footprints (x0, x1, y0, y1)
+    if receptacles:
+        _add_receptacles(env, W, D, foot)
+        left -= 5
 
     def counter(x0, x1, y0, y1, h=0.9):
         env.static((0.5 * (x0 + x1), 0.5 * (y0 + y1), 0.5 * h),
@@ -740,8 +784,11 @@ def make_config(idx: int, num_envs: int | None = None, seed: int = 0, env_start:
        4x16, goal position per env.
     5: 16384 envs, apartment rooms with 50 static boxes, 32 objects
        (spheres, capsules, boxes; log-uniform mass), mobile manipulator, 4x20.
+    6: 4096 envs, the apartment rooms of 3 with a cabinet drawer and a fridge
+       door (articulated receptacles, passive), U{4..32} objects, 4x20; the
+       workload of the 20 Hz control wrapper.
     """
-    defaults = {1: 64, 2: 1024, 3: 4096, 4: 512, 5: 16384}
+    defaults = {1: 64, 2: 1024, 3: 4096, 4: 512, 5: 16384, 6: 4096}
     E = defaults[idx] if num_envs is None else int(num_envs)
     envs = []
     for e in range(env_start, env_start + E):
@@ -760,6 +807,11 @@ def make_config(idx: int, num_envs: int | None = None, seed: int = 0, env_start:
         elif idx == 5:
             envs.append(_apartment_env(rng, 32, 50, (SPHERE, CAPSULE, BOX), 0.03, 0.20,
                                        lambda: float(np.exp(rng.uniform(np.log(0.05), np.log(5.0))))))
+        elif idx == 6:
+            n_obj = int(rng.integers(4, 33))
+            n_st = int(rng.integers(15, 61))
+            envs.append(_apartment_env(rng, n_obj, n_st, (SPHERE, CAPSULE, BOX), 0.03, 0.15,
+                                       lambda: rng.uniform(0.05, 0.5), receptacles=True))
         else:
             raise ValueError(idx)
     scene = _pack(f"config{idx}", envs, seed, meta={"config": idx})
@@ -770,7 +822,8 @@ def make_config(idx: int, num_envs: int | None = None, seed: int = 0, env_start:
         3: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=160, max_pairs=96),
         4: SolverCfg(dt=0.01, substeps=4, iterations=16, max_contacts=48, max_pairs=24),
         5: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=128, max_pairs=64),
+        6: SolverCfg(dt=0.01, substeps=4, iterations=20, max_contacts=160, max_pairs=96),
     }[idx]
-    steps = {1: 100, 2: 200, 3: 500, 4: 64, 5: 500}[idx]
+    steps = {1: 100, 2: 200, 3: 500, 4: 64, 5: 500, 6: 500}[idx]
     scene.meta["steps"] = steps
     return scene, cfg

@@ -15,7 +15,7 @@ from paper_2412_13211_b300 import scenes as S
 
 pytestmark = pytest.mark.gpu
 
-SMALL = {1: 16, 2: 8, 3: 16, 4: 8, 5: 6}
+SMALL = {1: 16, 2: 8, 3: 16, 4: 8, 5: 6, 6: 8}
 TOL_X, TOL_V = 1e-5, 1e-4
 
 _cache = {}
@@ -50,7 +50,7 @@ def oracle_states(sc, cfg, steps):
     return out + [a, b]
 
 
-@pytest.mark.parametrize("idx", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("idx", [1, 2, 3, 4, 5, 6])
 def test_collision_stage_bit_exact(idx):
     sc, cfg = scene(idx)
     sim = make_sim(sc, cfg)
@@ -96,7 +96,7 @@ def _err(a, b):
 
 
 @pytest.mark.parametrize("mode", [S.MODE_COLOURED, S.MODE_JACOBI])
-@pytest.mark.parametrize("idx", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("idx", [1, 2, 3, 4, 5, 6])
 def test_one_step_parity(idx, mode, record_property):
     sc, cfg = scene(idx, mode=mode)
     gpu, o32, o64, status, st32 = _step_both(sc, cfg, 1)
@@ -132,7 +132,7 @@ def test_hundred_steps_non_chaotic(idx, record_property):
     assert not (status & 8).any()
 
 
-@pytest.mark.parametrize("idx", [2, 3])
+@pytest.mark.parametrize("idx", [2, 3, 6])
 def test_plain_fused_graph_and_block_sizes_bitwise_equal(idx):
     sc, cfg = scene(idx)
     import torch

@@ -36,7 +36,7 @@ def _gpu(sc, cfg, tg, steps, W, H, body, pose):
 
 
 @pytest.mark.parametrize("idx,envs,W,H", [(1, 8, 128, 128), (2, 4, 128, 128), (3, 6, 128, 128), (4, 4, 70, 45),
-                                          (5, 3, 96, 128)])
+                                          (5, 3, 96, 128), (6, 3, 128, 128)])
 def test_depth_matches_oracle_bitwise(idx, envs, W, H):
     sc, cfg = S.make_config(idx, num_envs=envs)
     tg = sc.target_walk(3) if sc.max_dof > 0 else None

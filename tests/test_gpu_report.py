@@ -48,7 +48,7 @@ def _settled_state(sc, cfg, targets, n):
     return [np.ascontiguousarray(a, np.float32) for a in out]
 
 
-@pytest.mark.parametrize("idx,envs", [(2, 16), (4, 16), (3, 8)])
+@pytest.mark.parametrize("idx,envs", [(2, 16), (4, 16), (3, 8), (6, 8)])
 def test_report_matches_oracle_one_step(idx, envs):
     sc, cfg = S.make_config(idx, num_envs=envs)
     spec = sc.report_spec()
