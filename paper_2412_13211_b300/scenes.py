@@ -31,6 +31,8 @@ import numpy as np
 SPHERE, CAPSULE, BOX = 0, 1, 2
 REVOLUTE, PRISMATIC, PLANAR = 0, 1, 2
 MODE_COLOURED, MODE_JACOBI = 0, 1
+# controller kinds of a DoF column (the control wrapper's descriptor)
+CTRL_HOLD, CTRL_DELTA, CTRL_ABS, CTRL_BASE_X, CTRL_BASE_Y, CTRL_BASE_YAW = 0, 1, 2, 3, 4, 5
 
 _S2 = float(np.sqrt(0.5))
 Q_ID = (1.0, 0.0, 0.0, 0.0)
@@ -88,6 +90,22 @@ class SolverCfg:
     slop: float = 0.001
     max_contacts: int = 256
     max_pairs: int = 1024
+
+
+@dataclass
+class ControllerSpec:
+    """Per-DoF-column controller descriptor, shared by every env of a scene
+    (Sec. 4.1: joint delta-position control of the arm, base linear and
+    angular velocity, actions normalised to [-1, 1]; Sec. 4.2: 100 Hz physics
+    under 20 Hz control, i.e. 5 physics steps per action)."""
+    action_dim: int
+    kind: np.ndarray     # int32 [max_dof]  CTRL_*
+    action: np.ndarray   # int32 [max_dof]  action column (-1 for CTRL_HOLD)
+    scale: np.ndarray    # f32 [max_dof]    delta per action (DELTA) or speed per action (BASE_*)
+    lo: np.ndarray       # f32 [max_dof]    target range
+    hi: np.ndarray       # f32 [max_dof]
+    yaw_dof: int         # the base's yaw column (-1: no base)
+    steps_per_action: int = 5
 
 
 @dataclass
@@ -209,6 +227,63 @@ class Scene:
                      w0 * y1 - x0 * z1 + y0 * w1 + z0 * x1, w0 * z1 + x0 * y1 - y0 * x1 + z0 * w1)
                 pose[e, 1] = (0.0, -1.5, 1.2) + q
         return body, pose
+
+    def controller_spec(self, arm_delta: float = 0.1, base_speed: float = 1.0, base_turn: float = 1.5,
+                        steps_per_action: int = 5) -> ControllerSpec:
+        """The robot's action layout: one column per arm joint (delta position,
+        `arm_delta` rad per action), one gripper column driving both fingers to
+        an absolute opening in their range, and for a mobile base a linear
+        (`base_speed` m/s) and an angular (`base_turn` rad/s) velocity column.
+        Joints whose drive has no stiffness (the passive drawer and door) keep
+        their targets. Every env must share one DoF layout."""
+        E, D = self.num_envs, self.max_dof
+        if E == 0 or D == 0:
+            raise ValueError("the scene has no actuated joints")
+        specs = []
+        for e in range(E):
+            kind = np.zeros(D, np.int32)
+            act = np.full(D, -1, np.int32)
+            scale = np.zeros(D, np.float32)
+            arm, grip, yaw = [], [], -1
+            for g in range(self.joint_off[e], self.joint_off[e + 1]):
+                d, jt = int(self.joint_dof[g]), int(self.joint_type[g])
+                if self.joint_gains[g][0] <= 0.0:
+                    continue
+                if jt == PLANAR:
+                    kind[d:d + 3] = (CTRL_BASE_X, CTRL_BASE_Y, CTRL_BASE_YAW)
+                    yaw = d + 2
+                elif jt == REVOLUTE:
+                    arm.append(d)
+                elif jt == PRISMATIC and self.joint_parent[g] >= 0:
+                    grip.append(d)
+            for k, d in enumerate(arm):
+                kind[d], act[d], scale[d] = CTRL_DELTA, k, arm_delta
+            na = len(arm)
+            for d in grip:
+                kind[d], act[d] = CTRL_ABS, na
+            A = na + (1 if grip else 0)
+            if yaw >= 0:
+                for d in (yaw - 2, yaw - 1):
+                    act[d], scale[d] = A, base_speed
+                act[yaw], scale[yaw] = A + 1, base_turn
+                A += 2
+            specs.append((A, kind, act, scale, yaw))
+        A, kind, act, scale, yaw = specs[0]
+        for s_ in specs[1:]:
+            if s_[0] != A or s_[4] != yaw or not (np.array_equal(s_[1], kind) and np.array_equal(s_[2], act)):
+                raise ValueError("envs differ in their DoF layout")
+        lo, hi = self.dof_lo[0].copy(), self.dof_hi[0].copy()
+        ctl = kind != CTRL_HOLD
+        if not (np.all(self.dof_lo[:, ctl] == lo[ctl]) and np.all(self.dof_hi[:, ctl] == hi[ctl])):
+            raise ValueError("envs differ in the ranges of their actuated DoFs")
+        return ControllerSpec(action_dim=int(A), kind=kind, action=act, scale=scale, lo=lo, hi=hi,
+                              yaw_dof=int(yaw), steps_per_action=int(steps_per_action))
+
+    def random_actions(self, steps: int, action_dim: int, seed: int = 0, amp: float = 0.3) -> np.ndarray:
+        """Seeded uniform actions in [-amp, amp], f32 [steps, E, action_dim]
+        (the paper's random-action benchmark clips actions to [-0.3, 0.3])."""
+        rng = np.random.Generator(np.random.PCG64(7_000_001 * (seed + 1) + self.seed))
+        return rng.uniform(-amp, amp, size=(steps, self.num_envs, action_dim)).astype(np.float32)
 
     def state(self):
         """Fresh copies of the initial state arrays (pos, quat, linvel, angvel)."""
