@@ -301,6 +301,78 @@ def time_render(sim, scene, stream, hbm_peak, width=128, height=128, reps=10, cp
     return res
 
 
+def time_control(dev, stream, start, envs=4096, steps=20, warmup=3, width=128, height=128, cpu=True):
+    """Control steps of the articulated-receptacle apartment batch (config 6):
+    per sample, the controller turns a normalised action into PD targets, five
+    100 Hz physics steps run under it (one CUDA graph), and the two depth
+    cameras of every env render 128x128 (Sec. 4.2's benchmark loop: 20 Hz
+    control, 100 Hz physics, 2 cameras). Seeded uniform actions in
+    [-0.3, 0.3]. CUDA events per sample with an L2 flush between samples."""
+    import torch
+    from paper_2412_13211_b300 import autotune, scenes
+    from paper_2412_13211_b300.sim import MshSim
+    sc, cfg = scenes.make_config(6, num_envs=envs, env_start=start)
+    spec = sc.controller_spec()
+    sim = MshSim(sc, cfg, device=dev, exec_form="fused", use_graph=True)
+    t0 = torch.as_tensor(sc.targets0).to(dev)
+    tuning = autotune.tune(sim, t0, steps=3, warmup=2)
+    sim.set_exec(*tuning["best"], True)
+    init = tuple(t.clone() for t in (sim.pos, sim.quat, sim.linvel, sim.angvel))
+    sim.set_controller(spec)
+    body, pose = sc.camera_mounts()
+    sim.set_cameras(body, pose, width, height, np.pi / 2, 0.01, 10.0)
+    depth = torch.empty((sc.num_envs, body.shape[1], height, width), dtype=torch.float32, device=dev)
+    acts = torch.as_tensor(sc.random_actions(warmup + steps, spec.action_dim, amp=0.3)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run(parts, k0, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        with torch.cuda.stream(stream):
+            for i in range(n):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                if "ctrl" in parts:
+                    sim.control_step(acts[k0 + i], stream=stream)
+                if "render" in parts:
+                    sim.render_depth(depth, stream=stream)
+                ev[i][1].record(stream)
+        stream.synchronize()
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    run(("ctrl", "render"), 0, warmup)
+    ms = run(("ctrl", "render"), warmup, steps)
+    status = sim.status()
+    ms_ctrl = run(("ctrl",), 0, max(3, steps // 2))
+    ms_render = run(("render",), 0, max(3, steps // 2))
+    res = {"metric": "samples/s (control steps x envs, 2 depth cameras rendered per sample)",
+           "value": sc.num_envs / (ms / 1e3), "ms_per_control_step": ms, "steps": steps,
+           "physics_ms": ms_ctrl, "render_ms": ms_render,
+           "physics_steps_per_sample": spec.steps_per_action, "form": list(tuning["best"]),
+           "workload": f"config6 apartments with a drawer and a fridge door, {sc.num_envs} envs, "
+                       f"{sc.num_bodies} bodies, {sc.num_statics} static boxes, {sc.num_joints} joints, "
+                       f"{body.shape[1]} cameras x {width}x{height}, actions U[-0.3, 0.3]",
+           "gpu_launches_per_sample": 1 + spec.steps_per_action * sim.launches_per_step + 1,
+           "status_nonzero_envs": int((status != 0).sum())}
+    if cpu:
+        import oracle
+        from oracle import control as K
+        n = 64
+        sub = sc.subset(np.arange(n))
+        st = tuple(t[:sc.body_off[n]].cpu().numpy() for t in init)
+        a = acts[0, :n].cpu().numpy()
+        c0 = time.perf_counter()
+        st2, _, _ = K.control_step(sub, cfg, spec, st, a, sub.targets0, "f32")
+        oracle.render_depth(sub, st2[0], st2[1], body[:n], pose[:n], width, height,
+                            float(np.float32(height * 0.5 / np.tan(float(np.float32(np.pi / 2)) * 0.5))), 0.01, 10.0,
+                            "f32")
+        dt = time.perf_counter() - c0
+        res["cpu_baseline"] = {"value": n / dt, "unit": "samples/s", "cores": oracle.cores(), "kind": "oracle",
+                               "sample": f"one control step (controller, 5 physics steps, 2 depth cameras) "
+                                         f"of the first {n} envs"}
+    sim.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,6 +389,7 @@ def main():
     ap.add_argument("--no-report", action="store_true")
     ap.add_argument("--no-labels", action="store_true")
     ap.add_argument("--no-render", action="store_true")
+    ap.add_argument("--no-control", action="store_true")
     ap.add_argument("--bwd-horizon", type=int, default=16)
     ap.add_argument("--profile-backward", action="store_true",
                     help="only a short fwd+bwd rollout of the 512-env differentiation workload (small case for ncu)")
@@ -456,6 +529,8 @@ def main():
     labels = None if args.no_labels else time_labels(dev, stream, hbm_peak, cpu=rank == 0 and not args.no_cpu_baseline)
     render = None if args.no_render else time_render(sim, scene, stream, hbm_peak,
                                                      cpu=rank == 0 and not args.no_cpu_baseline)
+    control = None if args.no_control else time_control(dev, stream, start, envs=args.envs,
+                                                        cpu=rank == 0 and not args.no_cpu_baseline)
     bytes_step = algorithmic(scene)
     flops_step = FLOP_ROW * rows * cfg.substeps * cfg.iterations
     alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x clock, TFLOP/s
@@ -481,6 +556,7 @@ def main():
                          "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": bytes_step},
         "plain_step": plain, "contact_report": report, "event_labeling": labels, "depth_cameras": render,
+        "control_wrapper": control,
         "fwd_bwd": fwd_bwd,
         "e2e": {"value": scene.num_envs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": n_e2e},

@@ -245,6 +245,58 @@ typedef struct msh_report_desc {
 int msh_set_report(msh_handle* h, const msh_report_desc* desc);
 
 /*
+ * Control wrapper (Sec. 4.1: PD joint delta-position control of the arm,
+ * linear and angular velocity of the base, actions normalised to [-1, 1];
+ * Sec. 4.2: 100 Hz physics under 20 Hz control). One control step applies
+ * the controller to every env's joint targets, then runs steps_per_action
+ * physics steps (the configured dt and substeps) with the new targets. Each
+ * DoF column d (shared by every env) has a kind:
+ *   MSH_CTRL_HOLD      the target is kept (passive joints);
+ *   MSH_CTRL_DELTA     t += a * scale, a = action[e][action_col[d]];
+ *   MSH_CTRL_ABS       t = ((a + 1) * 0.5) * (hi - lo) + lo;
+ *   MSH_CTRL_BASE_X    t += ((a * scale) * cos(yaw)) * dt_c;
+ *   MSH_CTRL_BASE_Y    t += ((a * scale) * sin(yaw)) * dt_c;
+ *   MSH_CTRL_BASE_YAW  t += (a * scale) * dt_c;
+ * where a is the action component clipped to [-1, 1] (fmaxf then fminf, so
+ * NaN counts as -1), yaw is column yaw_dof's target before this update,
+ * dt_c = steps_per_action * dt in FP32, and every written target is then
+ * clipped to [lo[d], hi[d]]. All in FP32 in the order shown, without FMA
+ * contraction. kind, action_col, scale, lo and hi are HOST arrays of
+ * max_dof entries read during msh_set_controller (not retained).
+ * Returns MSH_ERR_INVALID_ARG for a bad kind, an action column outside
+ * [0, action_dim), lo > hi, a base column without yaw_dof, or a handle with
+ * no DoFs.
+ */
+enum { MSH_CTRL_HOLD = 0, MSH_CTRL_DELTA = 1, MSH_CTRL_ABS = 2, MSH_CTRL_BASE_X = 3, MSH_CTRL_BASE_Y = 4,
+       MSH_CTRL_BASE_YAW = 5 };
+
+typedef struct msh_controller_desc {
+  int32_t action_dim;        /* action components per env, >= 1 */
+  int32_t steps_per_action;  /* physics steps per control step, >= 1 (5: 100 Hz under 20 Hz) */
+  int32_t yaw_dof;           /* the base's yaw column, -1 when no column is MSH_CTRL_BASE_X/Y */
+  const int32_t* kind;       /* [max_dof] MSH_CTRL_* */
+  const int32_t* action_col; /* [max_dof] action column; ignored for MSH_CTRL_HOLD */
+  const float* scale;        /* [max_dof] rad or m per unit action (DELTA), m/s or rad/s (BASE_*) */
+  const float* lo;           /* [max_dof] target range */
+  const float* hi;
+} msh_controller_desc;
+
+int msh_set_controller(msh_handle* h, const msh_controller_desc* desc);
+
+/*
+ * One control step of every env: the controller reads action, DEVICE
+ * [num_envs][action_dim], and updates targets, DEVICE [num_envs][max_dof]
+ * (the caller-owned PD targets, read and written in place), then
+ * steps_per_action physics steps run with them (recorded one by one while a
+ * tape is set, writing the contact report while one is set). With use_graph
+ * (msh_set_exec) the controller and the physics steps are one CUDA graph,
+ * captured on first use and re-captured when the state, action or targets
+ * pointers change. Asynchronous on `stream`. Returns MSH_ERR_INVALID_ARG
+ * without a controller or with NULL pointers.
+ */
+int msh_control_step(msh_handle* h, const msh_state* st, const float* action, float* targets, void* stream);
+
+/*
  * Depth cameras (the paper's per-env RGB-D cameras, Sec. 4.2; the depth
  * channel, ray-cast against the env's primitives instead of rasterised).
  * Pinhole camera looking along its frame's +x (image right = -y, image down

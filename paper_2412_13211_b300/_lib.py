@@ -18,7 +18,7 @@ EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_s
            "msh_detect", "msh_get_status", "msh_clear_status", "msh_scratch_bytes", "msh_workspace_bytes",
            "msh_launches_per_step", "msh_step_static_scratch", "msh_set_tape", "msh_tape_reset",
            "msh_tape_count", "msh_backward", "msh_set_report", "msh_label_events", "msh_set_cameras",
-           "msh_render_depth")
+           "msh_render_depth", "msh_set_controller", "msh_control_step")
 TASK_PICK, TASK_PLACE, TASK_OPEN, TASK_CLOSE = 0, 1, 2, 3
 
 
@@ -48,6 +48,12 @@ class ReportDesc(C.Structure):
 class CameraDesc(C.Structure):
     _fields_ = [("num_cameras", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("fov_y", C.c_float),
                 ("near_", C.c_float), ("far_", C.c_float), ("body", C.c_void_p), ("pose", C.c_void_p)]
+
+
+class ControllerDesc(C.Structure):
+    _fields_ = [("action_dim", C.c_int32), ("steps_per_action", C.c_int32), ("yaw_dof", C.c_int32),
+                ("kind", C.c_void_p), ("action_col", C.c_void_p), ("scale", C.c_void_p), ("lo", C.c_void_p),
+                ("hi", C.c_void_p)]
 
 
 class TrajBatch(C.Structure):
@@ -88,6 +94,8 @@ def load(build_if_missing: bool = True):
     lib.msh_set_report.argtypes = [P, P]
     lib.msh_set_cameras.argtypes = [P, P]
     lib.msh_render_depth.argtypes = [P, P, P, P]
+    lib.msh_set_controller.argtypes = [P, P]
+    lib.msh_control_step.argtypes = [P, P, P, P, P]
     lib.msh_label_events.argtypes = [I32, P, I32, P, P, P, P]
     lib.msh_tape_reset.argtypes = [P]
     lib.msh_tape_count.argtypes = [P]

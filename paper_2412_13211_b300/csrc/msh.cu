@@ -287,6 +287,38 @@ __global__ void k_static(int S, const float* pose, const float* half, float off,
   if (g < S) static_world(pose + 7 * g, half + 3 * g, off, sworld + (size_t)SW_N * g);
 }
 
+// The control wrapper's controller (Sec. 4.1 normalised actions), one thread
+// per env: every column reads the targets from before the update (the base's
+// x and y turn with the old yaw), in FP32 in the documented operation order.
+struct CtrlCol {
+  int kind, col;
+  float scale, lo, hi;
+};
+
+__global__ void k_control(int E, int D, int A, int yaw_dof, float dtc, const CtrlCol* __restrict__ cols,
+                          const float* __restrict__ action, float* __restrict__ targets) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  float* t = targets + (size_t)e * D;
+  const float* a = action + (size_t)e * A;
+  const float yaw = yaw_dof >= 0 ? t[yaw_dof] : 0.f;
+  const float c = cosf(yaw), s = sinf(yaw);
+  for (int d = 0; d < D; ++d) {
+    const CtrlCol k = cols[d];
+    if (k.kind == MSH_CTRL_HOLD) continue;
+    const float u = fminf(fmaxf(a[k.col], -1.f), 1.f);
+    float v = t[d];
+    switch (k.kind) {
+      case MSH_CTRL_DELTA: v = v + u * k.scale; break;
+      case MSH_CTRL_ABS: v = (u + 1.f) * 0.5f * (k.hi - k.lo) + k.lo; break;
+      case MSH_CTRL_BASE_X: v = v + u * k.scale * c * dtc; break;
+      case MSH_CTRL_BASE_Y: v = v + u * k.scale * s * dtc; break;
+      default: v = v + u * k.scale * dtc; break;   // MSH_CTRL_BASE_YAW
+    }
+    t[d] = fminf(fmaxf(v, k.lo), k.hi);
+  }
+}
+
 // Copies the collision stage results of every env out of the plain workspace.
 __global__ void k_export(Params p, float* aabb_body, float* aabb_static, int* pair_count, int* pairs,
                          int* contact_count, int* contact_ids, float* contact_geom, int* manifold_count,
@@ -440,6 +472,14 @@ struct msh_handle {
   float cam_focal = 0.f, cam_near = 0.f, cam_far = 0.f;
   int* d_cam_body = nullptr;
   float* d_cam_pose = nullptr;
+  // control wrapper (msh_set_controller)
+  CtrlCol* d_ctrl = nullptr;
+  int ctrl_on = 0, ctrl_A = 0, ctrl_steps = 0, ctrl_yaw = -1;
+  cudaGraphExec_t cgexec = nullptr;   // controller + physics steps
+  msh_state cgkey{};
+  const float* cgkey_action = nullptr;
+  float* cgkey_targets = nullptr;
+  int cgkey_exec = -1, cgkey_tpe = 0;
   // contact report (msh_set_report)
   int rep_on = 0;
   int *d_rep_flags = nullptr, *d_rep_fingers = nullptr, *d_rep_target = nullptr;
@@ -619,6 +659,8 @@ int configure_fused(msh_handle* h) {
 void drop_graph(msh_handle* h) {
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   h->gkey_exec = -1;
+  if (h->cgexec) { cudaGraphExecDestroy(h->cgexec); h->cgexec = nullptr; }
+  h->cgkey_exec = -1;
 }
 
 int check_cfg(const msh_solver_cfg* c) {
@@ -778,7 +820,7 @@ void msh_destroy(msh_handle* h) {
   void* ptrs[] = {h->d_body_off, h->d_static_off, h->d_joint_off, h->d_env_order, h->d_bdims, h->d_binv,
                   h->d_static_pose, h->d_static_half, h->d_sworld, h->d_joints, h->d_status, h->d_queue, h->d_targets,
                   h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused, h->d_tape, h->d_aws,
-                  h->d_rep_flags, h->d_rep_fingers, h->d_rep_target, h->d_cam_body, h->d_cam_pose};
+                  h->d_rep_flags, h->d_rep_fingers, h->d_rep_target, h->d_cam_body, h->d_cam_pose, h->d_ctrl};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -1046,6 +1088,91 @@ int msh_set_report(msh_handle* h, const msh_report_desc* d) {
   h->rep_fmin = d->grasp_min_force;
   h->rep_cosmax = (float)std::cos((double)d->grasp_max_angle_deg * 3.14159265358979323846 / 180.0);
   h->rep_on = 1;
+  return MSH_OK;
+}
+
+int msh_set_controller(msh_handle* h, const msh_controller_desc* d) {
+  if (!h || !d || !d->kind || !d->action_col || !d->scale || !d->lo || !d->hi)
+    return fail(MSH_ERR_INVALID_ARG, "handle, descriptor or arrays are NULL");
+  const int D = h->max_dof;
+  if (D < 1) return fail(MSH_ERR_INVALID_ARG, "the scene has no DoFs to control");
+  if (d->action_dim < 1 || d->steps_per_action < 1)
+    return fail(MSH_ERR_INVALID_ARG, "action_dim and steps_per_action must be >= 1");
+  if (d->yaw_dof < -1 || d->yaw_dof >= D) return fail(MSH_ERR_INVALID_ARG, "yaw_dof out of range");
+  std::vector<CtrlCol> cols(D);
+  for (int k = 0; k < D; ++k) {
+    const int kind = d->kind[k];
+    if (kind < MSH_CTRL_HOLD || kind > MSH_CTRL_BASE_YAW)
+      return fail(MSH_ERR_INVALID_ARG, "column " + std::to_string(k) + ": unknown controller kind");
+    if (kind != MSH_CTRL_HOLD && (d->action_col[k] < 0 || d->action_col[k] >= d->action_dim))
+      return fail(MSH_ERR_INVALID_ARG, "column " + std::to_string(k) + ": action column out of range");
+    if (!(d->lo[k] <= d->hi[k]) || !std::isfinite(d->scale[k]))
+      return fail(MSH_ERR_INVALID_ARG, "column " + std::to_string(k) + ": need lo <= hi and a finite scale");
+    if ((kind == MSH_CTRL_BASE_X || kind == MSH_CTRL_BASE_Y) && d->yaw_dof < 0)
+      return fail(MSH_ERR_INVALID_ARG, "base columns need yaw_dof");
+    cols[k] = CtrlCol{kind, kind == MSH_CTRL_HOLD ? 0 : d->action_col[k], d->scale[k], d->lo[k], d->hi[k]};
+  }
+  cudaDeviceSynchronize();
+  drop_graph(h);
+  if (!h->d_ctrl) {
+    int rc = dalloc(h, &h->d_ctrl, (size_t)D);
+    if (rc) return rc;
+  }
+  CK(cudaMemcpy(h->d_ctrl, cols.data(), sizeof(CtrlCol) * D, cudaMemcpyHostToDevice));
+  h->ctrl_on = 1;
+  h->ctrl_A = d->action_dim;
+  h->ctrl_steps = d->steps_per_action;
+  h->ctrl_yaw = d->yaw_dof;
+  return MSH_OK;
+}
+
+static int enqueue_control(msh_handle* h, const float* action, float* targets, cudaStream_t s) {
+  const float dtc = (float)h->ctrl_steps * h->cfg.dt;
+  k_control<<<(h->E + 127) / 128, 128, 0, s>>>(h->E, h->max_dof, h->ctrl_A, h->ctrl_yaw, dtc, h->d_ctrl, action,
+                                               targets);
+  CK(cudaGetLastError());
+  return MSH_OK;
+}
+
+int msh_control_step(msh_handle* h, const msh_state* st, const float* action, float* targets, void* stream) {
+  if (!h || !st || !st->pos || !st->quat || !st->linvel || !st->angvel || !action || !targets)
+    return fail(MSH_ERR_INVALID_ARG, "handle, state, action or targets pointer is NULL");
+  if (!h->ctrl_on) return fail(MSH_ERR_INVALID_ARG, "no controller: call msh_set_controller first");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float dt = h->cfg.dt;
+  const int S = h->cfg.substeps;
+  int rc;
+  if (h->tape_max > 0 || !h->use_graph) {
+    // direct launches (a recording handle records each physics step)
+    if (h->tape_max > 0 && h->tape_count + h->ctrl_steps > h->tape_max)
+      return fail(MSH_ERR_INVALID_ARG, "tape full: call msh_backward or msh_tape_reset");
+    if ((rc = enqueue_control(h, action, targets, s))) return rc;
+    for (int k = 0; k < h->ctrl_steps; ++k)
+      if ((rc = step_impl(h, st, targets, dt, S, s))) return rc;
+    return MSH_OK;
+  }
+  bool hit = h->cgexec && h->cgkey.pos == st->pos && h->cgkey.quat == st->quat && h->cgkey.linvel == st->linvel &&
+             h->cgkey.angvel == st->angvel && h->cgkey_action == action && h->cgkey_targets == targets &&
+             h->cgkey_exec == h->exec && h->cgkey_tpe == h->tpe;
+  if (!hit) {
+    if (h->cgexec) { cudaGraphExecDestroy(h->cgexec); h->cgexec = nullptr; }
+    h->cgkey_exec = -1;
+    if (h->exec != MSH_EXEC_FUSED) { if ((rc = ensure_plain_ws(h))) return rc; }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_control(h, action, targets, h->cap_stream);
+    for (int k = 0; k < h->ctrl_steps && !rc; ++k)
+      rc = enqueue_step(h, make_params(h, st, targets, dt, S), h->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ce != cudaSuccess) return fail(MSH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&h->cgexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { h->cgexec = nullptr; return fail(MSH_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce)); }
+    h->cgkey = *st; h->cgkey_action = action; h->cgkey_targets = targets;
+    h->cgkey_exec = h->exec; h->cgkey_tpe = h->tpe;
+  }
+  CK(cudaGraphLaunch(h->cgexec, s));
   return MSH_OK;
 }
 

@@ -13,7 +13,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import EXEC_FUSED, EXEC_PLAIN, EXEC_SUBSTEP, CameraDesc, ReportDesc, SceneDesc, SolverCfg, State, check
+from ._lib import EXEC_FUSED, EXEC_PLAIN, EXEC_SUBSTEP, CameraDesc, ControllerDesc, ReportDesc, SceneDesc, SolverCfg, State, check
 
 
 def _c(a, dt):
@@ -187,6 +187,48 @@ class MshSim:
         res["aabb_body"] = res["aabb_body"][:sc.num_bodies]
         res["aabb_static"] = res["aabb_static"][:sc.num_statics]
         return res
+
+    # -- control wrapper --------------------------------------------------------
+    def set_controller(self, spec):
+        """Controller of the control steps (msh_set_controller) from a
+        scenes.ControllerSpec; makes `self.ctrl_targets` [E, max_dof], the
+        PD targets the controller updates, start at the scene's targets0."""
+        D = self.max_dof
+        kind = np.ascontiguousarray(spec.kind, np.int32).reshape(D)
+        col = np.ascontiguousarray(np.where(spec.kind == 0, 0, spec.action), np.int32).reshape(D)
+        scale = np.ascontiguousarray(spec.scale, np.float32).reshape(D)
+        lo = np.ascontiguousarray(spec.lo, np.float32).reshape(D)
+        hi = np.ascontiguousarray(spec.hi, np.float32).reshape(D)
+        d = ControllerDesc(int(spec.action_dim), int(spec.steps_per_action), int(spec.yaw_dof), kind.ctypes.data,
+                           col.ctypes.data, scale.ctypes.data, lo.ctypes.data, hi.ctypes.data)
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_set_controller(self.handle, C.byref(d)), "msh_set_controller")
+        self.ctrl_spec = spec
+        self.ctrl_targets = torch.as_tensor(np.asarray(self.scene.targets0, np.float32)).to(self.device).contiguous()
+        self.ctrl_action = torch.zeros((self.scene.num_envs, int(spec.action_dim)), dtype=torch.float32,
+                                       device=self.device)
+
+    def control_step(self, action=None, targets=None, stream=None):
+        """One control step (msh_control_step): the controller turns `action`
+        [E, action_dim] into new PD targets (in place in `targets`, default
+        self.ctrl_targets), then the physics steps run. A CUDA float32
+        contiguous `action` is used as is; anything else is copied into a
+        buffer owned by this object first."""
+        if action is not None:
+            if not (isinstance(action, torch.Tensor) and action.is_cuda and action.dtype == torch.float32
+                    and action.is_contiguous()):
+                self.ctrl_action.copy_(torch.as_tensor(np.asarray(action, np.float32)).reshape(self.ctrl_action.shape))
+                action = self.ctrl_action
+        else:
+            action = self.ctrl_action
+        if targets is None:
+            targets = self.ctrl_targets
+        assert targets.is_cuda and targets.dtype == torch.float32 and targets.is_contiguous()
+        st = self._state()
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_control_step(self.handle, C.byref(st), _ptr(action), _ptr(targets), _stream(stream)),
+                  "msh_control_step")
+        return targets
 
     # -- depth cameras ---------------------------------------------------------
     def set_cameras(self, body, pose, width: int = 128, height: int = 128, fov_y: float = np.pi / 2,

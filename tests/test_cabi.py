@@ -97,6 +97,8 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.msh_get_status(None, None, None) == _lib.MSH_ERR_INVALID_ARG
     assert lib.msh_scratch_bytes(None) == 0
     assert lib.msh_set_report(None, None) == _lib.MSH_ERR_INVALID_ARG
+    assert lib.msh_set_controller(None, None) == _lib.MSH_ERR_INVALID_ARG
+    assert lib.msh_control_step(None, C.byref(st), None, None, None) == _lib.MSH_ERR_INVALID_ARG
     lib.msh_destroy(None)
 
 
