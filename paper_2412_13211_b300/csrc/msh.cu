@@ -152,24 +152,46 @@ using FusedKernel = void (*)(Params, int);
 
 static FusedKernel fused_kernel(int tpe) { return tpe <= 256 ? k_fused<256> : k_fused<512>; }
 
-// Adjoint of the recorded step in tape slot q.slot, one CTA per env (see
-// msh_adjoint.cuh). Replays the step's collision stage from the recorded
-// start state, then reverses the substeps and finally the narrowphase.
-__global__ void k_backward(Params p, AdjParams q) {
-  __shared__ int scr[33];
-  // p.G threads per env: with 8 or 16, several envs share a warp (group-local barriers)
+// Adjoint of the recorded step in tape slot q.slot (see msh_adjoint.cuh), as
+// a sequence of launches that each run one phase for every env: the replay of
+// the step's collision stage from the recorded start state, then per substep
+// (last first) the reverse of the position update with the row rebuild, the
+// reversed sweeps, and the reverse of the row set-up; finally the reverse of
+// the narrowphase and the outputs. Every phase keeps its per-env data in the
+// device-memory workspaces, so the phases are separate kernels: each gets the
+// registers and instruction footprint of its own code instead of the largest
+// phase's. A CTA of 32 threads holds 32/G env groups of G threads.
+struct BwdEnv {
+  EnvInfo e;
+  Ws w;
+  AWs a;
+  const float* tape;
+  TapeLayout tl;
+};
+
+__device__ __forceinline__ bool bwd_env(const Params& p, const AdjParams& q, BwdEnv& b) {
   const int G = p.G > 0 && p.G < (int)blockDim.x ? p.G : (int)blockDim.x;
   const int gi = threadIdx.x / G, lane = threadIdx.x % G;
   const unsigned mask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
   const int env = blockIdx.x * (blockDim.x / G) + gi;
-  if (env >= p.E) return;   // whole groups exit together
-  EnvInfo e = env_info(p, env, lane, G, mask);
-  Ws w = plain_ws(p, env);
-  AWs a = make_aws(q.aws + (long long)env * q.aws_stride, q.A);
-  const TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
-  const float* tape = p.tape + ((long long)q.slot * p.E + env) * p.tape_slab;
-  const float* tg = tape + tl.t3;
-  load_from_tape(p, e, w, tape);
+  if (env >= p.E) return false;   // whole groups exit together
+  b.e = env_info(p, env, lane, G, mask);
+  b.w = plain_ws(p, env);
+  b.a = make_aws(q.aws + (long long)env * q.aws_stride, q.A);
+  b.tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+  b.tape = p.tape + ((long long)q.slot * p.E + env) * p.tape_slab;
+  return true;
+}
+
+// Replay of the collision stage; the state adjoints are loaded.
+__global__ void k_bwd_replay(Params p, AdjParams q) {
+  __shared__ int scr[33];
+  BwdEnv b;
+  if (!bwd_env(p, q, b)) return;
+  const EnvInfo& e = b.e;
+  const Ws& w = b.w;
+  const AWs& a = b.a;
+  load_from_tape(p, e, w, b.tape);
   gsync(e);
   stage_aabb(p, e, w);
   gsync(e);
@@ -188,38 +210,96 @@ __global__ void k_backward(Params p, AdjParams q) {
   const int nc = w.misc[MC_CONTACTS];
   for (int c = e.lane; c < 3 * nc; c += e.nthr) a.cg[c] = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int k = e.lane; k < p.max_dof; k += e.nthr) a.tg[k] = 0.f;
+}
+
+// Substep s: its poses and velocities from the tape, the reverse of its
+// position update, and its solver rows rebuilt at those poses.
+__global__ void k_bwd_rows(Params p, AdjParams q, int s) {
+  BwdEnv b;
+  if (!bwd_env(p, q, b)) return;
+  const EnvInfo& e = b.e;
+  const Ws& w = b.w;
+  const float* st = b.tape + b.tl.t1 + 19LL * s * p.L.Dm;
+  for (int i = e.lane; i < e.D; i += e.nthr) {
+    const float* t = st + 19 * i;
+    const float4 inv = p.binv[e.b0 + i];
+    w.bx[i] = make_float4(t[0], t[1], t[2], inv.x);
+    w.bq[i] = make_float4(t[3], t[4], t[5], t[6]);
+    w.bv[i] = make_float4(t[13], t[14], t[15], 0.f);
+    w.bw[i] = make_float4(t[16], t[17], t[18], 0.f);
+    Q4<float> qq; qq.w = t[3]; qq.x = t[4]; qq.y = t[5]; qq.z = t[6];
+    float dI[3] = {inv.y, inv.z, inv.w}, W6[6];
+    world_inv_inertia<float>(qq, dI, W6);
+    w.bIw0[i] = make_float4(W6[0], W6[1], W6[2], W6[3]);
+    w.bIw1[i] = make_float4(W6[4], W6[5], 1.f, 0.f);
+  }
+  reverse_integrate(p, e, b.a, st);
   gsync(e);
-  for (int s = p.S - 1; s >= 0; --s) {
-    const float* st = tape + tl.t1 + 19LL * s * p.L.Dm;
+  build_rows(p, e, w, b.a, b.tape + b.tl.t3);
+}
+
+// Substep s: the N sweeps in reverse. Each env group has `slice` bytes of
+// shared memory; an env whose rows (parameters and adjoint accumulators) and
+// body velocities and velocity adjoints fit is staged there for the N sweeps
+// (the rows are re-read and the adjoints re-written once per row per sweep),
+// a larger env runs on its device-memory workspace.
+__global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
+  extern __shared__ float4 bsm[];
+  BwdEnv b;
+  if (!bwd_env(p, q, b)) return;
+  const EnvInfo& e = b.e;
+  const float* lam0 = b.tape + b.tl.t2 + (long long)s * p.N * p.tape_Rm;
+  const int R = ROWS_PER_JOINT * p.L.Jm + 3 * b.w.misc[MC_CONTACTS];   // rows in use, joints first
+  const int need = 2 * R * ROW_F4 * 16 + 4 * e.D * 16;
+  Ws w = b.w;
+  AWs a = b.a;
+  const bool staged = need <= slice;
+  if (staged) {
+    float4* base = bsm + (size_t)(threadIdx.x / e.nthr) * (slice / 16);
+    a.rows = base;
+    a.radj = base + (size_t)R * ROW_F4;
+    w.bv = a.radj + (size_t)R * ROW_F4;
+    w.bw = w.bv + e.D;
+    a.bv = w.bw + e.D;
+    a.bw = a.bv + e.D;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = e.lane; i < R * ROW_F4; i += e.nthr) { a.rows[i] = b.a.rows[i]; a.radj[i] = z; }
     for (int i = e.lane; i < e.D; i += e.nthr) {
-      const float* t = st + 19 * i;
-      const float4 inv = p.binv[e.b0 + i];
-      w.bx[i] = make_float4(t[0], t[1], t[2], inv.x);
-      w.bq[i] = make_float4(t[3], t[4], t[5], t[6]);
-      w.bv[i] = make_float4(t[13], t[14], t[15], 0.f);
-      w.bw[i] = make_float4(t[16], t[17], t[18], 0.f);
-      Q4<float> qq; qq.w = t[3]; qq.x = t[4]; qq.y = t[5]; qq.z = t[6];
-      float dI[3] = {inv.y, inv.z, inv.w}, W6[6];
-      world_inv_inertia<float>(qq, dI, W6);
-      w.bIw0[i] = make_float4(W6[0], W6[1], W6[2], W6[3]);
-      w.bIw1[i] = make_float4(W6[4], W6[5], 1.f, 0.f);
+      w.bv[i] = b.w.bv[i]; w.bw[i] = b.w.bw[i]; a.bv[i] = b.a.bv[i]; a.bw[i] = b.a.bw[i];
     }
-    reverse_integrate(p, e, a, st);
-    gsync(e);
-    build_rows(p, e, w, a, tg);
-    gsync(e);
-    const float* lam0 = tape + tl.t2 + (long long)s * p.N * p.tape_Rm;
-    for (int it = p.N - 1; it >= 0; --it)
-      reverse_sweep(p, e, w, a, lam0 + (long long)it * p.tape_Rm, it > 0 ? lam0 + (long long)(it - 1) * p.tape_Rm : nullptr);
-    reverse_setup(p, e, w, a, tg);
-    gsync(e);
-    gather_bodies(e, a, true);
-    gsync(e);
-    reverse_inertia(p, e, w, a);
     gsync(e);
   }
+  for (int it = p.N - 1; it >= 0; --it)
+    reverse_sweep(p, e, w, a, lam0 + (long long)it * p.tape_Rm, it > 0 ? lam0 + (long long)(it - 1) * p.tape_Rm : nullptr);
+  if (staged) {
+    for (int i = e.lane; i < R * ROW_F4; i += e.nthr) b.a.radj[i] = a.radj[i];
+    for (int i = e.lane; i < e.D; i += e.nthr) {
+      b.w.bv[i] = w.bv[i]; b.w.bw[i] = w.bw[i]; b.a.bv[i] = a.bv[i]; b.a.bw[i] = a.bw[i];
+    }
+  }
+}
+
+// Substep s: the reverse of the row set-up, gathered per body, and of the
+// world inverse inertias.
+__global__ void k_bwd_setup(Params p, AdjParams q, int s) {
+  BwdEnv b;
+  if (!bwd_env(p, q, b)) return;
+  reverse_setup(p, b.e, b.w, b.a, b.tape + b.tl.t3);
+  gsync(b.e);
+  gather_bodies(b.e, b.a, true);
+  gsync(b.e);
+  reverse_inertia(p, b.e, b.w, b.a);
+}
+
+// The reverse of the narrowphase at the step-start poses, and the outputs.
+__global__ void k_bwd_finish(Params p, AdjParams q) {
+  BwdEnv b;
+  if (!bwd_env(p, q, b)) return;
+  const EnvInfo& e = b.e;
+  const Ws& w = b.w;
+  const AWs& a = b.a;
   for (int i = e.lane; i < e.D; i += e.nthr) {
-    const float* t = tape + 13 * i;
+    const float* t = b.tape + 13 * i;
     w.bx[i] = make_float4(t[0], t[1], t[2], w.bx[i].w);
     w.bq[i] = make_float4(t[3], t[4], t[5], t[6]);
   }
@@ -243,7 +323,7 @@ __global__ void k_backward(Params p, AdjParams q) {
     }
   }
   if (q.otg)
-    for (int k = e.lane; k < p.max_dof; k += e.nthr) q.otg[(long long)env * p.max_dof + k] = a.tg[k];
+    for (int k = e.lane; k < p.max_dof; k += e.nthr) q.otg[(long long)e.env * p.max_dof + k] = a.tg[k];
 }
 
 // Inverse mass and principal inverse inertia from mass and shape (solid
@@ -656,6 +736,13 @@ int configure_fused(msh_handle* h) {
   return MSH_OK;
 }
 
+// Shared memory per env of the reversed sweeps: as much as keeps `per_sm`
+// envs resident per SM; envs beyond it run from device memory.
+int bwd_sweep_slice(const msh_handle* h, int per_sm = 8) {
+  const int per_cta = (h->smem_optin + 1024) / per_sm - 1024;
+  return std::max(0, std::min(per_cta, h->smem_optin - 1024)) & ~15;
+}
+
 void drop_graph(msh_handle* h) {
   if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
   h->gkey_exec = -1;
@@ -1020,15 +1107,28 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
   // G = 32 at 512 envs.
   if (h->bwd_warps == 0) {
     int blocks = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_backward, 32, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_setup, 32, 0));
     h->bwd_warps = std::max(1, blocks) * h->num_sms;
+    CK(cudaFuncSetAttribute(k_bwd_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_optin - 1024));
   }
   int G = 32;
   for (int g : {8, 16})
     if ((long long)h->E * g / 32 >= h->bwd_warps) { G = g; break; }
   p.G = G;
   const int per_block = 32 / G;
-  k_backward<<<(h->E + per_block - 1) / per_block, 32, 0, (cudaStream_t)stream>>>(p, q);
+  const int grid = (h->E + per_block - 1) / per_block;
+  // the sweeps: one env per warp, `slice` bytes of shared memory each
+  const int slice = bwd_sweep_slice(h);
+  Params ps = p;
+  ps.G = 32;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_bwd_replay<<<grid, 32, 0, s>>>(p, q);
+  for (int sub = p.S - 1; sub >= 0; --sub) {
+    k_bwd_rows<<<grid, 32, 0, s>>>(p, q, sub);
+    k_bwd_sweeps<<<h->E, 32, slice, s>>>(ps, q, sub, slice);
+    k_bwd_setup<<<grid, 32, 0, s>>>(p, q, sub);
+  }
+  k_bwd_finish<<<grid, 32, 0, s>>>(p, q);
   CK(cudaGetLastError());
   h->tape_count--;
   return MSH_OK;
