@@ -249,21 +249,27 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   if (!bwd_env(p, q, b)) return;
   const EnvInfo& e = b.e;
   const float* lam0 = b.tape + b.tl.t2 + (long long)s * p.N * p.tape_Rm;
-  const int R = ROWS_PER_JOINT * p.L.Jm + 3 * b.w.misc[MC_CONTACTS];   // rows in use, joints first
-  const int need = 2 * R * ROW_F4 * 16 + 4 * e.D * 16;
+  const int RJ = ROWS_PER_JOINT * e.J;                 // joint row slots in use
+  const int nc = b.w.misc[MC_CONTACTS], nm = b.w.misc[MC_MANIFOLDS];
+  const int need = (2 * RJ * ROW_F4 + 10 * nc + 4 * nm + 4 * e.D) * 16;
   Ws w = b.w;
   AWs a = b.a;
   const bool staged = need <= slice;
   if (staged) {
     float4* base = bsm + (size_t)(threadIdx.x / e.nthr) * (slice / 16);
     a.rows = base;
-    a.radj = base + (size_t)R * ROW_F4;
-    w.bv = a.radj + (size_t)R * ROW_F4;
+    a.radj = a.rows + (size_t)RJ * ROW_F4;
+    a.cpar = a.radj + (size_t)RJ * ROW_F4;
+    a.cadj = a.cpar + 4 * nc;
+    a.madj = a.cadj + 6 * nc;
+    w.bv = a.madj + 4 * nm;
     w.bw = w.bv + e.D;
     a.bv = w.bw + e.D;
     a.bw = a.bv + e.D;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = e.lane; i < R * ROW_F4; i += e.nthr) { a.rows[i] = b.a.rows[i]; a.radj[i] = z; }
+    for (int i = e.lane; i < RJ * ROW_F4; i += e.nthr) { a.rows[i] = b.a.rows[i]; a.radj[i] = b.a.radj[i]; }
+    for (int i = e.lane; i < 4 * nc; i += e.nthr) a.cpar[i] = b.a.cpar[i];
+    for (int i = e.lane; i < 6 * nc; i += e.nthr) a.cadj[i] = b.a.cadj[i];
+    for (int i = e.lane; i < 4 * nm; i += e.nthr) a.madj[i] = b.a.madj[i];
     for (int i = e.lane; i < e.D; i += e.nthr) {
       w.bv[i] = b.w.bv[i]; w.bw[i] = b.w.bw[i]; a.bv[i] = b.a.bv[i]; a.bw[i] = b.a.bw[i];
     }
@@ -272,7 +278,10 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   for (int it = p.N - 1; it >= 0; --it)
     reverse_sweep(p, e, w, a, lam0 + (long long)it * p.tape_Rm, it > 0 ? lam0 + (long long)(it - 1) * p.tape_Rm : nullptr);
   if (staged) {
-    for (int i = e.lane; i < R * ROW_F4; i += e.nthr) b.a.radj[i] = a.radj[i];
+    gsync(e);
+    for (int i = e.lane; i < RJ * ROW_F4; i += e.nthr) b.a.radj[i] = a.radj[i];
+    for (int i = e.lane; i < 6 * nc; i += e.nthr) b.a.cadj[i] = a.cadj[i];
+    for (int i = e.lane; i < 4 * nm; i += e.nthr) b.a.madj[i] = a.madj[i];
     for (int i = e.lane; i < e.D; i += e.nthr) {
       b.w.bv[i] = w.bv[i]; b.w.bw[i] = w.bw[i]; b.a.bv[i] = a.bv[i]; b.a.bw[i] = a.bw[i];
     }
@@ -516,7 +525,7 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi) {
 AdjLayout make_adj_layout(const Layout& L, int md) {
   AdjLayout A;
   std::memset(&A, 0, sizeof(A));
-  A.Rm = ROWS_PER_JOINT * L.Jm + 3 * L.C;
+  A.Rm = ROWS_PER_JOINT * L.Jm;   // joint row slots (contact points are stored compactly)
   A.Km = L.K;
   int o = 0;
   auto take = [&](long long bytes) { int r = o; o = align16((int)(o + bytes)); return r; };
@@ -524,7 +533,9 @@ AdjLayout make_adj_layout(const Layout& L, int md) {
   A.bx = take(L.Dm * f4); A.bq = take(L.Dm * f4); A.bv = take(L.Dm * f4); A.bw = take(L.Dm * f4);
   A.bI0 = take(L.Dm * f4); A.bI1 = take(L.Dm * f4); A.bm = take(L.Dm * f4);
   A.rows = take((long long)A.Rm * ROW_F4 * f4); A.radj = take((long long)A.Rm * ROW_F4 * f4);
-  A.rkind = take((long long)A.Rm * 4);
+  A.cpar = take((long long)L.C * 4 * f4); A.cadj = take((long long)L.C * 6 * f4);
+  A.madj = take((long long)L.P * 4 * f4);
+  A.cpose = take((long long)L.C * 4 * f4);
   A.gat = take((long long)A.Km * 8 * f4);
   A.cg = take((long long)L.C * 3 * f4);
   A.inc_off = take((L.Dm + 1) * 4); A.inc = take(2LL * A.Km * 4);

@@ -12,7 +12,14 @@
 //     reverse order, rows of a constraint in reverse order); velocities before
 //     each row update are rebuilt from the velocities after it and the
 //     recorded lambdas (v_before = v_after - M^-1 J^T (lambda_after -
-//     lambda_before)); clamp states come from the recorded lambdas;
+//     lambda_before)); clamp states come from the recorded lambdas. Joint rows
+//     are stored whole (Jacobians, inertia products, mass, bias, softness);
+//     a contact point keeps only its normal, world lever arms, bias and three
+//     effective masses, its rows are re-formed on the fly, and its adjoint
+//     accumulators are those of the normal, tangents and arms (the row
+//     Jacobians' adjoints are pulled back through the cross products at every
+//     update), with the inverse-inertia and inverse-mass adjoints kept per
+//     manifold;
 //   * row set-up (lever arms, Jacobians, biases, drives) and the narrowphase:
 //     local Jacobians by single-tangent dual numbers, one input direction at a
 //     time, contracted with the row/contact adjoints;
@@ -30,7 +37,10 @@ namespace msh {
 struct AdjLayout {
   int Rm, Km;
   int bx, bq, bv, bw, bI0, bI1, bm;   // per body: x, q, v, w adjoints; Iw adjoint (6) + 1/m adjoint; mass accum
-  int rows, radj, rkind;              // per row: 5 float4 params, 5 float4 adjoints, kind
+  int rows, radj;                     // per joint row: 5 float4 params, 5 float4 adjoints
+  int cpar, cadj;                     // per contact point: 4 float4 params, 6 float4 adjoints
+  int madj;                           // per manifold: 4 float4 (gIw_a, gIw_b, g(1/m_a), g(1/m_b))
+  int cpose;                          // per contact point: 16 floats, its pose adjoints in gather-slot order
   int gat;                            // per constraint: 8 float4 (xa, qa, xb, qb, Iwa0, Iwa1|ima, Iwb0, Iwb1|imb)
   int cg;                             // per contact point: 3 float4 (n, ra, rb adjoints)
   int inc_off, inc, tg, bytes;
@@ -50,7 +60,8 @@ struct AdjParams {
 struct AWs {
   float4 *bx, *bq, *bv, *bw, *bI0, *bI1, *bm;
   float4 *rows, *radj;
-  int* rkind;
+  float4 *cpar, *cadj, *madj;
+  float* cpose;
   float4* gat;
   float4* cg;
   int *inc_off, *inc;
@@ -61,7 +72,9 @@ __device__ __forceinline__ AWs make_aws(char* b, const AdjLayout& A) {
   AWs a;
   a.bx = (float4*)(b + A.bx); a.bq = (float4*)(b + A.bq); a.bv = (float4*)(b + A.bv); a.bw = (float4*)(b + A.bw);
   a.bI0 = (float4*)(b + A.bI0); a.bI1 = (float4*)(b + A.bI1); a.bm = (float4*)(b + A.bm);
-  a.rows = (float4*)(b + A.rows); a.radj = (float4*)(b + A.radj); a.rkind = (int*)(b + A.rkind);
+  a.rows = (float4*)(b + A.rows); a.radj = (float4*)(b + A.radj);
+  a.cpar = (float4*)(b + A.cpar); a.cadj = (float4*)(b + A.cadj); a.madj = (float4*)(b + A.madj);
+  a.cpose = (float*)(b + A.cpose);
   a.gat = (float4*)(b + A.gat); a.cg = (float4*)(b + A.cg);
   a.inc_off = (int*)(b + A.inc_off); a.inc = (int*)(b + A.inc); a.tg = (float*)(b + A.tg);
   return a;
@@ -70,9 +83,17 @@ __device__ __forceinline__ AWs make_aws(char* b, const AdjLayout& A) {
 __device__ __forceinline__ void add4(float4& a, const V3<float>& v) { a.x += v.x; a.y += v.y; a.z += v.z; }
 __device__ __forceinline__ V3<float> sym_outer_diag(const V3<float>& g, const V3<float>& a) { return v3<float>(g.x * a.x, g.y * a.y, g.z * a.z); }
 
-// Row index of joint k row r, or of contact point c row i.
+// Row index of joint k row r, or of contact point c row i (the recorded
+// lambdas of a step use this numbering).
 __device__ __forceinline__ int jrow(int k, int r) { return k * ROWS_PER_JOINT + r; }
 __device__ __forceinline__ int crow(const Layout& L, int c, int i) { return ROWS_PER_JOINT * L.Jm + 3 * c + i; }
+
+// Adds the symmetric outer product g a^T + a g^T (diagonal once) of an
+// inverse-inertia adjoint, in the entry order xx xy xz yy yz zz.
+__device__ __forceinline__ void add_sym(float* G, const V3<float>& g, const V3<float>& a) {
+  G[0] += g.x * a.x; G[1] += g.x * a.y + g.y * a.x; G[2] += g.x * a.z + g.z * a.x;
+  G[3] += g.y * a.y; G[4] += g.y * a.z + g.z * a.y; G[5] += g.z * a.z;
+}
 
 // ---------------------------------------------------------------------------
 // replay helpers
@@ -154,7 +175,6 @@ __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const
         float4* R = a.rows + ROW_F4 * jrow(t, r);
         R[0] = f4(x.la, x.m); R[1] = f4(x.aa, x.bias); R[2] = f4(x.ab, x.gamma);
         R[3] = f4(x.Ia, 0.f); R[4] = f4(x.Ib, g[r].clamp);
-        a.rkind[jrow(t, r)] = 0;
         float4* G = a.radj + ROW_F4 * jrow(t, r);
         for (int q = 0; q < ROW_F4; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -174,20 +194,21 @@ __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const
       V3<float> t1, t2;
       onb(n, t1, t2);
       V3<float> dirs[3] = {n, t1, t2};
+      float m[3];
       for (int r = 0; r < 3; ++r) {
         JRow x = blank_row();
         x.la = -dirs[r]; x.lb = dirs[r]; x.aa = -cross(ra, dirs[r]); x.ab = cross(rb, dirs[r]);
-        x.bias = r == 0 ? bias : 0.f;
         finish_row(x, ctx, false);
-        float4* R = a.rows + ROW_F4 * crow(p.L, ci, r);
-        R[0] = f4(x.la, x.m); R[1] = f4(x.aa, x.bias); R[2] = f4(x.ab, 0.f);
-        R[3] = f4(x.Ia, 0.f); R[4] = f4(x.Ib, r == 0 ? CLAMP_UNI : CLAMP_FRIC);
-        a.rkind[crow(p.L, ci, r)] = r;
-        float4* G = a.radj + ROW_F4 * crow(p.L, ci, r);
-        for (int q = 0; q < ROW_F4; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        m[r] = x.m;
       }
+      float4* P = a.cpar + 4 * ci;
+      P[0] = f4(n, m[0]); P[1] = f4(ra, bias); P[2] = f4(rb, m[1]); P[3] = make_float4(m[2], 0.f, 0.f, 0.f);
+      float4* G = a.cadj + 6 * ci;
+      for (int q = 0; q < 6; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+  const int M = w.misc[MC_MANIFOLDS];
+  for (int m = e.lane; m < 4 * M; m += e.nthr) a.madj[m] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -273,13 +294,111 @@ __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, f
   G[0] = f4(gla, gm); G[1] = f4(gaa, gbias); G[2] = f4(gab, glam_before); G[3] = f4(gIa, gima); G[4] = f4(gIb, gimb);
 }
 
-// The i-th row of manifold mf in reverse update order (points last to
-// first, each t2, t1, normal); nrow receives the point's normal row.
-__device__ __forceinline__ int rev_contact_row(const Layout& L, int4 mf, int i, int& nrow) {
-  const int ci = mf.z + mf.w - 1 - i / 3;
-  const int rn = crow(L, ci, 0);
-  nrow = rn;
-  return rn + 2 - i % 3;
+// Reverse of the three row updates of contact point ci (t2, t1, then the
+// normal row, undoing the forward order n, t1, t2). The rows are re-formed
+// from the point's normal n, arms ra, rb and masses: J_lin = -d on body a and
+// +d on b, J_ang = -(ra x d) on a and rb x d on b, d in {n, t1, t2}. The
+// adjoints of a row's Jacobian and inertia products are pulled back at once
+// onto d, ra, rb (through the cross products) and onto the manifold's
+// inverse-inertia and inverse-mass accumulators `mi` (gIw_a[6], gIw_b[6],
+// g(1/m_a), g(1/m_b)). A friction row at its limit mu * lambda_n sends its
+// adjoint to the normal row's lambda.
+__device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool bdyn, float ima, float imb,
+                                              const Sym3& Iwa, const Sym3& Iwb, BodyVel& v, BodyAdj& g,
+                                              const float* lam_it, const float* lam_prev, float mu, float* mi) {
+  const float4* P = a.cpar + 4 * ci;
+  float4* Q = a.cadj + 6 * ci;
+  const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3];
+  const float4 Q0 = Q[0], Q1 = Q[1], Q2 = Q[2], Q3 = Q[3], Q4 = Q[4], Q5 = Q[5];
+  const V3<float> n = f3(P0), ra = f3(P1), rb = f3(P2);
+  const float ms[3] = {P0.w, P2.w, P3.x};
+  const float bias = P1.w;
+  V3<float> t1, t2;
+  onb(n, t1, t2);
+  const V3<float> dirs[3] = {n, t1, t2};
+  V3<float> gd[3] = {f3(Q0), f3(Q1), f3(Q2)};
+  float gm[3] = {Q0.w, Q1.w, Q2.w};
+  V3<float> gra = f3(Q3), grb = f3(Q4);
+  float gbias = Q3.w;
+  float glam[3] = {Q4.w, Q5.x, Q5.y};
+  float l_after[3], l_before[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    l_after[q] = lam_it[rn + q];
+    l_before[q] = lam_prev ? lam_prev[rn + q] : 0.f;
+  }
+  const V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  float pend = 0.f;
+#pragma unroll
+  for (int q = 2; q >= 0; --q) {
+    const V3<float> d = dirs[q];
+    const V3<float> ca = cross(ra, d), cb = cross(rb, d);          // J_ang: -ca on a, cb on b
+    const V3<float> ia = smul(Iwa, ca), ib = bdyn ? smul(Iwb, cb) : z;
+    const float D = l_after[q] - l_before[q];
+    // velocities before the update
+    v.va = v.va + d * (ima * D);
+    v.wa = v.wa + ia * D;
+    if (bdyn) { v.vb = v.vb - d * (imb * D); v.wb = v.wb - ib * D; }
+    // adjoint of D through the velocity update
+    const float dga = dot(d, g.va);
+    float gD = -ima * dga - dot(ia, g.wa);
+    V3<float> glin = g.va * (ima * D);                             // adjoint of J_lin(a) = -d
+    const V3<float> gIa = g.wa * D;                                // adjoint of Iw_a J_ang(a)
+    V3<float> gIb = z;
+    mi[12] += -dga * D;
+    if (bdyn) {
+      const float dgb = dot(d, g.vb);
+      gD += imb * dgb + dot(ib, g.wb);
+      glin = glin - g.vb * (imb * D);
+      gIb = g.wb * D;
+      mi[13] += dgb * D;
+    }
+    if (q == 0) glam[0] += pend;                                   // what t1 and t2 sent to lambda_n
+    const float a_after = glam[q] + gD;
+    float glam_before = -gD;
+    // pre-clamp value of the update
+    float jv = 0.f;
+    if (bdyn) jv = dotf(cb, v.wb) + dotf(d, v.vb);
+    jv = jv - dotf(d, v.va) - dotf(ca, v.wa);
+    const float u = q == 0 ? jv + bias : jv;
+    bool clamped;
+    float sgn = 0.f;
+    if (q == 0) clamped = l_after[0] == 0.f;
+    else {
+      const float lim = mu * l_after[0];
+      clamped = l_after[q] == lim || l_after[q] == -lim;
+      sgn = l_after[q] == lim ? 1.f : -1.f;
+    }
+    const float gpre = clamped ? 0.f : a_after;
+    if (q > 0 && clamped) pend += sgn * mu * a_after;
+    glam_before += gpre;
+    const float gu = -ms[q] * gpre;
+    gm[q] += -u * gpre;
+    if (q == 0) gbias += gu;
+    V3<float> gaa = v.wa * gu;                                     // adjoint of J_ang(a) = -ca
+    g.va = g.va - d * gu;
+    g.wa = g.wa - ca * gu;
+    glin = glin + (v.va - v.vb) * gu;
+    // Iw_a J_ang(a): onto J_ang(a) and Iw_a
+    gaa = gaa + smul(Iwa, gIa);
+    add_sym(mi, gIa, -ca);
+    // J_lin(a) = -d, J_ang(a) = d x ra
+    gd[q] = gd[q] - glin + cross(ra, gaa);
+    gra = gra + cross(gaa, d);
+    if (bdyn) {
+      V3<float> gab = v.wb * gu;                                   // adjoint of J_ang(b) = cb
+      g.vb = g.vb + d * gu;
+      g.wb = g.wb + cb * gu;
+      gab = gab + smul(Iwb, gIb);
+      add_sym(mi + 6, gIb, cb);
+      // J_ang(b) = rb x d
+      grb = grb + cross(d, gab);
+      gd[q] = gd[q] + cross(gab, rb);
+    }
+    glam[q] = glam_before;
+  }
+  Q[0] = f4(gd[0], gm[0]); Q[1] = f4(gd[1], gm[1]); Q[2] = f4(gd[2], gm[2]);
+  Q[3] = f4(gra, gbias); Q[4] = f4(grb, glam[0]); Q[5] = make_float4(glam[1], glam[2], 0.f, 0.f);
 }
 
 __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* lam_it,
@@ -298,29 +417,32 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
       g.va = A >= 0 ? f3(a.bv[A]) : z; g.wa = A >= 0 ? f3(a.bw[A]) : z;
       g.vb = B >= 0 ? f3(a.bv[B]) : z; g.wb = B >= 0 ? f3(a.bw[B]) : z;
       const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
-      int nrows, jnr = 0;
-      int4 mf = make_int4(0, 0, 0, 0);
-      if (k < J) { jnr = w.jinfo[k].w; nrows = jnr; }
-      else { mf = w.man[k - J]; nrows = 3 * mf.w; }
-      const float mu = k < J ? 0.f : p.mu;
-      // software pipelining: the next row's parameters, adjoints and lambdas
-      // load while this row runs (rows of a constraint never alias)
-      int nr_cur = -1;
-      int r_cur = k < J ? jrow(k, jnr - 1) : rev_contact_row(p.L, mf, 0, nr_cur);
-      RevRow cur, nxt;
-      load_rev_row(a, r_cur, lam_it, lam_prev, k < J ? -1 : nr_cur, cur);
-      float pend = 0.f;   // friction adjoints owed to the current point's normal row
-      for (int i = 0; i < nrows; ++i) {
-        int r_nxt = -1, nr_nxt = -1;
-        if (i + 1 < nrows) {
-          r_nxt = k < J ? jrow(k, jnr - 2 - i) : rev_contact_row(p.L, mf, i + 1, nr_nxt);
-          load_rev_row(a, r_nxt, lam_it, lam_prev, k < J ? -1 : nr_nxt, nxt);
+      if (k < J) {
+        const int jnr = w.jinfo[k].w;
+        // software pipelining: the next row's parameters, adjoints and lambdas
+        // load while this row runs (rows of a constraint never alias)
+        int r_cur = jrow(k, jnr - 1);
+        RevRow cur, nxt;
+        load_rev_row(a, r_cur, lam_it, lam_prev, -1, cur);
+        for (int i = 0; i < jnr; ++i) {
+          const int r_nxt = jrow(k, jnr - 2 - i);
+          if (i + 1 < jnr) load_rev_row(a, r_nxt, lam_it, lam_prev, -1, nxt);
+          float gfric;
+          reverse_row(a, r_cur, A, B, ima, imb, v, g, cur, 0.f, gfric);
+          if (i + 1 < jnr) { cur = nxt; r_cur = r_nxt; }
         }
-        if (k >= J && r_cur == nr_cur) { cur.g2.w += pend; pend = 0.f; }   // the normal row: add what t1, t2 sent
-        float gfric;
-        reverse_row(a, r_cur, A, B, ima, imb, v, g, cur, mu, gfric);
-        pend += gfric;
-        if (i + 1 < nrows) { cur = nxt; r_cur = r_nxt; nr_cur = nr_nxt; }
+      } else {
+        const int4 mf = w.man[k - J];
+        const Sym3 Iwa = load_Iw(w, A);
+        Sym3 Iwb = Iwa;
+        if (B >= 0) Iwb = load_Iw(w, B);
+        float4* MA = a.madj + 4 * (k - J);
+        float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
+        float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
+        for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
+          reverse_point(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
+        MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
+        MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
       }
       if (A >= 0) { w.bv[A] = f4(v.va, 0.f); w.bw[A] = f4(v.wa, 0.f); a.bv[A] = f4(g.va, 0.f); a.bw[A] = f4(g.wa, 0.f); }
       if (B >= 0) { w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f); }
@@ -370,87 +492,161 @@ __device__ __forceinline__ void reverse_mass_part(const AWs& a, int r, int A, in
   G[0] = f4(gla, 0.f); G[1] = f4(gaa, G[1].w); G[2] = f4(gab, G[2].w);
 }
 
+// The effective-mass part of a contact point's three rows (m = 1/K, K =
+// ima |d|^2 + ca.Iw_a ca [+ imb |d|^2 + cb.Iw_b cb]): moves each row's mass
+// adjoint onto d, the arms, the inverse inertias and the inverse masses.
+__device__ __forceinline__ void contact_mass_adjoint(const AWs& a, int ci, bool bdyn, float ima, float imb,
+                                                     const Sym3& Iwa, const Sym3& Iwb, float* gIwa, float* gIwb,
+                                                     float& gima, float& gimb) {
+  const float4* P = a.cpar + 4 * ci;
+  float4* Q = a.cadj + 6 * ci;
+  const V3<float> n = f3(P[0]), ra = f3(P[1]), rb = f3(P[2]);
+  const float ms[3] = {P[0].w, P[2].w, P[3].x};
+  V3<float> t1, t2;
+  onb(n, t1, t2);
+  const V3<float> dirs[3] = {n, t1, t2};
+  V3<float> gra = f3(Q[3]), grb = f3(Q[4]);
+  for (int q = 0; q < 3; ++q) {
+    const float m = ms[q];
+    const float gK = m > 0.f ? -m * m * Q[q].w : 0.f;
+    const V3<float> d = dirs[q];
+    const V3<float> ca = cross(ra, d), cb = cross(rb, d);
+    const float ll = dot(d, d);
+    V3<float> gd = f3(Q[q]);
+    // body a: K_a = ima |d|^2 + J_ang.Iw_a J_ang with J_ang = -ca
+    gd = gd + d * (2.f * gK * ima);
+    gima += gK * ll;
+    const V3<float> gaa = smul(Iwa, ca) * (-2.f * gK);
+    add_sym(gIwa, ca * gK, ca);
+    gd = gd + cross(ra, gaa);
+    gra = gra + cross(gaa, d);
+    if (bdyn) {
+      gd = gd + d * (2.f * gK * imb);
+      gimb += gK * ll;
+      const V3<float> gab = smul(Iwb, cb) * (2.f * gK);
+      add_sym(gIwb, cb * gK, cb);
+      grb = grb + cross(d, gab);
+      gd = gd + cross(gab, rb);
+    }
+    Q[q] = f4(gd, 0.f);
+  }
+  Q[3] = f4(gra, Q[3].w);
+  Q[4] = f4(grb, Q[4].w);
+}
+
 __device__ __forceinline__ d1 tan_of(int idx, int k, float v) { return d1(v, idx == k ? 1.f : 0.f); }
 
-// Adjoints of a joint's pose inputs and targets from its row adjoints, by
-// dual passes over (x_a, q_a)[if A], x_b, q_b, targets.
-__device__ void joint_geom_adjoint(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int k,
-                                   const float* tg, float* out /* xa3 qa4 xb3 qb4 tg3 */) {
+// One dual pass of a joint's row set-up along input `idx` (x_a 0-2, q_a 3-6,
+// x_b 7-9, q_b 10-13, targets 14-16): the row adjoints contracted with the
+// rows' derivatives along that input (0 for an input the joint lacks).
+__device__ float joint_geom_pass(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int k, int idx,
+                                 const float* tg) {
   const JointDesc& j = p.joints[e.j0 + k];
   const int A = j.parent, B = j.child;
   const bool drive = j.k > 0.f || j.d > 0.f;
   const int nd = drive ? joint_ndof(j.type) : 0;
+  if ((idx < 7 && A < 0) || (idx >= 14 && idx - 14 >= nd)) return 0.f;
   const int nr = joint_row_count(j);
   float4 xa4 = A >= 0 ? w.bx[A] : make_float4(0.f, 0.f, 0.f, 0.f);
   float4 qa4 = A >= 0 ? w.bq[A] : make_float4(1.f, 0.f, 0.f, 0.f);
   float4 xb4 = w.bx[B], qb4 = w.bq[B];
-  for (int q = 0; q < 17; ++q) out[q] = 0.f;
-  for (int idx = 0; idx < 17; ++idx) {
-    if (idx < 7 && A < 0) continue;
-    if (idx >= 14 && idx - 14 >= nd) continue;
-    V3<d1> xa = v3<d1>(tan_of(idx, 0, xa4.x), tan_of(idx, 1, xa4.y), tan_of(idx, 2, xa4.z));
-    Q4<d1> qa; qa.w = tan_of(idx, 3, qa4.x); qa.x = tan_of(idx, 4, qa4.y); qa.y = tan_of(idx, 5, qa4.z); qa.z = tan_of(idx, 6, qa4.w);
-    V3<d1> xb = v3<d1>(tan_of(idx, 7, xb4.x), tan_of(idx, 8, xb4.y), tan_of(idx, 9, xb4.z));
-    Q4<d1> qb; qb.w = tan_of(idx, 10, qb4.x); qb.x = tan_of(idx, 11, qb4.y); qb.y = tan_of(idx, 12, qb4.z); qb.z = tan_of(idx, 13, qb4.w);
-    d1 t[3];
-    for (int c = 0; c < 3; ++c) t[c] = tan_of(idx, 14 + c, c < nd ? tg[j.dof + c] : 0.f);
-    GRow<d1> g[ROWS_PER_JOINT];
-    int n = joint_geom<d1>(j, A >= 0, xa, qa, xb, qb, t, p.h, p.jbeta, g);
-    float acc = 0.f;
-    for (int r = 0; r < n && r < nr; ++r) {
-      const float4* G = a.radj + ROW_F4 * jrow(k, r);
-      acc += G[0].x * g[r].la.x.d + G[0].y * g[r].la.y.d + G[0].z * g[r].la.z.d;
-      acc += G[1].x * g[r].aa.x.d + G[1].y * g[r].aa.y.d + G[1].z * g[r].aa.z.d;
-      acc += G[2].x * g[r].ab.x.d + G[2].y * g[r].ab.y.d + G[2].z * g[r].ab.z.d;
-      acc += G[1].w * g[r].bias.d;
-    }
-    out[idx] = acc;
+  V3<d1> xa = v3<d1>(tan_of(idx, 0, xa4.x), tan_of(idx, 1, xa4.y), tan_of(idx, 2, xa4.z));
+  Q4<d1> qa; qa.w = tan_of(idx, 3, qa4.x); qa.x = tan_of(idx, 4, qa4.y); qa.y = tan_of(idx, 5, qa4.z); qa.z = tan_of(idx, 6, qa4.w);
+  V3<d1> xb = v3<d1>(tan_of(idx, 7, xb4.x), tan_of(idx, 8, xb4.y), tan_of(idx, 9, xb4.z));
+  Q4<d1> qb; qb.w = tan_of(idx, 10, qb4.x); qb.x = tan_of(idx, 11, qb4.y); qb.y = tan_of(idx, 12, qb4.z); qb.z = tan_of(idx, 13, qb4.w);
+  d1 t[3];
+  for (int c = 0; c < 3; ++c) t[c] = tan_of(idx, 14 + c, c < nd ? tg[j.dof + c] : 0.f);
+  GRow<d1> g[ROWS_PER_JOINT];
+  int n = joint_geom<d1>(j, A >= 0, xa, qa, xb, qb, t, p.h, p.jbeta, g);
+  float acc = 0.f;
+  for (int r = 0; r < n && r < nr; ++r) {
+    const float4* G = a.radj + ROW_F4 * jrow(k, r);
+    acc += G[0].x * g[r].la.x.d + G[0].y * g[r].la.y.d + G[0].z * g[r].la.z.d;
+    acc += G[1].x * g[r].aa.x.d + G[1].y * g[r].aa.y.d + G[1].z * g[r].aa.z.d;
+    acc += G[2].x * g[r].ab.x.d + G[2].y * g[r].ab.y.d + G[2].z * g[r].ab.z.d;
+    acc += G[1].w * g[r].bias.d;
   }
+  return acc;
 }
 
-// Adjoints of one contact point's inputs (x_a, q_a, x_b, q_b, n, ra_l, rb_l)
-// from its three rows' adjoints, by dual passes.
-__device__ void contact_geom_adjoint(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int ci, int ia,
-                                     int ib, float* out /* xa3 qa4 xb3 qb4 n3 ra3 rb3 */) {
-  float4 xa4 = w.bx[ia], qa4 = w.bq[ia];
-  float4 xb4 = ib >= 0 ? w.bx[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 qb4 = ib >= 0 ? w.bq[ib] : make_float4(1.f, 0.f, 0.f, 0.f);
-  float4 n4 = w.cn[ci], ra4 = w.cra[ci], rb4 = w.crb[ci];
-  for (int q = 0; q < 23; ++q) out[q] = 0.f;
-  const float4* G0 = a.radj + ROW_F4 * crow(p.L, ci, 0);
-  for (int idx = 0; idx < 23; ++idx) {
-    if (ib < 0 && idx >= 7 && idx < 14) continue;
-    V3<d1> xa = v3<d1>(tan_of(idx, 0, xa4.x), tan_of(idx, 1, xa4.y), tan_of(idx, 2, xa4.z));
-    Q4<d1> qa; qa.w = tan_of(idx, 3, qa4.x); qa.x = tan_of(idx, 4, qa4.y); qa.y = tan_of(idx, 5, qa4.z); qa.z = tan_of(idx, 6, qa4.w);
-    V3<d1> xb = v3<d1>(tan_of(idx, 7, xb4.x), tan_of(idx, 8, xb4.y), tan_of(idx, 9, xb4.z));
-    Q4<d1> qb; qb.w = tan_of(idx, 10, qb4.x); qb.x = tan_of(idx, 11, qb4.y); qb.y = tan_of(idx, 12, qb4.z); qb.z = tan_of(idx, 13, qb4.w);
-    V3<d1> n = v3<d1>(tan_of(idx, 14, n4.x), tan_of(idx, 15, n4.y), tan_of(idx, 16, n4.z));
-    V3<d1> ral = v3<d1>(tan_of(idx, 17, ra4.x), tan_of(idx, 18, ra4.y), tan_of(idx, 19, ra4.z));
-    V3<d1> rbl = v3<d1>(tan_of(idx, 20, rb4.x), tan_of(idx, 21, rb4.y), tan_of(idx, 22, rb4.z));
-    V3<d1> ra, rb;
-    d1 bias;
-    contact_geom<d1>(xa, qa, xb, qb, ib >= 0, n, ral, rbl, p.h, p.beta, p.slop, ra, rb, bias);
-    V3<d1> t1, t2;
-    onb(n, t1, t2);
-    V3<d1> dirs[3] = {n, t1, t2};
-    float acc = 0.f;
-    for (int r = 0; r < 3; ++r) {
-      const float4* G = G0 + ROW_F4 * r;
-      V3<d1> la = -dirs[r], aa = -cross(ra, dirs[r]), ab = cross(rb, dirs[r]);
-      acc += G[0].x * la.x.d + G[0].y * la.y.d + G[0].z * la.z.d;
-      acc += G[1].x * aa.x.d + G[1].y * aa.y.d + G[1].z * aa.z.d;
-      if (ib >= 0) acc += G[2].x * ab.x.d + G[2].y * ab.y.d + G[2].z * ab.z.d;
-      if (r == 0) acc += G[1].w * bias.d;
-    }
-    out[idx] = acc;
-  }
+// Adjoint of r = R(q) v (R the rotation matrix of the quaternion q = (w, u),
+// as qmat forms it, R v = v + 2w (u x v) + 2 u x (u x v)) for the adjoint g of
+// r: adds R^T g to gv and dr/dq^T g to gq (w, x, y, z).
+__device__ __forceinline__ void rotate_adjoint(const float4& q4, const V3<float>& v, const V3<float>& g,
+                                               V3<float>& gv, float* gq) {
+  const V3<float> u = v3<float>(q4.y, q4.z, q4.w);
+  const float w = q4.x;
+  const M3<float> R = qmat(ldq4(q4));
+  gv = gv + mulT(R, g);
+  gq[0] += 2.f * dot(g, cross(u, v));
+  const V3<float> gu = cross(v, g) * (2.f * w) + g * (2.f * dot(u, v)) + v * (2.f * dot(u, g)) - u * (4.f * dot(v, g));
+  gq[1] += gu.x; gq[2] += gu.y; gq[3] += gu.z;
 }
 
-// Per constraint: effective-mass reverse, then the geometry reverse; writes
-// pose/inertia/mass adjoints to the constraint's gather slot, contact geometry
-// adjoints to the contact points, target adjoints to the joint's DoFs.
+// Adjoint of one contact point's row geometry (contact_geom, then the
+// tangent basis of the normal) for the adjoints of its normal, tangents,
+// world arms and bias: out = adjoints of x_a 0-2, q_a 3-6, x_b 7-9, q_b
+// 10-13, n 14-16, ra_l 17-19, rb_l 20-22 (a static b's anchor is in world).
+__device__ void contact_geom_adjoint(const Params& p, const Ws& w, const AWs& a, int ci, int ia, int ib,
+                                     float* out) {
+  for (int k = 0; k < 23; ++k) out[k] = 0.f;
+  const float4* Q = a.cadj + 6 * ci;
+  const float4 xa4 = w.bx[ia], qa4 = w.bq[ia];
+  const V3<float> n = f3(w.cn[ci]), ral = f3(w.cra[ci]), rbl = f3(w.crb[ci]);
+  V3<float> gn = f3(Q[0]);
+  const V3<float> gt1 = f3(Q[1]), gt2 = f3(Q[2]);
+  // the tangent basis (Duff et al.): t1, t2 from n
+  {
+    const float sg = n.z >= 0.f ? 1.f : -1.f;
+    const float al = -1.f / (sg + n.z);
+    const float gb = gt1.y * sg + gt2.x;
+    const float gal = gt1.x * sg * n.x * n.x + gt2.y * n.y * n.y + gb * n.x * n.y;
+    gn.x += gt1.x * 2.f * sg * n.x * al + gb * n.y * al - gt1.z * sg;
+    gn.y += gb * n.x * al + gt2.y * 2.f * n.y * al - gt2.z;
+    gn.z += gal * al * al;
+  }
+  // arms and separation
+  const V3<float> ra = mul(qmat(ldq4(qa4)), ral);
+  const V3<float> pa = f3(xa4) + ra;
+  V3<float> pb;
+  float4 xb4 = make_float4(0.f, 0.f, 0.f, 0.f), qb4 = make_float4(1.f, 0.f, 0.f, 0.f);
+  if (ib >= 0) {
+    xb4 = w.bx[ib]; qb4 = w.bq[ib];
+    pb = f3(xb4) + mul(qmat(ldq4(qb4)), rbl);
+  } else pb = rbl;
+  const float sep = dot(n, pb - pa);
+  const float gbias = Q[3].w;
+  const float gs = sep > 0.f ? gbias / p.h : (-sep - p.slop > 0.f ? gbias * (p.beta / p.h) : 0.f);
+  gn = gn + (pb - pa) * gs;
+  const V3<float> gpa = n * (-gs), gpb = n * gs;
+  // a: pa = xa + R(qa) ra_l
+  out[0] = gpa.x; out[1] = gpa.y; out[2] = gpa.z;
+  V3<float> gral = v3<float>(0.f, 0.f, 0.f);
+  rotate_adjoint(qa4, ral, f3(Q[3]) + gpa, gral, out + 3);
+  // b: pb = xb + R(qb) rb_l, or the world anchor rb_l
+  V3<float> grbl = v3<float>(0.f, 0.f, 0.f);
+  if (ib >= 0) {
+    out[7] = gpb.x; out[8] = gpb.y; out[9] = gpb.z;
+    rotate_adjoint(qb4, rbl, f3(Q[4]) + gpb, grbl, out + 10);
+  } else grbl = gpb;
+  out[14] = gn.x; out[15] = gn.y; out[16] = gn.z;
+  out[17] = gral.x; out[18] = gral.y; out[19] = gral.z;
+  out[20] = grbl.x; out[21] = grbl.y; out[22] = grbl.z;
+}
+
+// Component `idx` (0-13) of a gather slot's pose part: x_a in 0-2, q_a in
+// 4-7, x_b in 8-10, q_b in 12-15 of the slot's first four float4.
+__device__ __forceinline__ int pose_slot(int idx) { return idx < 3 ? idx : idx < 7 ? idx + 1 : idx < 10 ? idx + 1 : idx + 2; }
+
+// The reverse of the row set-up: per constraint the effective-mass part
+// (onto Jacobians, arms, inverse inertias and inverse masses, written to the
+// constraint's gather slot); then one item per joint and input (a dual pass
+// of the joint's rows) and per contact point (the hand-written reverse of its
+// geometry); a contact point's pose adjoints are summed per manifold in point
+// order, its normal and arm adjoints added to the point, a joint's target
+// adjoints to its DoFs.
 __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
-  const int J = e.J, K = J + w.misc[MC_MANIFOLDS];
+  const int J = e.J, M = w.misc[MC_MANIFOLDS], K = J + M, nc = w.misc[MC_CONTACTS];
   for (int k = e.lane; k < K; k += e.nthr) {
     int A, B;
     con_bodies(p, e, w, k, J, A, B);
@@ -460,39 +656,66 @@ __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, co
     if (B >= 0) Iwb = load_Iw(w, B);
     float gIwa[6] = {0, 0, 0, 0, 0, 0}, gIwb[6] = {0, 0, 0, 0, 0, 0};
     float gima = 0.f, gimb = 0.f;
-    float pose[14];
-    for (int q = 0; q < 14; ++q) pose[q] = 0.f;
     if (k < J) {
       const JointDesc& j = p.joints[e.j0 + k];
       const int nr = joint_row_count(j);
       for (int r = 0; r < nr; ++r) reverse_mass_part(a, jrow(k, r), A, B, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
-      float out[17];
-      joint_geom_adjoint(p, e, w, a, k, tg, out);
-      for (int q = 0; q < 14; ++q) pose[q] = out[q];
-      const int nd = (j.k > 0.f || j.d > 0.f) ? joint_ndof(j.type) : 0;
-      for (int c = 0; c < nd; ++c) a.tg[j.dof + c] += out[14 + c];
     } else {
       int4 mf = w.man[k - J];
-      for (int ci = mf.z; ci < mf.z + mf.w; ++ci) {
-        for (int r = 0; r < 3; ++r)
-          reverse_mass_part(a, crow(p.L, ci, r), A, B, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
-        float out[23];
-        contact_geom_adjoint(p, e, w, a, ci, A, B, out);
-        for (int q = 0; q < 14; ++q) pose[q] += out[q];
-        add4(a.cg[3 * ci + 0], v3<float>(out[14], out[15], out[16]));
-        add4(a.cg[3 * ci + 1], v3<float>(out[17], out[18], out[19]));
-        add4(a.cg[3 * ci + 2], v3<float>(out[20], out[21], out[22]));
-      }
+      const float4* MA = a.madj + 4 * (k - J);
+      gIwa[0] = MA[0].x; gIwa[1] = MA[0].y; gIwa[2] = MA[0].z; gIwa[3] = MA[0].w; gIwa[4] = MA[1].x; gIwa[5] = MA[1].y;
+      gIwb[0] = MA[1].z; gIwb[1] = MA[1].w; gIwb[2] = MA[2].x; gIwb[3] = MA[2].y; gIwb[4] = MA[2].z; gIwb[5] = MA[2].w;
+      gima = MA[3].x; gimb = MA[3].y;
+      for (int ci = mf.z; ci < mf.z + mf.w; ++ci)
+        contact_mass_adjoint(a, ci, B >= 0, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
     }
     float4* S = a.gat + 8 * k;
-    S[0] = make_float4(pose[0], pose[1], pose[2], 0.f);
-    S[1] = make_float4(pose[3], pose[4], pose[5], pose[6]);
-    S[2] = make_float4(pose[7], pose[8], pose[9], 0.f);
-    S[3] = make_float4(pose[10], pose[11], pose[12], pose[13]);
     S[4] = make_float4(gIwa[0], gIwa[1], gIwa[2], gIwa[3]);
     S[5] = make_float4(gIwa[4], gIwa[5], gima, 0.f);
     S[6] = make_float4(gIwb[0], gIwb[1], gIwb[2], gIwb[3]);
     S[7] = make_float4(gIwb[4], gIwb[5], gimb, 0.f);
+  }
+  gsync(e);
+  const int NJ = 17 * J, NC = nc;
+  for (int t = e.lane; t < NJ + NC; t += e.nthr) {
+    if (t < NJ) {
+      const int k = t / 17, idx = t % 17;
+      const float v = joint_geom_pass(p, e, w, a, k, idx, tg);
+      if (idx < 14) {
+        float* S = (float*)(a.gat + 8 * k);
+        S[pose_slot(idx)] = v;
+        if (idx == 2 || idx == 9) S[pose_slot(idx) + 1] = 0.f;
+      } else {
+        const JointDesc& j = p.joints[e.j0 + k];
+        if (idx - 14 < ((j.k > 0.f || j.d > 0.f) ? joint_ndof(j.type) : 0)) a.tg[j.dof + idx - 14] += v;
+      }
+    } else {
+      const int ci = t - NJ;
+      const int ids = w.cid[ci];
+      const int ia = ids & 0xffff, bc = ids >> 16;
+      float out[23];
+      contact_geom_adjoint(p, w, a, ci, ia, bc < e.D ? bc : -1, out);
+      float* cp = a.cpose + 16 * ci;
+      for (int idx = 0; idx < 14; ++idx) cp[pose_slot(idx)] = out[idx];
+      add4(a.cg[3 * ci + 0], v3<float>(out[14], out[15], out[16]));
+      add4(a.cg[3 * ci + 1], v3<float>(out[17], out[18], out[19]));
+      add4(a.cg[3 * ci + 2], v3<float>(out[20], out[21], out[22]));
+    }
+  }
+  gsync(e);
+  for (int m = e.lane; m < M; m += e.nthr) {
+    const int4 mf = w.man[m];
+    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+    for (int ci = mf.z; ci < mf.z + mf.w; ++ci) {
+      const float4* c = (const float4*)(a.cpose + 16 * ci);
+      const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3];
+      s0.x += c0.x; s0.y += c0.y; s0.z += c0.z;
+      s1.x += c1.x; s1.y += c1.y; s1.z += c1.z; s1.w += c1.w;
+      s2.x += c2.x; s2.y += c2.y; s2.z += c2.z;
+      s3.x += c3.x; s3.y += c3.y; s3.z += c3.z; s3.w += c3.w;
+    }
+    float4* S = a.gat + 8 * (J + m);
+    S[0] = s0; S[1] = s1; S[2] = s2; S[3] = s3;
   }
 }
 
