@@ -584,7 +584,8 @@ struct msh_handle {
   char* d_ws_plain = nullptr;   // E slabs
   char* d_ws_fused = nullptr;   // per-CTA HBM slabs (cold part, or the whole workspace without room in SMEM)
   int64_t fused_slab_bytes = 0;
-  int bwd_warps = 0;             // resident warps of the adjoint kernel on this GPU
+  int bwd_warps = 0;             // resident warps of the adjoint kernels on this GPU
+  int bwd_sweep_warps = 0;       // ... of the reversed sweeps without shared memory
   FusedKernel fused_fn = nullptr;  // instantiation chosen for the block size and workspace
   int fused_blocks_per_sm = 0;
   // adjoint
@@ -1128,15 +1129,25 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
   p.G = G;
   const int per_block = 32 / G;
   const int grid = (h->E + per_block - 1) / per_block;
-  // the sweeps: one env per warp, `slice` bytes of shared memory each
-  const int slice = bwd_sweep_slice(h);
+  // The sweeps: two envs per warp (16 lanes each; a colour holds about a
+  // dozen constraints) while that still fills the resident warps, with the
+  // device-memory workspace; otherwise one env per warp, staged in `slice`
+  // bytes of shared memory when it fits.
+  if (h->bwd_sweep_warps == 0) {
+    int blocks = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_sweeps, 32, 0));
+    h->bwd_sweep_warps = std::max(1, blocks) * h->num_sms;
+  }
+  const int Gs = (long long)h->E * 16 / 32 >= h->bwd_sweep_warps ? 16 : 32;
+  const int slice = Gs == 32 ? bwd_sweep_slice(h) : 0;
+  const int sweep_grid = (h->E + 32 / Gs - 1) / (32 / Gs);
   Params ps = p;
-  ps.G = 32;
+  ps.G = Gs;
   cudaStream_t s = (cudaStream_t)stream;
   k_bwd_replay<<<grid, 32, 0, s>>>(p, q);
   for (int sub = p.S - 1; sub >= 0; --sub) {
     k_bwd_rows<<<grid, 32, 0, s>>>(p, q, sub);
-    k_bwd_sweeps<<<h->E, 32, slice, s>>>(ps, q, sub, slice);
+    k_bwd_sweeps<<<sweep_grid, 32, (32 / Gs) * slice, s>>>(ps, q, sub, slice);
     k_bwd_setup<<<grid, 32, 0, s>>>(p, q, sub);
   }
   k_bwd_finish<<<grid, 32, 0, s>>>(p, q);
