@@ -239,10 +239,11 @@ __global__ void k_bwd_rows(Params p, AdjParams q, int s) {
 }
 
 // Substep s: the N sweeps in reverse. Each env group has `slice` bytes of
-// shared memory; an env whose rows (parameters and adjoint accumulators) and
-// body velocities and velocity adjoints fit is staged there for the N sweeps
-// (the rows are re-read and the adjoints re-written once per row per sweep),
-// a larger env runs on its device-memory workspace.
+// shared memory: the body velocities and velocity adjoints (read and written
+// by every constraint update) are staged there when they fit, and the rows
+// (parameters and adjoint accumulators, re-read and re-written once per row
+// per sweep) too when everything fits; the rest stays in the device-memory
+// workspace.
 __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   extern __shared__ float4 bsm[];
   BwdEnv b;
@@ -251,39 +252,44 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   const float* lam0 = b.tape + b.tl.t2 + (long long)s * p.N * p.tape_Rm;
   const int RJ = ROWS_PER_JOINT * e.J;                 // joint row slots in use
   const int nc = b.w.misc[MC_CONTACTS], nm = b.w.misc[MC_MANIFOLDS];
-  const int need = (2 * RJ * ROW_F4 + 10 * nc + 4 * nm + 4 * e.D) * 16;
+  const int need_b = 4 * e.D * 16;
+  const int need_r = (2 * RJ * ROW_F4 + 10 * nc + 4 * nm) * 16;
   Ws w = b.w;
   AWs a = b.a;
-  const bool staged = need <= slice;
-  if (staged) {
+  const bool bodies = need_b <= slice, rows = need_b + need_r <= slice;
+  if (bodies) {
     float4* base = bsm + (size_t)(threadIdx.x / e.nthr) * (slice / 16);
-    a.rows = base;
-    a.radj = a.rows + (size_t)RJ * ROW_F4;
-    a.cpar = a.radj + (size_t)RJ * ROW_F4;
-    a.cadj = a.cpar + 4 * nc;
-    a.madj = a.cadj + 6 * nc;
-    w.bv = a.madj + 4 * nm;
+    w.bv = base;
     w.bw = w.bv + e.D;
     a.bv = w.bw + e.D;
     a.bw = a.bv + e.D;
-    for (int i = e.lane; i < RJ * ROW_F4; i += e.nthr) { a.rows[i] = b.a.rows[i]; a.radj[i] = b.a.radj[i]; }
-    for (int i = e.lane; i < 4 * nc; i += e.nthr) a.cpar[i] = b.a.cpar[i];
-    for (int i = e.lane; i < 6 * nc; i += e.nthr) a.cadj[i] = b.a.cadj[i];
-    for (int i = e.lane; i < 4 * nm; i += e.nthr) a.madj[i] = b.a.madj[i];
     for (int i = e.lane; i < e.D; i += e.nthr) {
       w.bv[i] = b.w.bv[i]; w.bw[i] = b.w.bw[i]; a.bv[i] = b.a.bv[i]; a.bw[i] = b.a.bw[i];
+    }
+    if (rows) {
+      a.rows = a.bw + e.D;
+      a.radj = a.rows + (size_t)RJ * ROW_F4;
+      a.cpar = a.radj + (size_t)RJ * ROW_F4;
+      a.cadj = a.cpar + 4 * nc;
+      a.madj = a.cadj + 6 * nc;
+      for (int i = e.lane; i < RJ * ROW_F4; i += e.nthr) { a.rows[i] = b.a.rows[i]; a.radj[i] = b.a.radj[i]; }
+      for (int i = e.lane; i < 4 * nc; i += e.nthr) a.cpar[i] = b.a.cpar[i];
+      for (int i = e.lane; i < 6 * nc; i += e.nthr) a.cadj[i] = b.a.cadj[i];
+      for (int i = e.lane; i < 4 * nm; i += e.nthr) a.madj[i] = b.a.madj[i];
     }
     gsync(e);
   }
   for (int it = p.N - 1; it >= 0; --it)
     reverse_sweep(p, e, w, a, lam0 + (long long)it * p.tape_Rm, it > 0 ? lam0 + (long long)(it - 1) * p.tape_Rm : nullptr);
-  if (staged) {
+  if (bodies) {
     gsync(e);
-    for (int i = e.lane; i < RJ * ROW_F4; i += e.nthr) b.a.radj[i] = a.radj[i];
-    for (int i = e.lane; i < 6 * nc; i += e.nthr) b.a.cadj[i] = a.cadj[i];
-    for (int i = e.lane; i < 4 * nm; i += e.nthr) b.a.madj[i] = a.madj[i];
     for (int i = e.lane; i < e.D; i += e.nthr) {
       b.w.bv[i] = w.bv[i]; b.w.bw[i] = w.bw[i]; b.a.bv[i] = a.bv[i]; b.a.bw[i] = a.bw[i];
+    }
+    if (rows) {
+      for (int i = e.lane; i < RJ * ROW_F4; i += e.nthr) b.a.radj[i] = a.radj[i];
+      for (int i = e.lane; i < 6 * nc; i += e.nthr) b.a.cadj[i] = a.cadj[i];
+      for (int i = e.lane; i < 4 * nm; i += e.nthr) b.a.madj[i] = a.madj[i];
     }
   }
 }
@@ -1130,16 +1136,16 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
   const int per_block = 32 / G;
   const int grid = (h->E + per_block - 1) / per_block;
   // The sweeps: two envs per warp (16 lanes each; a colour holds about a
-  // dozen constraints) while that still fills the resident warps, with the
-  // device-memory workspace; otherwise one env per warp, staged in `slice`
-  // bytes of shared memory when it fits.
+  // dozen constraints) while that still fills the resident warps, each with
+  // its bodies staged in shared memory; otherwise one env per warp with a
+  // larger slice that also holds the rows of envs that fit.
   if (h->bwd_sweep_warps == 0) {
     int blocks = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_sweeps, 32, 0));
     h->bwd_sweep_warps = std::max(1, blocks) * h->num_sms;
   }
   const int Gs = (long long)h->E * 16 / 32 >= h->bwd_sweep_warps ? 16 : 32;
-  const int slice = Gs == 32 ? bwd_sweep_slice(h) : 0;
+  const int slice = Gs == 32 ? bwd_sweep_slice(h) : 4 * h->Dm * 16;
   const int sweep_grid = (h->E + 32 / Gs - 1) / (32 / Gs);
   Params ps = p;
   ps.G = Gs;
