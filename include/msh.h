@@ -348,6 +348,11 @@ int msh_render_depth(msh_handle* h, const msh_state* st, float* depth, void* str
 int msh_set_tape(msh_handle* h, int32_t max_steps);
 int msh_tape_reset(msh_handle* h);
 int32_t msh_tape_count(const msh_handle* h);
+/* Pauses (on = 0) or resumes (on != 0) recording without dropping the
+ * recorded steps: while paused, steps run as without a tape and msh_backward
+ * still reverses the recorded ones. Resuming needs a tape (msh_set_tape);
+ * msh_set_tape resumes as well. */
+int msh_tape_record(msh_handle* h, int32_t on);
 int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, float* adj_targets,
                  float* adj_mass, void* stream);
 

@@ -18,7 +18,8 @@ EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_s
            "msh_detect", "msh_get_status", "msh_clear_status", "msh_scratch_bytes", "msh_workspace_bytes",
            "msh_launches_per_step", "msh_step_static_scratch", "msh_set_tape", "msh_tape_reset",
            "msh_tape_count", "msh_backward", "msh_set_report", "msh_label_events", "msh_set_cameras",
-           "msh_render_depth", "msh_set_controller", "msh_control_step")
+           "msh_render_depth", "msh_set_controller", "msh_control_step",
+           "msh_tape_record")
 TASK_PICK, TASK_PLACE, TASK_OPEN, TASK_CLOSE = 0, 1, 2, 3
 
 
@@ -98,6 +99,7 @@ def load(build_if_missing: bool = True):
     lib.msh_control_step.argtypes = [P, P, P, P, P]
     lib.msh_label_events.argtypes = [I32, P, I32, P, P, P, P]
     lib.msh_tape_reset.argtypes = [P]
+    lib.msh_tape_record.argtypes = [P, I32]
     lib.msh_tape_count.argtypes = [P]
     lib.msh_tape_count.restype = C.c_int32
     lib.msh_backward.argtypes = [P, P, P, P, P, P]

@@ -5,7 +5,10 @@ through targets[0..T) and returns the final state. Its backward pass keeps
 only every k-th state from the forward pass (step checkpointing): for each
 segment, last first, it restores the segment's start state, re-runs the
 segment with the library recording a tape, and reverses the recorded steps
-with msh_backward. Memory is O(T/k states + k tapes).
+with msh_backward. The forward pass records the last segment itself and
+pauses the tape, so the backward pass reverses that segment without a
+re-run when nothing has touched the tape in between. Memory is O(T/k
+states + k tapes).
 
 `mass` must hold the scene's body masses (the library derived the inverse
 masses and inertias from them at msh_create); only its gradient is used.
@@ -24,11 +27,17 @@ class _Rollout(torch.autograd.Function):
         for dst, src in ((sim.pos, pos), (sim.quat, quat), (sim.linvel, linvel), (sim.angvel, angvel)):
             dst.copy_(src)
         ckpts = []
+        last = ((T - 1) // k) * k          # first step of the last segment
         for t in range(T):
             if t % k == 0:
                 ckpts.append(tuple(x.clone() for x in (sim.pos, sim.quat, sim.linvel, sim.angvel)))
+            if t == last:
+                sim.set_tape(k)             # record the last segment now
             sim.step(targets[t])
-        ctx.sim, ctx.k, ctx.T, ctx.ckpts = sim, k, T, ckpts
+        sim.tape_record(False)              # keep it, record nothing else
+        ctx.token = object()
+        sim.tape_owner = ctx.token
+        ctx.sim, ctx.k, ctx.T, ctx.ckpts, ctx.recorded = sim, k, T, ckpts, T - last
         ctx.save_for_backward(targets)
         return tuple(x.clone() for x in (sim.pos, sim.quat, sim.linvel, sim.angvel))
 
@@ -41,15 +50,16 @@ class _Rollout(torch.autograd.Function):
                     for g, x in zip((gpos, gquat, glv, gav), like))
         adj_targets = torch.zeros_like(targets)
         adj_mass = torch.zeros(sim.scene.num_bodies, dtype=torch.float32, device=sim.device)
-        sim.set_tape(k)
         nseg = (T + k - 1) // k
+        kept = sim.tape_owner is ctx.token and sim.tape_count == ctx.recorded
         for seg in reversed(range(nseg)):
             t0, t1 = seg * k, min(T, seg * k + k)
-            for dst, src in zip((sim.pos, sim.quat, sim.linvel, sim.angvel), ctx.ckpts[seg]):
-                dst.copy_(src)
-            sim.tape_reset()
-            for t in range(t0, t1):
-                sim.step(targets[t])
+            if not (kept and seg == nseg - 1):
+                for dst, src in zip((sim.pos, sim.quat, sim.linvel, sim.angvel), ctx.ckpts[seg]):
+                    dst.copy_(src)
+                sim.set_tape(k)
+                for t in range(t0, t1):
+                    sim.step(targets[t])
             for t in reversed(range(t0, t1)):
                 adj = sim.backward(adj, adj_targets[t], adj_mass)
         sim.set_tape(0)        # stop recording; the tape memory is kept for the next backward pass

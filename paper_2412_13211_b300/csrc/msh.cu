@@ -598,6 +598,7 @@ struct msh_handle {
   float* d_tape = nullptr;      // tape_max recorded steps x E env slabs
   long long tape_slab = 0;
   int tape_max = 0, tape_count = 0, tape_Rm = 0, tape_cap = 0;   // recording capacity, recorded, rows, allocated
+  int tape_paused = 0;          // msh_tape_record(h, 0): steps are not recorded, the recorded ones are kept
   char* d_aws = nullptr;        // adjoint workspace slabs (E)
   AdjLayout A;
   int64_t bytes = 0;
@@ -956,7 +957,7 @@ static int step_impl(msh_handle* h, const msh_state* st, const float* targets, f
   if (h->max_dof > 0 && !targets) return fail(MSH_ERR_INVALID_ARG, "joint_targets is NULL but max_dof > 0");
   if (!(dt > 0.f)) dt = h->cfg.dt;
   if (substeps < 1) substeps = h->cfg.substeps;
-  if (h->tape_max > 0) {
+  if (h->tape_max > 0 && !h->tape_paused) {
     // recording for the adjoint: direct launches, one tape slot per step
     if (h->tape_count >= h->tape_max) return fail(MSH_ERR_INVALID_ARG, "tape full: call msh_backward or msh_tape_reset");
     if (substeps != h->cfg.substeps) return fail(MSH_ERR_INVALID_ARG, "recorded steps must use the configured substeps");
@@ -1057,6 +1058,7 @@ int msh_set_tape(msh_handle* h, int32_t max_steps) {
   if (max_steps > 0 && h->cfg.restitution > 0.f)
     return fail(MSH_ERR_UNSUPPORTED, "the adjoint supports restitution 0 only");
   h->tape_count = 0;
+  h->tape_paused = 0;
   if (max_steps <= 0) {
     h->tape_max = 0;                       // stop recording
     if (max_steps == -1 && h->d_tape) {    // and free the tape
@@ -1096,6 +1098,13 @@ int msh_tape_reset(msh_handle* h) {
 }
 
 int32_t msh_tape_count(const msh_handle* h) { return h ? h->tape_count : 0; }
+
+int msh_tape_record(msh_handle* h, int32_t on) {
+  if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
+  if (on && h->tape_max <= 0) return fail(MSH_ERR_INVALID_ARG, "no tape: call msh_set_tape first");
+  h->tape_paused = on ? 0 : 1;
+  return MSH_OK;
+}
 
 int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, float* adj_targets, float* adj_mass,
                  void* stream) {
@@ -1270,9 +1279,10 @@ int msh_control_step(msh_handle* h, const msh_state* st, const float* action, fl
   const float dt = h->cfg.dt;
   const int S = h->cfg.substeps;
   int rc;
-  if (h->tape_max > 0 || !h->use_graph) {
+  const bool rec = h->tape_max > 0 && !h->tape_paused;
+  if (rec || !h->use_graph) {
     // direct launches (a recording handle records each physics step)
-    if (h->tape_max > 0 && h->tape_count + h->ctrl_steps > h->tape_max)
+    if (rec && h->tape_count + h->ctrl_steps > h->tape_max)
       return fail(MSH_ERR_INVALID_ARG, "tape full: call msh_backward or msh_tape_reset");
     if ((rc = enqueue_control(h, action, targets, s))) return rc;
     for (int k = 0; k < h->ctrl_steps; ++k)

@@ -79,6 +79,7 @@ class MshSim:
             raise RuntimeError("MshSim needs a CUDA device; the step has no CPU implementation")
         self.lib = _lib.load()
         self.scene, self.cfg = scene, cfg
+        self.tape_owner = None   # the rollout whose forward pass recorded the tape (see autograd.rollout)
         self.device = torch.device(device)
         with torch.cuda.device(self.device):
             desc, keep = make_desc(scene)
@@ -302,11 +303,17 @@ class MshSim:
     def set_tape(self, max_steps: int):
         """max_steps > 0: record the next steps (room for max_steps); 0: stop
         recording (memory kept); -1: stop and free the tape."""
+        self.tape_owner = None
         with torch.cuda.device(self.device):
             check(self.lib.msh_set_tape(self.handle, int(max_steps)), "msh_set_tape")
 
     def tape_reset(self):
+        self.tape_owner = None
         check(self.lib.msh_tape_reset(self.handle), "msh_tape_reset")
+
+    def tape_record(self, on: bool):
+        """Pauses (False) or resumes (True) recording, keeping the recorded steps."""
+        check(self.lib.msh_tape_record(self.handle, int(bool(on))), "msh_tape_record")
 
     @property
     def tape_count(self) -> int:

@@ -152,3 +152,37 @@ def test_steps_after_backward_do_not_record():
         sim.step(tg[0].detach())
     assert sim.tape_count == 0
     sim.set_tape(-1)
+
+
+def test_forward_pass_keeps_the_last_segment_for_the_backward_pass():
+    """The forward pass records its last segment and pauses the tape: steps in
+    between are not recorded, and the gradients equal those of a backward
+    pass that re-runs every segment (forced by touching the tape)."""
+    import torch
+    from paper_2412_13211_b300.autograd import goal_loss, rollout
+    from paper_2412_13211_b300.sim import MshSim
+    sc, cfg = S.make_config(4, num_envs=4)
+    tgn = sc.target_walk(5)
+    grads = []
+    for touch in (False, True):
+        sim = MshSim(sc, cfg)
+        st = [torch.tensor(np.asarray(a, np.float32), device="cuda", requires_grad=True) for a in sc.state()]
+        mass = torch.tensor(np.asarray(sc.body_mass, np.float32), device="cuda", requires_grad=True)
+        tg = torch.tensor(tgn, device="cuda", requires_grad=True)
+        out = rollout(sim, st, tg, mass, 2)
+        assert sim.tape_count == 1                      # the last segment (step 4) is kept
+        loss = goal_loss(sim, out[0]).sum()
+        if touch:
+            sim.tape_reset()                            # the backward pass must re-run it
+        else:
+            snap = tuple(x.clone() for x in (sim.pos, sim.quat, sim.linvel, sim.angvel))
+            sim.step(tg[0].detach())                    # paused: not recorded
+            assert sim.tape_count == 1
+            for x, y in zip((sim.pos, sim.quat, sim.linvel, sim.angvel), snap):
+                x.copy_(y)
+        loss.backward()
+        grads.append([t.grad.cpu().numpy() for t in (st[2], st[3], tg, mass)])
+        assert sim.tape_count == 0
+        sim.close()
+    for a, b in zip(*grads):
+        assert np.array_equal(a, b)
