@@ -51,7 +51,9 @@ __global__ void k_narrow(Params p) {
 }
 __global__ void k_colour(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
-  stage_colour(p, e, plain_ws(p, blockIdx.x));
+  const Ws w = plain_ws(p, blockIdx.x);
+  stage_colour(p, e, w);
+  if (p.tape) tape_collision(p, e, w);
 }
 __global__ void k_intvel(Params p) {
   EnvInfo e = env_info(p, blockIdx.x);
@@ -125,6 +127,7 @@ __device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
     stage_broadphase(p, e, w, scr);
     stage_narrowphase(p, e, w, scr);
     stage_colour(p, e, w);
+    if (p.tape) tape_collision(p, e, w);
     for (int s = 0; s < p.S; ++s) {
       stage_integrate_vel(p, e, w, s);
       gsync(e);
@@ -178,26 +181,22 @@ __device__ __forceinline__ bool bwd_env(const Params& p, const AdjParams& q, Bwd
   b.e = env_info(p, env, lane, G, mask);
   b.w = plain_ws(p, env);
   b.a = make_aws(q.aws + (long long)env * q.aws_stride, q.A);
-  b.tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+  b.tl = tape_layout(p.L, p.S, p.N, p.max_dof);
   b.tape = p.tape + ((long long)q.slot * p.E + env) * p.tape_slab;
   return true;
 }
 
-// Replay of the collision stage; the state adjoints are loaded.
+// The recorded step-start state and collision stage back into the
+// workspace; the state adjoints are loaded.
 __global__ void k_bwd_replay(Params p, AdjParams q) {
-  __shared__ int scr[33];
   BwdEnv b;
   if (!bwd_env(p, q, b)) return;
   const EnvInfo& e = b.e;
   const Ws& w = b.w;
   const AWs& a = b.a;
   load_from_tape(p, e, w, b.tape);
+  untape_collision(p, e, w, b.tape);
   gsync(e);
-  stage_aabb(p, e, w);
-  gsync(e);
-  stage_broadphase(p, e, w, scr);
-  stage_narrowphase(p, e, w, scr);
-  stage_colour(p, e, w);
   build_incidence(p, e, w, a);
   for (int i = e.lane; i < e.D; i += e.nthr) {
     const int g = e.b0 + i;
@@ -1071,7 +1070,7 @@ int msh_set_tape(msh_handle* h, int32_t max_steps) {
     return MSH_OK;
   }
   drop_graph(h);
-  const TapeLayout tl = tape_layout(h->L.Dm, h->L.Jm, h->L.C, h->cfg.substeps, h->cfg.iterations, h->max_dof);
+  const TapeLayout tl = tape_layout(h->L, h->cfg.substeps, h->cfg.iterations, h->max_dof);
   h->tape_slab = tl.slab;
   h->tape_Rm = ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C;
   int rc;

@@ -99,7 +99,7 @@ __device__ __forceinline__ void add_sym(float* G, const V3<float>& g, const V3<f
 // replay helpers
 // ---------------------------------------------------------------------------
 // Loads the recorded step-start state into the workspace (as stage_load does
-// from the state arrays).
+// from the state arrays) and the joints' row information.
 __device__ void load_from_tape(const Params& p, const EnvInfo& e, const Ws& w, const float* tape) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
     const float* t = tape + 13 * i;
@@ -111,8 +111,6 @@ __device__ void load_from_tape(const Params& p, const EnvInfo& e, const Ws& w, c
     w.bIw1[i] = make_float4(0.f, 0.f, 1.f, 0.f);
   }
   load_jinfo(p, e, w);
-  load_statics(p, e, w);
-  if (e.lane < MC_N) w.misc[e.lane] = 0;
 }
 
 // World inverse inertia from an orientation and principal inverse inertia.

@@ -106,17 +106,33 @@ struct Params {
 //   per substep s:                 Dm x 19  (x_s, q_s, v_s, w_s after gravity; v, w after the solve)
 //   lambda after every sweep:      S x N x Rm (joint k row r: k*8 + r; contact c row i: 8*Jm + 3c + i)
 //   joint targets of the step:     max_dof
-struct TapeLayout { long long t0, t1, t2, t3, slab; };
-__host__ __device__ __forceinline__ TapeLayout tape_layout(int Dm, int Jm, int C, int S, int N, int md) {
+// Tape of one recorded step, floats per env: t0 the start state (13 per
+// body), t1 per substep the poses and velocities (19 per body), t2 the
+// lambdas after every sweep, t3 the targets, t4 the collision stage's results
+// (contact normals, anchors and ids, manifolds, colour order and offsets,
+// counts) so that the adjoint need not run it again.
+struct TapeLayout { long long t0, t1, t2, t3, t4, slab; };
+__host__ __device__ __forceinline__ TapeLayout tape_layout(const Layout& L, int S, int N, int md) {
   TapeLayout t;
-  const long long Rm = (long long)ROWS_PER_JOINT * Jm + 3LL * C;
+  const long long Rm = (long long)ROWS_PER_JOINT * L.Jm + 3LL * L.C;
   t.t0 = 0;
-  t.t1 = t.t0 + 13LL * Dm;
-  t.t2 = t.t1 + 19LL * Dm * S;
+  t.t1 = t.t0 + 13LL * L.Dm;
+  t.t2 = t.t1 + 19LL * L.Dm * S;
   t.t3 = t.t2 + (long long)S * N * Rm;
-  t.slab = (t.t3 + md + 3) & ~3LL;
+  t.t4 = (t.t3 + md + 3) & ~3LL;
+  t.slab = (t.t4 + ((13LL * L.C + 3) & ~3LL) + 4LL * L.P + L.K + (MAX_COLOURS + 1) + MC_N + 3) & ~3LL;
   return t;
 }
+// Offsets (floats) inside the t4 record; the float4/int4 arrays start on
+// 16-byte boundaries (t4 and the tape slab are multiples of 4 floats).
+__host__ __device__ __forceinline__ long long tc_cn(const Layout&) { return 0; }
+__host__ __device__ __forceinline__ long long tc_cra(const Layout& L) { return 4LL * L.C; }
+__host__ __device__ __forceinline__ long long tc_crb(const Layout& L) { return 8LL * L.C; }
+__host__ __device__ __forceinline__ long long tc_cid(const Layout& L) { return 12LL * L.C; }
+__host__ __device__ __forceinline__ long long tc_man(const Layout& L) { return (13LL * L.C + 3) & ~3LL; }
+__host__ __device__ __forceinline__ long long tc_corder(const Layout& L) { return tc_man(L) + 4LL * L.P; }
+__host__ __device__ __forceinline__ long long tc_coff(const Layout& L) { return tc_corder(L) + L.K; }
+__host__ __device__ __forceinline__ long long tc_misc(const Layout& L) { return tc_coff(L) + MAX_COLOURS + 1; }
 __device__ __forceinline__ float* tape_env(const Params& p, int env) { return p.tape + (long long)env * p.tape_slab; }
 
 // World data of a static box, 6 float4: centre, the three rows of its
@@ -269,7 +285,7 @@ __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
     }
   }
   if (p.tape) {
-    TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+    TapeLayout tl = tape_layout(p.L, p.S, p.N, p.max_dof);
     for (int k = e.lane; k < p.max_dof; k += e.nthr)
       tape_env(p, e.env)[tl.t3 + k] = p.targets ? p.targets[(size_t)e.env * p.max_dof + k] : 0.f;
   }
@@ -521,6 +537,46 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
   gsync(e);
 }
 
+// Records the collision stage's results of a recorded step (tape record t4).
+__device__ void tape_collision(const Params& p, const EnvInfo& e, const Ws& w) {
+  const Layout& L = p.L;
+  float* t = tape_env(p, e.env) + tape_layout(L, p.S, p.N, p.max_dof).t4;
+  const int nc = w.misc[MC_CONTACTS], nm = w.misc[MC_MANIFOLDS], K = e.J + nm, ncol = w.misc[MC_COLOURS];
+  float4* cn = (float4*)(t + tc_cn(L));
+  float4* cra = (float4*)(t + tc_cra(L));
+  float4* crb = (float4*)(t + tc_crb(L));
+  int* cid = (int*)(t + tc_cid(L));
+  int4* man = (int4*)(t + tc_man(L));
+  int* corder = (int*)(t + tc_corder(L));
+  int* coff = (int*)(t + tc_coff(L));
+  int* misc = (int*)(t + tc_misc(L));
+  for (int i = e.lane; i < nc; i += e.nthr) { cn[i] = w.cn[i]; cra[i] = w.cra[i]; crb[i] = w.crb[i]; cid[i] = w.cid[i]; }
+  for (int i = e.lane; i < nm; i += e.nthr) man[i] = w.man[i];
+  for (int i = e.lane; i < K; i += e.nthr) corder[i] = w.corder[i];
+  for (int i = e.lane; i <= ncol; i += e.nthr) coff[i] = w.coff[i];
+  for (int i = e.lane; i < MC_N; i += e.nthr) misc[i] = w.misc[i];
+}
+
+// The recorded collision stage back into a workspace (the adjoint's replay).
+__device__ void untape_collision(const Params& p, const EnvInfo& e, const Ws& w, const float* tape) {
+  const Layout& L = p.L;
+  const float* t = tape + tape_layout(L, p.S, p.N, p.max_dof).t4;
+  const int* misc = (const int*)(t + tc_misc(L));
+  const int nc = misc[MC_CONTACTS], nm = misc[MC_MANIFOLDS], K = e.J + nm, ncol = misc[MC_COLOURS];
+  const float4* cn = (const float4*)(t + tc_cn(L));
+  const float4* cra = (const float4*)(t + tc_cra(L));
+  const float4* crb = (const float4*)(t + tc_crb(L));
+  const int* cid = (const int*)(t + tc_cid(L));
+  const int4* man = (const int4*)(t + tc_man(L));
+  const int* corder = (const int*)(t + tc_corder(L));
+  const int* coff = (const int*)(t + tc_coff(L));
+  for (int i = e.lane; i < nc; i += e.nthr) { w.cn[i] = cn[i]; w.cra[i] = cra[i]; w.crb[i] = crb[i]; w.cid[i] = cid[i]; }
+  for (int i = e.lane; i < nm; i += e.nthr) w.man[i] = man[i];
+  for (int i = e.lane; i < K; i += e.nthr) w.corder[i] = corder[i];
+  for (int i = e.lane; i <= ncol; i += e.nthr) w.coff[i] = coff[i];
+  for (int i = e.lane; i < MC_N; i += e.nthr) w.misc[i] = misc[i];
+}
+
 // ---------------------------------------------------------------------------
 // a1: gravity; world inverse inertia
 // ---------------------------------------------------------------------------
@@ -530,7 +586,7 @@ __device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws&
     v.x = v.x + p.gx * p.h; v.y = v.y + p.gy * p.h; v.z = v.z + p.gz * p.h;
     w.bv[i] = v;
     if (p.tape) {
-      TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+      TapeLayout tl = tape_layout(p.L, p.S, p.N, p.max_dof);
       float* t = tape_env(p, e.env) + tl.t1 + 19LL * (sub * p.L.Dm + i);
       float4 x = w.bx[i], q = w.bq[i], wv = w.bw[i];
       t[0] = x.x; t[1] = x.y; t[2] = x.z; t[3] = q.x; t[4] = q.y; t[5] = q.z; t[6] = q.w;
@@ -958,7 +1014,7 @@ __device__ __forceinline__ BodyVel load_vel(const Ws& w, int a, int b) {
 
 // Records the lambdas of constraint k after its update in sweep `it`.
 __device__ __forceinline__ void tape_lambdas(const Params& p, const EnvInfo& e, const Ws& w, int k, int sub, int it) {
-  TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+  TapeLayout tl = tape_layout(p.L, p.S, p.N, p.max_dof);
   float* t = tape_env(p, e.env) + tl.t2 + (long long)(sub * p.N + it) * p.tape_Rm;
   if (k < e.J) {
     const JointDesc& j = p.joints[e.j0 + k];
@@ -1032,7 +1088,7 @@ __device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws&
   for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 x = w.bx[i], v = w.bv[i], wv = w.bw[i], q = w.bq[i];
     if (p.tape) {
-      TapeLayout tl = tape_layout(p.L.Dm, p.L.Jm, p.L.C, p.S, p.N, p.max_dof);
+      TapeLayout tl = tape_layout(p.L, p.S, p.N, p.max_dof);
       float* t = tape_env(p, e.env) + tl.t1 + 19LL * (sub * p.L.Dm + i) + 13;
       t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = wv.x; t[4] = wv.y; t[5] = wv.z;
     }

@@ -18,11 +18,11 @@ from paper_2412_13211_b300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_grads(sc, cfg, tg, nsteps, k):
+def _gpu_grads(sc, cfg, tg, nsteps, k, **sim_kw):
     import torch
     from paper_2412_13211_b300.autograd import goal_loss, rollout
     from paper_2412_13211_b300.sim import MshSim
-    sim = MshSim(sc, cfg)
+    sim = MshSim(sc, cfg, **sim_kw)
     st = [torch.tensor(np.asarray(a, np.float32), device="cuda", requires_grad=True) for a in sc.state()]
     mass = torch.tensor(np.asarray(sc.body_mass, np.float32), device="cuda", requires_grad=True)
     targets = torch.tensor(np.asarray(tg[:nsteps], np.float32), device="cuda", requires_grad=True)
@@ -99,6 +99,17 @@ def test_checkpoint_interval_does_not_change_gradients(diff_case):
         gk = _gpu_grads(sc, cfg, tg, nsteps, k)
         for key in ("v", "w", "tg", "m"):
             assert np.array_equal(gk[key], g4[key]), (k, key)
+
+
+def test_steps_recorded_by_every_form_give_the_same_gradients(diff_case):
+    """The recorded steps (state, lambdas and the collision stage's results)
+    of the plain, substep and fused forms are bitwise equal, so are the
+    gradients."""
+    sc, cfg, tg, nsteps, _, _, g4 = diff_case
+    for kw in (dict(exec_form="plain"), dict(exec_form="substep"), dict(exec_form="fused", threads_per_env=16)):
+        gk = _gpu_grads(sc, cfg, tg, nsteps, 4, **kw)
+        for key in ("v", "w", "tg", "m"):
+            assert np.array_equal(gk[key], g4[key]), (kw, key)
 
 
 def test_backward_through_c_abi_directly():
