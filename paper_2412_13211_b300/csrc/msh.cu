@@ -306,6 +306,7 @@ __global__ void k_bwd_setup(Params p, AdjParams q, int s) {
 }
 
 // The reverse of the narrowphase at the step-start poses, and the outputs.
+template <bool PER_ITEM>
 __global__ void k_bwd_finish(Params p, AdjParams q) {
   BwdEnv b;
   if (!bwd_env(p, q, b)) return;
@@ -318,7 +319,7 @@ __global__ void k_bwd_finish(Params p, AdjParams q) {
     w.bq[i] = make_float4(t[3], t[4], t[5], t[6]);
   }
   gsync(e);
-  reverse_detection(p, e, w, a);
+  reverse_detection<PER_ITEM>(p, e, w, a);
   gsync(e);
   gather_bodies(e, a, false);
   gsync(e);
@@ -541,6 +542,7 @@ AdjLayout make_adj_layout(const Layout& L, int md) {
   A.cpar = take((long long)L.C * 4 * f4); A.cadj = take((long long)L.C * 6 * f4);
   A.madj = take((long long)L.P * 4 * f4);
   A.cpose = take((long long)L.C * 4 * f4);
+  A.moff = take((long long)(L.P + 1) * 4);
   A.gat = take((long long)A.Km * 8 * f4);
   A.cg = take((long long)L.C * 3 * f4);
   A.inc_off = take((L.Dm + 1) * 4); A.inc = take(2LL * A.Km * 4);
@@ -1164,7 +1166,10 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
     k_bwd_sweeps<<<sweep_grid, 32, (32 / Gs) * slice, s>>>(ps, q, sub, slice);
     k_bwd_setup<<<grid, 32, 0, s>>>(p, q, sub);
   }
-  k_bwd_finish<<<grid, 32, 0, s>>>(p, q);
+  // the narrowphase reverse: one pass per lane for one-env warps (small
+  // batches: few manifolds per lane), all passes of a manifold per lane else
+  if (G == 32) k_bwd_finish<true><<<grid, 32, 0, s>>>(p, q);
+  else k_bwd_finish<false><<<grid, 32, 0, s>>>(p, q);
   CK(cudaGetLastError());
   h->tape_count--;
   return MSH_OK;
