@@ -24,8 +24,11 @@
 //     soft PD drives in Catto's 2011 soft-constraint form, Baumgarte joints;
 //   * greedy graph colouring (joints first, then manifolds) for PGS; Jacobi
 //     with Tonge et al. 2012 mass splitting as the variant.
-// Parity unpinned: capsule-capsule, capsule-box and box-box edge-edge manifolds
-// and the whole step beyond the closed forms the tests check.
+// Pinned by brute force (tests/test_oracle_manifolds.py): capsule-capsule,
+// capsule-box (segment outside the box), box-box face and edge manifolds,
+// sphere centres inside boxes. Parity unpinned: the capsule-box manifold of
+// a segment that enters the box, and box-box clipping on nearly degenerate
+// polygons (the 8-vertex cap).
 //
 // Compile with -ffp-contract=off: the collision stages (AABB, broadphase,
 // narrowphase) must be bit-reproducible in FP32 from identical inputs.
