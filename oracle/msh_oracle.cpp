@@ -25,10 +25,9 @@
 //   * greedy graph colouring (joints first, then manifolds) for PGS; Jacobi
 //     with Tonge et al. 2012 mass splitting as the variant.
 // Pinned by brute force (tests/test_oracle_manifolds.py): capsule-capsule,
-// capsule-box (segment outside the box), box-box face and edge manifolds,
-// sphere centres inside boxes. Parity unpinned: the capsule-box manifold of
-// a segment that enters the box, and box-box clipping on nearly degenerate
-// polygons (the 8-vertex cap).
+// capsule-box (outside and entering), box-box face and edge manifolds,
+// sphere centres inside boxes. Parity unpinned: box-box clipping on nearly
+// degenerate polygons (the 8-vertex cap).
 //
 // Compile with -ffp-contract=off: the collision stages (AABB, broadphase,
 // narrowphase) must be bit-reproducible in FP32 from identical inputs.

@@ -439,3 +439,69 @@ def test_sphere_centre_inside_a_box_is_pushed_out_of_the_nearest_face(seed):
     assert abs(g[9] - (-dist - rad)) < TOL_FRAME
     np.testing.assert_allclose(g[:3], -nk, atol=TOL_FRAME)     # from the sphere into the box
     np.testing.assert_allclose(g[6:9], xs + nk * dist, atol=TOL_FRAME)   # the face point (world)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_capsule_entering_a_box_contacts_at_its_ends_and_entry(seed):
+    """A capsule whose segment enters a box: the manifold holds the sphere-box
+    contacts of both end caps and of the sphere at the first point where the
+    segment meets the box (the first minimiser of the segment's outside
+    distance; dropped within 1 mm of an end), each with its signed distance
+    (negative inside, from the nearest face) minus the radius."""
+    rng = np.random.default_rng(500 + seed)
+    h = rng.uniform(0.05, 0.15, 3)
+    qb = axis_angle(rng.normal(size=3), rng.uniform(0, np.pi))
+    Rb = _rot(qb)
+    cb = np.array([0.0, 0.0, 1.0])
+    r, L = rng.uniform(0.02, 0.04), rng.uniform(0.06, 0.12)
+    # the segment crosses a face near its middle, one end inside, one outside
+    k = int(rng.integers(3))
+    sg = rng.choice([-1.0, 1.0])
+    loc = rng.uniform(-0.5, 0.5, 3) * h
+    loc[k] = sg * h[k]
+    dl = rng.normal(size=3) * 0.4
+    dl[k] = sg if seed % 2 else -sg      # odd seeds start inside, even ones enter from outside
+    ac = Rb @ (dl / np.linalg.norm(dl))
+    cc = cb + Rb @ loc + ac * rng.uniform(-0.3, 0.3) * L
+    e = env()
+    e.body(S.CAPSULE, (r, L), 0.5, tuple(cc), _quat_from_x(ac))
+    e.static(tuple(cb), tuple(h), qb)
+    sc = scene_from_envs([e])
+    d = _detect(sc)
+    xc, Rc = _pose(sc, 0)
+    rad, Lc = float(sc.body_dims[0, 0]), float(sc.body_dims[0, 1])
+    pst = sc.static_pose[0].astype(np.float64)
+    xb, Rbs, hb = pst[:3], _rot(pst[3:]), sc.static_half[0].astype(np.float64)
+    a = Rc[:, 0]
+
+    def outside(t):
+        l = Rbs.T @ (xc + a * t - xb)
+        return float(np.linalg.norm(l - np.clip(l, -hb, hb)))
+    ts = np.linspace(-Lc, Lc, 40001)
+    ov = np.array([outside(t) for t in ts])
+    assert (ov == 0).any() and (ov[0] > 0 or ov[-1] > 0)
+    i = int(np.argmax(ov == 0))
+    if i == 0:
+        t_entry = -Lc
+    else:
+        lo, hi = ts[i - 1], ts[i]
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if outside(mid) > 0:
+                lo = mid
+            else:
+                hi = mid
+        t_entry = hi
+    want = [-Lc, Lc] + ([t_entry] if (t_entry + Lc) > 1e-3 + 1e-6 and (Lc - t_entry) > 1e-3 + 1e-6 else [])
+    want = [t for t in want if _point_box(xc + a * t, xb, Rbs, hb)[0] - rad < OFF]
+    cnt = d.contact_count[0]
+    assert cnt == len(want)
+    got = []
+    for j in range(cnt):
+        g = d.contact_geom[0, j]
+        centre = xc + Rc @ g[3:6] - g[:3] * rad
+        t = float(a @ (centre - xc))
+        got.append(t)
+        assert abs(g[9] - (_point_box(centre, xb, Rbs, hb)[0] - rad)) < TOL_FRAME
+    for t in want:
+        assert min(abs(t - u) for u in got) < 1e-6
