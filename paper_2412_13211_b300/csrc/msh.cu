@@ -164,6 +164,15 @@ static FusedKernel fused_kernel(int tpe) { return tpe <= 256 ? k_fused<256> : k_
 // device-memory workspaces, so the phases are separate kernels: each gets the
 // registers and instruction footprint of its own code instead of the largest
 // phase's. A CTA of 32 threads holds 32/G env groups of G threads.
+// Asynchronous 4-byte copy from device to shared memory (cp.async), its
+// group commit and the wait for every committed group of the thread.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 struct BwdEnv {
   EnvInfo e;
   Ws w;
@@ -238,11 +247,12 @@ __global__ void k_bwd_rows(Params p, AdjParams q, int s) {
 }
 
 // Substep s: the N sweeps in reverse. Each env group has `slice` bytes of
-// shared memory: the body velocities and velocity adjoints (read and written
-// by every constraint update) are staged there when they fit, and the rows
-// (parameters and adjoint accumulators, re-read and re-written once per row
-// per sweep) too when everything fits; the rest stays in the device-memory
-// workspace.
+// shared memory: the recorded lambdas of the sweep being reversed and of the
+// one before it (streamed in from the tape one sweep ahead), the body
+// velocities and velocity adjoints (read and written by every constraint
+// update), and the rows (parameters and adjoint accumulators, re-read and
+// re-written once per row per sweep) when everything fits; the rest stays in
+// the device-memory workspace.
 __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   extern __shared__ float4 bsm[];
   BwdEnv b;
@@ -251,14 +261,18 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   const float* lam0 = b.tape + b.tl.t2 + (long long)s * p.N * p.tape_Rm;
   const int RJ = ROWS_PER_JOINT * e.J;                 // joint row slots in use
   const int nc = b.w.misc[MC_CONTACTS], nm = b.w.misc[MC_MANIFOLDS];
+  const int RU = ROWS_PER_JOINT * p.L.Jm + 3 * nc;     // lambda slots in use (joints of the largest env first)
+  const int RU4 = (RU + 3) / 4;                        // float4s per lambda buffer
+  const int need_l = 3 * RU4 * 16;
   const int need_b = 4 * e.D * 16;
   const int need_r = (2 * RJ * ROW_F4 + 10 * nc + 4 * nm) * 16;
   Ws w = b.w;
   AWs a = b.a;
-  const bool bodies = need_b <= slice, rows = need_b + need_r <= slice;
+  const bool lams = need_l <= slice, bodies = need_l + need_b <= slice, rows = need_l + need_b + need_r <= slice;
+  float4* base = bsm + (size_t)(threadIdx.x / e.nthr) * (slice / 16);
+  float* lbuf[3] = {(float*)base, (float*)(base + RU4), (float*)(base + 2 * RU4)};
   if (bodies) {
-    float4* base = bsm + (size_t)(threadIdx.x / e.nthr) * (slice / 16);
-    w.bv = base;
+    w.bv = base + 3 * RU4;
     w.bw = w.bv + e.D;
     a.bv = w.bw + e.D;
     a.bw = a.bv + e.D;
@@ -276,10 +290,35 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
       for (int i = e.lane; i < 6 * nc; i += e.nthr) a.cadj[i] = b.a.cadj[i];
       for (int i = e.lane; i < 4 * nm; i += e.nthr) a.madj[i] = b.a.madj[i];
     }
-    gsync(e);
   }
-  for (int it = p.N - 1; it >= 0; --it)
-    reverse_sweep(p, e, w, a, lam0 + (long long)it * p.tape_Rm, it > 0 ? lam0 + (long long)(it - 1) * p.tape_Rm : nullptr);
+  // the lambdas of sweep `it` live in lbuf[it % 3]: the two the reversed
+  // sweep reads are in place, the one the next reversed sweep adds is copied
+  // asynchronously while this one runs
+  if (lams) {
+    for (int k = p.N - 1; k >= 0 && k >= p.N - 2; --k) {
+      const float* src = lam0 + (long long)k * p.tape_Rm;
+      for (int i = e.lane; i < RU; i += e.nthr) cp_async4(lbuf[k % 3] + i, src + i);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+  }
+  for (int it = p.N - 1; it >= 0; --it) {
+    const float* lit = lam0 + (long long)it * p.tape_Rm;
+    const float* lpr = it > 0 ? lam0 + (long long)(it - 1) * p.tape_Rm : nullptr;
+    if (lams) {
+      if (it >= 2) {
+        // lbuf[(it - 2) % 3] held sweep it + 1, whose reversal has finished
+        const float* src = lam0 + (long long)(it - 2) * p.tape_Rm;
+        for (int i = e.lane; i < RU; i += e.nthr) cp_async4(lbuf[(it - 2) % 3] + i, src + i);
+      }
+      cp_async_commit();
+      lit = lbuf[it % 3];
+      lpr = it > 0 ? lbuf[(it - 1) % 3] : nullptr;
+    }
+    gsync(e);
+    reverse_sweep(p, e, w, a, lit, lpr);
+    if (lams) cp_async_wait_all();
+  }
   if (bodies) {
     gsync(e);
     for (int i = e.lane; i < e.D; i += e.nthr) {
@@ -1155,7 +1194,8 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
     h->bwd_sweep_warps = std::max(1, blocks) * h->num_sms;
   }
   const int Gs = (long long)h->E * 16 / 32 >= h->bwd_sweep_warps ? 16 : 32;
-  const int slice = Gs == 32 ? bwd_sweep_slice(h) : 4 * h->Dm * 16;
+  const int lam_bytes = 3 * ((ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C + 3) / 4) * 16;
+  const int slice = Gs == 32 ? bwd_sweep_slice(h) : lam_bytes + 4 * h->Dm * 16;
   const int sweep_grid = (h->E + 32 / Gs - 1) / (32 / Gs);
   Params ps = p;
   ps.G = Gs;
