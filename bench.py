@@ -562,6 +562,10 @@ def main():
                 "steps": n_e2e},
         "gpu_launches": args.steps * sim.launches_per_step,
         "status_nonzero_envs": int((status != 0).sum()),
+        "device_memory": {"library_bytes": int(sim.scratch_bytes),
+                          "torch_peak_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                          "note": "library: the step's workspaces, tape and adjoint workspaces of the 4096-env "
+                                  "handle; torch: state, targets, L2 flush buffer and the other legs' tensors"},
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline:
