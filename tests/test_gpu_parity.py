@@ -275,3 +275,44 @@ def test_handles_with_different_workspaces_coexist():
     small.close()
     big.step(torch.zeros((big_sc.num_envs, big_sc.max_dof)).cuda())
     assert not big.status().any()
+
+
+def test_maximum_capacities_use_the_device_memory_workspace():
+    """At the largest capacities (1024 contacts, 4096 pairs per env) one env's
+    workspace takes 171 KB of shared memory (one env per SM); two envs per
+    warp exceed it and the fused form runs on device-memory slabs. Both stay
+    bitwise equal to the plain form and within the one-step tolerance of the
+    oracle."""
+    import torch
+    sc, cfg = scene(2, max_contacts=1024, max_pairs=4096)
+    tg = sc.target_walk(2)
+    res = []
+    for kw in (dict(exec_form="fused"), dict(exec_form="fused", threads_per_env=16), dict(exec_form="plain")):
+        sim = make_sim(sc, cfg, **kw)
+        assert sim.workspace_bytes > 113 * 1024      # two exceed the 227 KB of one CTA
+        for t in range(2):
+            sim.step(torch.as_tensor(tg[t]).cuda())
+        res.append(sim.state_numpy())
+        assert not sim.status().any()
+        sim.close()
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(bits(a), bits(b))
+    o32, _ = oracle.step(sc, cfg, sc.state(), tg, 2, "f32")
+    assert _err(res[0][0], o32[0]) <= 2 * TOL_X and _err(res[0][2], o32[2]) <= 2 * TOL_V
+
+
+def test_empty_envs_in_a_batch():
+    """Envs without any body (statics only, or nothing at all) between
+    ordinary ones: they step as no-ops and leave their neighbours intact."""
+    from helpers import env, scene_from_envs
+    envs = []
+    e = env(); e.body(S.SPHERE, (0.05,), 1.0, (0.0, 0.0, 0.049)); envs.append(e)
+    envs.append(env())
+    e = env(); e.static((0.0, 0.0, 0.5), (0.2, 0.2, 0.5)); envs.append(e)
+    e = env(); e.body(S.BOX, (0.05, 0.05, 0.05), 1.0, (0.0, 0.0, 0.3)); envs.append(e)
+    sc = scene_from_envs(envs)
+    cfg = S.SolverCfg(substeps=2, iterations=8)
+    gpu, o32, _, status, st32 = _step_both(sc, cfg, 3)
+    assert np.array_equal(status, st32) and not status.any()
+    assert _err(gpu[0], o32[0]) <= TOL_X and _err(gpu[2], o32[2]) <= TOL_V
