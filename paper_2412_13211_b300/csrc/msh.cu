@@ -118,7 +118,7 @@ __device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
       __syncthreads();
       idx = s_next;
     }
-    if (idx >= p.E) break;
+    if (idx >= p.En) break;
     EnvInfo e = env_info(p, p.env_order[idx], lane, G, mask);
     stage_load(p, e, w);
     gsync(e);
@@ -592,6 +592,10 @@ AdjLayout make_adj_layout(const Layout& L, int md) {
 
 }  // namespace
 
+#ifndef MSH_HOST_CHUNKS
+#define MSH_HOST_CHUNKS 4   // env chunks of a pipelined host-buffer step
+#endif
+
 struct msh_handle {
   int E = 0, B = 0, S = 0, J = 0, max_dof = 0;
   msh_solver_cfg cfg;
@@ -603,6 +607,16 @@ struct msh_handle {
   float *d_static_pose = nullptr, *d_static_half = nullptr;
   float4* d_sworld = nullptr;
   std::vector<int> body_off_host;   // CSR body offsets (host copy, for argument checks)
+  std::vector<int> order_host;      // envs by decreasing estimated cost
+  // host-buffer steps in chunks of envs whose copies overlap the other chunks' steps
+  int nchunk = 0;
+  std::vector<int> chunk_env;       // chunk k holds envs [chunk_env[k], chunk_env[k + 1])
+  int* d_chunk_order = nullptr;     // chunk k's envs by decreasing cost, at offset chunk_env[k]
+  int* d_chunk_queue = nullptr;
+  char* d_ws_chunks = nullptr;      // one set of per-slot slabs per chunk (their launches overlap)
+  int64_t chunk_ws_bytes = 0;
+  cudaStream_t cstream[MSH_HOST_CHUNKS] = {};
+  cudaEvent_t cev[MSH_HOST_CHUNKS + 1] = {};
   std::vector<int> static_off_host;
   // depth cameras (msh_set_cameras)
   int cam_n = 0, cam_w = 0, cam_h = 0;
@@ -683,7 +697,7 @@ Params make_params(const msh_handle* h, const msh_state* st, const float* target
   p.body_off = h->d_body_off; p.static_off = h->d_static_off; p.joint_off = h->d_joint_off;
   p.bdims = h->d_bdims; p.binv = h->d_binv;
   p.static_pose = h->d_static_pose; p.static_half = h->d_static_half; p.sworld = h->d_sworld;
-  p.joints = h->d_joints; p.env_order = h->d_env_order;
+  p.joints = h->d_joints; p.env_order = h->d_env_order; p.En = h->E;
   p.G = h->tpe;
   p.rep_on = h->rep_on;
   p.rep_flags = h->d_rep_flags; p.rep_fingers = h->d_rep_fingers; p.rep_target = h->d_rep_target;
@@ -789,6 +803,10 @@ int configure_fused(msh_handle* h) {
   h->fused_grid = std::min((h->E + ng - 1) / ng, blocks * h->num_sms);
   // per-group HBM slabs: the cold part (shared-memory form) or the whole workspace
   if (h->d_ws_fused) { cudaFree(h->d_ws_fused); h->bytes -= h->fused_slab_bytes; h->d_ws_fused = nullptr; }
+  if (h->d_ws_chunks) {   // the host-step chunks' slabs follow the fused configuration
+    cudaFree(h->d_ws_chunks); h->bytes -= (int64_t)h->nchunk * h->chunk_ws_bytes; h->d_ws_chunks = nullptr;
+  }
+  h->nchunk = 0;
   h->fused_slab_bytes = (int64_t)h->fused_grid * ng * h->L.bytes;
   int rc = dalloc(h, &h->d_ws_fused, (size_t)h->fused_slab_bytes);
   if (rc) return rc;
@@ -913,6 +931,7 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
     cost[e] = D * (D + Sb) * 0.05 + 4.0 * D + 6.0 * Jn;
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  h->order_host = order;
   if ((rc = upload(h, &h->d_body_off, d->body_off, E + 1))) return bail(rc);
   if ((rc = upload(h, &h->d_static_off, d->static_off, E + 1))) return bail(rc);
   if ((rc = upload(h, &h->d_joint_off, d->joint_off, E + 1))) return bail(rc);
@@ -963,10 +982,13 @@ void msh_destroy(msh_handle* h) {
   cudaDeviceSynchronize();
   drop_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaStream_t& c : h->cstream) if (c) cudaStreamDestroy(c);
+  for (cudaEvent_t& v : h->cev) if (v) cudaEventDestroy(v);
   void* ptrs[] = {h->d_body_off, h->d_static_off, h->d_joint_off, h->d_env_order, h->d_bdims, h->d_binv,
                   h->d_static_pose, h->d_static_half, h->d_sworld, h->d_joints, h->d_status, h->d_queue, h->d_targets,
                   h->d_pos, h->d_quat, h->d_lv, h->d_av, h->d_ws_plain, h->d_ws_fused, h->d_tape, h->d_aws,
-                  h->d_rep_flags, h->d_rep_fingers, h->d_rep_target, h->d_cam_body, h->d_cam_pose, h->d_ctrl};
+                  h->d_rep_flags, h->d_rep_fingers, h->d_rep_target, h->d_cam_body, h->d_cam_pose, h->d_ctrl,
+                  h->d_chunk_order, h->d_chunk_queue, h->d_ws_chunks};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete h;
@@ -1039,6 +1061,94 @@ int msh_step(msh_handle* h, const msh_state* st, const float* joint_targets, flo
   return step_impl(h, st, joint_targets, dt, substeps, (cudaStream_t)stream);
 }
 
+// Chunks for host-buffer steps of the fused form: MSH_HOST_CHUNKS contiguous env ranges
+// of about equal body counts, each with its envs in cost order, its own queue
+// counter, workspace slabs and stream. Batches too small to fill the GPU
+// (under 256 envs per chunk) are not chunked (nchunk stays 0).
+static int ensure_chunks(msh_handle* h) {
+  if (h->nchunk > 0) return MSH_OK;
+  const int K = MSH_HOST_CHUNKS;
+  if (h->E < 256 * K) return MSH_OK;
+  h->chunk_env.assign(K + 1, h->E);
+  h->chunk_env[0] = 0;
+  const long long B = h->body_off_host[h->E];
+  for (int k = 1, e = 0; k < K; ++k) {
+    while (e < h->E && (long long)h->body_off_host[e] * K < B * k) ++e;
+    h->chunk_env[k] = e;
+  }
+  std::vector<int> corder(h->E);
+  for (int k = 0; k < K; ++k) {
+    int o = h->chunk_env[k];
+    for (int env : h->order_host)
+      if (env >= h->chunk_env[k] && env < h->chunk_env[k + 1]) corder[o++] = env;
+  }
+  int rc;
+  if (!h->d_chunk_order && (rc = dalloc(h, &h->d_chunk_order, (size_t)h->E))) return rc;
+  CK(cudaMemcpy(h->d_chunk_order, corder.data(), sizeof(int) * h->E, cudaMemcpyHostToDevice));
+  if (!h->d_chunk_queue && (rc = dalloc(h, &h->d_chunk_queue, (size_t)K))) return rc;
+  h->chunk_ws_bytes = h->fused_slab_bytes;
+  if ((rc = dalloc(h, &h->d_ws_chunks, (size_t)K * h->chunk_ws_bytes))) return rc;
+  for (int k = 0; k < K; ++k)
+    if (!h->cstream[k] && cudaStreamCreateWithFlags(&h->cstream[k], cudaStreamNonBlocking) != cudaSuccess)
+      return fail(MSH_ERR_CUDA, "stream create");
+  for (int k = 0; k <= K; ++k)
+    if (!h->cev[k] && cudaEventCreateWithFlags(&h->cev[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(MSH_ERR_CUDA, "event create");
+  h->nchunk = K;
+  return MSH_OK;
+}
+
+// The host-buffer step in chunks: each chunk's copies in, fused launch and
+// copies out run on its own stream, so one chunk's copies overlap the others'
+// steps. Every env's computation is the same as in one launch.
+static int step_host_chunked(msh_handle* h, float* pos, float* quat, float* linvel, float* angvel,
+                             const float* targets, float dt, int32_t substeps, cudaStream_t s) {
+  if (!(dt > 0.f)) dt = h->cfg.dt;
+  if (substeps < 1) substeps = h->cfg.substeps;
+  msh_state st{h->d_pos, h->d_quat, h->d_lv, h->d_av};
+  const int T = h->tpe, ng = fused_groups(T), blk = fused_block(T);
+  CK(cudaEventRecord(h->cev[h->nchunk], s));
+  for (int k = 0; k < h->nchunk; ++k) {
+    cudaStream_t c = h->cstream[k];
+    CK(cudaStreamWaitEvent(c, h->cev[h->nchunk], 0));
+    const int e0 = h->chunk_env[k], e1 = h->chunk_env[k + 1];
+    const size_t b0 = h->body_off_host[e0], nb = h->body_off_host[e1] - b0;
+    if (nb) {
+      CK(cudaMemcpyAsync(h->d_pos + 3 * b0, pos + 3 * b0, nb * 12, cudaMemcpyHostToDevice, c));
+      CK(cudaMemcpyAsync(h->d_quat + 4 * b0, quat + 4 * b0, nb * 16, cudaMemcpyHostToDevice, c));
+      CK(cudaMemcpyAsync(h->d_lv + 3 * b0, linvel + 3 * b0, nb * 12, cudaMemcpyHostToDevice, c));
+      CK(cudaMemcpyAsync(h->d_av + 3 * b0, angvel + 3 * b0, nb * 12, cudaMemcpyHostToDevice, c));
+    }
+    if (h->max_dof > 0 && e1 > e0)
+      CK(cudaMemcpyAsync(h->d_targets + (size_t)e0 * h->max_dof, targets + (size_t)e0 * h->max_dof,
+                         (size_t)(e1 - e0) * h->max_dof * 4, cudaMemcpyHostToDevice, c));
+    if (e1 > e0) {
+      Params p = make_params(h, &st, h->d_targets, dt, substeps);
+      p.G = T;
+      p.env_order = h->d_chunk_order + e0;
+      p.En = e1 - e0;
+      p.queue = h->d_chunk_queue + k;
+      p.ws = h->d_ws_chunks + (long long)k * h->chunk_ws_bytes;
+      p.ws_stride = h->L.bytes;
+      CK(cudaMemsetAsync(p.queue, 0, sizeof(int), c));
+      const int grid = std::min((p.En + ng - 1) / ng, h->fused_grid);
+      if (h->fused_smem) h->fused_fn<<<grid, blk, (size_t)ng * h->L.hot_bytes, c>>>(p, 1);
+      else h->fused_fn<<<grid, blk, 0, c>>>(p, 0);
+      CK(cudaGetLastError());
+    }
+    if (nb) {
+      CK(cudaMemcpyAsync(pos + 3 * b0, h->d_pos + 3 * b0, nb * 12, cudaMemcpyDeviceToHost, c));
+      CK(cudaMemcpyAsync(quat + 4 * b0, h->d_quat + 4 * b0, nb * 16, cudaMemcpyDeviceToHost, c));
+      CK(cudaMemcpyAsync(linvel + 3 * b0, h->d_lv + 3 * b0, nb * 12, cudaMemcpyDeviceToHost, c));
+      CK(cudaMemcpyAsync(angvel + 3 * b0, h->d_av + 3 * b0, nb * 12, cudaMemcpyDeviceToHost, c));
+    }
+    CK(cudaEventRecord(h->cev[k], c));
+    CK(cudaStreamWaitEvent(s, h->cev[k], 0));
+  }
+  CK(cudaStreamSynchronize(s));
+  return MSH_OK;
+}
+
 int msh_step_host(msh_handle* h, float* pos, float* quat, float* linvel, float* angvel, const float* targets,
                   float dt, int32_t substeps, void* stream) {
   if (!h || !pos || !quat || !linvel || !angvel) return fail(MSH_ERR_INVALID_ARG, "NULL argument");
@@ -1049,6 +1159,10 @@ int msh_step_host(msh_handle* h, float* pos, float* quat, float* linvel, float* 
     if ((rc = dalloc(h, &h->d_pos, (size_t)3 * h->B)) || (rc = dalloc(h, &h->d_quat, (size_t)4 * h->B)) ||
         (rc = dalloc(h, &h->d_lv, (size_t)3 * h->B)) || (rc = dalloc(h, &h->d_av, (size_t)3 * h->B)))
       return rc;
+  }
+  if (h->exec == MSH_EXEC_FUSED && !(h->tape_max > 0 && !h->tape_paused)) {
+    if ((rc = ensure_chunks(h))) return rc;
+    if (h->nchunk > 0) return step_host_chunked(h, pos, quat, linvel, angvel, targets, dt, substeps, s);
   }
   const size_t b3 = (size_t)3 * h->B * 4, b4 = (size_t)4 * h->B * 4;
   CK(cudaMemcpyAsync(h->d_pos, pos, b3, cudaMemcpyHostToDevice, s));

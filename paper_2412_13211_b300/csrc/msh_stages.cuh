@@ -64,6 +64,7 @@ struct Params {
   const float4* sworld;  // per static box: StaticWorld
   const JointDesc* joints;
   const int* env_order;
+  int En;                // fused form: envs in this launch's work queue (env_order[0..En))
   // solver
   float dt, h;
   int S, N, mode;

@@ -316,3 +316,28 @@ def test_empty_envs_in_a_batch():
     gpu, o32, _, status, st32 = _step_both(sc, cfg, 3)
     assert np.array_equal(status, st32) and not status.any()
     assert _err(gpu[0], o32[0]) <= TOL_X and _err(gpu[2], o32[2]) <= TOL_V
+
+
+def test_chunked_host_step_equals_device_step():
+    """Large batches step from host buffers in env chunks whose copies overlap
+    the other chunks' launches: bitwise the device step, report included."""
+    import torch
+    sc, cfg = S.make_config(3, num_envs=1536)
+    tg = sc.target_walk(2)
+    sim = make_sim(sc, cfg)
+    sim.set_report(*sc.report_spec())
+    for t in range(2):
+        sim.step(torch.as_tensor(tg[t]).cuda())
+    dev = sim.state_numpy()
+    rep_dev = sim.report()
+    host = [np.ascontiguousarray(a, np.float32).copy() for a in sc.state()]
+    sim2 = make_sim(sc, cfg)
+    sim2.set_report(*sc.report_spec())
+    for t in range(2):
+        sim2.step_host(*host, np.ascontiguousarray(tg[t]))
+    for a, b in zip(dev, host):
+        assert np.array_equal(bits(a), bits(b))
+    rep_host = sim2.report()
+    for k in rep_dev:
+        assert np.array_equal(np.asarray(rep_dev[k]).view(np.int32), np.asarray(rep_host[k]).view(np.int32)), k
+    assert not sim2.status().any()
