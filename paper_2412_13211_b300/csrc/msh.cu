@@ -535,7 +535,7 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi) {
   int o = 0;
   auto take = [&](int bytes) { int r = o; o = align16(o + bytes); return r; };
   const int f4 = 16;
-  L.bx = take(Dm * f4); L.bq = take(Dm * f4); L.bv = take(Dm * f4); L.bw = take(Dm * f4);
+  L.bv = take(Dm * f4); L.bw = take(Dm * f4);
   L.bIw0 = take(Dm * f4); L.bIw1 = take(Dm * f4);
   L.cn = take(C * f4);
   L.man = take(P * 16);
@@ -550,7 +550,6 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi) {
   L.misc = take(MC_N * 4);
   // shared region: collision-only arrays | per-substep contact rows
   const int region = o;
-  L.sw = take(SW_N * Sm * f4);
   L.alo = take(Dm * f4); L.ahi = take(Dm * f4);
   L.pairs = take(P * 4);
   L.masks = take(Dm * 8);
@@ -562,6 +561,7 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi) {
   // cold part: offsets relative to the cold base
   o = 0;
   L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4); L.crep = take(C * f4);
+  L.bx = take(Dm * f4); L.bq = take(Dm * f4);   // poses: read per substep, not per sweep
   L.cold_bytes = align16(o);
   L.bytes = L.hot_bytes + L.cold_bytes;
   return L;

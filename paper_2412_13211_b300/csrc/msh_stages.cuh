@@ -41,13 +41,13 @@ __host__ __device__ __forceinline__ int joint_row_count(const JointDesc& j) {
 struct Layout {
   int Dm, Sm, Jm, P, C, K, R;   // R: joint solver rows of the largest env
   int bx, bq, bv, bw, bIw0, bIw1;
-  int sw, alo, ahi;
+  int alo, ahi;
   int pairs, cn, cra, crb, cid, crep;
   int kra, krb, klam;
   int man, jr, jinfo, ccol, corder, coff, masks;
   int jdv, inc_off, inc, misc;
   int hot_bytes;    // shared memory in the fused form
-  int cold_bytes;   // contact anchors and ids (read once per substep), always in HBM
+  int cold_bytes;   // contact anchors and ids, body poses (read once per substep), always in HBM
   int bytes;        // hot + cold: one HBM slab in the plain form
 };
 
@@ -143,7 +143,6 @@ enum { SW_C = 0, SW_M = 1, SW_LO = 4, SW_HI = 5, SW_N = 6 };
 
 struct Ws {
   float4 *bx, *bq, *bv, *bw, *bIw0, *bIw1;
-  float4 *sw;         // static boxes' StaticWorld records (collision stages only)
   float4 *alo, *ahi;  // body AABBs
   int* pairs;
   float4 *cn, *cra, *crb;
@@ -162,9 +161,10 @@ struct Ws {
 // hot: the first L.hot_bytes of a slab or shared memory; cold: HBM.
 __device__ __forceinline__ Ws make_ws(char* b, char* cold, const Layout& L) {
   Ws w;
-  w.bx = (float4*)(b + L.bx); w.bq = (float4*)(b + L.bq); w.bv = (float4*)(b + L.bv); w.bw = (float4*)(b + L.bw);
+  w.bx = (float4*)(cold + L.bx); w.bq = (float4*)(cold + L.bq);
+  w.bv = (float4*)(b + L.bv); w.bw = (float4*)(b + L.bw);
   w.bIw0 = (float4*)(b + L.bIw0); w.bIw1 = (float4*)(b + L.bIw1);
-  w.sw = (float4*)(b + L.sw); w.alo = (float4*)(b + L.alo); w.ahi = (float4*)(b + L.ahi);
+  w.alo = (float4*)(b + L.alo); w.ahi = (float4*)(b + L.ahi);
   w.pairs = (int*)(b + L.pairs);
   w.cn = (float4*)(b + L.cn);
   w.cra = (float4*)(cold + L.cra); w.crb = (float4*)(cold + L.crb); w.cid = (int*)(cold + L.cid);
@@ -254,11 +254,6 @@ __device__ __forceinline__ int group_exscan(const EnvInfo& e, int v, int* scr, i
 // ---------------------------------------------------------------------------
 // a0: stage the env's bodies and statics
 // ---------------------------------------------------------------------------
-// The env's static boxes (StaticWorld records) into the collision region.
-__device__ __forceinline__ void load_statics(const Params& p, const EnvInfo& e, const Ws& w) {
-  const float4* src = p.sworld + (size_t)SW_N * e.s0;
-  for (int k = e.lane; k < SW_N * e.S; k += e.nthr) w.sw[k] = __ldg(src + k);
-}
 
 // Per-joint solver bookkeeping into the workspace (read by every sweep).
 __device__ __forceinline__ void load_jinfo(const Params& p, const EnvInfo& e, const Ws& w) {
@@ -291,7 +286,6 @@ __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
       tape_env(p, e.env)[tl.t3 + k] = p.targets ? p.targets[(size_t)e.env * p.max_dof + k] : 0.f;
   }
   load_jinfo(p, e, w);
-  load_statics(p, e, w);
   if (e.lane < MC_N) w.misc[e.lane] = 0;
 }
 
@@ -326,11 +320,13 @@ __device__ __forceinline__ void static_world(const float* sp, const float* sh, f
 }
 
 // AABB corners of collision index i < D + S (body or static box).
+// (A static box's record is read from the scene's table, through the
+// read-only cache.)
 __device__ __forceinline__ float4 aabb_lo(const Params& p, const Ws& w, const EnvInfo& e, int i) {
-  return i < e.D ? w.alo[i] : w.sw[SW_N * (i - e.D) + SW_LO];
+  return i < e.D ? w.alo[i] : __ldg(p.sworld + (size_t)SW_N * (e.s0 + i - e.D) + SW_LO);
 }
 __device__ __forceinline__ float4 aabb_hi(const Params& p, const Ws& w, const EnvInfo& e, int i) {
-  return i < e.D ? w.ahi[i] : w.sw[SW_N * (i - e.D) + SW_HI];
+  return i < e.D ? w.ahi[i] : __ldg(p.sworld + (size_t)SW_N * (e.s0 + i - e.D) + SW_HI);
 }
 
 // Collision shape of index i: dynamic body, static box or the plane.
@@ -344,7 +340,7 @@ __device__ __forceinline__ Shape<nf> coll_shape(const Params& p, const Ws& w, co
     s.M = qmat(q);
     s.d0 = nf(d.x); s.d1 = nf(d.y); s.d2 = nf(d.z);
   } else if (i < e.D + e.S) {
-    s = static_shape<nf>(w.sw + SW_N * (i - e.D));
+    s = static_shape<nf>(p.sworld + (size_t)SW_N * (e.s0 + i - e.D));
   } else {
     s.type = SH_PLANE;
     s.c = v3<nf>(nf(0.f), nf(0.f), nf(0.f));
@@ -605,7 +601,7 @@ __device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws&
       for (int b = 0; b < 3; ++b)
         W[a][b] = R.m[a][0] * d[0] * R.m[b][0] + R.m[a][1] * d[1] * R.m[b][1] + R.m[a][2] * d[2] * R.m[b][2];
     w.bIw0[i] = make_float4(W[0][0], W[0][1], W[0][2], W[1][1]);
-    w.bIw1[i] = make_float4(W[1][2], W[2][2], split, 0.f);
+    w.bIw1[i] = make_float4(W[1][2], W[2][2], split, w.bx[i].w);   // .w: 1/m for the sweeps
   }
 }
 
@@ -908,7 +904,7 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
                                             BodyVel* dacc) {
   const int4 ji = w.jinfo[k];   // parent, child, first row, row count
   const int A = ji.x;
-  const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = w.bx[ji.y].w;
+  const float ima = A >= 0 ? w.bIw1[A].w : 0.f, imb = w.bIw1[ji.y].w;
   const float sa = A >= 0 ? w.bIw1[A].z : 1.f, sb = w.bIw1[ji.y].z;
   const float ka = sa * ima, kb = sb * imb;
   const int nr = ji.w;
@@ -949,7 +945,7 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
                                                BodyVel* dacc) {
   int4 mf = w.man[m];
   const int a = mf.x, b = mf.y;
-  const float ima = w.bx[a].w, imb = b >= 0 ? w.bx[b].w : 0.f;
+  const float ima = w.bIw1[a].w, imb = b >= 0 ? w.bIw1[b].w : 0.f;
   const float sa = w.bIw1[a].z, sb = b >= 0 ? w.bIw1[b].z : 1.f;
   const float ka = sa * ima, kb = sb * imb;
   Sym3 Ia = load_Iw(w, a), Ib;
