@@ -170,7 +170,7 @@ def cpu_baseline(scene, cfg, budget_s=12.0):
                       f"{dt:.1f} s of CPU time"}
 
 
-def time_fwd_bwd(sim, scene, tg, horizon, k, stream, reps=2):
+def time_fwd_bwd(sim, scene, tg, horizon, k, stream, reps=2, threads_per_env=32):
     """env-steps/s of forward + backward through a differentiable rollout of
     `horizon` steps (step checkpointing every k): CUDA events around the whole
     forward and backward pass, after one untimed warm-up pass."""
@@ -197,7 +197,7 @@ def time_fwd_bwd(sim, scene, tg, horizon, k, stream, reps=2):
         return st[2].grad
 
     with torch.cuda.stream(stream):
-        sim.set_exec("fused", 32, False)
+        sim.set_exec("fused", threads_per_env, False)
         once()
         stream.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -503,7 +503,8 @@ def main():
     # the same batch, loss = squared goal distance of one object per env
     fwd_bwd = None
     if not args.no_backward:
-        fwd_bwd = time_fwd_bwd(sim, scene, tg, horizon=args.bwd_horizon, k=8, stream=stream)
+        fwd_bwd = time_fwd_bwd(sim, scene, tg, horizon=args.bwd_horizon, k=8, stream=stream,
+                               threads_per_env=tpe if form == "fused" else 32)
         sim.set_exec(form, tpe, True)
         # the differentiation workload: 512 envs, arm pushing a goal box, 64-step horizon
         sc4, cfg4 = scenes.make_config(4, num_envs=512, env_start=rank * 512)
