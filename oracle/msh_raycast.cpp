@@ -16,7 +16,10 @@
 //     capsules (cylinder plus end spheres), boxes (slabs) and the ground
 //     plane, 0 when nothing is hit;
 //   * every intersection is the textbook closed form, evaluated without FMA
-//     contraction in a fixed order, so FP32 results are reproducible.
+//     contraction in a fixed order, so FP32 results are reproducible; the
+//     distances are products with reciprocals rounded once (1/(D.D) per ray
+//     for the sphere roots, 1/A per cylinder, 1/D_i per box axis) rather than
+//     quotients.
 // Brute force: every pixel tests every primitive.
 
 #include <cmath>
@@ -77,15 +80,17 @@ template <class R> void qmul(const R* a, const R* b, R* o) {
   o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
 }
 
-// Smallest root s >= near of |w + s D|^2 = r^2 (w = origin - centre); inf if none.
-template <class R> R hit_sphere(V<R> w, V<R> D, R r, R near_) {
-  const R a = dot(D, D), b = dot(D, w), c = dot(w, w) - r * r;
+// Smallest root s >= near of |w + s D|^2 = r^2 (w = origin - centre); inf if
+// none. a = D.D and ia = 1 / a belong to the ray (formed once per pixel); the
+// roots are (-b -+ sqrt(disc)) * ia.
+template <class R> R hit_sphere(V<R> w, V<R> D, R a, R ia, R r, R near_) {
+  const R b = dot(D, w), c = dot(w, w) - r * r;
   const R disc = b * b - a * c;
   if (disc < R(0)) return std::numeric_limits<R>::infinity();
   const R sq = std::sqrt(disc);
-  R s = (-b - sq) / a;
+  R s = (-b - sq) * ia;
   if (s >= near_) return s;
-  s = (-b + sq) / a;
+  s = (-b + sq) * ia;
   return s >= near_ ? s : std::numeric_limits<R>::infinity();
 }
 
@@ -99,7 +104,8 @@ template <class R> R hit_box(V<R> o, V<R> D, const R* h, R near_) {
       if (oo[i] < -h[i] || oo[i] > h[i]) return inf;
       continue;
     }
-    R t1 = (-h[i] - oo[i]) / dd[i], t2 = (h[i] - oo[i]) / dd[i];
+    const R inv = R(1) / dd[i];   // one reciprocal per axis, then products
+    R t1 = (-h[i] - oo[i]) * inv, t2 = (h[i] - oo[i]) * inv;
     R lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
     if (lo > tmin) tmin = lo;
     if (hi < tmax) tmax = hi;
@@ -110,7 +116,7 @@ template <class R> R hit_box(V<R> o, V<R> D, const R* h, R near_) {
 
 // Capsule along unit axis a through centre c, half length L, radius r:
 // the cylinder's side between the caps, then the two end spheres.
-template <class R> R hit_capsule(V<R> w, V<R> D, V<R> a, R L, R r, R near_) {
+template <class R> R hit_capsule(V<R> w, V<R> D, R dd, R idd, V<R> a, R L, R r, R near_) {
   const R inf = std::numeric_limits<R>::infinity();
   R best = inf;
   const R Da = dot(D, a), wa = dot(w, a);
@@ -120,7 +126,8 @@ template <class R> R hit_capsule(V<R> w, V<R> D, V<R> a, R L, R r, R near_) {
     const R disc = B * B - A * C;
     if (disc >= R(0)) {
       const R sq = std::sqrt(disc);
-      const R s1 = (-B - sq) / A, s2 = (-B + sq) / A;
+      const R iA = R(1) / A;
+      const R s1 = (-B - sq) * iA, s2 = (-B + sq) * iA;
       const R ss[2] = {s1, s2};
       for (int k = 0; k < 2; ++k) {
         const R s = ss[k];
@@ -130,8 +137,8 @@ template <class R> R hit_capsule(V<R> w, V<R> D, V<R> a, R L, R r, R near_) {
       }
     }
   }
-  const R s0 = hit_sphere(sub(w, scl(a, L)), D, r, near_);
-  const R s1 = hit_sphere(add(w, scl(a, L)), D, r, near_);
+  const R s0 = hit_sphere(sub(w, scl(a, L)), D, dd, idd, r, near_);
+  const R s1 = hit_sphere(add(w, scl(a, L)), D, dd, idd, r, near_);
   if (s0 < best) best = s0;
   if (s1 < best) best = s1;
   return best;
@@ -169,6 +176,7 @@ void render_env(const OracleRayScene& sc, int e, const T* pos, const T* quat, co
         const R u = R(col) + R(0.5), v = R(row) + R(0.5);
         const V<R> dc = mk<R>(R(1), -((u - cx) / f), -((v - cy) / f));
         const V<R> Dw = mul(Mc, dc);
+        const R dd = dot(Dw, Dw), idd = R(1) / dd;
         R best = std::numeric_limits<R>::infinity();
         for (int i = 0; i < D; ++i) {
           const int g = b0 + i;
@@ -177,12 +185,12 @@ void render_env(const OracleRayScene& sc, int e, const T* pos, const T* quat, co
           const V<R> w = sub(o, cen);
           R s;
           if (sh == 0) {
-            s = hit_sphere(w, Dw, R(sc.body_dims[4 * g]), near_);
+            s = hit_sphere(w, Dw, dd, idd, R(sc.body_dims[4 * g]), near_);
           } else {
             R M[3][3];
             qmat(R(quat[4 * g]), R(quat[4 * g + 1]), R(quat[4 * g + 2]), R(quat[4 * g + 3]), M);
             if (sh == 1) {
-              s = hit_capsule(w, Dw, mk<R>(M[0][0], M[1][0], M[2][0]), R(sc.body_dims[4 * g + 1]),
+              s = hit_capsule(w, Dw, dd, idd, mk<R>(M[0][0], M[1][0], M[2][0]), R(sc.body_dims[4 * g + 1]),
                               R(sc.body_dims[4 * g]), near_);
             } else {
               const R h[3] = {R(sc.body_dims[4 * g]), R(sc.body_dims[4 * g + 1]), R(sc.body_dims[4 * g + 2])};

@@ -54,14 +54,16 @@ __device__ __forceinline__ float3 mul3(const float M[3][3], float3 v) {
 }
 
 // Smallest root s >= near of |w + s D|^2 = r^2 (w = origin - centre).
-__device__ __forceinline__ float hit_sphere(float3 w, float3 D, float r, float near_) {
-  const float a = dot3(D, D), b = dot3(D, w), c = dot3(w, w) - r * r;
+// a = D.D and ia = 1/a belong to the ray (once per pixel): the roots are
+// products with the reciprocal, as the oracle forms them.
+__device__ __forceinline__ float hit_sphere(float3 w, float3 D, float a, float ia, float r, float near_) {
+  const float b = dot3(D, w), c = dot3(w, w) - r * r;
   const float disc = b * b - a * c;
   if (disc < 0.f) return INFINITY;
   const float sq = sqrtf(disc);
-  float s = (-b - sq) / a;
+  float s = (-b - sq) * ia;
   if (s >= near_) return s;
-  s = (-b + sq) / a;
+  s = (-b + sq) * ia;
   return s >= near_ ? s : INFINITY;
 }
 
@@ -75,7 +77,8 @@ __device__ __forceinline__ float hit_box(float3 o, float3 D, float3 h, float nea
       if (oo[i] < -hh[i] || oo[i] > hh[i]) return INFINITY;
       continue;
     }
-    const float t1 = (-hh[i] - oo[i]) / dd[i], t2 = (hh[i] - oo[i]) / dd[i];
+    const float inv = 1.f / dd[i];
+    const float t1 = (-hh[i] - oo[i]) * inv, t2 = (hh[i] - oo[i]) * inv;
     const float lo = t1 < t2 ? t1 : t2, hi = t1 < t2 ? t2 : t1;
     if (lo > tmin) tmin = lo;
     if (hi < tmax) tmax = hi;
@@ -84,7 +87,8 @@ __device__ __forceinline__ float hit_box(float3 o, float3 D, float3 h, float nea
   return tmin >= near_ ? tmin : tmax;
 }
 
-__device__ __forceinline__ float hit_capsule(float3 w, float3 D, float3 a, float L, float r, float near_) {
+__device__ __forceinline__ float hit_capsule(float3 w, float3 D, float dd, float idd, float3 a, float L, float r,
+                                             float near_) {
   float best = INFINITY;
   const float Da = dot3(D, a), wa = dot3(w, a);
   const float3 Dp = sub3(D, scl3(a, Da)), wp = sub3(w, scl3(a, wa));
@@ -93,13 +97,14 @@ __device__ __forceinline__ float hit_capsule(float3 w, float3 D, float3 a, float
     const float disc = B * B - A * C;
     if (disc >= 0.f) {
       const float sq = sqrtf(disc);
-      const float s1 = (-B - sq) / A, s2 = (-B + sq) / A;
+      const float iA = 1.f / A;
+      const float s1 = (-B - sq) * iA, s2 = (-B + sq) * iA;
       if (s1 >= near_ && wa + s1 * Da >= -L && wa + s1 * Da <= L) best = s1;
       else if (s2 >= near_ && wa + s2 * Da >= -L && wa + s2 * Da <= L) best = s2;
     }
   }
-  const float e0 = hit_sphere(sub3(w, scl3(a, L)), D, r, near_);
-  const float e1 = hit_sphere(add3(w, scl3(a, L)), D, r, near_);
+  const float e0 = hit_sphere(sub3(w, scl3(a, L)), D, dd, idd, r, near_);
+  const float e1 = hit_sphere(add3(w, scl3(a, L)), D, dd, idd, r, near_);
   if (e0 < best) best = e0;
   if (e1 < best) best = e1;
   return best;
@@ -260,6 +265,7 @@ __global__ void __launch_bounds__(RT_THREADS) k_render(RenderScene p, RenderCams
     if (col >= cm.width || row >= cm.height) break;
     const float u = (float)col + 0.5f, v = (float)row + 0.5f;
     const float3 Dw = mul3(Mc, mk3(1.f, -((u - cx) / f), -((v - cy) / f)));
+    const float dd = dot3(Dw, Dw), idd = 1.f / dd;
     float best = INFINITY;
     if (Dw.z < 0.f) {   // ground plane z = 0
       const float s = -o.z / Dw.z;
@@ -273,9 +279,9 @@ __global__ void __launch_bounds__(RT_THREADS) k_render(RenderScene p, RenderCams
       const float3 w = sub3(o, mk3(pr[1], pr[2], pr[3]));
       float s;
       if (ty == PR_SPHERE) {
-        s = hit_sphere(w, Dw, pr[4], cm.near_);
+        s = hit_sphere(w, Dw, dd, idd, pr[4], cm.near_);
       } else if (ty == PR_CAPSULE) {
-        s = hit_capsule(w, Dw, mk3(pr[4], pr[5], pr[6]), pr[7], pr[8], cm.near_);
+        s = hit_capsule(w, Dw, dd, idd, mk3(pr[4], pr[5], pr[6]), pr[7], pr[8], cm.near_);
       } else {
         // box frame: R^T w and R^T D, with R's rows in pr[4..12]
         const float3 ob = mk3(pr[4] * w.x + pr[7] * w.y + pr[10] * w.z, pr[5] * w.x + pr[8] * w.y + pr[11] * w.z,
