@@ -26,9 +26,15 @@ using namespace msh;
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+// One-env slab of the device-memory forms (plain, substep, adjoint): the
+// contact arrays are the full-capacity ones of the cold part.
 __device__ __forceinline__ Ws plain_ws(const Params& p, int env) {
   char* b = p.ws + (long long)env * p.ws_stride;
-  return make_ws(b, b + p.L.hot_bytes, p.L);
+  char* cold = b + p.L.hot_bytes;
+  Ws w = make_ws(b, cold, p.L);
+  w.cn = (float4*)(cold + p.L.cnc); w.kra = (float4*)(cold + p.L.krac);
+  w.krb = (float4*)(cold + p.L.krbc); w.klam = (float4*)(cold + p.L.klamc);
+  return w;
 }
 
 __global__ void k_load(Params p) {
@@ -125,7 +131,24 @@ __device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
     stage_aabb(p, e, w);
     gsync(e);
     stage_broadphase(p, e, w, scr);
+    // contacts first land in the full-capacity cold arrays; an env with at
+    // most L.Ch of them moves them into the hot part and solves there, a
+    // larger one solves from the cold arrays (same arithmetic, other memory)
+    char* cold = slab + p.L.hot_bytes;
+    w.cn = (float4*)(cold + p.L.cnc);
     stage_narrowphase(p, e, w, scr);
+    {
+      const int nc = w.misc[MC_CONTACTS];
+      if (nc <= p.L.Ch) {
+        float4* hcn = (float4*)(base + p.L.cn);
+        for (int i = e.lane; i < nc; i += e.nthr) hcn[i] = w.cn[i];
+        w.cn = hcn;
+        w.kra = (float4*)(base + p.L.kra); w.krb = (float4*)(base + p.L.krb); w.klam = (float4*)(base + p.L.klam);
+      } else {
+        w.kra = (float4*)(cold + p.L.krac); w.krb = (float4*)(cold + p.L.krbc); w.klam = (float4*)(cold + p.L.klamc);
+      }
+      gsync(e);
+    }
     stage_colour(p, e, w);
     if (p.tape) tape_collision(p, e, w);
     for (int s = 0; s < p.S; ++s) {
@@ -528,16 +551,17 @@ namespace {
 
 int align16(int x) { return (x + 15) & ~15; }
 
-Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi) {
+Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi, int Ch) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
   L.Dm = Dm; L.Sm = Sm; L.Jm = Jm; L.P = P; L.C = C; L.K = Jm + P; L.R = std::max(Rm, 1);
+  L.Ch = std::min(std::max(Ch, 1), C);
   int o = 0;
   auto take = [&](int bytes) { int r = o; o = align16(o + bytes); return r; };
   const int f4 = 16;
   L.bv = take(Dm * f4); L.bw = take(Dm * f4);
   L.bIw0 = take(Dm * f4); L.bIw1 = take(Dm * f4);
-  L.cn = take(C * f4);
+  L.cn = take(L.Ch * f4);
   L.man = take(P * 16);
   L.jr = take(L.R * ROW_F4 * f4);
   L.jinfo = take(Jm * 16);
@@ -555,13 +579,14 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi) {
   L.masks = take(Dm * 8);
   const int end_x = o;
   o = region;
-  L.kra = take(C * f4); L.krb = take(C * f4); L.klam = take(C * f4);
+  L.kra = take(L.Ch * f4); L.krb = take(L.Ch * f4); L.klam = take(L.Ch * f4);
   o = std::max(o, end_x);
   L.hot_bytes = align16(o);
   // cold part: offsets relative to the cold base
   o = 0;
   L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4); L.crep = take(C * f4);
   L.bx = take(Dm * f4); L.bq = take(Dm * f4);   // poses: read per substep, not per sweep
+  L.cnc = take(C * f4); L.krac = take(C * f4); L.krbc = take(C * f4); L.klamc = take(C * f4);
   L.cold_bytes = align16(o);
   L.bytes = L.hot_bytes + L.cold_bytes;
   return L;
@@ -915,12 +940,27 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
   h->body_off_host.assign(d->body_off, d->body_off + E + 1);
   h->static_off_host.assign(d->static_off, d->static_off + E + 1); h->max_dof = d->max_dof; h->cfg = *cfg;
   h->Dm = std::max(Dm, 1); h->Sm = std::max(Sm, 1); h->Jm = std::max(Jm, 1);
-  h->L = make_layout(h->Dm, h->Sm, h->Jm, Rm, cfg->max_pairs, cfg->max_contacts, cfg->mode == MSH_MODE_JACOBI);
   auto bail = [&](int code) { msh_destroy(h); return code; };
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return bail(fail(MSH_ERR_CUDA, "no CUDA device"));
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  {
+    // Hot contact capacity: all of it when the shared workspace already fits
+    // six two-env CTAs per SM; else the largest multiple of 8, down to half
+    // the capacity, that does (envs with more contacts solve from the cold
+    // arrays); all of it when even half does not fit.
+    const bool jac = cfg->mode == MSH_MODE_JACOBI;
+    const int C = cfg->max_contacts;
+    const int budget = ((h->smem_optin + 1024) / 6 - 1024) / 2;
+    int Ch = C;
+    if (make_layout(h->Dm, h->Sm, h->Jm, Rm, cfg->max_pairs, C, jac, C).hot_bytes > budget) {
+      int c = (C / 8) * 8;
+      while (c > C / 2 && make_layout(h->Dm, h->Sm, h->Jm, Rm, cfg->max_pairs, C, jac, c).hot_bytes > budget) c -= 8;
+      if (c > C / 2) Ch = c;
+    }
+    h->L = make_layout(h->Dm, h->Sm, h->Jm, Rm, cfg->max_pairs, C, jac, Ch);
+  }
   // envs ordered by decreasing estimated cost (longest first)
   std::vector<int> order(E);
   std::iota(order.begin(), order.end(), 0);

@@ -40,10 +40,12 @@ __host__ __device__ __forceinline__ int joint_row_count(const JointDesc& j) {
 // once per scene (StaticWorld) and copied into the collision region per step.
 struct Layout {
   int Dm, Sm, Jm, P, C, K, R;   // R: joint solver rows of the largest env
+  int Ch;                       // contacts of an env whose solver data fit the hot part (fused form)
   int bx, bq, bv, bw, bIw0, bIw1;
   int alo, ahi;
   int pairs, cn, cra, crb, cid, crep;
   int kra, krb, klam;
+  int cnc, krac, krbc, klamc;   // full-capacity contact arrays in the cold part
   int man, jr, jinfo, ccol, corder, coff, masks;
   int jdv, inc_off, inc, misc;
   int hot_bytes;    // shared memory in the fused form
