@@ -562,10 +562,10 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi, in
   L.bv = take(Dm * f4); L.bw = take(Dm * f4);
   L.bIw0 = take(Dm * f4); L.bIw1 = take(Dm * f4);
   L.cn = take(L.Ch * f4);
-  L.man = take(P * 16);
+  L.man = take(P * 8);
   L.jr = take(L.R * ROW_F4 * f4);
   L.jinfo = take(Jm * 16);
-  L.ccol = take(L.K * 4); L.corder = take(L.K * 4); L.coff = take((MAX_COLOURS + 1) * 4);
+  L.corder = take(L.K * 4); L.coff = take((MAX_COLOURS + 1) * 4);
   if (jacobi) {
     L.jdv = take(L.K * 4 * f4); L.inc_off = take((Dm + 1) * 4); L.inc = take(2 * L.K * 4);
   } else {
@@ -587,6 +587,7 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi, in
   L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4); L.crep = take(C * f4);
   L.bx = take(Dm * f4); L.bq = take(Dm * f4);   // poses: read per substep, not per sweep
   L.cnc = take(C * f4); L.krac = take(C * f4); L.krbc = take(C * f4); L.klamc = take(C * f4);
+  L.ccol = take(L.K * 4);                        // colours: the colouring stage only
   L.cold_bytes = align16(o);
   L.bytes = L.hot_bytes + L.cold_bytes;
   return L;

@@ -433,7 +433,7 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
           if (i + 1 < jnr) { cur = nxt; r_cur = r_nxt; }
         }
       } else {
-        const int4 mf = w.man[k - J];
+        const int4 mf = man_get(w, k - J);
         const Sym3 Iwa = load_Iw(w, A);
         Sym3 Iwb = Iwa;
         if (B >= 0) Iwb = load_Iw(w, B);
@@ -662,7 +662,7 @@ __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, co
       const int nr = joint_row_count(j);
       for (int r = 0; r < nr; ++r) reverse_mass_part(a, jrow(k, r), A, B, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
     } else {
-      int4 mf = w.man[k - J];
+      int4 mf = man_get(w, k - J);
       const float4* MA = a.madj + 4 * (k - J);
       gIwa[0] = MA[0].x; gIwa[1] = MA[0].y; gIwa[2] = MA[0].z; gIwa[3] = MA[0].w; gIwa[4] = MA[1].x; gIwa[5] = MA[1].y;
       gIwb[0] = MA[1].z; gIwb[1] = MA[1].w; gIwb[2] = MA[2].x; gIwb[3] = MA[2].y; gIwb[4] = MA[2].z; gIwb[5] = MA[2].w;
@@ -705,7 +705,7 @@ __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, co
   }
   gsync(e);
   for (int m = e.lane; m < M; m += e.nthr) {
-    const int4 mf = w.man[m];
+    const int4 mf = man_get(w, m);
     float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
     for (int ci = mf.z; ci < mf.z + mf.w; ++ci) {
       const float4* c = (const float4*)(a.cpose + 16 * ci);
@@ -813,7 +813,7 @@ __device__ void reverse_integrate(const Params& p, const EnvInfo& e, const AWs& 
 // points' normal and anchor adjoints.
 __device__ __forceinline__ float detect_pass(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int m,
                                              int idx) {
-  const int4 mf = w.man[m];
+  const int4 mf = man_get(w, m);
   const int ia = mf.x, ib = mf.y;
   const int pj = w.cid[mf.z] >> 16;
   const float4 xa4 = w.bx[ia], qa4 = w.bq[ia];
@@ -867,7 +867,7 @@ __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w
   const int J = e.J, M = w.misc[MC_MANIFOLDS];
   if (!PER_ITEM) {
     for (int m = e.lane; m < M; m += e.nthr) {
-      int4 mf = w.man[m];
+      int4 mf = man_get(w, m);
       const int ia = mf.x, ib = mf.y;
       const int pj = w.cid[mf.z] >> 16;
       float res[14];
@@ -923,7 +923,7 @@ __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w
   } else {
     if (e.lane == 0) {
       int acc = 0;
-      for (int m = 0; m < M; ++m) { a.moff[m] = acc; acc += w.man[m].y >= 0 ? 14 : 7; }
+      for (int m = 0; m < M; ++m) { a.moff[m] = acc; acc += man_get(w, m).y >= 0 ? 14 : 7; }
       a.moff[M] = acc;
     }
     gsync(e);
@@ -937,7 +937,7 @@ __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w
       const int m = lo, idx = t - a.moff[m];
       float* S = (float*)(a.gat + 8 * (J + m));
       if (idx == 2) S[3] = 0.f;
-      if (idx == 6 && w.man[m].y < 0)
+      if (idx == 6 && man_get(w, m).y < 0)
         for (int q = 8; q < 16; ++q) S[q] = 0.f;
       if (idx == 9) S[11] = 0.f;
       S[pose_slot(idx)] = detect_pass(p, e, w, a, m, idx);

@@ -151,7 +151,7 @@ struct Ws {
   float4* crep;       // contact report: impulse sums over the substeps, then forces
   int* cid;
   float4 *kra, *krb, *klam;
-  int4* man;
+  int2* man;          // manifolds packed: (a | (b + 1) << 16, first contact | count << 16)
   float4* jr;
   int4* jinfo;      // per joint: parent, child, first solver row, row count
   int *ccol, *corder, *coff;
@@ -172,12 +172,21 @@ __device__ __forceinline__ Ws make_ws(char* b, char* cold, const Layout& L) {
   w.cra = (float4*)(cold + L.cra); w.crb = (float4*)(cold + L.crb); w.cid = (int*)(cold + L.cid);
   w.crep = (float4*)(cold + L.crep);
   w.kra = (float4*)(b + L.kra); w.krb = (float4*)(b + L.krb); w.klam = (float4*)(b + L.klam);
-  w.man = (int4*)(b + L.man); w.jr = (float4*)(b + L.jr); w.jinfo = (int4*)(b + L.jinfo);
-  w.ccol = (int*)(b + L.ccol); w.corder = (int*)(b + L.corder); w.coff = (int*)(b + L.coff);
+  w.man = (int2*)(b + L.man); w.jr = (float4*)(b + L.jr); w.jinfo = (int4*)(b + L.jinfo);
+  w.ccol = (int*)(cold + L.ccol); w.corder = (int*)(b + L.corder); w.coff = (int*)(b + L.coff);
   w.masks = (unsigned long long*)(b + L.masks);
   w.jdv = (float4*)(b + L.jdv); w.inc_off = (int*)(b + L.inc_off); w.inc = (int*)(b + L.inc);
   w.misc = (int*)(b + L.misc);
   return w;
+}
+
+// Manifold m as (body a, body b or -1, first contact, contact count).
+__device__ __forceinline__ int4 man_get(const Ws& w, int m) {
+  const int2 v = w.man[m];
+  return make_int4(v.x & 0xffff, (int)((unsigned)v.x >> 16) - 1, v.y & 0xffff, (int)((unsigned)v.y >> 16));
+}
+__device__ __forceinline__ void man_set(const Ws& w, int m, int4 v) {
+  w.man[m] = make_int2(v.x | ((v.y + 1) << 16), v.z | (v.w << 16));
 }
 
 // One env and the threads that work on it: `nthr` threads with group-local
@@ -458,7 +467,7 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
     int mt;
     int mpre = group_exscan(e, kept > 0 ? 1 : 0, scr, &mt);
     if (idx < npairs && kept > 0)
-      w.man[mbase + mpre] = make_int4(pi, pj < e.D ? pj : -1, start, kept);
+      man_set(w, mbase + mpre, make_int4(pi, pj < e.D ? pj : -1, start, kept));
     if (cbase + tot > p.C) over = true;
     cbase = min(cbase + tot, p.C);
     mbase += mt;
@@ -485,7 +494,7 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
     for (int k = 0; k < K; ++k) {
       int a, b;
       if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
-      else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
+      else { int4 m = man_get(w, k - J); a = m.x; b = m.y; }
       unsigned long long msk = 0ull;
       if (a >= 0) msk |= w.masks[a];
       if (b >= 0) msk |= w.masks[b];
@@ -514,7 +523,7 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
       for (int k = 0; k < K; ++k) {
         int a, b;
         if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
-        else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
+        else { int4 m = man_get(w, k - J); a = m.x; b = m.y; }
         if (a >= 0) w.inc_off[a + 1]++;
         if (b >= 0) w.inc_off[b + 1]++;
       }
@@ -527,7 +536,7 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
       for (int k = 0; k < K; ++k) {
         int a, b;
         if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
-        else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
+        else { int4 m = man_get(w, k - J); a = m.x; b = m.y; }
         if (a >= 0) w.inc[w.masks[a]++] = 2 * k;
         if (b >= 0) w.inc[w.masks[b]++] = 2 * k + 1;
       }
@@ -550,7 +559,7 @@ __device__ void tape_collision(const Params& p, const EnvInfo& e, const Ws& w) {
   int* coff = (int*)(t + tc_coff(L));
   int* misc = (int*)(t + tc_misc(L));
   for (int i = e.lane; i < nc; i += e.nthr) { cn[i] = w.cn[i]; cra[i] = w.cra[i]; crb[i] = w.crb[i]; cid[i] = w.cid[i]; }
-  for (int i = e.lane; i < nm; i += e.nthr) man[i] = w.man[i];
+  for (int i = e.lane; i < nm; i += e.nthr) man[i] = man_get(w, i);
   for (int i = e.lane; i < K; i += e.nthr) corder[i] = w.corder[i];
   for (int i = e.lane; i <= ncol; i += e.nthr) coff[i] = w.coff[i];
   for (int i = e.lane; i < MC_N; i += e.nthr) misc[i] = w.misc[i];
@@ -570,7 +579,7 @@ __device__ void untape_collision(const Params& p, const EnvInfo& e, const Ws& w,
   const int* corder = (const int*)(t + tc_corder(L));
   const int* coff = (const int*)(t + tc_coff(L));
   for (int i = e.lane; i < nc; i += e.nthr) { w.cn[i] = cn[i]; w.cra[i] = cra[i]; w.crb[i] = crb[i]; w.cid[i] = cid[i]; }
-  for (int i = e.lane; i < nm; i += e.nthr) w.man[i] = man[i];
+  for (int i = e.lane; i < nm; i += e.nthr) man_set(w, i, man[i]);
   for (int i = e.lane; i < K; i += e.nthr) w.corder[i] = corder[i];
   for (int i = e.lane; i <= ncol; i += e.nthr) w.coff[i] = coff[i];
   for (int i = e.lane; i < MC_N; i += e.nthr) w.misc[i] = misc[i];
@@ -945,7 +954,7 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
 // are formed off the row-to-row dependency chain.
 __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e, const Ws& w, int m, BodyVel& bv,
                                                BodyVel* dacc) {
-  int4 mf = w.man[m];
+  int4 mf = man_get(w, m);
   const int a = mf.x, b = mf.y;
   const float ima = w.bIw1[a].w, imb = b >= 0 ? w.bIw1[b].w : 0.f;
   const float sa = w.bIw1[a].z, sb = b >= 0 ? w.bIw1[b].z : 1.f;
@@ -1000,7 +1009,7 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
 
 __device__ __forceinline__ void con_bodies(const Params& p, const EnvInfo& e, const Ws& w, int k, int J, int& a, int& b) {
   if (k < J) { int4 ji = w.jinfo[k]; a = ji.x; b = ji.y; }
-  else { int4 m = w.man[k - J]; a = m.x; b = m.y; }
+  else { int4 m = man_get(w, k - J); a = m.x; b = m.y; }
 }
 
 __device__ __forceinline__ BodyVel load_vel(const Ws& w, int a, int b) {
@@ -1021,7 +1030,7 @@ __device__ __forceinline__ void tape_lambdas(const Params& p, const EnvInfo& e, 
     const float4* rows = w.jr + (size_t)j.roff * ROW_F4;
     for (int r = 0; r < nr; ++r) t[k * ROWS_PER_JOINT + r] = rows[ROW_F4 * r + 3].w;
   } else {
-    int4 mf = w.man[k - e.J];
+    int4 mf = man_get(w, k - e.J);
     for (int c = mf.z; c < mf.z + mf.w; ++c) {
       float4 l = w.klam[c];
       float* q = t + ROWS_PER_JOINT * p.L.Jm + 3 * c;
