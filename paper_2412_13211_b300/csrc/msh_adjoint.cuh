@@ -835,7 +835,7 @@ __device__ __forceinline__ float detect_pass(const Params& p, const EnvInfo& e, 
     Sj.M = qmat(q);
     Sj.d0 = d1(d.x); Sj.d1 = d1(d.y); Sj.d2 = d1(d.z);
   } else if (pj < e.D + e.S) {
-    Sj = static_shape<d1>(p.sworld + (size_t)SW_N * (e.s0 + pj - e.D));   // the region is reused by then
+    Sj = static_shape<d1>(p.sworld + (size_t)SW_N * (e.s0 + pj - e.D));   // the scene's static record
   } else {
     Sj.type = SH_PLANE;
     Sj.c = v3<d1>(d1(0.f), d1(0.f), d1(0.f));
@@ -894,7 +894,7 @@ __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w
           Sj.M = qmat(q);
           Sj.d0 = d1(d.x); Sj.d1 = d1(d.y); Sj.d2 = d1(d.z);
         } else if (pj < e.D + e.S) {
-          Sj = static_shape<d1>(p.sworld + (size_t)SW_N * (e.s0 + pj - e.D));   // the region is reused by then
+          Sj = static_shape<d1>(p.sworld + (size_t)SW_N * (e.s0 + pj - e.D));   // the scene's static record
         } else {
           Sj.type = SH_PLANE;
           Sj.c = v3<d1>(d1(0.f), d1(0.f), d1(0.f));

@@ -37,7 +37,7 @@ __host__ __device__ __forceinline__ int joint_row_count(const JointDesc& j) {
 // The collision-only arrays (body AABBs, pairs, colouring masks) and the
 // per-substep contact rows are never live at the same time and share one
 // region. Static boxes never move: their world frames and AABBs are computed
-// once per scene (StaticWorld) and copied into the collision region per step.
+// once per scene (StaticWorld) and the collision stage reads them from that table.
 struct Layout {
   int Dm, Sm, Jm, P, C, K, R;   // R: joint solver rows of the largest env
   int Ch;                       // contacts of an env whose solver data fit the hot part (fused form)
