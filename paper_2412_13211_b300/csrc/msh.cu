@@ -756,7 +756,7 @@ int launch_collision_plain(msh_handle* h, Params p, cudaStream_t s) {
   if (rc) return rc;
   p.ws = h->d_ws_plain;
   p.ws_stride = h->L.bytes;
-  const int T = h->tpe;
+  const int T = h->tpe < 32 ? 32 : h->tpe;   // one env per CTA here: at least a full warp
   k_load<<<h->E, T, 0, s>>>(p);
   k_aabb<<<h->E, T, 0, s>>>(p);
   k_broad<<<h->E, T, 0, s>>>(p);

@@ -249,17 +249,25 @@ __device__ __forceinline__ int block_exscan(int v, int* scr, int* total) {
   return off + x - v;
 }
 
-// Exclusive prefix sum over the env's threads (all of them must call it);
-// warp shuffles within a group of at most 32 threads.
-__device__ __forceinline__ int group_exscan(const EnvInfo& e, int v, int* scr, int* total) {
+// Exclusive count of the set flags over the env's threads (all of them must
+// call it): one warp vote within a group of at most 32 threads.
+__device__ __forceinline__ int group_flag_exscan(const EnvInfo& e, int flag, int* scr, int* total) {
+  if (e.nthr > 32) return block_exscan(flag, scr, total);
+  const unsigned b = __ballot_sync(e.mask, flag) & e.mask;
+  *total = __popc(b);
+  return __popc(b & ((1u << (threadIdx.x & 31)) - 1u));
+}
+
+// Exclusive prefix sum of values in 0..7 over the env's threads (all of them
+// must call it): one warp vote per bit within a group of at most 32 threads.
+__device__ __forceinline__ int group_small_exscan(const EnvInfo& e, int v, int* scr, int* total) {
   if (e.nthr > 32) return block_exscan(v, scr, total);
-  int x = v;
-  for (int o = 1; o < e.nthr; o <<= 1) {
-    int y = __shfl_up_sync(e.mask, x, o, e.nthr);
-    if (e.lane >= o) x += y;
-  }
-  *total = __shfl_sync(e.mask, x, e.nthr - 1, e.nthr);
-  return x - v;
+  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+  const unsigned b0 = __ballot_sync(e.mask, v & 1) & e.mask;
+  const unsigned b1 = __ballot_sync(e.mask, v & 2) & e.mask;
+  const unsigned b2 = __ballot_sync(e.mask, v & 4) & e.mask;
+  *total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+  return __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,23 +394,18 @@ __device__ __forceinline__ bool jointed(const Params& p, const EnvInfo& e, int i
 
 __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w, int* scr) {
   const int D = e.D, W = e.D + e.S;   // j in (i, W]; W is the plane
-  // row i holds candidates j = i+1..W: W - i of them; start(i) = i*W - i*(i-1)/2
+  // The candidates (i, j), i < D, i < j <= W, in row order: row i holds W - i
+  // of them. A round tests nthr consecutive candidates; each thread walks its
+  // own (i, j) forward by nthr per round (past the end of row i, j restarts
+  // at i + 2), and (i, j) with i = D marks the end.
   const long long total = (long long)D * W - (long long)D * (D - 1) / 2;
+  int pi = 0, pj = 1 + e.lane;
+  while (pj > W && pi < D) { pj -= W - pi - 1; ++pi; }
   int count = 0;
   int status = 0;
   for (long long base = 0; base < total; base += e.nthr) {
-    long long k = base + e.lane;
-    int flag = 0, pi = 0, pj = 0;
-    if (k < total) {
-      int lo = 0, hi = D - 1;
-      while (lo < hi) {   // largest i with start(i) <= k
-        int mid = (lo + hi + 1) >> 1;
-        long long st = (long long)mid * W - (long long)mid * (mid - 1) / 2;
-        if (st <= k) lo = mid; else hi = mid - 1;
-      }
-      pi = lo;
-      long long st = (long long)pi * W - (long long)pi * (pi - 1) / 2;
-      pj = pi + 1 + (int)(k - st);
+    int flag = 0;
+    if (pi < D) {
       float4 al = w.alo[pi];
       if (pj == W) {
         flag = al.z <= 0.f;
@@ -413,12 +416,14 @@ __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w,
       }
     }
     int tot;
-    int pre = group_exscan(e, flag, scr, &tot);
+    int pre = group_flag_exscan(e, flag, scr, &tot);
     if (flag) {
       int slot = count + pre;
       if (slot < p.P) w.pairs[slot] = pi | (pj << 16);
     }
     count += tot;
+    pj += e.nthr;
+    while (pj > W && pi < D) { pj -= W - pi - 1; ++pi; }
   }
   if (count > p.P) { status |= ST_PAIR_OVERFLOW; count = p.P; }
   if (e.lane == 0) {
@@ -449,7 +454,7 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
       n = collide(Si, Sj, nf(p.off), pts);
     }
     int tot;
-    int pre = group_exscan(e, n, scr, &tot);
+    int pre = group_small_exscan(e, n, scr, &tot);   // n <= 4
     int start = cbase + pre;
     int kept = n;
     if (start + kept > p.C) kept = max(0, p.C - start);
@@ -465,7 +470,7 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
       }
     }
     int mt;
-    int mpre = group_exscan(e, kept > 0 ? 1 : 0, scr, &mt);
+    int mpre = group_flag_exscan(e, kept > 0 ? 1 : 0, scr, &mt);
     if (idx < npairs && kept > 0)
       man_set(w, mbase + mpre, make_int4(pi, pj < e.D ? pj : -1, start, kept));
     if (cbase + tot > p.C) over = true;
