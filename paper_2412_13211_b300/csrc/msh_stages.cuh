@@ -491,15 +491,33 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
 // ---------------------------------------------------------------------------
 __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS], K = J + M;
+  // The constraints of a colour share no dynamic body, so their order does
+  // not change the result. They are listed by decreasing work (classes 0..4:
+  // manifolds of 4 and 3 points, joints, manifolds of 2 and 1 points) so that
+  // the threads of one round of a sweep take similar work: a counting sort on
+  // (colour, class) whose keys and bucket counters use the contact-row
+  // lambdas as scratch (free until the rows are built). Without room there
+  // the constraints keep their index order.
+  constexpr int NB = 5 * MAX_COLOURS;
+  int* key = reinterpret_cast<int*>(w.klam);
+  int* bucket = key + K;
+  const bool keyed = K + NB <= 4 * min(p.L.Ch, p.L.C);
+  if (keyed)
+    for (int i = e.lane; i < NB; i += e.nthr) bucket[i] = 0;
+  gsync(e);
   if (e.lane == 0) {
     for (int i = 0; i < e.D; ++i) w.masks[i] = 0ull;
     int ncol = 0, status = 0;
     int cnt[MAX_COLOURS + 1];
-    for (int c = 0; c <= MAX_COLOURS; ++c) cnt[c] = 0;
+    if (!keyed)
+      for (int c = 0; c <= MAX_COLOURS; ++c) cnt[c] = 0;
     for (int k = 0; k < K; ++k) {
-      int a, b;
+      int a, b, cls = 2;
       if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
-      else { int4 m = man_get(w, k - J); a = m.x; b = m.y; }
+      else {
+        int4 m = man_get(w, k - J); a = m.x; b = m.y;
+        cls = m.w >= 4 ? 0 : m.w == 3 ? 1 : m.w == 2 ? 3 : 4;
+      }
       unsigned long long msk = 0ull;
       if (a >= 0) msk |= w.masks[a];
       if (b >= 0) msk |= w.masks[b];
@@ -509,17 +527,31 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
         c = __ffsll((long long)~msk) - 1;
         if (a >= 0) w.masks[a] |= 1ull << c;
         if (b >= 0) w.masks[b] |= 1ull << c;
-        cnt[c]++;
+        if (keyed) bucket[5 * c + cls]++;
+        else cnt[c]++;
         if (c + 1 > ncol) ncol = c + 1;
       }
       w.ccol[k] = c;
+      if (keyed) key[k] = c < 0 ? -1 : 5 * c + cls;
     }
     int acc = 0;
-    for (int c = 0; c < ncol; ++c) { w.coff[c] = acc; acc += cnt[c]; cnt[c] = w.coff[c]; }
-    w.coff[ncol] = acc;
-    for (int k = 0; k < K; ++k) {
-      int c = w.ccol[k];
-      if (c >= 0) w.corder[cnt[c]++] = k;
+    if (keyed) {
+      for (int c = 0; c < ncol; ++c) {
+        w.coff[c] = acc;
+        for (int q = 0; q < 5; ++q) { const int n = bucket[5 * c + q]; bucket[5 * c + q] = acc; acc += n; }
+      }
+      w.coff[ncol] = acc;
+      for (int k = 0; k < K; ++k) {
+        const int v = key[k];
+        if (v >= 0) w.corder[bucket[v]++] = k;
+      }
+    } else {
+      for (int c = 0; c < ncol; ++c) { w.coff[c] = acc; acc += cnt[c]; cnt[c] = w.coff[c]; }
+      w.coff[ncol] = acc;
+      for (int k = 0; k < K; ++k) {
+        const int c = w.ccol[k];
+        if (c >= 0) w.corder[cnt[c]++] = k;
+      }
     }
     w.misc[MC_COLOURS] = ncol;
     w.misc[MC_STATUS] |= status;
