@@ -384,10 +384,10 @@ __device__ void stage_aabb(const Params& p, const EnvInfo& e, const Ws& w) {
 // a3: broadphase over the flattened (i<j) candidate list, order-preserving
 // compaction with a block scan
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool jointed(const Params& p, const EnvInfo& e, int i, int j) {
+__device__ __forceinline__ bool jointed(const EnvInfo& e, const Ws& w, int i, int j) {
   for (int k = 0; k < e.J; ++k) {
-    const JointDesc& jd = p.joints[e.j0 + k];
-    if ((jd.parent == i && jd.child == j) || (jd.parent == j && jd.child == i)) return true;
+    const int4 jd = w.jinfo[k];   // parent, child (staged with the bodies)
+    if ((jd.x == i && jd.y == j) || (jd.x == j && jd.y == i)) return true;
   }
   return false;
 }
@@ -412,7 +412,7 @@ __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w,
       } else {
         float4 ah = w.ahi[pi], bl = aabb_lo(p, w, e, pj), bh = aabb_hi(p, w, e, pj);
         flag = al.x <= bh.x && bl.x <= ah.x && al.y <= bh.y && bl.y <= ah.y && al.z <= bh.z && bl.z <= ah.z;
-        if (flag && pj < D && jointed(p, e, pi, pj)) flag = 0;
+        if (flag && pj < D && jointed(e, w, pi, pj)) flag = 0;
       }
     }
     int tot;
@@ -513,7 +513,7 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
       for (int c = 0; c <= MAX_COLOURS; ++c) cnt[c] = 0;
     for (int k = 0; k < K; ++k) {
       int a, b, cls = 2;
-      if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
+      if (k < J) { const int4 jd = w.jinfo[k]; a = jd.x; b = jd.y; }
       else {
         int4 m = man_get(w, k - J); a = m.x; b = m.y;
         cls = m.w >= 4 ? 0 : m.w == 3 ? 1 : m.w == 2 ? 3 : 4;
@@ -559,7 +559,7 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
       for (int i = 0; i <= e.D; ++i) w.inc_off[i] = 0;
       for (int k = 0; k < K; ++k) {
         int a, b;
-        if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
+        if (k < J) { const int4 jd = w.jinfo[k]; a = jd.x; b = jd.y; }
         else { int4 m = man_get(w, k - J); a = m.x; b = m.y; }
         if (a >= 0) w.inc_off[a + 1]++;
         if (b >= 0) w.inc_off[b + 1]++;
@@ -572,7 +572,7 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
       for (int i = 0; i < e.D; ++i) w.masks[i] = (unsigned long long)w.inc_off[i];   // fill cursor
       for (int k = 0; k < K; ++k) {
         int a, b;
-        if (k < J) { a = p.joints[e.j0 + k].parent; b = p.joints[e.j0 + k].child; }
+        if (k < J) { const int4 jd = w.jinfo[k]; a = jd.x; b = jd.y; }
         else { int4 m = man_get(w, k - J); a = m.x; b = m.y; }
         if (a >= 0) w.inc[w.masks[a]++] = 2 * k;
         if (b >= 0) w.inc[w.masks[b]++] = 2 * k + 1;
