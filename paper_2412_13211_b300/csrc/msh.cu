@@ -587,6 +587,7 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi, in
   L.cra = take(C * f4); L.crb = take(C * f4); L.cid = take(C * 4); L.crep = take(C * f4);
   L.bx = take(Dm * f4); L.bq = take(Dm * f4);   // poses: read per substep, not per sweep
   L.cnc = take(C * f4); L.krac = take(C * f4); L.krbc = take(C * f4); L.klamc = take(C * f4);
+  L.kxc = take(C * f4);                          // row couplings: read per sweep (L1)
   L.ccol = take(L.K * 4);                        // colours: the colouring stage only
   L.cold_bytes = align16(o);
   L.bytes = L.hot_bytes + L.cold_bytes;

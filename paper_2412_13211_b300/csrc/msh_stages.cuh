@@ -46,6 +46,7 @@ struct Layout {
   int pairs, cn, cra, crb, cid, crep;
   int kra, krb, klam;
   int cnc, krac, krbc, klamc;   // full-capacity contact arrays in the cold part
+  int kxc;                      // per contact point: coupling terms of its rows (cold part)
   int man, jr, jinfo, ccol, corder, coff, masks;
   int jdv, inc_off, inc, misc;
   int hot_bytes;    // shared memory in the fused form
@@ -151,6 +152,7 @@ struct Ws {
   float4* crep;       // contact report: impulse sums over the substeps, then forces
   int* cid;
   float4 *kra, *krb, *klam;
+  float4* kx;         // per contact point: K(t1,n), K(t2,n), K(t2,t1)
   int2* man;          // manifolds packed: (a | (b + 1) << 16, first contact | count << 16)
   float4* jr;
   int4* jinfo;      // per joint: parent, child, first solver row, row count
@@ -172,6 +174,7 @@ __device__ __forceinline__ Ws make_ws(char* b, char* cold, const Layout& L) {
   w.cra = (float4*)(cold + L.cra); w.crb = (float4*)(cold + L.crb); w.cid = (int*)(cold + L.cid);
   w.crep = (float4*)(cold + L.crep);
   w.kra = (float4*)(b + L.kra); w.krb = (float4*)(b + L.krb); w.klam = (float4*)(b + L.klam);
+  w.kx = (float4*)(cold + L.kxc);
   w.man = (int2*)(b + L.man); w.jr = (float4*)(b + L.jr); w.jinfo = (int4*)(b + L.jinfo);
   w.ccol = (int*)(cold + L.ccol); w.corder = (int*)(b + L.corder); w.coff = (int*)(b + L.coff);
   w.masks = (unsigned long long*)(b + L.masks);
@@ -903,6 +906,22 @@ __device__ __forceinline__ float eff_mass(const RowCtx& c, const V3<float>& d, c
   return K > 0.f ? 1.f / K : 0.f;
 }
 
+// Coupling J_x M^-1 J_y^T of two rows (directions x, y) of one contact point:
+// the change of the relative velocity along x per unit impulse along y.
+__device__ __forceinline__ float coupling(const RowCtx& c, const V3<float>& x, const V3<float>& y,
+                                          const V3<float>& ra, const V3<float>& rb) {
+  float K = 0.f;
+  if (c.a >= 0) {
+    const V3<float> xa = crossf(ra, x), ya = crossf(ra, y);
+    K = fmaf(c.sa, fmaf(c.ima, dotf(x, y), dotf(xa, smulf(c.Ia, ya))), K);
+  }
+  if (c.b >= 0) {
+    const V3<float> xb = crossf(rb, x), yb = crossf(rb, y);
+    K = fmaf(c.sb, fmaf(c.imb, dotf(x, y), dotf(xb, smulf(c.Ib, yb))), K);
+  }
+  return K;
+}
+
 __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int ci) {
   int ids = w.cid[ci];
   int a = ids & 0xffff, bc = ids >> 16;
@@ -928,6 +947,7 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
   w.krb[ci] = f4(rb, bias);
   w.klam[ci] = make_float4(0.f, 0.f, 0.f, eff_mass(ctx, t1, ra, rb));
   w.cn[ci].w = eff_mass(ctx, t2, ra, rb);   // the separation s0 is not needed after the narrowphase
+  w.kx[ci] = make_float4(coupling(ctx, t1, n, ra, rb), coupling(ctx, t2, n, ra, rb), coupling(ctx, t2, t1, ra, rb), 0.f);
 }
 
 __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
@@ -986,9 +1006,11 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
 }
 
 // One manifold's points in order, each as a normal row then two friction
-// rows (Gauss-Seidel). For a row along d: the lever terms ra x d, rb x d and
-// their images under the inverse inertias do not depend on the velocities and
-// are formed off the row-to-row dependency chain.
+// rows (Gauss-Seidel). Per point the velocity of b relative to a at the
+// point is formed once; each row's impulse moves the later rows' relative
+// velocities by the point's coupling terms (J_x M^-1 J_y^T, fixed within a
+// substep), and the point's total impulse is applied to the bodies once.
+// This is the row-by-row sequential-impulse update, regrouped.
 __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e, const Ws& w, int m, BodyVel& bv,
                                                BodyVel* dacc) {
   int4 mf = man_get(w, m);
@@ -1000,47 +1022,44 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
   if (b >= 0) Ib = load_Iw(w, b);
   const int c1 = mf.z + mf.w;
   // software pipelining: the next point's data is loaded while this point's rows run
-  float4 cn = w.cn[mf.z], kra = w.kra[mf.z], krb = w.krb[mf.z], lam = w.klam[mf.z];
+  float4 cn = w.cn[mf.z], kra = w.kra[mf.z], krb = w.krb[mf.z], lam = w.klam[mf.z], kx = w.kx[mf.z];
   for (int c = mf.z; c < c1; ++c) {
-    float4 ncn = cn, nkra = kra, nkrb = krb, nlam = lam;
-    if (c + 1 < c1) { ncn = w.cn[c + 1]; nkra = w.kra[c + 1]; nkrb = w.krb[c + 1]; nlam = w.klam[c + 1]; }
-    V3<float> n = f3(cn);
-    V3<float> ra = f3(kra), rb = f3(krb);
+    float4 ncn = cn, nkra = kra, nkrb = krb, nlam = lam, nkx = kx;
+    if (c + 1 < c1) {
+      ncn = w.cn[c + 1]; nkra = w.kra[c + 1]; nkrb = w.krb[c + 1]; nlam = w.klam[c + 1]; nkx = w.kx[c + 1];
+    }
+    const V3<float> n = f3(cn), ra = f3(kra), rb = f3(krb);
     V3<float> t1, t2;
     onb(n, t1, t2);
-    V3<float> dirs[3] = {n, t1, t2};
-    float ms[3] = {kra.w, lam.w, cn.w};
-    float ls[3] = {lam.x, lam.y, lam.z};
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const V3<float> d = dirs[r];
-      const V3<float> ca = crossf(ra, d), cb = crossf(rb, d);
-      const V3<float> ia = smulf(Ia, ca);
-      // v_rel . d = d.(vb - va) + (rb x d).wb - (ra x d).wa   (static b: vb = wb = 0)
-      float vn = dotf(d, bv.vb - bv.va) + dotf(cb, bv.wb) - dotf(ca, bv.wa);
-      float dl, nl;
-      if (r == 0) {
-        dl = -ms[0] * (vn + krb.w);
-        nl = fmaxf(ls[0] + dl, 0.f);
-      } else {
-        dl = -ms[r] * vn;
-        float lim = p.mu * ls[0];
-        nl = fminf(fmaxf(ls[r] + dl, -lim), lim);
-      }
-      dl = nl - ls[r];
-      ls[r] = nl;
-      bv.va = axpyf(bv.va, d, -(ka * dl));
-      bv.wa = axpyf(bv.wa, ia, -(sa * dl));
-      if (dacc) { dacc->va = axpyf(dacc->va, d, -(ima * dl)); dacc->wa = axpyf(dacc->wa, ia, -dl); }
-      if (b >= 0) {
-        const V3<float> ib = smulf(Ib, cb);
-        bv.vb = axpyf(bv.vb, d, kb * dl);
-        bv.wb = axpyf(bv.wb, ib, sb * dl);
-        if (dacc) { dacc->vb = axpyf(dacc->vb, d, imb * dl); dacc->wb = axpyf(dacc->wb, ib, dl); }
-      }
+    // velocity of b relative to a at the point (static b: vb = wb = 0)
+    V3<float> vr = bv.va + crossf(bv.wa, ra);
+    vr = b >= 0 ? (bv.vb + crossf(bv.wb, rb)) - vr : -vr;
+    float u0 = dotf(n, vr), u1 = dotf(t1, vr), u2 = dotf(t2, vr);
+    const float l0 = lam.x, l1 = lam.y, l2 = lam.z;
+    const float nl0 = fmaxf(l0 + -kra.w * (u0 + krb.w), 0.f);
+    const float d0 = nl0 - l0;
+    u1 = fmaf(kx.x, d0, u1);
+    u2 = fmaf(kx.y, d0, u2);
+    const float lim = p.mu * nl0;
+    const float nl1 = fminf(fmaxf(l1 + -lam.w * u1, -lim), lim);
+    const float d1 = nl1 - l1;
+    u2 = fmaf(kx.z, d1, u2);
+    const float nl2 = fminf(fmaxf(l2 + -cn.w * u2, -lim), lim);
+    const float d2 = nl2 - l2;
+    w.klam[c] = make_float4(nl0, nl1, nl2, lam.w);
+    // the point's impulse on b (its negative on a)
+    const V3<float> P = axpyf(axpyf(n * d0, t1, d1), t2, d2);
+    const V3<float> ia = smulf(Ia, crossf(ra, P));
+    bv.va = axpyf(bv.va, P, -ka);
+    bv.wa = axpyf(bv.wa, ia, -sa);
+    if (dacc) { dacc->va = axpyf(dacc->va, P, -ima); dacc->wa = dacc->wa - ia; }
+    if (b >= 0) {
+      const V3<float> ib = smulf(Ib, crossf(rb, P));
+      bv.vb = axpyf(bv.vb, P, kb);
+      bv.wb = axpyf(bv.wb, ib, sb);
+      if (dacc) { dacc->vb = axpyf(dacc->vb, P, imb); dacc->wb = dacc->wb + ib; }
     }
-    w.klam[c] = make_float4(ls[0], ls[1], ls[2], lam.w);
-    cn = ncn; kra = nkra; krb = nkrb; lam = nlam;
+    cn = ncn; kra = nkra; krb = nkrb; lam = nlam; kx = nkx;
   }
 }
 
