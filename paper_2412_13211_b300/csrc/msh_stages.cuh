@@ -899,29 +899,6 @@ __device__ __forceinline__ void contact_geom(const V3<T>& xa, const Q4<T>& qa, c
   bias = s > T(0.f) ? s / T(h) : -T(beta / h) * maxv(T(0.f), -s - T(slop));
 }
 
-__device__ __forceinline__ float eff_mass(const RowCtx& c, const V3<float>& d, const V3<float>& ra, const V3<float>& rb) {
-  float K = 0.f;
-  if (c.a >= 0) { V3<float> x = crossf(ra, d); K = fmaf(c.sa, fmaf(c.ima, dotf(d, d), dotf(x, smulf(c.Ia, x))), K); }
-  if (c.b >= 0) { V3<float> x = crossf(rb, d); K = fmaf(c.sb, fmaf(c.imb, dotf(d, d), dotf(x, smulf(c.Ib, x))), K); }
-  return K > 0.f ? 1.f / K : 0.f;
-}
-
-// Coupling J_x M^-1 J_y^T of two rows (directions x, y) of one contact point:
-// the change of the relative velocity along x per unit impulse along y.
-__device__ __forceinline__ float coupling(const RowCtx& c, const V3<float>& x, const V3<float>& y,
-                                          const V3<float>& ra, const V3<float>& rb) {
-  float K = 0.f;
-  if (c.a >= 0) {
-    const V3<float> xa = crossf(ra, x), ya = crossf(ra, y);
-    K = fmaf(c.sa, fmaf(c.ima, dotf(x, y), dotf(xa, smulf(c.Ia, ya))), K);
-  }
-  if (c.b >= 0) {
-    const V3<float> xb = crossf(rb, x), yb = crossf(rb, y);
-    K = fmaf(c.sb, fmaf(c.imb, dotf(x, y), dotf(xb, smulf(c.Ib, yb))), K);
-  }
-  return K;
-}
-
 __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int ci) {
   int ids = w.cid[ci];
   int a = ids & 0xffff, bc = ids >> 16;
@@ -943,11 +920,27 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
   }
   V3<float> t1, t2;
   onb(n, t1, t2);
-  w.kra[ci] = f4(ra, eff_mass(ctx, n, ra, rb));
+  // the point's 3x3 matrix K(x, y) = J_x M^-1 J_y^T over its rows x, y in
+  // (n, t1, t2): the lever terms r x d and their images under the inverse
+  // inertias are formed once per row and shared by the matrix entries
+  const V3<float> d[3] = {n, t1, t2};
+  V3<float> la[3], ma[3], lb[3], mb[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    la[r] = crossf(ra, d[r]); ma[r] = smulf(ctx.Ia, la[r]);
+    if (b >= 0) { lb[r] = crossf(rb, d[r]); mb[r] = smulf(ctx.Ib, lb[r]); }
+  }
+  auto K = [&](int i, int j) {
+    float k = fmaf(ctx.sa, fmaf(ctx.ima, dotf(d[i], d[j]), dotf(la[i], ma[j])), 0.f);
+    if (b >= 0) k = fmaf(ctx.sb, fmaf(ctx.imb, dotf(d[i], d[j]), dotf(lb[i], mb[j])), k);
+    return k;
+  };
+  auto inv = [](float k) { return k > 0.f ? 1.f / k : 0.f; };
+  w.kra[ci] = f4(ra, inv(K(0, 0)));
   w.krb[ci] = f4(rb, bias);
-  w.klam[ci] = make_float4(0.f, 0.f, 0.f, eff_mass(ctx, t1, ra, rb));
-  w.cn[ci].w = eff_mass(ctx, t2, ra, rb);   // the separation s0 is not needed after the narrowphase
-  w.kx[ci] = make_float4(coupling(ctx, t1, n, ra, rb), coupling(ctx, t2, n, ra, rb), coupling(ctx, t2, t1, ra, rb), 0.f);
+  w.klam[ci] = make_float4(0.f, 0.f, 0.f, inv(K(1, 1)));
+  w.cn[ci].w = inv(K(2, 2));   // the separation s0 is not needed after the narrowphase
+  w.kx[ci] = make_float4(K(1, 0), K(2, 0), K(2, 1), 0.f);
 }
 
 __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
