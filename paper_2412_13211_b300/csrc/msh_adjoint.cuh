@@ -407,7 +407,7 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
   const int J = e.J;
   const int ncol = w.misc[MC_COLOURS];
   for (int c = ncol - 1; c >= 0; --c) {
-    const int c0 = w.coff[c], c1 = w.coff[c + 1];
+    const int c0 = w.coff[c] & 0xffff, c1 = w.coff[c + 1] & 0xffff;   // high bits: the colour's joint count
     for (int idx = c0 + e.lane; idx < c1; idx += e.nthr) {
       const int k = w.corder[idx];
       int A, B;

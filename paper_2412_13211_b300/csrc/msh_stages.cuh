@@ -495,12 +495,14 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
 __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS], K = J + M;
   // The constraints of a colour share no dynamic body, so their order does
-  // not change the result. They are listed by decreasing work (classes 0..4:
-  // manifolds of 4 and 3 points, joints, manifolds of 2 and 1 points) so that
-  // the threads of one round of a sweep take similar work: a counting sort on
-  // (colour, class) whose keys and bucket counters use the contact-row
-  // lambdas as scratch (free until the rows are built). Without room there
-  // the constraints keep their index order.
+  // not change the result. A colour lists its joints first, then its
+  // manifolds by decreasing point count (classes 0..4: joints, manifolds of
+  // 4, 3, 2 and 1 points), so that a sweep runs each colour's joints and its
+  // manifolds as two loops of like work: a counting sort on (colour, class)
+  // whose keys and bucket counters use the contact-row lambdas as scratch
+  // (free until the rows are built). Without room there the constraints keep
+  // their index order (joints first too). coff[c] holds the colour's first
+  // entry in its low 16 bits and its joint count in the high 16 bits.
   constexpr int NB = 5 * MAX_COLOURS;
   int* key = reinterpret_cast<int*>(w.klam);
   int* bucket = key + K;
@@ -515,11 +517,11 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
     if (!keyed)
       for (int c = 0; c <= MAX_COLOURS; ++c) cnt[c] = 0;
     for (int k = 0; k < K; ++k) {
-      int a, b, cls = 2;
+      int a, b, cls = 0;
       if (k < J) { const int4 jd = w.jinfo[k]; a = jd.x; b = jd.y; }
       else {
         int4 m = man_get(w, k - J); a = m.x; b = m.y;
-        cls = m.w >= 4 ? 0 : m.w == 3 ? 1 : m.w == 2 ? 3 : 4;
+        cls = 5 - min(m.w, 4);
       }
       unsigned long long msk = 0ull;
       if (a >= 0) msk |= w.masks[a];
@@ -555,6 +557,12 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
         const int c = w.ccol[k];
         if (c >= 0) w.corder[cnt[c]++] = k;
       }
+    }
+    for (int c = 0; c < ncol; ++c) {
+      const int c0 = w.coff[c], c1 = w.coff[c + 1];
+      int j = c0;
+      while (j < c1 && w.corder[j] < J) ++j;
+      w.coff[c] = c0 | ((j - c0) << 16);
     }
     w.misc[MC_COLOURS] = ncol;
     w.misc[MC_STATUS] |= status;
@@ -1094,16 +1102,25 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w,
   if (p.mode == MODE_COLOURED) {
     const int ncol = w.misc[MC_COLOURS];
     for (int c = 0; c < ncol; ++c) {
-      const int c0 = w.coff[c], c1 = w.coff[c + 1];
-      for (int idx = c0 + e.lane; idx < c1; idx += e.nthr) {
-        int k = w.corder[idx];
-        int a, b;
-        con_bodies(p, e, w, k, J, a, b);
-        BodyVel bv = load_vel(w, a, b);
-        if (k < J) solve_joint(p, e, w, k, bv, nullptr);
-        else solve_manifold(p, e, w, k - J, bv, nullptr);
-        if (a >= 0) { w.bv[a] = f4(bv.va, 0.f); w.bw[a] = f4(bv.wa, 0.f); }
-        if (b >= 0) { w.bv[b] = f4(bv.vb, 0.f); w.bw[b] = f4(bv.wb, 0.f); }
+      // the colour's joints, then its manifolds (no barrier between: a
+      // colour's constraints share no dynamic body)
+      const int v = w.coff[c], c0 = v & 0xffff, cm = c0 + (v >> 16), c1 = w.coff[c + 1] & 0xffff;
+      for (int idx = c0 + e.lane; idx < cm; idx += e.nthr) {
+        const int k = w.corder[idx];
+        const int4 ji = w.jinfo[k];
+        BodyVel bv = load_vel(w, ji.x, ji.y);
+        solve_joint(p, e, w, k, bv, nullptr);
+        if (ji.x >= 0) { w.bv[ji.x] = f4(bv.va, 0.f); w.bw[ji.x] = f4(bv.wa, 0.f); }
+        w.bv[ji.y] = f4(bv.vb, 0.f); w.bw[ji.y] = f4(bv.wb, 0.f);
+        if (p.tape) tape_lambdas(p, e, w, k, sub, it);
+      }
+      for (int idx = cm + e.lane; idx < c1; idx += e.nthr) {
+        const int k = w.corder[idx];
+        const int4 mf = man_get(w, k - J);
+        BodyVel bv = load_vel(w, mf.x, mf.y);
+        solve_manifold(p, e, w, k - J, bv, nullptr);
+        w.bv[mf.x] = f4(bv.va, 0.f); w.bw[mf.x] = f4(bv.wa, 0.f);
+        if (mf.y >= 0) { w.bv[mf.y] = f4(bv.vb, 0.f); w.bw[mf.y] = f4(bv.wb, 0.f); }
         if (p.tape) tape_lambdas(p, e, w, k, sub, it);
       }
       gsync(e);
