@@ -185,6 +185,8 @@ def time_fwd_bwd(sim, scene, tg, horizon, k, stream, reps=2, threads_per_env=32)
     goal = torch.as_tensor(goal_np, device=dev)
     init = [torch.as_tensor(np.asarray(a, np.float32), device=dev) for a in scene.state()]
     mass0 = torch.as_tensor(np.asarray(scene.body_mass, np.float32), device=dev)
+    if tg.shape[0] < horizon:
+        raise ValueError(f"{tg.shape[0]} target rows for a {horizon}-step rollout")
     targets0 = tg[:horizon].contiguous()
 
     def once():
@@ -423,7 +425,8 @@ def main():
     from paper_2412_13211_b300 import autotune
     sim = MshSim(scene, cfg, device=dev, exec_form="fused", use_graph=True)
     total = args.warmup + args.steps
-    tg = torch.as_tensor(scene.target_walk(total)).to(dev)
+    # targets for the timed steps and for the differentiable rollout's horizon
+    tg = torch.as_tensor(scene.target_walk(max(total, args.bwd_horizon))).to(dev)
     if args.threads_per_env:
         sim.set_exec("fused", args.threads_per_env, True)
         tuning = {"best": ("fused", args.threads_per_env), "ms": {}}

@@ -402,52 +402,63 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
   Q[3] = f4(gra, gbias); Q[4] = f4(grb, glam[0]); Q[5] = make_float4(glam[1], glam[2], 0.f, 0.f);
 }
 
+// Reverse of one constraint's update in a sweep (JOINT: a joint's rows in
+// reverse order, else a manifold's points in reverse order).
+template <bool JOINT>
+__device__ __forceinline__ void reverse_constraint(const Params& p, const Ws& w, const AWs& a, int k, int J,
+                                                   const float* lam_it, const float* lam_prev) {
+  int A, B;
+  if (JOINT) { const int4 ji = w.jinfo[k]; A = ji.x; B = ji.y; }
+  else { const int4 mf = man_get(w, k - J); A = mf.x; B = mf.y; }
+  BodyVel v = load_vel(w, A, B);
+  BodyAdj g;
+  V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  g.va = A >= 0 ? f3(a.bv[A]) : z; g.wa = A >= 0 ? f3(a.bw[A]) : z;
+  g.vb = B >= 0 ? f3(a.bv[B]) : z; g.wb = B >= 0 ? f3(a.bw[B]) : z;
+  const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
+  if (JOINT) {
+    const int jnr = w.jinfo[k].w;
+    // software pipelining: the next row's parameters, adjoints and lambdas
+    // load while this row runs (rows of a constraint never alias)
+    int r_cur = jrow(k, jnr - 1);
+    RevRow cur, nxt;
+    load_rev_row(a, r_cur, lam_it, lam_prev, -1, cur);
+    for (int i = 0; i < jnr; ++i) {
+      const int r_nxt = jrow(k, jnr - 2 - i);
+      if (i + 1 < jnr) load_rev_row(a, r_nxt, lam_it, lam_prev, -1, nxt);
+      float gfric;
+      reverse_row(a, r_cur, A, B, ima, imb, v, g, cur, 0.f, gfric);
+      if (i + 1 < jnr) { cur = nxt; r_cur = r_nxt; }
+    }
+  } else {
+    const int4 mf = man_get(w, k - J);
+    const Sym3 Iwa = load_Iw(w, A);
+    Sym3 Iwb = Iwa;
+    if (B >= 0) Iwb = load_Iw(w, B);
+    float4* MA = a.madj + 4 * (k - J);
+    float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
+    float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
+    for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
+      reverse_point(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
+    MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
+    MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
+  }
+  if (A >= 0) { w.bv[A] = f4(v.va, 0.f); w.bw[A] = f4(v.wa, 0.f); a.bv[A] = f4(g.va, 0.f); a.bw[A] = f4(g.wa, 0.f); }
+  if (B >= 0) { w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f); }
+}
+
+// Reverse of one sweep: colours in reverse order; within a colour (its
+// constraints share no dynamic body) the joints, then the manifolds.
 __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* lam_it,
                               const float* lam_prev) {
   const int J = e.J;
   const int ncol = w.misc[MC_COLOURS];
   for (int c = ncol - 1; c >= 0; --c) {
-    const int c0 = w.coff[c] & 0xffff, c1 = w.coff[c + 1] & 0xffff;   // high bits: the colour's joint count
-    for (int idx = c0 + e.lane; idx < c1; idx += e.nthr) {
-      const int k = w.corder[idx];
-      int A, B;
-      con_bodies(p, e, w, k, J, A, B);
-      BodyVel v = load_vel(w, A, B);
-      BodyAdj g;
-      V3<float> z = v3<float>(0.f, 0.f, 0.f);
-      g.va = A >= 0 ? f3(a.bv[A]) : z; g.wa = A >= 0 ? f3(a.bw[A]) : z;
-      g.vb = B >= 0 ? f3(a.bv[B]) : z; g.wb = B >= 0 ? f3(a.bw[B]) : z;
-      const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
-      if (k < J) {
-        const int jnr = w.jinfo[k].w;
-        // software pipelining: the next row's parameters, adjoints and lambdas
-        // load while this row runs (rows of a constraint never alias)
-        int r_cur = jrow(k, jnr - 1);
-        RevRow cur, nxt;
-        load_rev_row(a, r_cur, lam_it, lam_prev, -1, cur);
-        for (int i = 0; i < jnr; ++i) {
-          const int r_nxt = jrow(k, jnr - 2 - i);
-          if (i + 1 < jnr) load_rev_row(a, r_nxt, lam_it, lam_prev, -1, nxt);
-          float gfric;
-          reverse_row(a, r_cur, A, B, ima, imb, v, g, cur, 0.f, gfric);
-          if (i + 1 < jnr) { cur = nxt; r_cur = r_nxt; }
-        }
-      } else {
-        const int4 mf = man_get(w, k - J);
-        const Sym3 Iwa = load_Iw(w, A);
-        Sym3 Iwb = Iwa;
-        if (B >= 0) Iwb = load_Iw(w, B);
-        float4* MA = a.madj + 4 * (k - J);
-        float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
-        float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
-        for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
-          reverse_point(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
-        MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
-        MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
-      }
-      if (A >= 0) { w.bv[A] = f4(v.va, 0.f); w.bw[A] = f4(v.wa, 0.f); a.bv[A] = f4(g.va, 0.f); a.bw[A] = f4(g.wa, 0.f); }
-      if (B >= 0) { w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f); }
-    }
+    const int v = w.coff[c], c0 = v & 0xffff, cm = c0 + (v >> 16), c1 = w.coff[c + 1] & 0xffff;
+    for (int idx = c0 + e.lane; idx < cm; idx += e.nthr)
+      reverse_constraint<true>(p, w, a, w.corder[idx], J, lam_it, lam_prev);
+    for (int idx = cm + e.lane; idx < c1; idx += e.nthr)
+      reverse_constraint<false>(p, w, a, w.corder[idx], J, lam_it, lam_prev);
     gsync(e);
   }
 }
