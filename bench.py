@@ -31,6 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/sec at 4096 envs (fwd and fwd+bwd) vs plain step; % HBM roofline"
+WORKLOADS = {1: "falling spheres over static boxes", 2: "fixed-base arm and gripper at a counter",
+             3: "apartment batch of uneven size with a mobile manipulator",
+             4: "arm pushing a goal box on a table", 5: "scale batch, 32 objects and 50 static boxes per env",
+             6: "apartment batch with drawer and fridge-door receptacles"}
 UNIT = "env-steps/s"
 # bytes per env-step the method must move when contacts stay on chip:
 # per dynamic body state read + write + params, per static box, plane, per
@@ -544,7 +548,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"config{args.config} apartment batch, 4096 envs of uneven size",
+        "config": {"workload": f"config{args.config}: {WORKLOADS.get(args.config, 'batch')}, {scene.num_envs} envs",
                    "envs": scene.num_envs, "bodies": scene.num_bodies, "static_boxes": scene.num_statics,
                    "joints": scene.num_joints, "dt": cfg.dt, "substeps": cfg.substeps,
                    "iterations": cfg.iterations, "solver": "coloured PGS", "form": f"{form} (autotuned) + CUDA graph",
