@@ -953,10 +953,9 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
 
 __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
   const int nc = w.misc[MC_CONTACTS];
-  for (int t = e.lane; t < e.J + nc; t += e.nthr) {
-    if (t < e.J) joint_rows(p, e, w, t);
-    else contact_rows(p, e, w, t - e.J);
-  }
+  // joints, then contacts: two loops, so that a round of threads takes one kind
+  for (int t = e.lane; t < e.J; t += e.nthr) joint_rows(p, e, w, t);
+  for (int t = e.lane; t < nc; t += e.nthr) contact_rows(p, e, w, t);
 }
 
 // ---------------------------------------------------------------------------
