@@ -193,7 +193,8 @@ __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const
       contact_geom<float>(f3(w.bx[ia]), ldq4(w.bq[ia]), xb, qb, ib >= 0, n, f3(w.cra[ci]), f3(w.crb[ci]), p.h,
                           p.beta, p.slop, ra, rb, bias);
       V3<float> t1, t2;
-      onb(n, t1, t2);
+      const float sc = onb_scale(n);
+      onb_with(n, sc, t1, t2);
       V3<float> dirs[3] = {n, t1, t2};
       float m[3];
       for (int r = 0; r < 3; ++r) {
@@ -203,7 +204,7 @@ __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const
         m[r] = x.m;
       }
       float4* P = a.cpar + 4 * ci;
-      P[0] = f4(n, m[0]); P[1] = f4(ra, bias); P[2] = f4(rb, m[1]); P[3] = make_float4(m[2], 0.f, 0.f, 0.f);
+      P[0] = f4(n, m[0]); P[1] = f4(ra, bias); P[2] = f4(rb, m[1]); P[3] = make_float4(m[2], sc, 0.f, 0.f);
       float4* G = a.cadj + 6 * ci;
       for (int q = 0; q < 6; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -315,7 +316,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
   const float ms[3] = {P0.w, P2.w, P3.x};
   const float bias = P1.w;
   V3<float> t1, t2;
-  onb(n, t1, t2);
+  onb_with(n, P3.y, t1, t2);
   const V3<float> dirs[3] = {n, t1, t2};
   V3<float> gd[3] = {f3(Q0), f3(Q1), f3(Q2)};
   float gm[3] = {Q0.w, Q1.w, Q2.w};
@@ -515,7 +516,7 @@ __device__ __forceinline__ void contact_mass_adjoint(const AWs& a, int ci, bool 
   const V3<float> n = f3(P[0]), ra = f3(P[1]), rb = f3(P[2]);
   const float ms[3] = {P[0].w, P[2].w, P[3].x};
   V3<float> t1, t2;
-  onb(n, t1, t2);
+  onb_with(n, P[3].y, t1, t2);
   const V3<float> dirs[3] = {n, t1, t2};
   V3<float> gra = f3(Q[3]), grb = f3(Q[4]);
   for (int q = 0; q < 3; ++q) {

@@ -883,13 +883,21 @@ __device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k
   }
 }
 
-// Duff et al. (2017) orthonormal basis from a unit normal.
-template <class T> __device__ __forceinline__ void onb(const V3<T>& n, V3<T>& t1, V3<T>& t2) {
+// Duff et al. (2017) orthonormal basis from a unit normal: the scale
+// a = -1/(sign(n_z) + n_z), then the two tangents from it. The solver keeps a
+// per contact point, so its sweeps form the tangents without the division.
+template <class T> __device__ __forceinline__ T onb_scale(const V3<T>& n) {
   T sg = n.z >= T(0.f) ? T(1.f) : T(-1.f);
-  T a = T(-1.f) / (sg + n.z);
+  return T(-1.f) / (sg + n.z);
+}
+template <class T> __device__ __forceinline__ void onb_with(const V3<T>& n, T a, V3<T>& t1, V3<T>& t2) {
+  T sg = n.z >= T(0.f) ? T(1.f) : T(-1.f);
   T b = n.x * n.y * a;
   t1 = v3<T>(T(1.f) + sg * n.x * n.x * a, sg * b, -sg * n.x);
   t2 = v3<T>(b, sg + n.y * n.y * a, -n.y);
+}
+template <class T> __device__ __forceinline__ void onb(const V3<T>& n, V3<T>& t1, V3<T>& t2) {
+  onb_with(n, onb_scale(n), t1, t2);
 }
 
 // World lever arms and speculative bias of one contact point from the body
@@ -927,7 +935,8 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
     if (vn < -1.f) bias = fminf(bias, p.rest * vn);
   }
   V3<float> t1, t2;
-  onb(n, t1, t2);
+  const float sc = onb_scale(n);
+  onb_with(n, sc, t1, t2);
   // the point's 3x3 matrix K(x, y) = J_x M^-1 J_y^T over its rows x, y in
   // (n, t1, t2): the lever terms r x d and their images under the inverse
   // inertias are formed once per row and shared by the matrix entries
@@ -948,7 +957,7 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
   w.krb[ci] = f4(rb, bias);
   w.klam[ci] = make_float4(0.f, 0.f, 0.f, inv(K(1, 1)));
   w.cn[ci].w = inv(K(2, 2));   // the separation s0 is not needed after the narrowphase
-  w.kx[ci] = make_float4(K(1, 0), K(2, 0), K(2, 1), 0.f);
+  w.kx[ci] = make_float4(K(1, 0), K(2, 0), K(2, 1), sc);
 }
 
 __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
@@ -1030,7 +1039,7 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
     }
     const V3<float> n = f3(cn), ra = f3(kra), rb = f3(krb);
     V3<float> t1, t2;
-    onb(n, t1, t2);
+    onb_with(n, kx.w, t1, t2);
     // velocity of b relative to a at the point (static b: vb = wb = 0)
     V3<float> vr = bv.va + crossf(bv.wa, ra);
     vr = b >= 0 ? (bv.vb + crossf(bv.wb, rb)) - vr : -vr;
