@@ -288,7 +288,7 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   const int RU4 = (RU + 3) / 4;                        // float4s per lambda buffer
   const int need_l = 3 * RU4 * 16;
   const int need_b = 4 * e.D * 16;
-  const int need_r = (2 * RJ * ROW_F4 + 10 * nc + 4 * nm) * 16;
+  const int need_r = (2 * RJ * ROW_F4 + (CPAR_F4 + CADJ_F4) * nc + 4 * nm) * 16;
   Ws w = b.w;
   AWs a = b.a;
   const bool lams = need_l <= slice, bodies = need_l + need_b <= slice, rows = need_l + need_b + need_r <= slice;
@@ -306,11 +306,11 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
       a.rows = a.bw + e.D;
       a.radj = a.rows + (size_t)RJ * ROW_F4;
       a.cpar = a.radj + (size_t)RJ * ROW_F4;
-      a.cadj = a.cpar + 4 * nc;
-      a.madj = a.cadj + 6 * nc;
+      a.cadj = a.cpar + CPAR_F4 * nc;
+      a.madj = a.cadj + CADJ_F4 * nc;
       for (int i = e.lane; i < RJ * ROW_F4; i += e.nthr) { a.rows[i] = b.a.rows[i]; a.radj[i] = b.a.radj[i]; }
-      for (int i = e.lane; i < 4 * nc; i += e.nthr) a.cpar[i] = b.a.cpar[i];
-      for (int i = e.lane; i < 6 * nc; i += e.nthr) a.cadj[i] = b.a.cadj[i];
+      for (int i = e.lane; i < CPAR_F4 * nc; i += e.nthr) a.cpar[i] = b.a.cpar[i];
+      for (int i = e.lane; i < CADJ_F4 * nc; i += e.nthr) a.cadj[i] = b.a.cadj[i];
       for (int i = e.lane; i < 4 * nm; i += e.nthr) a.madj[i] = b.a.madj[i];
     }
   }
@@ -349,7 +349,7 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
     }
     if (rows) {
       for (int i = e.lane; i < RJ * ROW_F4; i += e.nthr) b.a.radj[i] = a.radj[i];
-      for (int i = e.lane; i < 6 * nc; i += e.nthr) b.a.cadj[i] = a.cadj[i];
+      for (int i = e.lane; i < CADJ_F4 * nc; i += e.nthr) b.a.cadj[i] = a.cadj[i];
       for (int i = e.lane; i < 4 * nm; i += e.nthr) b.a.madj[i] = a.madj[i];
     }
   }
@@ -605,7 +605,7 @@ AdjLayout make_adj_layout(const Layout& L, int md) {
   A.bx = take(L.Dm * f4); A.bq = take(L.Dm * f4); A.bv = take(L.Dm * f4); A.bw = take(L.Dm * f4);
   A.bI0 = take(L.Dm * f4); A.bI1 = take(L.Dm * f4); A.bm = take(L.Dm * f4);
   A.rows = take((long long)A.Rm * ROW_F4 * f4); A.radj = take((long long)A.Rm * ROW_F4 * f4);
-  A.cpar = take((long long)L.C * 4 * f4); A.cadj = take((long long)L.C * 6 * f4);
+  A.cpar = take((long long)L.C * CPAR_F4 * f4); A.cadj = take((long long)L.C * CADJ_F4 * f4);
   A.madj = take((long long)L.P * 4 * f4);
   A.cpose = take((long long)L.C * 4 * f4);
   A.moff = take((long long)(L.P + 1) * 4);

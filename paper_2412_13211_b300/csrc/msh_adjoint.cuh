@@ -38,7 +38,7 @@ struct AdjLayout {
   int Rm, Km;
   int bx, bq, bv, bw, bI0, bI1, bm;   // per body: x, q, v, w adjoints; Iw adjoint (6) + 1/m adjoint; mass accum
   int rows, radj;                     // per joint row: 5 float4 params, 5 float4 adjoints
-  int cpar, cadj;                     // per contact point: 4 float4 params, 6 float4 adjoints
+  int cpar, cadj;                     // per contact point: CPAR_F4 float4 params, CADJ_F4 float4 adjoints
   int madj;                           // per manifold: 4 float4 (gIw_a, gIw_b, g(1/m_a), g(1/m_b))
   int cpose;                          // per contact point: 16 floats, its pose adjoints in gather-slot order
   int moff;                           // per manifold + 1: first dual-pass item of the narrowphase reverse
@@ -57,6 +57,11 @@ struct AdjParams {
   float* otg;            // [E, max_dof] adjoint of this step's targets
   float* omass;          // [B] accumulated mass adjoint
 };
+
+// float4s per contact point: parameters (n|m_n, ra|bias, rb|m_t1, m_t2|onb
+// scale|K(t1,n)|K(t2,n), K(t2,t1)) and adjoint accumulators (d|m x3, ra|bias,
+// rb|lambda_n, lambda_t1|lambda_t2|K(t1,n)|K(t2,n), K(t2,t1)).
+enum { CPAR_F4 = 5, CADJ_F4 = 7 };
 
 struct AWs {
   float4 *bx, *bq, *bv, *bw, *bI0, *bI1, *bm;
@@ -203,10 +208,13 @@ __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const
         finish_row(x, ctx, false);
         m[r] = x.m;
       }
-      float4* P = a.cpar + 4 * ci;
-      P[0] = f4(n, m[0]); P[1] = f4(ra, bias); P[2] = f4(rb, m[1]); P[3] = make_float4(m[2], sc, 0.f, 0.f);
-      float4* G = a.cadj + 6 * ci;
-      for (int q = 0; q < 6; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      float K[6];
+      point_K(ctx, dirs, ra, rb, K);   // the couplings the forward sweeps use
+      float4* P = a.cpar + CPAR_F4 * ci;
+      P[0] = f4(n, m[0]); P[1] = f4(ra, bias); P[2] = f4(rb, m[1]); P[3] = make_float4(m[2], sc, K[3], K[4]);
+      P[4] = make_float4(K[5], 0.f, 0.f, 0.f);
+      float4* G = a.cadj + CADJ_F4 * ci;
+      for (int q = 0; q < CADJ_F4; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   const int M = w.misc[MC_MANIFOLDS];
@@ -296,111 +304,117 @@ __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, f
   G[0] = f4(gla, gm); G[1] = f4(gaa, gbias); G[2] = f4(gab, glam_before); G[3] = f4(gIa, gima); G[4] = f4(gIb, gimb);
 }
 
-// Reverse of the three row updates of contact point ci (t2, t1, then the
-// normal row, undoing the forward order n, t1, t2). The rows are re-formed
-// from the point's normal n, arms ra, rb and masses: J_lin = -d on body a and
-// +d on b, J_ang = -(ra x d) on a and rb x d on b, d in {n, t1, t2}. The
-// adjoints of a row's Jacobian and inertia products are pulled back at once
-// onto d, ra, rb (through the cross products) and onto the manifold's
-// inverse-inertia and inverse-mass accumulators `mi` (gIw_a[6], gIw_b[6],
-// g(1/m_a), g(1/m_b)). A friction row at its limit mu * lambda_n sends its
-// adjoint to the normal row's lambda.
+// Reverse of contact point ci's update in a sweep. The forward forms the
+// velocity of b relative to a at the point, vr = (vb + wb x rb) - (va + wa x
+// ra), its components u = d.vr along d in (n, t1, t2), updates lambda_n, then
+// lambda_t1, lambda_t2, each later row's u moved by the earlier rows' impulse
+// changes D through the couplings K(t1,n), K(t2,n), K(t2,t1), and applies the
+// point's impulse P = sum_d d D once (-P on a, +P on b, through 1/m and the
+// world inverse inertias). This undoes it: the velocities before the point,
+// then the adjoints of the velocities, of lambda before the update, of d, ra,
+// rb, the masses, the bias and the couplings (accumulated per point for the
+// set-up reverse), and of the manifold's inverse inertias and inverse masses
+// `mi` (gIw_a[6], gIw_b[6], g(1/m_a), g(1/m_b)). A friction row at its limit
+// mu * lambda_n sends its adjoint to lambda_n.
 __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool bdyn, float ima, float imb,
                                               const Sym3& Iwa, const Sym3& Iwb, BodyVel& v, BodyAdj& g,
                                               const float* lam_it, const float* lam_prev, float mu, float* mi) {
-  const float4* P = a.cpar + 4 * ci;
-  float4* Q = a.cadj + 6 * ci;
-  const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3];
-  const float4 Q0 = Q[0], Q1 = Q[1], Q2 = Q[2], Q3 = Q[3], Q4 = Q[4], Q5 = Q[5];
+  const float4* P = a.cpar + CPAR_F4 * ci;
+  float4* Q = a.cadj + CADJ_F4 * ci;
+  const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
+  const float4 Q0 = Q[0], Q1 = Q[1], Q2 = Q[2], Q3 = Q[3], Q4 = Q[4], Q5 = Q[5], Q6 = Q[6];
   const V3<float> n = f3(P0), ra = f3(P1), rb = f3(P2);
-  const float ms[3] = {P0.w, P2.w, P3.x};
-  const float bias = P1.w;
+  const float m0 = P0.w, m1 = P2.w, m2 = P3.x, bias = P1.w;
+  const float K10 = P3.z, K20 = P3.w, K21 = P4.x;
   V3<float> t1, t2;
   onb_with(n, P3.y, t1, t2);
-  const V3<float> dirs[3] = {n, t1, t2};
-  V3<float> gd[3] = {f3(Q0), f3(Q1), f3(Q2)};
-  float gm[3] = {Q0.w, Q1.w, Q2.w};
+  V3<float> gd0 = f3(Q0), gd1 = f3(Q1), gd2 = f3(Q2);
+  float gm0 = Q0.w, gm1 = Q1.w, gm2 = Q2.w;
   V3<float> gra = f3(Q3), grb = f3(Q4);
   float gbias = Q3.w;
-  float glam[3] = {Q4.w, Q5.x, Q5.y};
-  float l_after[3], l_before[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    l_after[q] = lam_it[rn + q];
-    l_before[q] = lam_prev ? lam_prev[rn + q] : 0.f;
+  float gl0 = Q4.w, gl1 = Q5.x, gl2 = Q5.y;
+  float gK10 = Q5.z, gK20 = Q5.w, gK21 = Q6.x;
+  const float la0 = lam_it[rn], la1 = lam_it[rn + 1], la2 = lam_it[rn + 2];
+  const float lb0 = lam_prev ? lam_prev[rn] : 0.f, lb1 = lam_prev ? lam_prev[rn + 1] : 0.f,
+              lb2 = lam_prev ? lam_prev[rn + 2] : 0.f;
+  const float D0 = la0 - lb0, D1 = la1 - lb1, D2 = la2 - lb2;
+  // the point's impulse and the velocities before the point
+  const V3<float> Pi = (n * D0 + t1 * D1) + t2 * D2;
+  const V3<float> ta = cross(ra, Pi);
+  v.va = v.va + Pi * ima;
+  v.wa = v.wa + smul(Iwa, ta);
+  V3<float> tb = v3<float>(0.f, 0.f, 0.f);
+  if (bdyn) {
+    tb = cross(rb, Pi);
+    v.vb = v.vb - Pi * imb;
+    v.wb = v.wb - smul(Iwb, tb);
   }
-  const V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  // adjoint of the impulse's application
+  const V3<float> sa = smul(Iwa, g.wa);
+  V3<float> gP = g.va * (-ima) + cross(ra, sa);
+  gra = gra + cross(sa, Pi);
+  add_sym(mi, g.wa, -ta);
+  mi[12] -= dot(Pi, g.va);
+  if (bdyn) {
+    const V3<float> sb = smul(Iwb, g.wb);
+    gP = gP + g.vb * imb + cross(sb, rb);
+    grb = grb + cross(Pi, sb);
+    add_sym(mi + 6, g.wb, tb);
+    mi[13] += dot(Pi, g.vb);
+  }
+  float gD0 = dot(n, gP), gD1 = dot(t1, gP), gD2 = dot(t2, gP);
+  gd0 = gd0 + gP * D0; gd1 = gd1 + gP * D1; gd2 = gd2 + gP * D2;
+  // the rows' inputs as the forward formed them
+  V3<float> vr = v3<float>(0.f, 0.f, 0.f) - (v.va + cross(v.wa, ra));
+  if (bdyn) vr = vr + (v.vb + cross(v.wb, rb));
+  const float u0 = dot(n, vr);
+  const float u1 = dot(t1, vr) + K10 * D0;
+  const float u2 = (dot(t2, vr) + K20 * D0) + K21 * D1;
+  const float lim = mu * la0;
   float pend = 0.f;
-#pragma unroll
-  for (int q = 2; q >= 0; --q) {
-    const V3<float> d = dirs[q];
-    const V3<float> ca = cross(ra, d), cb = cross(rb, d);          // J_ang: -ca on a, cb on b
-    const V3<float> ia = smul(Iwa, ca), ib = bdyn ? smul(Iwb, cb) : z;
-    const float D = l_after[q] - l_before[q];
-    // velocities before the update
-    v.va = v.va + d * (ima * D);
-    v.wa = v.wa + ia * D;
-    if (bdyn) { v.vb = v.vb - d * (imb * D); v.wb = v.wb - ib * D; }
-    // adjoint of D through the velocity update
-    const float dga = dot(d, g.va);
-    float gD = -ima * dga - dot(ia, g.wa);
-    V3<float> glin = g.va * (ima * D);                             // adjoint of J_lin(a) = -d
-    const V3<float> gIa = g.wa * D;                                // adjoint of Iw_a J_ang(a)
-    V3<float> gIb = z;
-    mi[12] += -dga * D;
-    if (bdyn) {
-      const float dgb = dot(d, g.vb);
-      gD += imb * dgb + dot(ib, g.wb);
-      glin = glin - g.vb * (imb * D);
-      gIb = g.wb * D;
-      mi[13] += dgb * D;
-    }
-    if (q == 0) glam[0] += pend;                                   // what t1 and t2 sent to lambda_n
-    const float a_after = glam[q] + gD;
-    float glam_before = -gD;
-    // pre-clamp value of the update
-    float jv = 0.f;
-    if (bdyn) jv = dotf(cb, v.wb) + dotf(d, v.vb);
-    jv = jv - dotf(d, v.va) - dotf(ca, v.wa);
-    const float u = q == 0 ? jv + bias : jv;
-    bool clamped;
-    float sgn = 0.f;
-    if (q == 0) clamped = l_after[0] == 0.f;
-    else {
-      const float lim = mu * l_after[0];
-      clamped = l_after[q] == lim || l_after[q] == -lim;
-      sgn = l_after[q] == lim ? 1.f : -1.f;
-    }
-    const float gpre = clamped ? 0.f : a_after;
-    if (q > 0 && clamped) pend += sgn * mu * a_after;
-    glam_before += gpre;
-    const float gu = -ms[q] * gpre;
-    gm[q] += -u * gpre;
-    if (q == 0) gbias += gu;
-    V3<float> gaa = v.wa * gu;                                     // adjoint of J_ang(a) = -ca
-    g.va = g.va - d * gu;
-    g.wa = g.wa - ca * gu;
-    glin = glin + (v.va - v.vb) * gu;
-    // Iw_a J_ang(a): onto J_ang(a) and Iw_a
-    gaa = gaa + smul(Iwa, gIa);
-    add_sym(mi, gIa, -ca);
-    // J_lin(a) = -d, J_ang(a) = d x ra
-    gd[q] = gd[q] - glin + cross(ra, gaa);
-    gra = gra + cross(gaa, d);
-    if (bdyn) {
-      V3<float> gab = v.wb * gu;                                   // adjoint of J_ang(b) = cb
-      g.vb = g.vb + d * gu;
-      g.wb = g.wb + cb * gu;
-      gab = gab + smul(Iwb, gIb);
-      add_sym(mi + 6, gIb, cb);
-      // J_ang(b) = rb x d
-      grb = grb + cross(d, gab);
-      gd[q] = gd[q] + cross(gab, rb);
-    }
-    glam[q] = glam_before;
+  // friction t2
+  const float a2 = gl2 + gD2;
+  const bool c2 = la2 == lim || la2 == -lim;
+  if (c2) pend += (la2 == lim ? 1.f : -1.f) * mu * a2;
+  const float gp2 = c2 ? 0.f : a2;
+  gl2 = gp2 - gD2;
+  gm2 += -u2 * gp2;
+  const float gu2 = -m2 * gp2;
+  gK21 += D1 * gu2;
+  gD1 += K21 * gu2;
+  // friction t1
+  const float a1 = gl1 + gD1;
+  const bool c1 = la1 == lim || la1 == -lim;
+  if (c1) pend += (la1 == lim ? 1.f : -1.f) * mu * a1;
+  const float gp1 = c1 ? 0.f : a1;
+  gl1 = gp1 - gD1;
+  gm1 += -u1 * gp1;
+  const float gu1 = -m1 * gp1;
+  gK10 += D0 * gu1;
+  gK20 += D0 * gu2;
+  gD0 += K10 * gu1 + K20 * gu2;
+  // normal
+  gl0 += pend;
+  const float a0 = gl0 + gD0;
+  const float gp0 = la0 == 0.f ? 0.f : a0;
+  gl0 = gp0 - gD0;
+  gm0 += -(u0 + bias) * gp0;
+  const float gu0 = -m0 * gp0;
+  gbias += gu0;
+  // u = d.vr
+  const V3<float> gvr = (n * gu0 + t1 * gu1) + t2 * gu2;
+  gd0 = gd0 + vr * gu0; gd1 = gd1 + vr * gu1; gd2 = gd2 + vr * gu2;
+  g.va = g.va - gvr;
+  g.wa = g.wa - cross(ra, gvr);
+  gra = gra - cross(gvr, v.wa);
+  if (bdyn) {
+    g.vb = g.vb + gvr;
+    g.wb = g.wb + cross(rb, gvr);
+    grb = grb + cross(gvr, v.wb);
   }
-  Q[0] = f4(gd[0], gm[0]); Q[1] = f4(gd[1], gm[1]); Q[2] = f4(gd[2], gm[2]);
-  Q[3] = f4(gra, gbias); Q[4] = f4(grb, glam[0]); Q[5] = make_float4(glam[1], glam[2], 0.f, 0.f);
+  Q[0] = f4(gd0, gm0); Q[1] = f4(gd1, gm1); Q[2] = f4(gd2, gm2);
+  Q[3] = f4(gra, gbias); Q[4] = f4(grb, gl0); Q[5] = make_float4(gl1, gl2, gK10, gK20);
+  Q[6] = make_float4(gK21, 0.f, 0.f, 0.f);
 }
 
 // Reverse of one constraint's update in a sweep (JOINT: a joint's rows in
@@ -505,44 +519,54 @@ __device__ __forceinline__ void reverse_mass_part(const AWs& a, int r, int A, in
   G[0] = f4(gla, 0.f); G[1] = f4(gaa, G[1].w); G[2] = f4(gab, G[2].w);
 }
 
-// The effective-mass part of a contact point's three rows (m = 1/K, K =
-// ima |d|^2 + ca.Iw_a ca [+ imb |d|^2 + cb.Iw_b cb]): moves each row's mass
-// adjoint onto d, the arms, the inverse inertias and the inverse masses.
+// The mass part of a contact point's rows: K(x, y) = J_x M^-1 J_y^T = ima
+// x.y + (ra x x).Iw_a (ra x y) [+ imb x.y + (rb x x).Iw_b (rb x y)] over x, y
+// in (n, t1, t2). The diagonal enters through the effective masses m = 1/K,
+// the off-diagonal (t1,n), (t2,n), (t2,t1) through the couplings of the
+// sweeps; their adjoints move onto the directions, the arms, the inverse
+// inertias and the inverse masses.
 __device__ __forceinline__ void contact_mass_adjoint(const AWs& a, int ci, bool bdyn, float ima, float imb,
                                                      const Sym3& Iwa, const Sym3& Iwb, float* gIwa, float* gIwb,
                                                      float& gima, float& gimb) {
-  const float4* P = a.cpar + 4 * ci;
-  float4* Q = a.cadj + 6 * ci;
+  const float4* P = a.cpar + CPAR_F4 * ci;
+  float4* Q = a.cadj + CADJ_F4 * ci;
   const V3<float> n = f3(P[0]), ra = f3(P[1]), rb = f3(P[2]);
   const float ms[3] = {P[0].w, P[2].w, P[3].x};
   V3<float> t1, t2;
   onb_with(n, P[3].y, t1, t2);
   const V3<float> dirs[3] = {n, t1, t2};
   V3<float> gra = f3(Q[3]), grb = f3(Q[4]);
-  for (int q = 0; q < 3; ++q) {
-    const float m = ms[q];
-    const float gK = m > 0.f ? -m * m * Q[q].w : 0.f;
-    const V3<float> d = dirs[q];
-    const V3<float> ca = cross(ra, d), cb = cross(rb, d);
-    const float ll = dot(d, d);
-    V3<float> gd = f3(Q[q]);
-    // body a: K_a = ima |d|^2 + J_ang.Iw_a J_ang with J_ang = -ca
-    gd = gd + d * (2.f * gK * ima);
-    gima += gK * ll;
-    const V3<float> gaa = smul(Iwa, ca) * (-2.f * gK);
-    add_sym(gIwa, ca * gK, ca);
-    gd = gd + cross(ra, gaa);
-    gra = gra + cross(gaa, d);
-    if (bdyn) {
-      gd = gd + d * (2.f * gK * imb);
-      gimb += gK * ll;
-      const V3<float> gab = smul(Iwb, cb) * (2.f * gK);
-      add_sym(gIwb, cb * gK, cb);
-      grb = grb + cross(d, gab);
-      gd = gd + cross(gab, rb);
+  V3<float> gd[3] = {f3(Q[0]), f3(Q[1]), f3(Q[2])};
+  const float gKo[3] = {Q[5].z, Q[5].w, Q[6].x};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int i = q < 3 ? q : (q == 5 ? 2 : q - 2), j = q < 3 ? q : (q == 5 ? 1 : 0);
+    float gK;
+    if (q < 3) { const float m = ms[q]; gK = m > 0.f ? -m * m * Q[q].w : 0.f; }
+    else gK = gKo[q - 3];
+    const V3<float> x = dirs[i], y = dirs[j];
+    const float xy = dot(x, y);
+    // body a
+    {
+      const V3<float> cx = cross(ra, x), cy = cross(ra, y);
+      const V3<float> gcx = smul(Iwa, cy) * gK, gcy = smul(Iwa, cx) * gK;
+      gd[i] = gd[i] + y * (gK * ima) + cross(gcx, ra);
+      gd[j] = gd[j] + x * (gK * ima) + cross(gcy, ra);
+      gima += gK * xy;
+      add_sym(gIwa, cx * gK, cy);
+      gra = gra + cross(x, gcx) + cross(y, gcy);
     }
-    Q[q] = f4(gd, 0.f);
+    if (bdyn) {
+      const V3<float> cx = cross(rb, x), cy = cross(rb, y);
+      const V3<float> gcx = smul(Iwb, cy) * gK, gcy = smul(Iwb, cx) * gK;
+      gd[i] = gd[i] + y * (gK * imb) + cross(gcx, rb);
+      gd[j] = gd[j] + x * (gK * imb) + cross(gcy, rb);
+      gimb += gK * xy;
+      add_sym(gIwb, cx * gK, cy);
+      grb = grb + cross(x, gcx) + cross(y, gcy);
+    }
   }
+  for (int q = 0; q < 3; ++q) Q[q] = f4(gd[q], 0.f);
   Q[3] = f4(gra, Q[3].w);
   Q[4] = f4(grb, Q[4].w);
 }
@@ -603,7 +627,7 @@ __device__ __forceinline__ void rotate_adjoint(const float4& q4, const V3<float>
 __device__ void contact_geom_adjoint(const Params& p, const Ws& w, const AWs& a, int ci, int ia, int ib,
                                      float* out) {
   for (int k = 0; k < 23; ++k) out[k] = 0.f;
-  const float4* Q = a.cadj + 6 * ci;
+  const float4* Q = a.cadj + CADJ_F4 * ci;
   const float4 xa4 = w.bx[ia], qa4 = w.bq[ia];
   const V3<float> n = f3(w.cn[ci]), ral = f3(w.cra[ci]), rbl = f3(w.crb[ci]);
   V3<float> gn = f3(Q[0]);

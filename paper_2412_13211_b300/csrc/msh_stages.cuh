@@ -915,6 +915,28 @@ __device__ __forceinline__ void contact_geom(const V3<T>& xa, const Q4<T>& qa, c
   bias = s > T(0.f) ? s / T(h) : -T(beta / h) * maxv(T(0.f), -s - T(slop));
 }
 
+// The 3x3 matrix K(x, y) = J_x M^-1 J_y^T of a contact point over its rows
+// x, y in (n, t1, t2) (d[0..2]): K[0..2] its diagonal, K[3..5] = K(t1, n),
+// K(t2, n), K(t2, t1). The lever terms r x d and their images under the
+// inverse inertias are formed once per row and shared by the entries.
+__device__ __forceinline__ void point_K(const RowCtx& ctx, const V3<float>* d, const V3<float>& ra,
+                                        const V3<float>& rb, float* K) {
+  V3<float> la[3], ma[3], lb[3], mb[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    la[r] = crossf(ra, d[r]); ma[r] = smulf(ctx.Ia, la[r]);
+    if (ctx.b >= 0) { lb[r] = crossf(rb, d[r]); mb[r] = smulf(ctx.Ib, lb[r]); }
+  }
+  const int I[6] = {0, 1, 2, 1, 2, 2}, J[6] = {0, 1, 2, 0, 0, 1};
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int i = I[q], j = J[q];
+    float k = fmaf(ctx.sa, fmaf(ctx.ima, dotf(d[i], d[j]), dotf(la[i], ma[j])), 0.f);
+    if (ctx.b >= 0) k = fmaf(ctx.sb, fmaf(ctx.imb, dotf(d[i], d[j]), dotf(lb[i], mb[j])), k);
+    K[q] = k;
+  }
+}
+
 __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int ci) {
   int ids = w.cid[ci];
   int a = ids & 0xffff, bc = ids >> 16;
@@ -937,27 +959,15 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
   V3<float> t1, t2;
   const float sc = onb_scale(n);
   onb_with(n, sc, t1, t2);
-  // the point's 3x3 matrix K(x, y) = J_x M^-1 J_y^T over its rows x, y in
-  // (n, t1, t2): the lever terms r x d and their images under the inverse
-  // inertias are formed once per row and shared by the matrix entries
   const V3<float> d[3] = {n, t1, t2};
-  V3<float> la[3], ma[3], lb[3], mb[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    la[r] = crossf(ra, d[r]); ma[r] = smulf(ctx.Ia, la[r]);
-    if (b >= 0) { lb[r] = crossf(rb, d[r]); mb[r] = smulf(ctx.Ib, lb[r]); }
-  }
-  auto K = [&](int i, int j) {
-    float k = fmaf(ctx.sa, fmaf(ctx.ima, dotf(d[i], d[j]), dotf(la[i], ma[j])), 0.f);
-    if (b >= 0) k = fmaf(ctx.sb, fmaf(ctx.imb, dotf(d[i], d[j]), dotf(lb[i], mb[j])), k);
-    return k;
-  };
+  float K[6];
+  point_K(ctx, d, ra, rb, K);
   auto inv = [](float k) { return k > 0.f ? 1.f / k : 0.f; };
-  w.kra[ci] = f4(ra, inv(K(0, 0)));
+  w.kra[ci] = f4(ra, inv(K[0]));
   w.krb[ci] = f4(rb, bias);
-  w.klam[ci] = make_float4(0.f, 0.f, 0.f, inv(K(1, 1)));
-  w.cn[ci].w = inv(K(2, 2));   // the separation s0 is not needed after the narrowphase
-  w.kx[ci] = make_float4(K(1, 0), K(2, 0), K(2, 1), sc);
+  w.klam[ci] = make_float4(0.f, 0.f, 0.f, inv(K[1]));
+  w.cn[ci].w = inv(K[2]);   // the separation s0 is not needed after the narrowphase
+  w.kx[ci] = make_float4(K[3], K[4], K[5], sc);
 }
 
 __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
