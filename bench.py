@@ -31,6 +31,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/sec at 4096 envs (fwd and fwd+bwd) vs plain step; % HBM roofline"
+# DRAM bytes (read + write) of one k_fused launch, from the ncu capture of
+# the kernel as built now (profiles/k_fused_apartment4096.md, version 7),
+# keyed by (config, envs, threads per env); other launches report null.
+FUSED_TRAFFIC = {(3, 4096, 16): 47.649792e6 + 7.145984e6}
 WORKLOADS = {1: "falling spheres over static boxes", 2: "fixed-base arm and gripper at a counter",
              3: "apartment batch of uneven size with a mobile manipulator",
              4: "arm pushing a goal box on a table", 5: "scale batch, 32 objects and 50 static boxes per env",
@@ -544,6 +548,7 @@ def main():
     alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x clock, TFLOP/s
     achieved_tf = flops_step / (t_step / 1e3) / 1e12
     achieved_gbs = bytes_step / (t_step / 1e3) / 1e9
+    traffic = FUSED_TRAFFIC.get((args.config, scene.num_envs, tpe)) if form == "fused" else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -557,11 +562,11 @@ def main():
                    "l2": "flushed between timed steps (256 MB write)", "contact_points": int(det["contact_count"].sum()),
                    "rows_per_substep": rows},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tf / alu_peak, "traffic": None,
+                     "frac": achieved_tf / alu_peak, "traffic": traffic,
                      "note": f"FP32 peak = 148 SMs x 128 lanes x 2 x {sm_max:.0f} MHz; achieved = {FLOP_ROW} flop x "
                              f"solver rows x substeps x iterations / fused-kernel step time"},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved_gbs / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": bytes_step},
         "plain_step": plain, "contact_report": report, "event_labeling": labels, "depth_cameras": render,
         "control_wrapper": control,
