@@ -152,7 +152,8 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"config{args.config} apartment batch", "envs": scene.num_envs,
+            "config": {"workload": f"config{args.config}: {WORKLOADS.get(args.config, 'batch')}, {scene.num_envs} envs",
+                       "envs": scene.num_envs,
                        "sampled_envs": n, "substeps": cfg.substeps, "iterations": cfg.iterations},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{n} of {scene.num_envs} envs per step, FP32 oracle, OpenMP over envs"},
