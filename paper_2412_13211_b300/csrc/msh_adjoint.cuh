@@ -10,20 +10,23 @@
 //     quaternion update;
 //   * coloured PGS: the sweeps run backwards (iterations, then colours in
 //     reverse order, rows of a constraint in reverse order); velocities before
-//     each row update are rebuilt from the velocities after it and the
-//     recorded lambdas (v_before = v_after - M^-1 J^T (lambda_after -
-//     lambda_before)); clamp states come from the recorded lambdas. Joint rows
-//     are stored whole (Jacobians, inertia products, mass, bias, softness);
-//     a contact point keeps only its normal, world lever arms, bias and three
-//     effective masses, its rows are re-formed on the fly, and its adjoint
-//     accumulators are those of the normal, tangents and arms (the row
-//     Jacobians' adjoints are pulled back through the cross products at every
-//     update), with the inverse-inertia and inverse-mass adjoints kept per
+//     each update are rebuilt from the velocities after it and the recorded
+//     lambdas (v_before = v_after - M^-1 J^T (lambda_after - lambda_before));
+//     clamp states come from the recorded lambdas. Joint rows are stored whole
+//     (Jacobians, inertia products, mass, bias, softness). A contact point
+//     keeps its normal, world lever arms, bias, three effective masses, the
+//     tangent-basis scale and the three couplings of its rows, and is reversed
+//     as the forward updates it: its impulse once, then the scalar chain of
+//     its three rows through the couplings; its adjoint accumulators are those
+//     of the normal, tangents, arms, masses, bias, carried lambdas and
+//     couplings, with the inverse-inertia and inverse-mass adjoints kept per
 //     manifold;
 //   * row set-up (lever arms, Jacobians, biases, drives) and the narrowphase:
 //     local Jacobians by single-tangent dual numbers, one input direction at a
-//     time, contracted with the row/contact adjoints;
-//   * effective masses and world inverse inertias: hand-written reverse.
+//     time, contracted with the row/contact adjoints; the contact geometry by
+//     a hand-written reverse;
+//   * effective masses, couplings and world inverse inertias: hand-written
+//     reverse.
 // Per-body sums are gathered in constraint order, so results are
 // deterministic (checkpointed and plain backward passes agree bitwise).
 #pragma once
