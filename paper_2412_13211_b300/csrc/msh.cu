@@ -577,6 +577,7 @@ Layout make_layout(int Dm, int Sm, int Jm, int Rm, int P, int C, bool jacobi, in
   L.alo = take(Dm * f4); L.ahi = take(Dm * f4);
   L.pairs = take(P * 4);
   L.masks = take(Dm * 8);
+  L.salo = take(Sm * f4); L.sahi = take(Sm * f4);
   const int end_x = o;
   o = region;
   L.kra = take(L.Ch * f4); L.krb = take(L.Ch * f4); L.klam = take(L.Ch * f4);

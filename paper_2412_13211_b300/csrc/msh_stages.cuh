@@ -42,7 +42,7 @@ struct Layout {
   int Dm, Sm, Jm, P, C, K, R;   // R: joint solver rows of the largest env
   int Ch;                       // contacts of an env whose solver data fit the hot part (fused form)
   int bx, bq, bv, bw, bIw0, bIw1;
-  int alo, ahi;
+  int alo, ahi, salo, sahi;
   int pairs, cn, cra, crb, cid, crep;
   int kra, krb, klam;
   int cnc, krac, krbc, klamc;   // full-capacity contact arrays in the cold part
@@ -147,6 +147,7 @@ enum { SW_C = 0, SW_M = 1, SW_LO = 4, SW_HI = 5, SW_N = 6 };
 struct Ws {
   float4 *bx, *bq, *bv, *bw, *bIw0, *bIw1;
   float4 *alo, *ahi;  // body AABBs
+  float4 *salo, *sahi;  // the static boxes' AABBs, staged for the broadphase
   int* pairs;
   float4 *cn, *cra, *crb;
   float4* crep;       // contact report: impulse sums over the substeps, then forces
@@ -169,6 +170,7 @@ __device__ __forceinline__ Ws make_ws(char* b, char* cold, const Layout& L) {
   w.bv = (float4*)(b + L.bv); w.bw = (float4*)(b + L.bw);
   w.bIw0 = (float4*)(b + L.bIw0); w.bIw1 = (float4*)(b + L.bIw1);
   w.alo = (float4*)(b + L.alo); w.ahi = (float4*)(b + L.ahi);
+  w.salo = (float4*)(b + L.salo); w.sahi = (float4*)(b + L.sahi);
   w.pairs = (int*)(b + L.pairs);
   w.cn = (float4*)(b + L.cn);
   w.cra = (float4*)(cold + L.cra); w.crb = (float4*)(cold + L.crb); w.cid = (int*)(cold + L.cid);
@@ -345,10 +347,10 @@ __device__ __forceinline__ void static_world(const float* sp, const float* sh, f
 // (A static box's record is read from the scene's table, through the
 // read-only cache.)
 __device__ __forceinline__ float4 aabb_lo(const Params& p, const Ws& w, const EnvInfo& e, int i) {
-  return i < e.D ? w.alo[i] : __ldg(p.sworld + (size_t)SW_N * (e.s0 + i - e.D) + SW_LO);
+  return i < e.D ? w.alo[i] : w.salo[i - e.D];
 }
 __device__ __forceinline__ float4 aabb_hi(const Params& p, const Ws& w, const EnvInfo& e, int i) {
-  return i < e.D ? w.ahi[i] : __ldg(p.sworld + (size_t)SW_N * (e.s0 + i - e.D) + SW_HI);
+  return i < e.D ? w.ahi[i] : w.sahi[i - e.D];
 }
 
 // Collision shape of index i: dynamic body, static box or the plane.
@@ -375,6 +377,12 @@ __device__ __forceinline__ Shape<nf> coll_shape(const Params& p, const Ws& w, co
 // a2: AABBs of the bodies (static boxes: StaticWorld)
 // ---------------------------------------------------------------------------
 __device__ void stage_aabb(const Params& p, const EnvInfo& e, const Ws& w) {
+  // the static boxes' AABBs (computed once per scene) next to the bodies'
+  for (int i = e.lane; i < e.S; i += e.nthr) {
+    const float4* r = p.sworld + (size_t)SW_N * (e.s0 + i);
+    w.salo[i] = __ldg(r + SW_LO);
+    w.sahi[i] = __ldg(r + SW_HI);
+  }
   for (int i = e.lane; i < e.D; i += e.nthr) {
     Shape<nf> s = coll_shape(p, w, e, i);
     AABBt<nf> b = shape_aabb(s, nf(p.off));
@@ -506,7 +514,12 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
   constexpr int NB = 5 * MAX_COLOURS;
   int* key = reinterpret_cast<int*>(w.klam);
   int* bucket = key + K;
-  const bool keyed = K + NB <= 4 * min(p.L.Ch, p.L.C);
+  // room for the keys, and no overlap with the colouring masks (the hot
+  // contact rows share a region with the collision arrays)
+  const char* k0 = reinterpret_cast<const char*>(key);
+  const char* m0 = reinterpret_cast<const char*>(w.masks);
+  const bool keyed = K + NB <= 4 * min(p.L.Ch, p.L.C) &&
+                     (k0 + 4 * (K + NB) <= m0 || k0 >= m0 + 8 * e.D);
   if (keyed)
     for (int i = e.lane; i < NB; i += e.nthr) bucket[i] = 0;
   gsync(e);
