@@ -32,9 +32,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/sec at 4096 envs (fwd and fwd+bwd) vs plain step; % HBM roofline"
 # DRAM bytes (read + write) of one k_fused launch, from the ncu capture of
-# the kernel as built now (profiles/k_fused_apartment4096.md, version 7),
+# the kernel as built now (profiles/k_fused_apartment4096.md, version 8),
 # keyed by (config, envs, threads per env); other launches report null.
-FUSED_TRAFFIC = {(3, 4096, 16): 47.649792e6 + 7.145984e6}
+FUSED_TRAFFIC = {(3, 4096, 16): 47.647744e6 + 7.761152e6}
 WORKLOADS = {1: "falling spheres over static boxes", 2: "fixed-base arm and gripper at a counter",
              3: "apartment batch of uneven size with a mobile manipulator",
              4: "arm pushing a goal box on a table", 5: "scale batch, 32 objects and 50 static boxes per env",
