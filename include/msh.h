@@ -198,7 +198,10 @@ int msh_detect(msh_handle* h, const msh_state* st, float* aabb_body, float* aabb
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture. All calls share the
  * array: calls that overlap on the GPU (other streams, other handles) race
- * and must be serialised by the caller. Results equal msh_step's.
+ * and must be serialised by the caller. Results equal msh_step's (bit for
+ * bit) when no tape is recording. It records nothing: while the handle is
+ * recording (msh_set_tape with n > 0, not paused by msh_tape_record) it
+ * returns MSH_ERR_INVALID_ARG and leaves the state untouched.
  */
 int msh_step_static_scratch(msh_handle* h, const msh_state* st, const float* joint_targets, float dt,
                             int32_t substeps, void* stream);

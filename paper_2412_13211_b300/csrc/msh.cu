@@ -1614,6 +1614,12 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   if (!h || !st || !st->pos || !st->quat || !st->linvel || !st->angvel)
     return fail(MSH_ERR_INVALID_ARG, "handle or state pointer is NULL");
   if (h->max_dof > 0 && !joint_targets) return fail(MSH_ERR_INVALID_ARG, "joint_targets is NULL but max_dof > 0");
+  // a recorded step needs its tape slot (device memory of the handle); this
+  // entry point records nothing, so it refuses to run while recording rather
+  // than advance the state past the recorded rollout
+  if (h->tape_max > 0 && !h->tape_paused)
+    return fail(MSH_ERR_INVALID_ARG, "msh_step_static_scratch does not record: pause or stop the tape first "
+                                     "(msh_tape_record(h, 0) or msh_set_tape(h, 0))");
   if (!(dt > 0.f)) dt = h->cfg.dt;
   if (substeps < 1) substeps = h->cfg.substeps;
   // layout: [0, 256) the env-queue counter, then one 256-aligned slab per env group
