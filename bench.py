@@ -31,10 +31,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/sec at 4096 envs (fwd and fwd+bwd) vs plain step; % HBM roofline"
-# DRAM bytes (read + write) of one k_fused launch, from the ncu capture of
-# the kernel as built now (profiles/k_fused_apartment4096.md, version 8),
-# keyed by (config, envs, threads per env); other launches report null.
-FUSED_TRAFFIC = {(3, 4096, 16): 47.647744e6 + 7.761152e6}
+# DRAM bytes (read + write) of one k_fused launch from an ncu capture, keyed by
+# (config, envs, threads per env) and stored with the hash of the step kernel's
+# sources it was captured on; a launch of any other build reports null.
+FUSED_TRAFFIC = {}
+KERNEL_SOURCES = ("msh.cu", "msh_stages.cuh", "msh_collide.cuh", "msh_math.cuh")
 WORKLOADS = {1: "falling spheres over static boxes", 2: "fixed-base arm and gripper at a counter",
              3: "apartment batch of uneven size with a mobile manipulator",
              4: "arm pushing a goal box on a table", 5: "scale batch, 32 objects and 50 static boxes per env",
@@ -129,34 +130,49 @@ def row_count(scene, contact_count):
     return int(3 * np.asarray(contact_count).sum() + joint_rows)
 
 
+def kernel_hash() -> str:
+    """Hash of the sources the fused step kernel is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    for n in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2412_13211_b300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def workload_config(args, scene, cfg):
+    """The workload a line measures (identical in both arms)."""
+    return {"workload": f"config{args.config}: {WORKLOADS.get(args.config, 'batch')}, {scene.num_envs} envs",
+            "envs": scene.num_envs, "bodies": scene.num_bodies, "static_boxes": scene.num_statics,
+            "joints": scene.num_joints, "dt": cfg.dt, "substeps": cfg.substeps, "iterations": cfg.iterations,
+            "solver": "coloured PGS",
+            "l2": "GPU arm: flushed between timed steps (256 MB write); the CPU arm has no GPU cache"}
+
+
 def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, over the whole batch: the
+    warm-up steps in one call, then the K timed steps in one call (each env
+    runs its steps inside one OpenMP task)."""
     import oracle
     from paper_2412_13211_b300 import scenes
     if rank != 0:
         return
     scene, cfg = scenes.make_config(args.config, num_envs=args.envs)
-    n = min(args.ref_sample, scene.num_envs)
-    sample = np.linspace(0, scene.num_envs - 1, n).astype(int)
-    sub = scene.subset(sample)
-    tg = sub.target_walk(args.steps + args.warmup)
-    st = sub.state()
+    tg = scene.target_walk(args.steps + args.warmup)
     threads = os.cpu_count() or 1
-    for w in range(args.warmup):
-        st, _ = oracle.step(sub, cfg, st, tg[w:w + 1], 1, "f32", threads=threads)
+    st, _ = oracle.step(scene, cfg, scene.state(), tg[:args.warmup], args.warmup, "f32", threads=threads)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        st, _ = oracle.step(sub, cfg, st, tg[args.warmup + k:args.warmup + k + 1], 1, "f32", threads=threads)
+    oracle.step(scene, cfg, st, tg[args.warmup:], args.steps, "f32", threads=threads)
     dt = time.perf_counter() - t0
-    value = n * args.steps / dt
+    value = scene.num_envs * args.steps / dt
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"config{args.config}: {WORKLOADS.get(args.config, 'batch')}, {scene.num_envs} envs",
-                       "envs": scene.num_envs,
-                       "sampled_envs": n, "substeps": cfg.substeps, "iterations": cfg.iterations},
+            "config": workload_config(args, scene, cfg),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{n} of {scene.num_envs} envs per step, FP32 oracle, OpenMP over envs"},
+                             "sample": f"all {scene.num_envs} envs x {args.steps} steps after {args.warmup} "
+                                       f"warm-up steps, FP32 oracle, OpenMP over envs"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -393,7 +409,6 @@ def main():
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--threads-per-env", type=int, default=0)
-    ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
@@ -549,23 +564,28 @@ def main():
     alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12     # FP32 FMA lanes x clock, TFLOP/s
     achieved_tf = flops_step / (t_step / 1e3) / 1e12
     achieved_gbs = bytes_step / (t_step / 1e3) / 1e9
-    traffic = FUSED_TRAFFIC.get((args.config, scene.num_envs, tpe)) if form == "fused" else None
+    khash = kernel_hash()
+    cap = FUSED_TRAFFIC.get((args.config, scene.num_envs, tpe)) if form == "fused" else None
+    traffic = cap[1] if cap and cap[0] == khash else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"config{args.config}: {WORKLOADS.get(args.config, 'batch')}, {scene.num_envs} envs",
-                   "envs": scene.num_envs, "bodies": scene.num_bodies, "static_boxes": scene.num_statics,
-                   "joints": scene.num_joints, "dt": cfg.dt, "substeps": cfg.substeps,
-                   "iterations": cfg.iterations, "solver": "coloured PGS", "form": f"{form} (autotuned) + CUDA graph",
-                   "threads_per_env": tpe, "workspace_bytes_per_env": sim.workspace_bytes,
-                   "tuning_ms_per_step": {k: round(v, 4) for k, v in tuning["ms"].items()},
-                   "l2": "flushed between timed steps (256 MB write)", "contact_points": int(det["contact_count"].sum()),
-                   "rows_per_substep": rows},
+        "config": workload_config(args, scene, cfg),
+        "implementation": {"form": f"{form} (autotuned) + CUDA graph", "threads_per_env": tpe,
+                           "workspace_bytes_per_env": sim.workspace_bytes,
+                           "tuning_ms_per_step": {k: round(v, 4) for k, v in tuning["ms"].items()},
+                           "contact_points": int(det["contact_count"].sum()), "rows_per_substep": rows,
+                           "kernel_sources_hash": khash},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved_tf / alu_peak, "traffic": traffic,
-                     "note": f"FP32 peak = 148 SMs x 128 lanes x 2 x {sm_max:.0f} MHz; achieved = {FLOP_ROW} flop x "
-                             f"solver rows x substeps x iterations / fused-kernel step time"},
+                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                             "peak_kind": peak_kind, "algorithmic_bytes_per_step": bytes_step},
+                     "note": f"FP32 peak = 148 SMs x 128 lanes x 2 x {sm_max:.0f} MHz (derived, not measured); "
+                             f"achieved = {FLOP_ROW} flop x solver rows x substeps x iterations / fused-kernel step "
+                             f"time; hbm = algorithmic bytes per step / step time against the measured copy "
+                             f"bandwidth; traffic = ncu DRAM bytes of one launch of this exact kernel build "
+                             f"(null when the sources changed since the capture)"},
         "roofline_hbm": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved_gbs / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_step": bytes_step},
