@@ -88,9 +88,85 @@ template <int N> inline Dual<N> atan2_(const Dual<N>& y, const Dual<N>& x) {
   double den = x.v * x.v + y.v * y.v;
   for (int i = 0; i < N; ++i) r.d[i] = (x.v * y.d[i] - y.v * x.d[i]) / den;
   return r; }
+// Reverse mode (the basic operator-overloading scheme of Griewank and
+// Walther, "Evaluating Derivatives", 2nd ed., Ch. 3 and 6): every result of an
+// arithmetic operation on a Rev is a node of the calling thread's tape that
+// stores the local partial derivatives with respect to its operands (at most
+// two); a sweep over the tape from the last node to the first accumulates the
+// adjoints of all nodes. The primal value has its own type P: with P = float
+// the primal arithmetic is exactly the FP32 oracle's (same operations in the
+// same order), so every branch decision equals the FP32 oracle's; partials and
+// adjoints are carried in double. Constants carry id -1 and record nothing.
+struct RevNode { int a, b; double da, db; };
+struct RevTape {
+  std::vector<RevNode> nodes;
+  std::vector<double> adj;
+  int push(int a, double da, int b, double db) {
+    RevNode n; n.a = a; n.b = b; n.da = da; n.db = db;
+    nodes.push_back(n);
+    return (int)nodes.size() - 1;
+  }
+  // adjoints of every node, seeded beforehand through adj (sized by seed())
+  void seed(int id, double w) {
+    if (id < 0) return;
+    if (adj.size() != nodes.size()) adj.assign(nodes.size(), 0.0);
+    adj[id] += w;
+  }
+  void sweep() {
+    if (adj.size() != nodes.size()) adj.assign(nodes.size(), 0.0);
+    for (int i = (int)nodes.size() - 1; i >= 0; --i) {
+      const double w = adj[i];
+      if (w == 0.0) continue;
+      const RevNode& n = nodes[i];
+      if (n.a >= 0) adj[n.a] += n.da * w;
+      if (n.b >= 0) adj[n.b] += n.db * w;
+    }
+  }
+  double get(int id) const { return id >= 0 && id < (int)adj.size() ? adj[id] : 0.0; }
+  void clear() { nodes.clear(); adj.clear(); }
+};
+inline RevTape*& rev_tape() { static thread_local RevTape* t = nullptr; return t; }
+
+template <class P> struct Rev {
+  P v;
+  int id;
+  Rev() : v(0), id(-1) {}
+  Rev(double x) : v(P(x)), id(-1) {}  // NOLINT
+  static Rev make(P value, int a, double da, int b, double db) {
+    Rev r; r.v = value;
+    r.id = (a < 0 && b < 0) ? -1 : rev_tape()->push(a, da, b, db);
+    return r;
+  }
+  static Rev leaf(P value) { Rev r; r.v = value; r.id = rev_tape()->push(-1, 0.0, -1, 0.0); return r; }
+};
+template <class P> inline Rev<P> operator+(const Rev<P>& a, const Rev<P>& b) {
+  return Rev<P>::make(a.v + b.v, a.id, 1.0, b.id, 1.0); }
+template <class P> inline Rev<P> operator-(const Rev<P>& a, const Rev<P>& b) {
+  return Rev<P>::make(a.v - b.v, a.id, 1.0, b.id, -1.0); }
+template <class P> inline Rev<P> operator-(const Rev<P>& a) { return Rev<P>::make(-a.v, a.id, -1.0, -1, 0.0); }
+template <class P> inline Rev<P> operator*(const Rev<P>& a, const Rev<P>& b) {
+  return Rev<P>::make(a.v * b.v, a.id, (double)b.v, b.id, (double)a.v); }
+template <class P> inline Rev<P> operator/(const Rev<P>& a, const Rev<P>& b) {
+  const double bv = b.v;
+  return Rev<P>::make(a.v / b.v, a.id, 1.0 / bv, b.id, -(double)a.v / (bv * bv)); }
+template <class P> inline bool operator<(const Rev<P>& a, const Rev<P>& b) { return a.v < b.v; }
+template <class P> inline bool operator>(const Rev<P>& a, const Rev<P>& b) { return a.v > b.v; }
+template <class P> inline bool operator<=(const Rev<P>& a, const Rev<P>& b) { return a.v <= b.v; }
+template <class P> inline bool operator>=(const Rev<P>& a, const Rev<P>& b) { return a.v >= b.v; }
+template <class P> inline bool operator==(const Rev<P>& a, const Rev<P>& b) { return a.v == b.v; }
+template <class P> inline bool operator!=(const Rev<P>& a, const Rev<P>& b) { return a.v != b.v; }
+template <class P> inline Rev<P> sqrt_(const Rev<P>& a) {
+  const P r = std::sqrt(a.v);
+  return Rev<P>::make(r, a.id, r > P(0) ? 0.5 / (double)r : 0.0, -1, 0.0); }
+template <class P> inline Rev<P> abs_(const Rev<P>& a) { return a.v < P(0) ? -a : a; }
+template <class P> inline Rev<P> atan2_(const Rev<P>& y, const Rev<P>& x) {
+  const double xv = x.v, yv = y.v, den = xv * xv + yv * yv;
+  return Rev<P>::make(std::atan2(y.v, x.v), y.id, xv / den, x.id, -yv / den); }
+
 inline double val(float x) { return x; }
 inline double val(double x) { return x; }
 template <int N> inline double val(const Dual<N>& a) { return a.v; }
+template <class P> inline double val(const Rev<P>& a) { return a.v; }
 template <class R> inline bool finite_(const R& x) { return std::isfinite(val(x)); }
 
 template <class R> inline R clampv(R x, R lo, R hi) { return x < lo ? lo : (x > hi ? hi : x); }
@@ -1540,9 +1616,107 @@ int grad_batch(const OracleScene* sc, const OracleCfg* cfg, const double* pos, c
   return 0;
 }
 
+// Reference vector-Jacobian products of ONE step by reverse mode. For env e
+// the step maps (state x, joint targets u, body masses m) to the state x';
+// given the adjoint w of x' (seed, double) it returns w^T dx'/dx, w^T dx'/du
+// and w^T dx'/dm (each written, not added), along with x' itself. Every
+// scalar of the step is a Rev<P>: inputs are tape leaves, the step runs as in
+// step_env, the outputs are seeded with w and the tape is swept once. Branch
+// decisions (contact set and features, colouring, clamps, bias cases) follow
+// the primal values, so the result is the derivative of the piecewise-smooth
+// step on the piece that contains this point; with P = float the primal and
+// hence every decision is the FP32 oracle's.
+template <class P, class T>
+int vjp_batch(const OracleScene* sc, const OracleCfg* cfg, const T* pos, const T* quat, const T* lv, const T* av,
+              const T* targets, const double* wpos, const double* wquat, const double* wlv, const double* wav,
+              T* opos, T* oquat, T* olv, T* oav, double* gpos, double* gquat, double* glv, double* gav,
+              double* gtg, double* gmass, int32_t* status, int nthreads) {
+  typedef Rev<P> RV;
+  const int E = sc->num_envs;
+  const int B = sc->body_off[E];
+  const int md = sc->max_dof > 0 ? sc->max_dof : 1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int e = 0; e < E; ++e) {
+    RevTape tape;
+    rev_tape() = &tape;
+    const int b0 = sc->body_off[e], D = sc->body_off[e + 1] - b0;
+    std::vector<RV> mass(B);
+    for (int i = 0; i < D; ++i) mass[b0 + i] = RV::leaf(P(sc->body_mass[b0 + i]));
+    EnvState<RV> S;
+    load_env<RV, T>(*sc, e, pos, quat, lv, av, mass.data(), S);
+    std::vector<int> in_id(13 * D);   // tape ids of the state leaves
+    for (int i = 0; i < D; ++i) {
+      Body<RV>& b = S.body[i];
+      RV* xs[13] = {&b.x.x, &b.x.y, &b.x.z, &b.q.w, &b.q.x, &b.q.y, &b.q.z, &b.v.x, &b.v.y, &b.v.z,
+                    &b.w.x, &b.w.y, &b.w.z};
+      for (int k = 0; k < 13; ++k) {
+        *xs[k] = RV::leaf(xs[k]->v);
+        in_id[13 * i + k] = xs[k]->id;
+      }
+    }
+    std::vector<RV> tg(md);
+    for (int k = 0; k < md; ++k)
+      tg[k] = RV::leaf(P(targets && sc->max_dof > 0 ? (double)targets[(size_t)e * sc->max_dof + k] : 0.0));
+    const int st = step_env(S, *cfg, tg.data(), (Detect<RV>*)nullptr);
+    for (int i = 0; i < D; ++i) {
+      const int g = b0 + i;
+      const Body<RV>& b = S.body[i];
+      const RV* ys[13] = {&b.x.x, &b.x.y, &b.x.z, &b.q.w, &b.q.x, &b.q.y, &b.q.z, &b.v.x, &b.v.y, &b.v.z,
+                          &b.w.x, &b.w.y, &b.w.z};
+      const double w[13] = {wpos[3 * g], wpos[3 * g + 1], wpos[3 * g + 2], wquat[4 * g], wquat[4 * g + 1],
+                            wquat[4 * g + 2], wquat[4 * g + 3], wlv[3 * g], wlv[3 * g + 1], wlv[3 * g + 2],
+                            wav[3 * g], wav[3 * g + 1], wav[3 * g + 2]};
+      for (int k = 0; k < 13; ++k) tape.seed(ys[k]->id, w[k]);
+      if (opos) {
+        opos[3 * g] = T(ys[0]->v); opos[3 * g + 1] = T(ys[1]->v); opos[3 * g + 2] = T(ys[2]->v);
+        for (int k = 0; k < 4; ++k) oquat[4 * g + k] = T(ys[3 + k]->v);
+        for (int k = 0; k < 3; ++k) { olv[3 * g + k] = T(ys[7 + k]->v); oav[3 * g + k] = T(ys[10 + k]->v); }
+      }
+    }
+    tape.sweep();
+    for (int i = 0; i < D; ++i) {
+      const int g = b0 + i;
+      gmass[g] = tape.get(mass[g].id);
+      const int* id = &in_id[13 * i];
+      for (int k = 0; k < 3; ++k) gpos[3 * g + k] = tape.get(id[k]);
+      for (int k = 0; k < 4; ++k) gquat[4 * g + k] = tape.get(id[3 + k]);
+      for (int k = 0; k < 3; ++k) { glv[3 * g + k] = tape.get(id[7 + k]); gav[3 * g + k] = tape.get(id[10 + k]); }
+    }
+    if (gtg && sc->max_dof > 0)
+      for (int k = 0; k < sc->max_dof; ++k) gtg[(size_t)e * sc->max_dof + k] = tape.get(tg[k].id);
+    if (status) status[e] = st;
+    rev_tape() = nullptr;
+  }
+  return 0;
+}
+
 }  // namespace orc
 
 extern "C" {
+
+// One step's vector-Jacobian products by reverse mode (see vjp_batch): the
+// FP32 form (primal arithmetic and decisions of the FP32 oracle, adjoints in
+// double) and the FP64 form. State arrays [B][3|4], targets [E][max_dof];
+// seeds w* and outputs g* are double; gtg [E][max_dof] and gmass [B] are
+// written; o* receive the stepped state (may be NULL together).
+int oracle_vjp_f32(const OracleScene* sc, const OracleCfg* cfg, const float* pos, const float* quat, const float* lv,
+                   const float* av, const float* targets, const double* wpos, const double* wquat, const double* wlv,
+                   const double* wav, float* opos, float* oquat, float* olv, float* oav, double* gpos, double* gquat,
+                   double* glv, double* gav, double* gtg, double* gmass, int32_t* status, int nthreads) {
+  return orc::vjp_batch<float, float>(sc, cfg, pos, quat, lv, av, targets, wpos, wquat, wlv, wav, opos, oquat, olv,
+                                      oav, gpos, gquat, glv, gav, gtg, gmass, status, nthreads);
+}
+int oracle_vjp_f64(const OracleScene* sc, const OracleCfg* cfg, const double* pos, const double* quat,
+                   const double* lv, const double* av, const double* targets, const double* wpos, const double* wquat,
+                   const double* wlv, const double* wav, double* opos, double* oquat, double* olv, double* oav,
+                   double* gpos, double* gquat, double* glv, double* gav, double* gtg, double* gmass, int32_t* status,
+                   int nthreads) {
+  return orc::vjp_batch<double, double>(sc, cfg, pos, quat, lv, av, targets, wpos, wquat, wlv, wav, opos, oquat, olv,
+                                        oav, gpos, gquat, glv, gav, gtg, gmass, status, nthreads);
+}
 
 int oracle_step_f32(const OracleScene* sc, const OracleCfg* cfg, float* pos, float* quat, float* lv,
                     float* av, const float* targets, int nsteps, int32_t* status, int nthreads) {

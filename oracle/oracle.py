@@ -71,6 +71,9 @@ def load():
         lib.oracle_grad_f64.argtypes = [P, P, P, P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, C.c_int]
         lib.oracle_grad_f64.restype = C.c_int
         lib.oracle_max_threads.restype = C.c_int
+        for fn in (lib.oracle_vjp_f32, lib.oracle_vjp_f64):
+            fn.argtypes = [P] * 22 + [C.c_int]
+            fn.restype = C.c_int
         for fn in (lib.oracle_render_depth_f32, lib.oracle_render_depth_f64):
             fn.argtypes = [P, P, P, P, P, C.c_int]
             fn.restype = C.c_int
@@ -312,6 +315,27 @@ def loss_and_directional(scene, cfg, state, targets, nsteps, goal_body, goal_pos
     return loss, dloss, status
 
 
+def step_f64x(scene, cfg, state, targets, nsteps, mass=None, threads: int = 0):
+    """FP64 rollout whose joint targets [nsteps,E,max_dof] and optional body
+    masses [B] are taken in double (exact perturbations for finite
+    differences). Returns (new_state, status)."""
+    lib = load()
+    E = scene.num_envs
+    md = max(scene.max_dof, 1)
+    st = [np.ascontiguousarray(a, dtype=np.float64).copy() for a in state]
+    tg = np.ascontiguousarray(np.zeros((nsteps, E, md)) if targets is None else targets,
+                              dtype=np.float64).reshape(-1, E, md)
+    m = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
+    status = np.zeros(E, np.int32)
+    keep = _Keep(scene)
+    c = _cfg(cfg)
+    rc = lib.oracle_step_f64x(C.byref(keep.struct), C.byref(c), _ptr(st[0]), _ptr(st[1]), _ptr(st[2]),
+                              _ptr(st[3]), _ptr(tg), _ptr(m), int(nsteps), _ptr(status), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle step failed: {rc}")
+    return tuple(st), status
+
+
 def loss_value(scene, cfg, state, targets, nsteps, goal_body, goal_pos, mass=None, threads: int = 0):
     """FP64 loss per env after `nsteps` steps; targets [nsteps,E,max_dof] and
     optional masses [B] are taken in double (for finite differences)."""
@@ -335,3 +359,89 @@ def loss_value(scene, cfg, state, targets, nsteps, goal_body, goal_pos, mass=Non
             d = st[0][scene.body_off[e] + g] - np.asarray(goal_pos[e], np.float64)
             L[e] = d @ d
     return L, status
+
+
+@dataclass
+class OracleVJP:
+    """Adjoints of one step's inputs for a seed on its output (all float64)."""
+    pos: np.ndarray       # [B,3]
+    quat: np.ndarray      # [B,4] (all four components, as the step reads them)
+    linvel: np.ndarray    # [B,3]
+    angvel: np.ndarray    # [B,3]
+    targets: np.ndarray   # [E,max_dof]
+    mass: np.ndarray      # [B]
+    out: tuple            # the stepped state (pos, quat, linvel, angvel)
+    status: np.ndarray    # [E]
+
+
+def step_vjp(scene, cfg, state, targets, seed, precision: str = "f32", threads: int = 0) -> OracleVJP:
+    """One step from `state` with joint targets [E, max_dof], and the
+    vector-Jacobian products of the seed (pos, quat, linvel, angvel adjoints of
+    the stepped state, float64) with respect to the step's state, targets and
+    body masses, by reverse mode. precision "f32": the FP32 oracle's primal
+    arithmetic and branch decisions (adjoints in double); "f64": the FP64
+    oracle's."""
+    lib = load()
+    dt = np.float32 if precision == "f32" else np.float64
+    E, B = scene.num_envs, scene.num_bodies
+    md = max(scene.max_dof, 1)
+    st = [np.ascontiguousarray(a, dtype=dt) for a in state]
+    tg = np.ascontiguousarray(np.zeros((E, md)) if targets is None else targets, dtype=dt).reshape(E, -1)
+    if scene.max_dof > 0:
+        assert tg.shape[1] == scene.max_dof
+    w = [np.ascontiguousarray(a, dtype=np.float64) for a in seed]
+    out = [np.zeros_like(a) for a in st]
+    g = [np.zeros(a.shape, np.float64) for a in st]
+    gtg = np.zeros((E, max(scene.max_dof, 1)), np.float64)
+    gm = np.zeros(B, np.float64)
+    status = np.zeros(E, np.int32)
+    keep = _Keep(scene)
+    c = _cfg(cfg)
+    fn = lib.oracle_vjp_f32 if precision == "f32" else lib.oracle_vjp_f64
+    rc = fn(C.byref(keep.struct), C.byref(c), *[_ptr(a) for a in st], _ptr(tg), *[_ptr(a) for a in w],
+            *[_ptr(a) for a in out], *[_ptr(a) for a in g], _ptr(gtg), _ptr(gm), _ptr(status), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle vjp failed: {rc}")
+    return OracleVJP(g[0], g[1], g[2], g[3], gtg[:, :scene.max_dof], gm, tuple(out), status)
+
+
+def trajectory(scene, cfg, state, targets, nsteps, precision: str = "f32", threads: int = 0):
+    """The states x_0 .. x_nsteps of a rollout, one oracle step at a time."""
+    xs = [tuple(np.ascontiguousarray(a, np.float32 if precision == "f32" else np.float64) for a in state)]
+    st = np.zeros(scene.num_envs, np.int32)
+    for t in range(nsteps):
+        nxt, s = step(scene, cfg, xs[-1], None if targets is None else targets[t:t + 1], 1, precision, threads)
+        xs.append(nxt)
+        st |= s
+    return xs, st
+
+
+def goal_seed(scene, x_pos, goal_body, goal_pos):
+    """Adjoint of the final state for the loss sum_e |x_goal(e) - goal(e)|^2."""
+    B = scene.num_bodies
+    w = [np.zeros((B, 3)), np.zeros((B, 4)), np.zeros((B, 3)), np.zeros((B, 3))]
+    for e in range(scene.num_envs):
+        gb = int(goal_body[e])
+        if gb >= 0:
+            i = scene.body_off[e] + gb
+            w[0][i] = 2.0 * (np.asarray(x_pos[i], np.float64) - np.asarray(goal_pos[e], np.float64))
+    return w
+
+
+def rollout_grad(scene, cfg, state, targets, nsteps, seed_final, precision: str = "f32", threads: int = 0):
+    """Reverse-mode gradient of a rollout: the step adjoints chained backwards
+    along the oracle's own trajectory. seed_final: the adjoint of the last
+    state (or a callable of that state returning it). Returns (grad of the
+    initial state (4 arrays), grad of targets [nsteps,E,max_dof], grad of the
+    masses [B], the trajectory, status)."""
+    xs, st = trajectory(scene, cfg, state, targets, nsteps, precision, threads)
+    w = seed_final(xs[-1]) if callable(seed_final) else [np.asarray(a, np.float64) for a in seed_final]
+    gtg = np.zeros((nsteps, scene.num_envs, scene.max_dof))
+    gm = np.zeros(scene.num_bodies)
+    for t in range(nsteps - 1, -1, -1):
+        r = step_vjp(scene, cfg, xs[t], None if targets is None else targets[t], w, precision, threads)
+        w = [r.pos, r.quat, r.linvel, r.angvel]
+        gtg[t] = r.targets
+        gm += r.mass
+        st |= r.status
+    return w, gtg, gm, xs, st
