@@ -109,11 +109,11 @@ struct RevTape {
   // adjoints of every node, seeded beforehand through adj (sized by seed())
   void seed(int id, double w) {
     if (id < 0) return;
-    if (adj.size() != nodes.size()) adj.assign(nodes.size(), 0.0);
+    if (adj.size() != nodes.size()) adj.resize(nodes.size(), 0.0);
     adj[id] += w;
   }
   void sweep() {
-    if (adj.size() != nodes.size()) adj.assign(nodes.size(), 0.0);
+    if (adj.size() != nodes.size()) adj.resize(nodes.size(), 0.0);
     for (int i = (int)nodes.size() - 1; i >= 0; --i) {
       const double w = adj[i];
       if (w == 0.0) continue;
@@ -170,6 +170,13 @@ template <class P> inline double val(const Rev<P>& a) { return a.v; }
 template <class R> inline bool finite_(const R& x) { return std::isfinite(val(x)); }
 
 template <class R> inline R clampv(R x, R lo, R hi) { return x < lo ? lo : (x > hi ? hi : x); }
+// The solver's impulse clamp to [lo, hi]: at an exact tie with a bound the
+// bound is returned (the clamp counts as active). The value is the same
+// either way, but derivatives then follow the bound; for a zero-width
+// interval (lo == hi, e.g. a friction limit mu * lambda_n with lambda_n = 0)
+// that is the only consistent choice, since the clamped impulse cannot move
+// away from it.
+template <class R> inline R clamp_active(R x, R lo, R hi) { return x <= lo ? lo : (x >= hi ? hi : x); }
 template <class R> inline R maxv(R a, R b) { return a > b ? a : b; }
 template <class R> inline R minv(R a, R b) { return a < b ? a : b; }
 
@@ -1045,8 +1052,8 @@ template <class R> struct Solver {
     R dl = -r.m * (acc + r.bias + r.gamma * r.lam);
     R nl = r.lam + dl;
     if (r.kind == ROW_UNILATERAL) nl = maxv(nl, R(0));
-    else if (r.kind == ROW_FRICTION) { R lim = r.mu * rows[r.ref].lam; nl = clampv(nl, -lim, lim); }
-    else if (r.kind == ROW_SOFT) nl = clampv(nl, r.lo, r.hi);
+    else if (r.kind == ROW_FRICTION) { R lim = r.mu * rows[r.ref].lam; nl = clamp_active(nl, -lim, lim); }
+    else if (r.kind == ROW_SOFT) nl = clamp_active(nl, r.lo, r.hi);
     dl = nl - r.lam;
     r.lam = nl;
     if (r.a >= 0) {
@@ -1640,7 +1647,8 @@ int vjp_batch(const OracleScene* sc, const OracleCfg* cfg, const T* pos, const T
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int e = 0; e < E; ++e) {
-    RevTape tape;
+    static thread_local RevTape tape;   // reused by the thread's envs (keeps its capacity)
+    tape.clear();
     rev_tape() = &tape;
     const int b0 = sc->body_off[e], D = sc->body_off[e + 1] - b0;
     std::vector<RV> mass(B);

@@ -120,15 +120,18 @@ def _fd(sc, c, tg, nsteps, dirs, eps):
     return np.array(out)
 
 
+@pytest.mark.parametrize("mode", [0, 1], ids=["coloured", "jacobi"])
 @pytest.mark.parametrize("which", [0, 1, 2], ids=["velocity", "targets", "mass"])
-def test_dual_gradient_matches_central_differences(which, record_property):
+def test_dual_gradient_matches_central_differences(which, mode, record_property):
     """Differentiation workload (arm pushing a box on a table), 8-step
-    horizon; directions in the initial velocities, the joint-target sequence
-    or the masses. Central differences of the FP64 oracle at eps = 1e-4 and
-    eps/4: envs whose two differences disagree by more than 1% are not smooth
-    within +-eps (a contact or clamp switches) and are excluded; the rest
-    match the dual derivative to 2%. Counts are reported."""
-    sc, c = S.make_config(4, num_envs=16)
+    horizon, in both solver modes; directions in the initial velocities, the
+    joint-target sequence or the masses. Central differences of the FP64
+    oracle at eps = 1e-4 and eps/4: envs whose two differences disagree by
+    more than 1% are not smooth within +-eps (a contact or clamp switches)
+    and are excluded; the rest match the dual derivative to 2%. Counts are
+    reported."""
+    sc, c = S.make_config(4, num_envs=32)
+    c.mode = mode
     nsteps = 8
     tg, dvel, dtg, dmass = _fd_case(sc, c, nsteps, 5)
     dirs = (dvel[which:which + 1], dtg[which:which + 1], dmass[which:which + 1])
