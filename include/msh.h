@@ -333,7 +333,7 @@ int msh_render_depth(msh_handle* h, const msh_state* st, float* depth, void* str
 /*
  * Differentiation (reverse mode). msh_set_tape(h, n), n > 0, makes room for
  * n recorded steps (reusing a large enough tape) and starts recording
- * (coloured solver and zero restitution only); n = 0 stops recording and
+ * (either solver mode; zero restitution only); n = 0 stops recording and
  * keeps the memory, n = -1 stops and frees it. Setting the tape drops any
  * recorded steps. While recording, every msh_step records the step (start state, per-substep poses and
  * velocities, the lambdas after every sweep, the targets) into the next slot;

@@ -262,7 +262,14 @@ __global__ void k_bwd_rows(Params p, AdjParams q, int s) {
     float dI[3] = {inv.y, inv.z, inv.w}, W6[6];
     world_inv_inertia<float>(qq, dI, W6);
     w.bIw0[i] = make_float4(W6[0], W6[1], W6[2], W6[3]);
-    w.bIw1[i] = make_float4(W6[4], W6[5], 1.f, 0.f);
+    // mass split: the body's constraint count in the Jacobi solve (as the
+    // forward's colouring stage sets it), 1 for coloured PGS
+    float split = 1.f;
+    if (p.mode == MODE_JACOBI) {
+      const int n = b.a.inc_off[i + 1] - b.a.inc_off[i];
+      split = (float)(n > 0 ? n : 1);
+    }
+    w.bIw1[i] = make_float4(W6[4], W6[5], split, 0.f);
   }
   reverse_integrate(p, e, b.a, st);
   gsync(e);
@@ -339,7 +346,8 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
       lpr = it > 0 ? lbuf[(it - 1) % 3] : nullptr;
     }
     gsync(e);
-    reverse_sweep(p, e, w, a, lit, lpr);
+    if (p.mode == MODE_JACOBI) reverse_sweep_jacobi(p, e, w, a, lit, lpr);
+    else reverse_sweep(p, e, w, a, lit, lpr);
     if (lams) cp_async_wait_all();
   }
   if (bodies) {
@@ -1250,8 +1258,6 @@ int msh_detect(msh_handle* h, const msh_state* st, float* aabb_body, float* aabb
 int msh_set_tape(msh_handle* h, int32_t max_steps) {
   if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
   if (max_steps < -1) return fail(MSH_ERR_INVALID_ARG, "max_steps must be >= -1");
-  if (max_steps > 0 && h->cfg.mode != MSH_MODE_COLOURED)
-    return fail(MSH_ERR_UNSUPPORTED, "the adjoint supports the coloured solver only");
   if (max_steps > 0 && h->cfg.restitution > 0.f)
     return fail(MSH_ERR_UNSUPPORTED, "the adjoint supports restitution 0 only");
   h->tape_count = 0;

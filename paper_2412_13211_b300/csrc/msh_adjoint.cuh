@@ -8,6 +8,9 @@
 // Gauss-Seidel sweeps.
 //   * integration: hand-written reverse of x += h v and of the normalised
 //     quaternion update;
+//   * mass-split Jacobi: per sweep, the iteration-start velocities from the
+//     recorded lambdas, every constraint's rows reversed on its local copies,
+//     and the copies' adjoints summed per body in constraint order;
 //   * coloured PGS: the sweeps run backwards (iterations, then colours in
 //     reverse order, rows of a constraint in reverse order); velocities before
 //     each update are rebuilt from the velocities after it and the recorded
@@ -251,31 +254,59 @@ __device__ __forceinline__ void load_rev_row(const AWs& a, int r, const float* l
 // Reverse of one row update on the loaded row `x` (writes its adjoints back
 // to row r). `gfric` receives the adjoint this row (a friction row at its
 // limit) sends to its normal row's lambda; the caller adds it when it
-// reaches that row.
+// reaches that row. JAC (mass-split Jacobi): the update moves the
+// constraint's local velocity copies through the split inverse masses (sa,
+// sb times the true ones) and adds the true-mass change to the bodies'
+// iteration sums, whose adjoint is G; v and g are the local copies and
+// their adjoints.
+template <bool JAC>
 __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, float ima, float imb, BodyVel& v,
-                                            BodyAdj& g, const RevRow& x, float mu, float& gfric) {
+                                            BodyAdj& g, const RevRow& x, float mu, float& gfric, float sa = 1.f,
+                                            float sb = 1.f, const BodyAdj* GS = nullptr) {
   V3<float> la = f3(x.r0), aa = f3(x.r1), ab = f3(x.r2), Ia = f3(x.r3), Ib = f3(x.r4);
   const float m = x.r0.w, bias = x.r1.w, gamma = x.r2.w, clamp = x.r4.w;
   const float lam_after = x.lam_after, lam_before = x.lam_before;
   const float D = lam_after - lam_before;
   // velocities before the update
-  if (A >= 0) { v.va = v.va - la * (ima * D); v.wa = v.wa - Ia * D; }
-  if (B >= 0) { v.vb = v.vb + la * (imb * D); v.wb = v.wb - Ib * D; }
+  if (JAC) {
+    if (A >= 0) { v.va = v.va - la * ((sa * ima) * D); v.wa = v.wa - Ia * (sa * D); }
+    if (B >= 0) { v.vb = v.vb + la * ((sb * imb) * D); v.wb = v.wb - Ib * (sb * D); }
+  } else {
+    if (A >= 0) { v.va = v.va - la * (ima * D); v.wa = v.wa - Ia * D; }
+    if (B >= 0) { v.vb = v.vb + la * (imb * D); v.wb = v.wb - Ib * D; }
+  }
   V3<float> gla = f3(x.g0), gaa = f3(x.g1), gab = f3(x.g2), gIa = f3(x.g3), gIb = f3(x.g4);
   float gm = x.g0.w, gbias = x.g1.w, glam = x.g2.w, gima = x.g3.w, gimb = x.g4.w;
   // adjoint of D through the velocity update
   float gD = 0.f;
-  if (A >= 0) {
-    gD += ima * dot(la, g.va) + dot(Ia, g.wa);
-    gla = gla + g.va * (ima * D);
-    gIa = gIa + g.wa * D;
-    gima += dot(la, g.va) * D;        // adjoint of 1/m_a (kept in the row, moved to the body later)
-  }
-  if (B >= 0) {
-    gD += -imb * dot(la, g.vb) + dot(Ib, g.wb);
-    gla = gla - g.vb * (imb * D);
-    gIb = gIb + g.wb * D;
-    gimb += -dot(la, g.vb) * D;       // adjoint of 1/m_b
+  if (JAC) {
+    if (A >= 0) {
+      const float lva = dot(la, g.va), LVa = dot(la, GS->va);
+      gD += (sa * ima) * lva + sa * dot(Ia, g.wa) + ima * LVa + dot(Ia, GS->wa);
+      gla = gla + (g.va * (sa * ima) + GS->va * ima) * D;
+      gIa = gIa + (g.wa * sa + GS->wa) * D;
+      gima += (sa * lva + LVa) * D;
+    }
+    if (B >= 0) {
+      const float lvb = dot(la, g.vb), LVb = dot(la, GS->vb);
+      gD += -(sb * imb) * lvb + sb * dot(Ib, g.wb) - imb * LVb + dot(Ib, GS->wb);
+      gla = gla - (g.vb * (sb * imb) + GS->vb * imb) * D;
+      gIb = gIb + (g.wb * sb + GS->wb) * D;
+      gimb += -(sb * lvb + LVb) * D;
+    }
+  } else {
+    if (A >= 0) {
+      gD += ima * dot(la, g.va) + dot(Ia, g.wa);
+      gla = gla + g.va * (ima * D);
+      gIa = gIa + g.wa * D;
+      gima += dot(la, g.va) * D;        // adjoint of 1/m_a (kept in the row, moved to the body later)
+    }
+    if (B >= 0) {
+      gD += -imb * dot(la, g.vb) + dot(Ib, g.wb);
+      gla = gla - g.vb * (imb * D);
+      gIb = gIb + g.wb * D;
+      gimb += -dot(la, g.vb) * D;       // adjoint of 1/m_b
+    }
   }
   const float a_after = glam + gD;
   float glam_before = -gD;
@@ -319,9 +350,14 @@ __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, f
 // set-up reverse), and of the manifold's inverse inertias and inverse masses
 // `mi` (gIw_a[6], gIw_b[6], g(1/m_a), g(1/m_b)). A friction row at its limit
 // mu * lambda_n sends its adjoint to lambda_n.
+// JAC: as in reverse_row, the local velocity copies move through the split
+// inverse masses and the bodies' iteration sums (adjoint G) through the true
+// ones.
+template <bool JAC>
 __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool bdyn, float ima, float imb,
                                               const Sym3& Iwa, const Sym3& Iwb, BodyVel& v, BodyAdj& g,
-                                              const float* lam_it, const float* lam_prev, float mu, float* mi) {
+                                              const float* lam_it, const float* lam_prev, float mu, float* mi,
+                                              float sa = 1.f, float sb = 1.f, const BodyAdj* GS = nullptr) {
   const float4* P = a.cpar + CPAR_F4 * ci;
   float4* Q = a.cadj + CADJ_F4 * ci;
   const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
@@ -344,26 +380,52 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
   // the point's impulse and the velocities before the point
   const V3<float> Pi = (n * D0 + t1 * D1) + t2 * D2;
   const V3<float> ta = cross(ra, Pi);
-  v.va = v.va + Pi * ima;
-  v.wa = v.wa + smul(Iwa, ta);
   V3<float> tb = v3<float>(0.f, 0.f, 0.f);
-  if (bdyn) {
-    tb = cross(rb, Pi);
-    v.vb = v.vb - Pi * imb;
-    v.wb = v.wb - smul(Iwb, tb);
-  }
-  // adjoint of the impulse's application
-  const V3<float> sa = smul(Iwa, g.wa);
-  V3<float> gP = g.va * (-ima) + cross(ra, sa);
-  gra = gra + cross(sa, Pi);
-  add_sym(mi, g.wa, -ta);
-  mi[12] -= dot(Pi, g.va);
-  if (bdyn) {
-    const V3<float> sb = smul(Iwb, g.wb);
-    gP = gP + g.vb * imb + cross(sb, rb);
-    grb = grb + cross(Pi, sb);
-    add_sym(mi + 6, g.wb, tb);
-    mi[13] += dot(Pi, g.vb);
+  V3<float> gP;
+  if (JAC) {
+    v.va = v.va + Pi * (sa * ima);
+    v.wa = v.wa + smul(Iwa, ta) * sa;
+    if (bdyn) {
+      tb = cross(rb, Pi);
+      v.vb = v.vb - Pi * (sb * imb);
+      v.wb = v.wb - smul(Iwb, tb) * sb;
+    }
+    // adjoint of the impulse's application to the local copies and the sums
+    const V3<float> ewa = g.wa * sa + GS->wa;
+    const V3<float> sI = smul(Iwa, ewa);
+    gP = (g.va * (sa * ima) + GS->va * ima) * (-1.f) + cross(ra, sI);
+    gra = gra + cross(sI, Pi);
+    add_sym(mi, ewa, -ta);
+    mi[12] -= dot(Pi, g.va * sa + GS->va);
+    if (bdyn) {
+      const V3<float> ewb = g.wb * sb + GS->wb;
+      const V3<float> sJ = smul(Iwb, ewb);
+      gP = gP + (g.vb * (sb * imb) + GS->vb * imb) + cross(sJ, rb);
+      grb = grb + cross(Pi, sJ);
+      add_sym(mi + 6, ewb, tb);
+      mi[13] += dot(Pi, g.vb * sb + GS->vb);
+    }
+  } else {
+    v.va = v.va + Pi * ima;
+    v.wa = v.wa + smul(Iwa, ta);
+    if (bdyn) {
+      tb = cross(rb, Pi);
+      v.vb = v.vb - Pi * imb;
+      v.wb = v.wb - smul(Iwb, tb);
+    }
+    // adjoint of the impulse's application
+    const V3<float> sI = smul(Iwa, g.wa);
+    gP = g.va * (-ima) + cross(ra, sI);
+    gra = gra + cross(sI, Pi);
+    add_sym(mi, g.wa, -ta);
+    mi[12] -= dot(Pi, g.va);
+    if (bdyn) {
+      const V3<float> sJ = smul(Iwb, g.wb);
+      gP = gP + g.vb * imb + cross(sJ, rb);
+      grb = grb + cross(Pi, sJ);
+      add_sym(mi + 6, g.wb, tb);
+      mi[13] += dot(Pi, g.vb);
+    }
   }
   float gD0 = dot(n, gP), gD1 = dot(t1, gP), gD2 = dot(t2, gP);
   gd0 = gd0 + gP * D0; gd1 = gd1 + gP * D1; gd2 = gd2 + gP * D2;
@@ -445,7 +507,7 @@ __device__ __forceinline__ void reverse_constraint(const Params& p, const Ws& w,
       const int r_nxt = jrow(k, jnr - 2 - i);
       if (i + 1 < jnr) load_rev_row(a, r_nxt, lam_it, lam_prev, -1, nxt);
       float gfric;
-      reverse_row(a, r_cur, A, B, ima, imb, v, g, cur, 0.f, gfric);
+      reverse_row<false>(a, r_cur, A, B, ima, imb, v, g, cur, 0.f, gfric);
       if (i + 1 < jnr) { cur = nxt; r_cur = r_nxt; }
     }
   } else {
@@ -457,7 +519,7 @@ __device__ __forceinline__ void reverse_constraint(const Params& p, const Ws& w,
     float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
     float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
     for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
-      reverse_point(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
+      reverse_point<false>(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
     MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
     MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
   }
@@ -482,6 +544,144 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
 }
 
 // ---------------------------------------------------------------------------
+// reverse of the mass-split Jacobi sweeps
+// ---------------------------------------------------------------------------
+// A Jacobi sweep: every constraint k copies the iteration-start velocities V
+// of its bodies, updates its rows on the copies through the split inverse
+// masses (the body's constraint count times the true ones), and adds its
+// true-mass velocity change dV_k to the bodies' sums; then every body takes
+// V + sum_k dV_k (constraint order). Reversed in three phases: dV_k from the
+// recorded lambda changes and V = V' - sum_k dV_k; each constraint's rows in
+// reverse on its copies (ending at V + split * dV_k) with the bodies'
+// after-sweep adjoint G as the adjoint of the sums, leaving the adjoint of
+// its copies at the start in the constraint's slot; then G + sum of the slots.
+// The slots are the forward's per-constraint velocity-change array.
+
+// True-mass velocity change of constraint k from its recorded lambda changes.
+__device__ void jacobi_dv(const Params& p, const Ws& w, const AWs& a, int k, int J, const float* lam_it,
+                          const float* lam_prev) {
+  V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  BodyVel d;
+  d.va = z; d.wa = z; d.vb = z; d.wb = z;
+  if (k < J) {
+    const int4 ji = w.jinfo[k];
+    const int A = ji.x;
+    const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = w.bx[ji.y].w;
+    for (int r = 0; r < ji.w; ++r) {
+      const int row = jrow(k, r);
+      const float4* R = a.rows + ROW_F4 * row;
+      const float D = lam_it[row] - (lam_prev ? lam_prev[row] : 0.f);
+      const V3<float> la = f3(R[0]);
+      if (A >= 0) { d.va = d.va + la * (ima * D); d.wa = d.wa + f3(R[3]) * D; }
+      d.vb = d.vb - la * (imb * D);
+      d.wb = d.wb + f3(R[4]) * D;
+    }
+  } else {
+    const int4 mf = man_get(w, k - J);
+    const int A = mf.x, B = mf.y;
+    const float ima = w.bx[A].w, imb = B >= 0 ? w.bx[B].w : 0.f;
+    const Sym3 Iwa = load_Iw(w, A);
+    Sym3 Iwb = Iwa;
+    if (B >= 0) Iwb = load_Iw(w, B);
+    for (int c = mf.z; c < mf.z + mf.w; ++c) {
+      const float4* P = a.cpar + CPAR_F4 * c;
+      const V3<float> n = f3(P[0]), ra = f3(P[1]), rb = f3(P[2]);
+      V3<float> t1, t2;
+      onb_with(n, P[3].y, t1, t2);
+      const int rn = crow(p.L, c, 0);
+      const float D0 = lam_it[rn] - (lam_prev ? lam_prev[rn] : 0.f);
+      const float D1 = lam_it[rn + 1] - (lam_prev ? lam_prev[rn + 1] : 0.f);
+      const float D2 = lam_it[rn + 2] - (lam_prev ? lam_prev[rn + 2] : 0.f);
+      const V3<float> Pi = (n * D0 + t1 * D1) + t2 * D2;
+      d.va = d.va - Pi * ima;
+      d.wa = d.wa - smul(Iwa, cross(ra, Pi));
+      if (B >= 0) { d.vb = d.vb + Pi * imb; d.wb = d.wb + smul(Iwb, cross(rb, Pi)); }
+    }
+  }
+  w.jdv[4 * k + 0] = f4(d.va, 0.f); w.jdv[4 * k + 1] = f4(d.wa, 0.f);
+  w.jdv[4 * k + 2] = f4(d.vb, 0.f); w.jdv[4 * k + 3] = f4(d.wb, 0.f);
+}
+
+// Phase 2 for constraint k: its reversed rows on its local copies.
+template <bool JOINT>
+__device__ void reverse_constraint_jacobi(const Params& p, const Ws& w, const AWs& a, int k, int J,
+                                          const float* lam_it, const float* lam_prev) {
+  int A, B;
+  if (JOINT) { const int4 ji = w.jinfo[k]; A = ji.x; B = ji.y; }
+  else { const int4 mf = man_get(w, k - J); A = mf.x; B = mf.y; }
+  const float sa = A >= 0 ? w.bIw1[A].z : 1.f, sb = B >= 0 ? w.bIw1[B].z : 1.f;
+  // the copies after the constraint's rows: V + split * dV_k
+  BodyVel v = load_vel(w, A, B);
+  const V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  if (A >= 0) { v.va = v.va + f3(w.jdv[4 * k]) * sa; v.wa = v.wa + f3(w.jdv[4 * k + 1]) * sa; }
+  if (B >= 0) { v.vb = v.vb + f3(w.jdv[4 * k + 2]) * sb; v.wb = v.wb + f3(w.jdv[4 * k + 3]) * sb; }
+  BodyAdj G, g;
+  G.va = A >= 0 ? f3(a.bv[A]) : z; G.wa = A >= 0 ? f3(a.bw[A]) : z;
+  G.vb = B >= 0 ? f3(a.bv[B]) : z; G.wb = B >= 0 ? f3(a.bw[B]) : z;
+  g.va = z; g.wa = z; g.vb = z; g.wb = z;
+  const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
+  if (JOINT) {
+    const int jnr = w.jinfo[k].w;
+    for (int i = jnr - 1; i >= 0; --i) {
+      RevRow x;
+      load_rev_row(a, jrow(k, i), lam_it, lam_prev, -1, x);
+      float gfric;
+      reverse_row<true>(a, jrow(k, i), A, B, ima, imb, v, g, x, 0.f, gfric, sa, sb, &G);
+    }
+  } else {
+    const int4 mf = man_get(w, k - J);
+    const Sym3 Iwa = load_Iw(w, A);
+    Sym3 Iwb = Iwa;
+    if (B >= 0) Iwb = load_Iw(w, B);
+    float4* MA = a.madj + 4 * (k - J);
+    float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
+    float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
+    for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
+      reverse_point<true>(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi,
+                          sa, sb, &G);
+    MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
+    MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
+  }
+  w.jdv[4 * k + 0] = f4(g.va, 0.f); w.jdv[4 * k + 1] = f4(g.wa, 0.f);
+  w.jdv[4 * k + 2] = f4(g.vb, 0.f); w.jdv[4 * k + 3] = f4(g.wb, 0.f);
+}
+
+__device__ void reverse_sweep_jacobi(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a,
+                                     const float* lam_it, const float* lam_prev) {
+  const int J = e.J, K = J + w.misc[MC_MANIFOLDS];
+  for (int k = e.lane; k < K; k += e.nthr) jacobi_dv(p, w, a, k, J, lam_it, lam_prev);
+  gsync(e);
+  // iteration-start velocities
+  for (int i = e.lane; i < e.D; i += e.nthr) {
+    V3<float> dv = v3<float>(0.f, 0.f, 0.f), dw = dv;
+    for (int q = a.inc_off[i]; q < a.inc_off[i + 1]; ++q) {
+      const int t = a.inc[q], k = t >> 1, side = t & 1;
+      dv = dv + f3(w.jdv[4 * k + 2 * side]);
+      dw = dw + f3(w.jdv[4 * k + 2 * side + 1]);
+    }
+    w.bv[i] = f4(f3(w.bv[i]) - dv, 0.f);
+    w.bw[i] = f4(f3(w.bw[i]) - dw, 0.f);
+  }
+  gsync(e);
+  for (int k = e.lane; k < K; k += e.nthr) {
+    if (k < J) reverse_constraint_jacobi<true>(p, w, a, k, J, lam_it, lam_prev);
+    else reverse_constraint_jacobi<false>(p, w, a, k, J, lam_it, lam_prev);
+  }
+  gsync(e);
+  for (int i = e.lane; i < e.D; i += e.nthr) {
+    V3<float> gv = f3(a.bv[i]), gw = f3(a.bw[i]);
+    for (int q = a.inc_off[i]; q < a.inc_off[i + 1]; ++q) {
+      const int t = a.inc[q], k = t >> 1, side = t & 1;
+      gv = gv + f3(w.jdv[4 * k + 2 * side]);
+      gw = gw + f3(w.jdv[4 * k + 2 * side + 1]);
+    }
+    a.bv[i] = f4(gv, 0.f);
+    a.bw[i] = f4(gw, 0.f);
+  }
+  gsync(e);
+}
+
+// ---------------------------------------------------------------------------
 // reverse of the row set-up
 // ---------------------------------------------------------------------------
 // Effective-mass and inertia terms of one row (K = ima la.la + aa.Ia + imb
@@ -490,7 +690,7 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
 // inverse inertias (gIwa/gIwb, unique entries xx xy xz yy yz zz) and 1/m.
 __device__ __forceinline__ void reverse_mass_part(const AWs& a, int r, int A, int B, float ima, float imb,
                                                   const Sym3& Iwa, const Sym3& Iwb, float* gIwa, float* gIwb,
-                                                  float& gima, float& gimb) {
+                                                  float& gima, float& gimb, float sa, float sb) {
   float4* R = a.rows + ROW_F4 * r;
   float4* G = a.radj + ROW_F4 * r;
   V3<float> la = f3(R[0]), aa = f3(R[1]), ab = f3(R[2]), Ia = f3(R[3]), Ib = f3(R[4]);
@@ -501,20 +701,24 @@ __device__ __forceinline__ void reverse_mass_part(const AWs& a, int r, int A, in
   gimb += G[4].w;
   const float gK = m > 0.f ? -m * m * gm : 0.f;
   const float ll = dot(la, la);
+  // K = sa (ima la.la + aa.Ia) + sb (imb la.la + ab.Ib): sa, sb the Jacobi
+  // mass splits (1 for coloured PGS)
   if (A >= 0) {
-    gla = gla + la * (2.f * gK * ima);
-    gima += gK * ll;
-    gaa = gaa + Ia * gK;
-    gIa = gIa + aa * gK;
+    const float gKa = gK * sa;
+    gla = gla + la * (2.f * gKa * ima);
+    gima += gKa * ll;
+    gaa = gaa + Ia * gKa;
+    gIa = gIa + aa * gKa;
     gaa = gaa + smul(Iwa, gIa);
     gIwa[0] += gIa.x * aa.x; gIwa[1] += gIa.x * aa.y + gIa.y * aa.x; gIwa[2] += gIa.x * aa.z + gIa.z * aa.x;
     gIwa[3] += gIa.y * aa.y; gIwa[4] += gIa.y * aa.z + gIa.z * aa.y; gIwa[5] += gIa.z * aa.z;
   }
   if (B >= 0) {
-    gla = gla + la * (2.f * gK * imb);
-    gimb += gK * ll;
-    gab = gab + Ib * gK;
-    gIb = gIb + ab * gK;
+    const float gKb = gK * sb;
+    gla = gla + la * (2.f * gKb * imb);
+    gimb += gKb * ll;
+    gab = gab + Ib * gKb;
+    gIb = gIb + ab * gKb;
     gab = gab + smul(Iwb, gIb);
     gIwb[0] += gIb.x * ab.x; gIwb[1] += gIb.x * ab.y + gIb.y * ab.x; gIwb[2] += gIb.x * ab.z + gIb.z * ab.x;
     gIwb[3] += gIb.y * ab.y; gIwb[4] += gIb.y * ab.z + gIb.z * ab.y; gIwb[5] += gIb.z * ab.z;
@@ -530,7 +734,7 @@ __device__ __forceinline__ void reverse_mass_part(const AWs& a, int r, int A, in
 // inertias and the inverse masses.
 __device__ __forceinline__ void contact_mass_adjoint(const AWs& a, int ci, bool bdyn, float ima, float imb,
                                                      const Sym3& Iwa, const Sym3& Iwb, float* gIwa, float* gIwb,
-                                                     float& gima, float& gimb) {
+                                                     float& gima, float& gimb, float sa, float sb) {
   const float4* P = a.cpar + CPAR_F4 * ci;
   float4* Q = a.cadj + CADJ_F4 * ci;
   const V3<float> n = f3(P[0]), ra = f3(P[1]), rb = f3(P[2]);
@@ -549,23 +753,25 @@ __device__ __forceinline__ void contact_mass_adjoint(const AWs& a, int ci, bool 
     else gK = gKo[q - 3];
     const V3<float> x = dirs[i], y = dirs[j];
     const float xy = dot(x, y);
-    // body a
+    // body a (its terms scaled by the Jacobi mass split sa; 1 for coloured PGS)
     {
+      const float gKa = gK * sa;
       const V3<float> cx = cross(ra, x), cy = cross(ra, y);
-      const V3<float> gcx = smul(Iwa, cy) * gK, gcy = smul(Iwa, cx) * gK;
-      gd[i] = gd[i] + y * (gK * ima) + cross(gcx, ra);
-      gd[j] = gd[j] + x * (gK * ima) + cross(gcy, ra);
-      gima += gK * xy;
-      add_sym(gIwa, cx * gK, cy);
+      const V3<float> gcx = smul(Iwa, cy) * gKa, gcy = smul(Iwa, cx) * gKa;
+      gd[i] = gd[i] + y * (gKa * ima) + cross(gcx, ra);
+      gd[j] = gd[j] + x * (gKa * ima) + cross(gcy, ra);
+      gima += gKa * xy;
+      add_sym(gIwa, cx * gKa, cy);
       gra = gra + cross(x, gcx) + cross(y, gcy);
     }
     if (bdyn) {
+      const float gKb = gK * sb;
       const V3<float> cx = cross(rb, x), cy = cross(rb, y);
-      const V3<float> gcx = smul(Iwb, cy) * gK, gcy = smul(Iwb, cx) * gK;
-      gd[i] = gd[i] + y * (gK * imb) + cross(gcx, rb);
-      gd[j] = gd[j] + x * (gK * imb) + cross(gcy, rb);
-      gimb += gK * xy;
-      add_sym(gIwb, cx * gK, cy);
+      const V3<float> gcx = smul(Iwb, cy) * gKb, gcy = smul(Iwb, cx) * gKb;
+      gd[i] = gd[i] + y * (gKb * imb) + cross(gcx, rb);
+      gd[j] = gd[j] + x * (gKb * imb) + cross(gcy, rb);
+      gimb += gKb * xy;
+      add_sym(gIwb, cx * gKb, cy);
       grb = grb + cross(x, gcx) + cross(y, gcy);
     }
   }
@@ -696,10 +902,12 @@ __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, co
     if (B >= 0) Iwb = load_Iw(w, B);
     float gIwa[6] = {0, 0, 0, 0, 0, 0}, gIwb[6] = {0, 0, 0, 0, 0, 0};
     float gima = 0.f, gimb = 0.f;
+    const float sa = A >= 0 ? w.bIw1[A].z : 1.f, sb = B >= 0 ? w.bIw1[B].z : 1.f;   // Jacobi mass splits
     if (k < J) {
       const JointDesc& j = p.joints[e.j0 + k];
       const int nr = joint_row_count(j);
-      for (int r = 0; r < nr; ++r) reverse_mass_part(a, jrow(k, r), A, B, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
+      for (int r = 0; r < nr; ++r)
+        reverse_mass_part(a, jrow(k, r), A, B, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb, sa, sb);
     } else {
       int4 mf = man_get(w, k - J);
       const float4* MA = a.madj + 4 * (k - J);
@@ -707,7 +915,7 @@ __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, co
       gIwb[0] = MA[1].z; gIwb[1] = MA[1].w; gIwb[2] = MA[2].x; gIwb[3] = MA[2].y; gIwb[4] = MA[2].z; gIwb[5] = MA[2].w;
       gima = MA[3].x; gimb = MA[3].y;
       for (int ci = mf.z; ci < mf.z + mf.w; ++ci)
-        contact_mass_adjoint(a, ci, B >= 0, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb);
+        contact_mass_adjoint(a, ci, B >= 0, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb, sa, sb);
     }
     float4* S = a.gat + 8 * k;
     S[4] = make_float4(gIwa[0], gIwa[1], gIwa[2], gIwa[3]);

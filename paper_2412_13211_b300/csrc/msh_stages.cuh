@@ -1169,6 +1169,7 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w,
       else solve_manifold(p, e, w, k - J, bv, &d);
       w.jdv[4 * k + 0] = f4(d.va, 0.f); w.jdv[4 * k + 1] = f4(d.wa, 0.f);
       w.jdv[4 * k + 2] = f4(d.vb, 0.f); w.jdv[4 * k + 3] = f4(d.wb, 0.f);
+      if (p.tape) tape_lambdas(p, e, w, k, sub, it);
     }
     gsync(e);
     for (int i = e.lane; i < e.D; i += e.nthr) {
