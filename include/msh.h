@@ -359,6 +359,20 @@ int msh_tape_record(msh_handle* h, int32_t on);
 int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, float* adj_targets,
                  float* adj_mass, void* stream);
 
+/*
+ * Inspection of a recorded step (for tests and debugging; the paper has no
+ * counterpart). msh_tape_lambdas copies the impulses that tape slot `slot`
+ * (0 = the oldest recorded step still on the tape) holds after every sweep
+ * into out_host, a HOST buffer of num_envs * substeps * iterations *
+ * msh_tape_rows(h) floats, laid out [env][substep][sweep][row]. Rows of an
+ * env: joint k's row r at k * 8 + r (8 slots per joint of the largest env),
+ * then contact point c's normal, first and second friction row at
+ * 8 * Jmax + 3 c + {0, 1, 2}; slots the step does not use are unspecified.
+ * Synchronises `stream`. Returns MSH_ERR_INVALID_ARG for an empty slot.
+ */
+int32_t msh_tape_rows(const msh_handle* h);
+int msh_tape_lambdas(msh_handle* h, int32_t slot, float* out_host, void* stream);
+
 /* Copies the per-env status words to host memory [num_envs] (synchronises
  * `stream`). */
 int msh_get_status(msh_handle* h, int32_t* status_host, void* stream);

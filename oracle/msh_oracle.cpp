@@ -177,6 +177,48 @@ template <class R> inline R clampv(R x, R lo, R hi) { return x < lo ? lo : (x > 
 // that is the only consistent choice, since the clamped impulse cannot move
 // away from it.
 template <class R> inline R clamp_active(R x, R lo, R hi) { return x <= lo ? lo : (x >= hi ? hi : x); }
+
+// Branch decisions of a step whose outcome rounding can decide. The step is
+// piecewise smooth; a decision taken at a value within rounding of its
+// threshold (an impulse within noise of its clamp bound, a joint-limit error
+// or a contact separation within noise of a kink of the bias) could go the
+// other way in another correct FP32 evaluation, and with it the derivative.
+// While a log is installed (reverse-mode adjoints only), every such decision
+// of the step gets the next index; those closer to their threshold than the
+// log's margins are listed as fragile, and the ones named in `flip` are taken
+// the other way (the other one-sided piece of the step).
+struct DecisionLog {
+  int next = 0;
+  double delta = 1e-4;     // impulse clamps: distance to the bound over the update's magnitude
+  double len_tol = 1e-6;   // joint limits and contact biases: absolute distance (m or rad)
+  int site = -1;           // solver row of the decision being taken (-1: a geometric branch)
+  int choice = 0;          // its natural outcome: 0 free (or the branch's first case), 1 clamped (or the second)
+  std::vector<int> fragile, fragile_site, fragile_choice;
+  std::vector<double> fragile_margin;
+  const int* flip = nullptr;
+  int nflip = 0;
+};
+inline DecisionLog*& dec_log() { static thread_local DecisionLog* d = nullptr; return d; }
+
+// Records the next decision with the given margin and threshold; returns
+// whether it is to be inverted. No log: nothing is recorded, nothing inverted.
+inline bool decision(double margin, double thr) {
+  DecisionLog* d = dec_log();
+  if (!d) return false;
+  const int idx = d->next++;
+  if (margin < thr) {
+    d->fragile.push_back(idx);
+    d->fragile_site.push_back(d->site);
+    d->fragile_choice.push_back(d->choice);
+    d->fragile_margin.push_back(margin);
+  }
+  d->site = -1;
+  d->choice = 0;
+  for (int i = 0; i < d->nflip; ++i)
+    if (d->flip[i] == idx) return true;
+  return false;
+}
+inline double dec_tol() { return dec_log() ? dec_log()->len_tol : 0.0; }
 template <class R> inline R maxv(R a, R b) { return a > b ? a : b; }
 template <class R> inline R minv(R a, R b) { return a < b ? a : b; }
 
@@ -824,6 +866,7 @@ template <class R> M3<R> world_invI(const Body<R>& b) {
 template <class R> struct Solver {
   const OracleCfg* cfg;
   R h;
+  int sub = 0;               // substep of the rows being built
   std::vector<M3<R>> Iw;     // world inverse inertia per dynamic body
   std::vector<R> split;      // Jacobi mass-splitting counts (1 in PGS)
   std::vector<Row<R>> rows;
@@ -931,7 +974,9 @@ template <class R> struct Solver {
         for (int e = 0; e < 2; ++e) {
           Row<R> r = ang_row(A, B, e == 0 ? ux : -ux, ROW_UNILATERAL);
           R C = e == 0 ? theta - j.lo : j.hi - theta;
-          r.bias = C > R(0) ? C / h : beta * C;
+          bool open = C > R(0);
+          if (decision(std::fabs(val(C)), dec_tol())) open = !open;
+          r.bias = open ? C / h : beta * C;
           rows.push_back(r);
         }
       }
@@ -958,7 +1003,9 @@ template <class R> struct Solver {
       for (int e = 0; e < 2; ++e) {
         Row<R> r = lin_row(A, B, e == 0 ? ux : -ux, raB, rb, ROW_UNILATERAL);
         R C = e == 0 ? dd - j.lo : j.hi - dd;
-        r.bias = C > R(0) ? C / h : beta * C;
+        bool open = C > R(0);
+        if (decision(std::fabs(val(C)), dec_tol())) open = !open;
+        r.bias = open ? C / h : beta * C;
         rows.push_back(r);
       }
     } else {  // PLANAR: normal = frame z; free x, y, yaw
@@ -1011,8 +1058,22 @@ template <class R> struct Solver {
       else { pb_w = c.rb; rb = v3<R>(R(0), R(0), R(0)); }
       R s = dot(c.n, pb_w - pa_w);
       Row<R> rn = lin_row(mf.a, bdyn, c.n, ra, rb, ROW_UNILATERAL);
-      if (s > R(0)) rn.bias = s / h;
-      else rn.bias = -(beta / h) * maxv(R(0), -s - slop);
+      // speculative above s = 0, nothing down to -slop, Baumgarte below; from
+      // the second substep on the poses carry the solver's rounding, so a
+      // separation within noise of a kink is a fragile decision there
+      bool spec = s > R(0);
+      if (sub > 0 && decision(std::fabs(val(s)), dec_tol())) spec = !spec;
+      if (spec) {
+        rn.bias = s / h;
+      } else {
+        // (at pen == 0 exactly the bias is 0 either way; the Baumgarte case is
+        // taken only for pen > 0, so a contact resting exactly at -slop has no
+        // bias derivative)
+        const R pen = -s - slop;
+        bool deep = pen > R(0);
+        if (sub > 0 && decision(std::fabs(val(pen)), dec_tol())) deep = !deep;
+        rn.bias = -(beta / h) * (deep ? pen : R(0));
+      }
       finish_row(rn, E);
       if (rest > R(0)) {
         R vn = jv(rn, E);
@@ -1051,7 +1112,35 @@ template <class R> struct Solver {
     if (r.b >= 0) acc = acc + dot(r.lb, *vb) + dot(r.ab, *wb);
     R dl = -r.m * (acc + r.bias + r.gamma * r.lam);
     R nl = r.lam + dl;
-    if (r.kind == ROW_UNILATERAL) nl = maxv(nl, R(0));
+    if (dec_log() && r.kind != ROW_BILATERAL) {
+      // the same clamps, with the decision logged (and possibly inverted)
+      R lo, hi, lim = R(0);
+      const bool has_hi = r.kind != ROW_UNILATERAL;
+      if (r.kind == ROW_UNILATERAL) { lo = R(0); hi = R(0); }
+      else if (r.kind == ROW_FRICTION) { lim = r.mu * rows[r.ref].lam; lo = -lim; hi = lim; }
+      else { lo = r.lo; hi = r.hi; }
+      int choice = r.kind == ROW_UNILATERAL ? (nl > R(0) ? 0 : -1) : (nl <= lo ? -1 : (nl >= hi ? 1 : 0));
+      // magnitude of what enters the update: the noise scale of nl
+      double a = 0.0;
+      if (r.a >= 0) a += std::fabs(val(r.la.x) * val(va->x)) + std::fabs(val(r.la.y) * val(va->y)) +
+                         std::fabs(val(r.la.z) * val(va->z)) + std::fabs(val(r.aa.x) * val(wa->x)) +
+                         std::fabs(val(r.aa.y) * val(wa->y)) + std::fabs(val(r.aa.z) * val(wa->z));
+      if (r.b >= 0) a += std::fabs(val(r.lb.x) * val(vb->x)) + std::fabs(val(r.lb.y) * val(vb->y)) +
+                         std::fabs(val(r.lb.z) * val(vb->z)) + std::fabs(val(r.ab.x) * val(wb->x)) +
+                         std::fabs(val(r.ab.y) * val(wb->y)) + std::fabs(val(r.ab.z) * val(wb->z));
+      const double scale = std::fabs(val(r.lam)) + std::fabs(val(r.m)) * (a + std::fabs(val(r.bias)) +
+                           std::fabs(val(r.gamma) * val(r.lam))) + std::fabs(val(lim)) + 1e-300;
+      const double dlo = std::fabs(val(nl) - val(lo));
+      const double dhi = has_hi ? std::fabs(val(nl) - val(hi)) : INFINITY;
+      // a zero-width interval (friction with lambda_n = 0) leaves one choice:
+      // its decision is never fragile
+      const double margin = has_hi && val(lo) == val(hi) ? INFINITY : std::min(dlo, dhi) / scale;
+      dec_log()->site = (int)(&r - rows.data());
+      dec_log()->choice = choice != 0;
+      if (decision(margin, dec_log()->delta))
+        choice = choice != 0 ? 0 : (dlo <= dhi ? -1 : 1);
+      nl = choice == 0 ? nl : (choice < 0 ? lo : hi);
+    } else if (r.kind == ROW_UNILATERAL) nl = maxv(nl, R(0));
     else if (r.kind == ROW_FRICTION) { R lim = r.mu * rows[r.ref].lam; nl = clamp_active(nl, -lim, lim); }
     else if (r.kind == ROW_SOFT) nl = clamp_active(nl, r.lo, r.hi);
     dl = nl - r.lam;
@@ -1254,6 +1343,12 @@ template <class R> void contact_report(const EnvState<R>& E, const OracleCfg& cf
   }
 }
 
+// Recorder of the impulses after every sweep of a step (tests): rows of an
+// env numbered as joint k row r -> k * 8 + r (jmax joints), then contact
+// point c row i -> 8 * jmax + 3 c + i; out holds [substep][sweep][rows].
+struct LambdaRec { float* out; int jmax, rows, iterations; };
+inline LambdaRec*& lambda_rec() { static thread_local LambdaRec* r = nullptr; return r; }
+
 // One step of one env: detection at the step start, then per substep:
 // gravity, rows from the current poses, N solver iterations, position update.
 // With `rp`, the contact report of the step is computed at its end.
@@ -1282,6 +1377,7 @@ template <class R> int step_env(EnvState<R>& E, const OracleCfg& cfg, const R* t
     for (int i = 0; i < D; ++i) sv.split[i] = R(cnt[i] > 0 ? cnt[i] : 1);
   }
   for (int s = 0; s < S; ++s) {
+    sv.sub = s;
     for (int i = 0; i < D; ++i) E.body[i].v = E.body[i].v + g * h;
     for (int i = 0; i < D; ++i) sv.Iw[i] = world_invI(E.body[i]);
     sv.rows.clear();
@@ -1321,6 +1417,16 @@ template <class R> int step_env(EnvState<R>& E, const OracleCfg& cfg, const R* t
           if (cn.b >= 0) { dv[cn.b] = dv[cn.b] + dvb; dw[cn.b] = dw[cn.b] + dwb; }
         }
         for (int i = 0; i < D; ++i) { E.body[i].v = E.body[i].v + dv[i]; E.body[i].w = E.body[i].w + dw[i]; }
+      }
+      if (LambdaRec* lr = lambda_rec()) {
+        float* o = lr->out + ((size_t)s * lr->iterations + it) * lr->rows;
+        for (int k = 0; k < E.J; ++k)
+          for (int q = 0; q < sv.cons[k].count; ++q) o[8 * k + q] = (float)val(sv.rows[sv.cons[k].first + q].lam);
+        for (size_t m = 0; m < det.manifolds.size(); ++m) {
+          const Con& cn = sv.cons[E.J + m];
+          for (int q = 0; q < cn.count; ++q)
+            o[8 * lr->jmax + 3 * det.manifolds[m].first + q] = (float)val(sv.rows[cn.first + q].lam);
+        }
       }
     }
     // accumulated impulse (normal, t1, t2) of every contact point over the substeps
@@ -1633,11 +1739,31 @@ int grad_batch(const OracleScene* sc, const OracleCfg* cfg, const double* pos, c
 // the primal values, so the result is the derivative of the piecewise-smooth
 // step on the piece that contains this point; with P = float the primal and
 // hence every decision is the FP32 oracle's.
+}  // namespace orc
+
+// Decision reporting and inversion of a reverse-mode step (see DecisionLog):
+// margins, and per env the number of fragile decisions with the first kmax
+// of their indices; flip_off [E+1] / flip_idx: per env (CSR) the decision
+// indices to take the other way. NULL in the entry points: no log.
+extern "C" struct OracleDecisions {
+  double delta, len_tol;
+  int32_t kmax;
+  int32_t* nfragile;        // [E]
+  int32_t* fragile;         // [E][kmax] decision indices
+  int32_t* fragile_site;    // [E][kmax] solver row of each (-1: joint limit or contact bias), may be NULL
+  int32_t* fragile_choice;  // [E][kmax] its natural outcome (1: the clamp is active), may be NULL
+  double* fragile_margin;   // [E][kmax] margin of each, may be NULL
+  const int32_t* flip_off;  // [E+1] or NULL
+  const int32_t* flip_idx;
+};
+
+namespace orc {
+
 template <class P, class T>
 int vjp_batch(const OracleScene* sc, const OracleCfg* cfg, const T* pos, const T* quat, const T* lv, const T* av,
               const T* targets, const double* wpos, const double* wquat, const double* wlv, const double* wav,
               T* opos, T* oquat, T* olv, T* oav, double* gpos, double* gquat, double* glv, double* gav,
-              double* gtg, double* gmass, int32_t* status, int nthreads) {
+              double* gtg, double* gmass, int32_t* status, int nthreads, const OracleDecisions* dec) {
   typedef Rev<P> RV;
   const int E = sc->num_envs;
   const int B = sc->body_off[E];
@@ -1650,6 +1776,16 @@ int vjp_batch(const OracleScene* sc, const OracleCfg* cfg, const T* pos, const T
     static thread_local RevTape tape;   // reused by the thread's envs (keeps its capacity)
     tape.clear();
     rev_tape() = &tape;
+    DecisionLog log;
+    if (dec) {
+      log.delta = dec->delta;
+      log.len_tol = dec->len_tol;
+      if (dec->flip_off) {
+        log.flip = dec->flip_idx + dec->flip_off[e];
+        log.nflip = dec->flip_off[e + 1] - dec->flip_off[e];
+      }
+      dec_log() = &log;
+    }
     const int b0 = sc->body_off[e], D = sc->body_off[e + 1] - b0;
     std::vector<RV> mass(B);
     for (int i = 0; i < D; ++i) mass[b0 + i] = RV::leaf(P(sc->body_mass[b0 + i]));
@@ -1697,6 +1833,17 @@ int vjp_batch(const OracleScene* sc, const OracleCfg* cfg, const T* pos, const T
       for (int k = 0; k < sc->max_dof; ++k) gtg[(size_t)e * sc->max_dof + k] = tape.get(tg[k].id);
     if (status) status[e] = st;
     rev_tape() = nullptr;
+    if (dec) {
+      dec_log() = nullptr;
+      dec->nfragile[e] = (int32_t)log.fragile.size();
+      for (int k = 0; k < dec->kmax && k < (int)log.fragile.size(); ++k) {
+        const size_t o = (size_t)e * dec->kmax + k;
+        dec->fragile[o] = log.fragile[k];
+        if (dec->fragile_site) dec->fragile_site[o] = log.fragile_site[k];
+        if (dec->fragile_choice) dec->fragile_choice[o] = log.fragile_choice[k];
+        if (dec->fragile_margin) dec->fragile_margin[o] = log.fragile_margin[k];
+      }
+    }
   }
   return 0;
 }
@@ -1709,21 +1856,23 @@ extern "C" {
 // FP32 form (primal arithmetic and decisions of the FP32 oracle, adjoints in
 // double) and the FP64 form. State arrays [B][3|4], targets [E][max_dof];
 // seeds w* and outputs g* are double; gtg [E][max_dof] and gmass [B] are
-// written; o* receive the stepped state (may be NULL together).
+// written; o* receive the stepped state (may be NULL together); dec (may be
+// NULL) reports fragile decisions and inverts chosen ones.
 int oracle_vjp_f32(const OracleScene* sc, const OracleCfg* cfg, const float* pos, const float* quat, const float* lv,
                    const float* av, const float* targets, const double* wpos, const double* wquat, const double* wlv,
                    const double* wav, float* opos, float* oquat, float* olv, float* oav, double* gpos, double* gquat,
-                   double* glv, double* gav, double* gtg, double* gmass, int32_t* status, int nthreads) {
+                   double* glv, double* gav, double* gtg, double* gmass, int32_t* status, int nthreads,
+                   const OracleDecisions* dec) {
   return orc::vjp_batch<float, float>(sc, cfg, pos, quat, lv, av, targets, wpos, wquat, wlv, wav, opos, oquat, olv,
-                                      oav, gpos, gquat, glv, gav, gtg, gmass, status, nthreads);
+                                      oav, gpos, gquat, glv, gav, gtg, gmass, status, nthreads, dec);
 }
 int oracle_vjp_f64(const OracleScene* sc, const OracleCfg* cfg, const double* pos, const double* quat,
                    const double* lv, const double* av, const double* targets, const double* wpos, const double* wquat,
                    const double* wlv, const double* wav, double* opos, double* oquat, double* olv, double* oav,
                    double* gpos, double* gquat, double* glv, double* gav, double* gtg, double* gmass, int32_t* status,
-                   int nthreads) {
+                   int nthreads, const OracleDecisions* dec) {
   return orc::vjp_batch<double, double>(sc, cfg, pos, quat, lv, av, targets, wpos, wquat, wlv, wav, opos, oquat, olv,
-                                        oav, gpos, gquat, glv, gav, gtg, gmass, status, nthreads);
+                                        oav, gpos, gquat, glv, gav, gtg, gmass, status, nthreads, dec);
 }
 
 int oracle_step_f32(const OracleScene* sc, const OracleCfg* cfg, float* pos, float* quat, float* lv,
@@ -1782,6 +1931,33 @@ int oracle_step_report_f64(const OracleScene* sc, const OracleCfg* cfg, double* 
   return orc::step_report_batch<double>(sc, cfg, pos, quat, lv, av, targets, nsteps, status, nthreads, spec,
                                         body_force, target_force, finger_force, robot_force, grasped);
 }
+// One FP32 step of every env with the impulses after every sweep written to
+// lam [E][substeps][iterations][8 * jmax + 3 * max_contacts] (see LambdaRec).
+int oracle_step_lambdas_f32(const OracleScene* sc, const OracleCfg* cfg, float* pos, float* quat, float* lv,
+                            float* av, const float* targets, int jmax, float* lam, int nthreads) {
+  const int E = sc->num_envs;
+  const int md = sc->max_dof > 0 ? sc->max_dof : 1;
+  const int rows = 8 * jmax + 3 * cfg->max_contacts;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int e = 0; e < E; ++e) {
+    orc::EnvState<float> S;
+    orc::load_env<float, float>(*sc, e, pos, quat, lv, av, nullptr, S);
+    std::vector<float> tg(md);
+    for (int k = 0; k < md; ++k) tg[k] = targets ? targets[(size_t)e * md + k] : 0.f;
+    orc::LambdaRec rec;
+    rec.out = lam + (size_t)e * cfg->substeps * cfg->iterations * rows;
+    rec.jmax = jmax; rec.rows = rows; rec.iterations = cfg->iterations;
+    orc::lambda_rec() = &rec;
+    orc::step_env(S, *cfg, tg.data(), (orc::Detect<float>*)nullptr);
+    orc::lambda_rec() = nullptr;
+    orc::store_env<float, float>(*sc, e, S, pos, quat, lv, av);
+  }
+  return 0;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -71,8 +71,10 @@ def load():
         lib.oracle_grad_f64.argtypes = [P, P, P, P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, C.c_int]
         lib.oracle_grad_f64.restype = C.c_int
         lib.oracle_max_threads.restype = C.c_int
+        lib.oracle_step_lambdas_f32.argtypes = [P] * 7 + [C.c_int, P, C.c_int]
+        lib.oracle_step_lambdas_f32.restype = C.c_int
         for fn in (lib.oracle_vjp_f32, lib.oracle_vjp_f64):
-            fn.argtypes = [P] * 22 + [C.c_int]
+            fn.argtypes = [P] * 22 + [C.c_int, P]
             fn.restype = C.c_int
         for fn in (lib.oracle_render_depth_f32, lib.oracle_render_depth_f64):
             fn.argtypes = [P, P, P, P, P, C.c_int]
@@ -361,6 +363,13 @@ def loss_value(scene, cfg, state, targets, nsteps, goal_body, goal_pos, mass=Non
     return L, status
 
 
+class _Decisions(C.Structure):
+    _fields_ = [("delta", C.c_double), ("len_tol", C.c_double), ("kmax", C.c_int32), ("nfragile", C.c_void_p),
+                ("fragile", C.c_void_p), ("fragile_site", C.c_void_p), ("fragile_choice", C.c_void_p),
+                ("fragile_margin", C.c_void_p),
+                ("flip_off", C.c_void_p), ("flip_idx", C.c_void_p)]
+
+
 @dataclass
 class OracleVJP:
     """Adjoints of one step's inputs for a seed on its output (all float64)."""
@@ -372,15 +381,27 @@ class OracleVJP:
     mass: np.ndarray      # [B]
     out: tuple            # the stepped state (pos, quat, linvel, angvel)
     status: np.ndarray    # [E]
+    nfragile: np.ndarray = None   # [E] fragile decisions per env (when requested)
+    fragile: list = None          # per env: the first `kmax` fragile decision indices
+    fragile_site: list = None     # per env: the solver row of each (-1: joint limit or contact bias)
+    fragile_choice: list = None   # per env: the natural outcome of each (1: clamp active)
+    fragile_margin: list = None   # per env: the margin of each
 
 
-def step_vjp(scene, cfg, state, targets, seed, precision: str = "f32", threads: int = 0) -> OracleVJP:
+def step_vjp(scene, cfg, state, targets, seed, precision: str = "f32", threads: int = 0, fragile: bool = False,
+             flips=None, delta: float = 1e-4, len_tol: float = 1e-6, kmax: int = 16) -> OracleVJP:
     """One step from `state` with joint targets [E, max_dof], and the
     vector-Jacobian products of the seed (pos, quat, linvel, angvel adjoints of
     the stepped state, float64) with respect to the step's state, targets and
     body masses, by reverse mode. precision "f32": the FP32 oracle's primal
     arithmetic and branch decisions (adjoints in double); "f64": the FP64
-    oracle's."""
+    oracle's.
+
+    fragile: also report, per env, the branch decisions taken within rounding
+    of their thresholds (impulse clamps within `delta` of the update's
+    magnitude, joint-limit errors and, after the first substep, contact
+    separations within `len_tol` of a kink). flips: per env a list of
+    decision indices to take the other way (the other one-sided piece)."""
     lib = load()
     dt = np.float32 if precision == "f32" else np.float64
     E, B = scene.num_envs, scene.num_bodies
@@ -397,12 +418,36 @@ def step_vjp(scene, cfg, state, targets, seed, precision: str = "f32", threads: 
     status = np.zeros(E, np.int32)
     keep = _Keep(scene)
     c = _cfg(cfg)
+    dec = None
+    nfr = frag = None
+    if fragile or flips is not None:
+        nfr = np.zeros(E, np.int32)
+        frag = np.full((E, kmax), -1, np.int32)
+        fsite = np.full((E, kmax), -1, np.int32)
+        fchoice = np.zeros((E, kmax), np.int32)
+        fmarg = np.zeros((E, kmax))
+        off = idx = None
+        if flips is not None:
+            off = np.zeros(E + 1, np.int32)
+            off[1:] = np.cumsum([len(f) for f in flips])
+            idx = np.ascontiguousarray(np.concatenate([np.asarray(f, np.int32) for f in flips] + [np.zeros(1, np.int32)]))
+        dec = _Decisions(float(delta), float(len_tol), int(kmax), nfr.ctypes.data, frag.ctypes.data,
+                         fsite.ctypes.data, fchoice.ctypes.data, fmarg.ctypes.data,
+                         None if off is None else off.ctypes.data, None if idx is None else idx.ctypes.data)
     fn = lib.oracle_vjp_f32 if precision == "f32" else lib.oracle_vjp_f64
     rc = fn(C.byref(keep.struct), C.byref(c), *[_ptr(a) for a in st], _ptr(tg), *[_ptr(a) for a in w],
-            *[_ptr(a) for a in out], *[_ptr(a) for a in g], _ptr(gtg), _ptr(gm), _ptr(status), int(threads))
+            *[_ptr(a) for a in out], *[_ptr(a) for a in g], _ptr(gtg), _ptr(gm), _ptr(status), int(threads),
+            None if dec is None else C.byref(dec))
     if rc != 0:
         raise RuntimeError(f"oracle vjp failed: {rc}")
-    return OracleVJP(g[0], g[1], g[2], g[3], gtg[:, :scene.max_dof], gm, tuple(out), status)
+    r = OracleVJP(g[0], g[1], g[2], g[3], gtg[:, :scene.max_dof], gm, tuple(out), status)
+    if nfr is not None:
+        r.nfragile = nfr
+        r.fragile = [list(frag[e, :min(int(nfr[e]), kmax)]) for e in range(E)]
+        r.fragile_site = [list(fsite[e, :min(int(nfr[e]), kmax)]) for e in range(E)]
+        r.fragile_choice = [list(fchoice[e, :min(int(nfr[e]), kmax)]) for e in range(E)]
+        r.fragile_margin = [list(fmarg[e, :min(int(nfr[e]), kmax)]) for e in range(E)]
+    return r
 
 
 def trajectory(scene, cfg, state, targets, nsteps, precision: str = "f32", threads: int = 0):
@@ -445,3 +490,25 @@ def rollout_grad(scene, cfg, state, targets, nsteps, seed_final, precision: str 
         gm += r.mass
         st |= r.status
     return w, gtg, gm, xs, st
+
+
+def step_lambdas(scene, cfg, state, targets=None, threads: int = 0):
+    """One FP32 step and the impulses after every sweep, [E, substeps,
+    iterations, 8 * Jmax + 3 * max_contacts] (joint k row r at 8 k + r, Jmax
+    the largest env's joint count; contact point c row i at 8 Jmax + 3 c + i;
+    unused slots are NaN). Returns (new_state, lambdas)."""
+    lib = load()
+    st = [np.ascontiguousarray(a, dtype=np.float32).copy() for a in state]
+    E = scene.num_envs
+    md = max(scene.max_dof, 1)
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.float32).reshape(E, md)
+    jmax = max(1, int(np.diff(scene.joint_off).max(initial=0)))
+    rows = 8 * jmax + 3 * cfg.max_contacts
+    lam = np.full((E, cfg.substeps, cfg.iterations, rows), np.nan, np.float32)
+    keep = _Keep(scene)
+    c = _cfg(cfg)
+    rc = lib.oracle_step_lambdas_f32(C.byref(keep.struct), C.byref(c), _ptr(st[0]), _ptr(st[1]), _ptr(st[2]),
+                                     _ptr(st[3]), _ptr(tg), int(jmax), _ptr(lam), int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle step_lambdas failed: {rc}")
+    return tuple(st), lam

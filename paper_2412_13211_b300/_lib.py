@@ -19,7 +19,7 @@ EXPORTS = ("msh_create", "msh_destroy", "msh_last_error", "msh_set_exec", "msh_s
            "msh_launches_per_step", "msh_step_static_scratch", "msh_set_tape", "msh_tape_reset",
            "msh_tape_count", "msh_backward", "msh_set_report", "msh_label_events", "msh_set_cameras",
            "msh_render_depth", "msh_set_controller", "msh_control_step",
-           "msh_tape_record")
+           "msh_tape_record", "msh_tape_rows", "msh_tape_lambdas")
 TASK_PICK, TASK_PLACE, TASK_OPEN, TASK_CLOSE = 0, 1, 2, 3
 
 
@@ -102,6 +102,9 @@ def load(build_if_missing: bool = True):
     lib.msh_tape_record.argtypes = [P, I32]
     lib.msh_tape_count.argtypes = [P]
     lib.msh_tape_count.restype = C.c_int32
+    lib.msh_tape_rows.argtypes = [P]
+    lib.msh_tape_rows.restype = C.c_int32
+    lib.msh_tape_lambdas.argtypes = [P, I32, P, P]
     lib.msh_backward.argtypes = [P, P, P, P, P, P]
     lib.msh_detect.argtypes = [P] * 12 + [P]
     lib.msh_get_status.argtypes = [P, P, P]
@@ -115,7 +118,7 @@ def load(build_if_missing: bool = True):
     for name in EXPORTS:
         getattr(lib, name)
         if name not in ("msh_destroy", "msh_last_error", "msh_scratch_bytes", "msh_workspace_bytes",
-                        "msh_launches_per_step", "msh_tape_count"):
+                        "msh_launches_per_step", "msh_tape_count", "msh_tape_rows"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib

@@ -1302,6 +1302,21 @@ int msh_tape_reset(msh_handle* h) {
 
 int32_t msh_tape_count(const msh_handle* h) { return h ? h->tape_count : 0; }
 
+int32_t msh_tape_rows(const msh_handle* h) { return h ? ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C : 0; }
+
+int msh_tape_lambdas(msh_handle* h, int32_t slot, float* out_host, void* stream) {
+  if (!h || !out_host) return fail(MSH_ERR_INVALID_ARG, "NULL argument");
+  if (slot < 0 || slot >= h->tape_count) return fail(MSH_ERR_INVALID_ARG, "no recorded step in that tape slot");
+  const TapeLayout tl = tape_layout(h->L, h->cfg.substeps, h->cfg.iterations, h->max_dof);
+  const size_t per_env = (size_t)h->cfg.substeps * h->cfg.iterations * msh_tape_rows(h);
+  cudaStream_t s = (cudaStream_t)stream;
+  const float* src = h->d_tape + ((long long)slot * h->E) * h->tape_slab + tl.t2;
+  CK(cudaMemcpy2DAsync(out_host, per_env * 4, src, (size_t)h->tape_slab * 4, per_env * 4, (size_t)h->E,
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return MSH_OK;
+}
+
 int msh_tape_record(msh_handle* h, int32_t on) {
   if (!h) return fail(MSH_ERR_INVALID_ARG, "handle is NULL");
   if (on && h->tape_max <= 0) return fail(MSH_ERR_INVALID_ARG, "no tape: call msh_set_tape first");

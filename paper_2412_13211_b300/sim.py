@@ -336,6 +336,16 @@ class MshSim:
                                         _stream(stream)), "msh_backward")
         return tuple(outs)
 
+    def tape_lambdas(self, slot: int = 0, stream=None) -> np.ndarray:
+        """Impulses after every sweep of recorded step `slot`:
+        [E, substeps, iterations, rows] (see msh_tape_lambdas for the rows)."""
+        rows = int(self.lib.msh_tape_rows(self.handle))
+        out = np.zeros((self.scene.num_envs, self.cfg.substeps, self.cfg.iterations, rows), np.float32)
+        with torch.cuda.device(self.device):
+            check(self.lib.msh_tape_lambdas(self.handle, int(slot), out.ctypes.data_as(C.c_void_p), _stream(stream)),
+                  "msh_tape_lambdas")
+        return out
+
     def status(self, stream=None) -> np.ndarray:
         out = np.zeros(self.scene.num_envs, np.int32)
         with torch.cuda.device(self.device):

@@ -1,13 +1,12 @@
-"""The CUDA adjoint (msh_backward) against the oracle's reference gradients.
+"""Differentiable rollouts through the CUDA adjoint (msh_backward).
 
-GPU gradients of the rollout loss (squared distance of each env's goal box to
-its goal) w.r.t. the initial velocities, the per-step joint targets and the
-masses, contracted with seeded directions, are compared with the oracle's
-forward-mode dual derivatives along the same directions (FP64). The GPU runs
-in FP32 and both sides freeze the same discrete decisions, so agreement is to
-a relative tolerance; the fraction of envs within it is recorded.
-Checkpointing must not change the result: backward passes with different
-checkpoint intervals are bitwise equal.
+The rollout gradient of the goal loss w.r.t. the initial velocities, the
+per-step joint targets and the masses: a closed form for free fall; bitwise
+independence of the checkpoint interval, of the execution form that recorded
+the steps, and of whether the forward pass kept its last segment; a central
+difference of the GPU step itself for one recorded step. The adjoint of every
+step is compared with the oracle element by element in
+test_gpu_adjoint_parity.py.
 """
 import numpy as np
 import pytest
@@ -35,11 +34,6 @@ def _gpu_grads(sc, cfg, tg, nsteps, k, **sim_kw):
     return res
 
 
-def _per_env(sc, x):
-    """Sum of a per-body array over each env's bodies."""
-    return np.array([x[sc.body_off[e]:sc.body_off[e + 1]].sum() for e in range(sc.num_envs)])
-
-
 def test_free_fall_gradient_closed_form():
     from helpers import env, scene_from_envs
     e = env()
@@ -61,40 +55,13 @@ def test_free_fall_gradient_closed_form():
 def diff_case():
     sc, cfg = S.make_config(4, num_envs=16)
     nsteps = 8
-    rng = np.random.default_rng(7)
     tg = sc.target_walk(nsteps, 3)
-    B, E, md = sc.num_bodies, sc.num_envs, sc.max_dof
-    dvel = rng.normal(size=(B, 6)) * 0.1
-    dtg = rng.normal(size=(nsteps, E, md)) * 0.05
-    dmass = rng.normal(size=B) * sc.body_mass * 0.1
-    _, dL, status = oracle.loss_and_directional(sc, cfg, sc.state(), tg, nsteps, sc.goal_body, sc.goal_pos,
-                                                dvel=np.stack([dvel, 0 * dvel, 0 * dvel]),
-                                                dtargets=np.stack([0 * dtg, dtg, 0 * dtg]),
-                                                dmass=np.stack([0 * dmass, 0 * dmass, dmass]))
     g = _gpu_grads(sc, cfg, tg, nsteps, 4)
-    gpu = np.stack([
-        _per_env(sc, (g["v"] * dvel[:, :3]).sum(1) + (g["w"] * dvel[:, 3:]).sum(1)),
-        (g["tg"] * dtg).sum(axis=(0, 2)),
-        _per_env(sc, g["m"] * dmass)])
-    return sc, cfg, tg, nsteps, dL, gpu, g
-
-
-@pytest.mark.parametrize("which", [0, 1, 2], ids=["velocity", "targets", "mass"])
-def test_gpu_gradient_matches_oracle_duals(diff_case, which, record_property):
-    sc, cfg, tg, nsteps, dL, gpu, g = diff_case
-    ref, got = dL[which], gpu[which]
-    scale = np.abs(ref).max() + 1e-12
-    close = np.abs(got - ref) <= 2e-2 * np.abs(ref) + 1e-3 * scale
-    nonzero = np.abs(ref) > 1e-3 * scale
-    record_property("agree_fraction", float(close.mean()))
-    record_property("nonzero_envs", int(nonzero.sum()))
-    assert nonzero.sum() >= 4
-    assert close.mean() >= 0.75, (ref, got)
-    assert not g["status"].any()
+    return sc, cfg, tg, nsteps, g
 
 
 def test_checkpoint_interval_does_not_change_gradients(diff_case):
-    sc, cfg, tg, nsteps, _, _, g4 = diff_case
+    sc, cfg, tg, nsteps, g4 = diff_case
     for k in (1, 3, 8):
         gk = _gpu_grads(sc, cfg, tg, nsteps, k)
         for key in ("v", "w", "tg", "m"):
@@ -105,7 +72,8 @@ def test_steps_recorded_by_every_form_give_the_same_gradients(diff_case):
     """The recorded steps (state, lambdas and the collision stage's results)
     of the plain, substep and fused forms are bitwise equal, so are the
     gradients."""
-    sc, cfg, tg, nsteps, _, _, g4 = diff_case
+    sc, cfg, tg, nsteps, g4 = diff_case
+    assert not g4["status"].any() and np.abs(g4["tg"]).max() > 0
     for kw in (dict(exec_form="plain"), dict(exec_form="substep"), dict(exec_form="fused", threads_per_env=16)):
         gk = _gpu_grads(sc, cfg, tg, nsteps, 4, **kw)
         for key in ("v", "w", "tg", "m"):

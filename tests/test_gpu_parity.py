@@ -404,3 +404,38 @@ def test_chunked_host_step_equals_device_step():
     for k in rep_dev:
         assert np.array_equal(np.asarray(rep_dev[k]).view(np.int32), np.asarray(rep_host[k]).view(np.int32)), k
     assert not sim2.status().any()
+
+
+@pytest.mark.parametrize("mode", [S.MODE_COLOURED, S.MODE_JACOBI])
+@pytest.mark.parametrize("idx", [1, 2, 3, 4, 5, 6])
+def test_recorded_impulses_match_oracle_per_sweep(idx, mode, record_property):
+    """The impulses a recorded step holds after every sweep of every substep
+    (msh_tape_lambdas) against the FP32 oracle's, row by row, from the FP32
+    oracle's state after 30 steps: within 1e-3 of the env's largest impulse
+    plus 1e-3 of the row's own. The regrouped per-point update and the fused
+    multiply-adds round differently, and on a statically indeterminate
+    contact set (a box on four points) the split of the load among the rows
+    is not unique, so rounding differences along it are not damped."""
+    import torch
+    sc, cfg = scene(idx, mode=mode)
+    tg = sc.target_walk(31)
+    x30, _ = oracle.step(sc, cfg, sc.state(), tg[:30], 30, "f32")
+    sim = make_sim(sc, cfg)
+    sim.set_state(*x30)
+    sim.set_tape(1)
+    sim.step(torch.as_tensor(tg[30]).cuda())
+    got = sim.tape_lambdas(0)
+    sim.set_tape(-1)
+    _, ref = oracle.step_lambdas(sc, cfg, x30, tg[30])
+    assert got.shape == ref.shape
+    used = np.isfinite(ref)
+    assert used.any()
+    worst = 0.0
+    for e in range(sc.num_envs):
+        r, g, m = ref[e], got[e], used[e]
+        if not m.any():
+            continue
+        tol = 1e-3 * np.abs(r[m]).max() + 1e-3 * np.abs(r[m])
+        worst = max(worst, float((np.abs(g[m] - r[m]) / np.maximum(tol, 1e-30)).max()))
+    record_property("worst_ratio", worst)
+    assert worst <= 1.0, worst
