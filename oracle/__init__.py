@@ -5,4 +5,5 @@ package. The product library never imports it.
 """
 from .oracle import (build, load, step, detect, OracleDetect, cores, loss_and_directional,  # noqa: F401
                      loss_value, step_report, OracleReport, render_depth, step_vjp, OracleVJP, trajectory,
-                     goal_seed, rollout_grad, step_f64x, step_lambdas)
+                     goal_seed, rollout_grad, step_f64x, step_lambdas,
+                     clip_cap_drops)

@@ -613,6 +613,9 @@ template <class R> int box_plane(const Shape<R>& box, R off, Pt<R>* out) {
 // (x, y, height), keeping the side where sg * coord - bound <= 0. The output
 // is capped at 8 vertices (a convex quad never exceeds it; rounding on a
 // nearly degenerate polygon could).
+// Number of clip outputs dropped by the 8-vertex cap (tests read it).
+inline long long& clip_cap_drops() { static long long n = 0; return n; }
+
 template <class R> int clip_poly(const R (*in)[3], int n, R (*out)[3], int axis, R sg, R bound) {
   int m = 0;
   for (int i = 0; i < n; ++i) {
@@ -620,11 +623,22 @@ template <class R> int clip_poly(const R (*in)[3], int n, R (*out)[3], int axis,
     const R* Q = in[(i + 1) % n];
     R dp = sg * P[axis] - bound;
     R dq = sg * Q[axis] - bound;
-    if (dp <= R(0) && m < 8) { out[m][0] = P[0]; out[m][1] = P[1]; out[m][2] = P[2]; ++m; }
-    if (((dp < R(0) && dq > R(0)) || (dp > R(0) && dq < R(0))) && m < 8) {
-      R t = dp / (dp - dq);
-      for (int k = 0; k < 3; ++k) out[m][k] = P[k] + (Q[k] - P[k]) * t;
-      ++m;
+    if (dp <= R(0)) {
+      if (m < 8) { out[m][0] = P[0]; out[m][1] = P[1]; out[m][2] = P[2]; ++m; }
+      else {
+#pragma omp atomic
+        ++clip_cap_drops();
+      }
+    }
+    if ((dp < R(0) && dq > R(0)) || (dp > R(0) && dq < R(0))) {
+      if (m < 8) {
+        R t = dp / (dp - dq);
+        for (int k = 0; k < 3; ++k) out[m][k] = P[k] + (Q[k] - P[k]) * t;
+        ++m;
+      } else {
+#pragma omp atomic
+        ++clip_cap_drops();
+      }
     }
   }
   return m;
@@ -1957,6 +1971,11 @@ int oracle_step_lambdas_f32(const OracleScene* sc, const OracleCfg* cfg, float* 
   }
   return 0;
 }
+
+// Clip outputs dropped by the box-box clipper's 8-vertex cap since the
+// library was loaded (a convex quad clipped by four half-planes has at most
+// 8 vertices in exact arithmetic; this counts any rounding case beyond it).
+long long oracle_clip_cap_drops(void) { return orc::clip_cap_drops(); }
 
 int oracle_max_threads(void) {
 #ifdef _OPENMP

@@ -71,6 +71,7 @@ def load():
         lib.oracle_grad_f64.argtypes = [P, P, P, P, P, P, P, C.c_int, P, P, C.c_int, P, P, P, P, P, P, C.c_int]
         lib.oracle_grad_f64.restype = C.c_int
         lib.oracle_max_threads.restype = C.c_int
+        lib.oracle_clip_cap_drops.restype = C.c_longlong
         lib.oracle_step_lambdas_f32.argtypes = [P] * 7 + [C.c_int, P, C.c_int]
         lib.oracle_step_lambdas_f32.restype = C.c_int
         for fn in (lib.oracle_vjp_f32, lib.oracle_vjp_f64):
@@ -512,3 +513,8 @@ def step_lambdas(scene, cfg, state, targets=None, threads: int = 0):
     if rc != 0:
         raise RuntimeError(f"oracle step_lambdas failed: {rc}")
     return tuple(st), lam
+
+
+def clip_cap_drops() -> int:
+    """Outputs the box-box clipper's 8-vertex cap has dropped so far."""
+    return int(load().oracle_clip_cap_drops())

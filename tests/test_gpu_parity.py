@@ -439,3 +439,26 @@ def test_recorded_impulses_match_oracle_per_sweep(idx, mode, record_property):
         worst = max(worst, float((np.abs(g[m] - r[m]) / np.maximum(tol, 1e-30)).max()))
     record_property("worst_ratio", worst)
     assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("mode", [S.MODE_COLOURED, S.MODE_JACOBI])
+def test_one_step_parity_with_restitution(mode, record_property):
+    """Restitution 0.5 (reading C5: contacts approaching faster than 1 m/s
+    target the rebound e * v_n): one step of the falling-sphere scene from the
+    FP32 oracle's state after 25 steps, when spheres strike the boxes and the
+    plane at 1-4 m/s, within the one-step tolerances of the FP32 oracle; the
+    oracle's own step with e = 0 differs, so restitution acted."""
+    sc, cfg = scene(1, 64, mode=mode, restitution=0.5)
+    x25, _ = oracle.step(sc, cfg, sc.state(), None, 25, "f32")
+    sim = make_sim(sc, cfg)
+    sim.set_state(*x25)
+    sim.step()
+    gpu = sim.state_numpy()
+    o32, st = oracle.step(sc, cfg, x25, None, 1, "f32")
+    plain, _ = oracle.step(sc, S.SolverCfg(**{**cfg.__dict__, "restitution": 0.0}), x25, None, 1, "f32")
+    assert _err(o32[2], plain[2]) > 0.1
+    assert np.array_equal(sim.status(), st)
+    ex, ev = _err(gpu[0], o32[0]), _err(gpu[2], o32[2])
+    record_property("err_vs_fp32", [ex, ev])
+    assert ex <= TOL_X and _err(gpu[1], o32[1]) <= TOL_X
+    assert ev <= TOL_V and _err(gpu[3], o32[3]) <= TOL_V

@@ -505,3 +505,45 @@ def test_capsule_entering_a_box_contacts_at_its_ends_and_entry(seed):
         assert abs(g[9] - (_point_box(centre, xb, Rbs, hb)[0] - rad)) < TOL_FRAME
     for t in want:
         assert min(abs(t - u) for u in got) < 1e-6
+
+
+def test_box_box_clipping_never_reaches_its_vertex_cap_on_near_degenerate_faces():
+    """The incident face (a quad) is clipped by the reference face's four side
+    planes one at a time; a convex polygon gains at most one vertex per
+    half-plane, so the result has at most 4 + 4 = 8 vertices in exact
+    arithmetic, the clipper's cap. Rounding could in principle add sign
+    changes where vertices lie within rounding of a side plane; these
+    near-degenerate cases (equal or nearly equal faces, edges aligned to
+    within rounding, tilts of 1e-7 to 1e-4 rad, incident faces larger than
+    the reference face) are run in FP32 and FP64 and the cap must drop
+    nothing."""
+    rng = np.random.default_rng(77)
+    envs = []
+    for k in range(600):
+        h = rng.uniform(0.03, 0.2, 3)
+        e = env()
+        e.static((0.0, 0.0, 0.5), tuple(h), axis_angle((0, 0, 1), float(rng.choice([0.0, np.pi / 2, rng.uniform(0, np.pi)]))))
+        mode = k % 3
+        if mode == 0:      # same footprint, aligned edges
+            hb = h.copy()
+        elif mode == 1:    # edges off by about rounding
+            hb = h * (1.0 + rng.choice([-1.0, 1.0], 3) * rng.uniform(0, 1e-6, 3))
+        else:              # incident face larger than the reference face
+            hb = h * np.array([1.5, 1.3, 1.0])
+        tilt = axis_angle(rng.normal(size=3), float(10.0 ** rng.uniform(-7, -4)))
+        w0, x0, y0, z0 = tilt
+        w1, x1, y1, z1 = e.statics[0][0][3:]
+        q = (w0 * w1 - x0 * x1 - y0 * y1 - z0 * z1, w0 * x1 + x0 * w1 + y0 * z1 - z0 * y1,
+             w0 * y1 - x0 * z1 + y0 * w1 + z0 * x1, w0 * z1 + x0 * y1 - y0 * x1 + z0 * w1)
+        shift = rng.choice([0.0, 1.0], 2) * rng.uniform(-1e-6, 1e-6, 2)
+        R = _rot(e.statics[0][0][3:])
+        c = np.array([0.0, 0.0, 0.5]) + R @ np.array([shift[0], shift[1], h[2] + hb[2] - 0.002])
+        e.body(S.BOX, tuple(hb), 1.0, tuple(c), quat=q)
+        envs.append(e)
+    sc = scene_from_envs(envs)
+    c = cfg(max_contacts=8, max_pairs=4)
+    before = oracle.clip_cap_drops()
+    for prec in ("f32", "f64"):
+        d = oracle.detect(sc, c, sc.pos, sc.quat, prec)
+        assert (d.contact_count >= 1).all()
+    assert oracle.clip_cap_drops() == before

@@ -919,3 +919,39 @@ def test_hinge_without_limits_keeps_turning():
     st, _ = oracle.step(sc, c, sc.state(), None, 50, "f64")
     assert abs(st[3][0][2] - 3.0) < 2e-3                         # free spin about the hinge (solver drift)
     assert abs(_door_angle(st[1][0]) - np.angle(np.exp(1j * 1.5))) < 1e-2   # 3 rad/s for 0.5 s
+
+
+@pytest.mark.parametrize("e_rest", [0.3, 0.5, 0.9])
+def test_restitution_rebounds_at_e_times_approach_speed(e_rest):
+    """Reading C5: a contact approaching faster than 1 m/s targets the
+    rebound speed e * v_n (bias = min(bias, e * v_n)). A sphere 4 mm above
+    the plane (inside the contact offset) falling at 2 m/s, one substep: its
+    approach speed after gravity is |v0| + g h; a single normal row (no
+    tangential motion, so the friction rows stay at zero) converges in the
+    first sweep, so the sphere leaves at exactly e (|v0| + g h)."""
+    r, z0, v0, h = 0.05, 0.054, -2.0, 0.01
+    e = env()
+    e.body(S.SPHERE, (r,), 0.7, (0.3, -0.1, z0), linvel=(0.0, 0.0, v0))
+    sc = scene_from_envs([e])
+    c = cfg(substeps=1, iterations=10, restitution=e_rest)
+    out, st = oracle.step(sc, c, sc.state(), None, 1, "f64")
+    assert not st.any()
+    z0 = float(sc.pos[0, 2])          # as stored (FP32 scene)
+    vz = e_rest * (-v0 + 9.81 * h)
+    assert abs(out[2][0, 2] - vz) < 1e-12
+    assert abs(out[0][0, 2] - (z0 + h * vz)) < 1e-12
+    assert np.abs(out[2][0, :2]).max() < 1e-15
+
+
+def test_restitution_is_off_below_one_metre_per_second():
+    """Below the 1 m/s threshold the speculative bias applies instead: the
+    sphere is stopped exactly where it reaches the plane (v = -s/h)."""
+    r, z0, v0, h = 0.05, 0.054, -0.5, 0.01
+    e = env()
+    e.body(S.SPHERE, (r,), 0.7, (0.3, -0.1, z0), linvel=(0.0, 0.0, v0))
+    sc = scene_from_envs([e])
+    c = cfg(substeps=1, iterations=10, restitution=0.5)
+    out, _ = oracle.step(sc, c, sc.state(), None, 1, "f64")
+    z0, r = float(sc.pos[0, 2]), float(sc.body_dims[0, 0])   # as stored (FP32 scene)
+    assert abs(out[2][0, 2] - (-(z0 - r) / h)) < 1e-12
+    assert abs(out[0][0, 2] - r) < 1e-12
