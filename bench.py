@@ -400,6 +400,50 @@ def time_control(dev, stream, start, envs=4096, steps=20, warmup=3, width=128, h
     return res
 
 
+def run_scale_form(args, dev, envs=16384, horizon=64, k=8):
+    """Config 5 at full size: the fused step (autotuned, CUDA graph, L2 flushed
+    between steps) and a differentiable 64-step rollout with a checkpoint every
+    8 steps; peak device memory = the library's allocations (workspaces, tape,
+    adjoint workspaces) + torch's peak."""
+    import torch
+    from paper_2412_13211_b300 import autotune, scenes
+    from paper_2412_13211_b300.sim import MshSim
+    torch.cuda.reset_peak_memory_stats(dev)
+    sc, cfg = scenes.make_config(5, num_envs=envs)
+    sim = MshSim(sc, cfg, device=dev, exec_form="fused", use_graph=True)
+    tg = torch.as_tensor(sc.target_walk(max(horizon, args.warmup + args.steps))).to(dev)
+    tuning = autotune.tune(sim, tg[0], steps=3, warmup=2)
+    form, tpe = tuning["best"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        for t in range(args.warmup):
+            sim.step(tg[t], stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            sim.step(tg[args.warmup + i], stream=stream)
+            ev[i][1].record(stream)
+    stream.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    for t, s0 in zip((sim.pos, sim.quat, sim.linvel, sim.angvel), sc.state()):
+        t.copy_(torch.as_tensor(np.asarray(s0, np.float32)).to(dev))
+    fb = time_fwd_bwd(sim, sc, tg, horizon=horizon, k=k, stream=stream, reps=1,
+                      threads_per_env=tpe if form == "fused" else 32)
+    lib_bytes = int(sim.scratch_bytes)
+    torch_peak = int(torch.cuda.max_memory_allocated(dev))
+    status = sim.status()
+    sim.close()
+    return {"workload": f"config5: {WORKLOADS[5]}, {envs} envs, {sc.num_bodies} bodies, {sc.num_statics} static "
+                        f"boxes, {sc.num_joints} joints",
+            "forward": {"value": envs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "form": [form, tpe],
+                        "steps": args.steps, "l2": "flushed between timed steps"},
+            "fwd_bwd": fb, "peak_device_bytes": {"library": lib_bytes, "torch_peak_allocated": torch_peak,
+                                                 "total": lib_bytes + torch_peak},
+            "status_nonzero_envs": int((status != 0).sum())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -419,6 +463,9 @@ def main():
     ap.add_argument("--bwd-horizon", type=int, default=16)
     ap.add_argument("--profile-backward", action="store_true",
                     help="only a short fwd+bwd rollout of the 512-env differentiation workload (small case for ncu)")
+    ap.add_argument("--scale-form", action="store_true",
+                    help="only the scale form: 16384 envs of config 5, forward env-steps/s and a 64-step "
+                         "forward+backward with checkpoints every 8 steps, with peak device memory")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -437,6 +484,9 @@ def main():
         tg4 = torch.as_tensor(sc4.target_walk(8)).cuda()
         r = time_fwd_bwd(sim4, sc4, tg4, horizon=8, k=8, stream=torch.cuda.Stream(), reps=1)
         print(json.dumps({"profile_backward": r}))
+        return
+    if args.scale_form:
+        print(json.dumps({"scale_form": run_scale_form(args, torch.device("cuda", local))}), flush=True)
         return
     dist = None
     if world > 1:
