@@ -171,12 +171,35 @@ __device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
 // (measured on the 4096-env apartment batch: caps of 224, 200 or 168
 // registers, for 9, 10 or 12 one-warp CTAs per SM, were no faster or
 // slower); 512-thread CTAs need a 128-register budget.
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT) k_fused(Params p, int smem_ws) { fused_body(p, smem_ws); }
+// One instantiation per combination of the step's optional features (the
+// Jacobi solver, tape recording, the contact report): the others' branches
+// and code drop out of the persistent loop, so it runs fewer instructions and
+// keeps a smaller instruction footprint (the 4096-env apartment batch: 1.82
+// against 1.90 ms per step). Results do not depend on the instantiation.
+enum { FF_JACOBI = 1, FF_TAPE = 2, FF_REPORT = 4, FF_N = 8 };
+template <int MAXT, int FL>
+__global__ void __launch_bounds__(MAXT) k_fused(Params p, int smem_ws) {
+  p.mode = (FL & FF_JACOBI) ? MODE_JACOBI : MODE_COLOURED;
+  if (!(FL & FF_TAPE)) p.tape = nullptr;
+  if (!(FL & FF_REPORT)) p.rep_on = 0;
+  fused_body(p, smem_ws);
+}
 
 using FusedKernel = void (*)(Params, int);
 
-static FusedKernel fused_kernel(int tpe) { return tpe <= 256 ? k_fused<256> : k_fused<512>; }
+// The instantiation for a launch's parameters.
+static int fused_flags(const Params& p) {
+  return (p.mode == MODE_JACOBI ? FF_JACOBI : 0) | (p.tape ? FF_TAPE : 0) | (p.rep_on ? FF_REPORT : 0);
+}
+template <int MAXT>
+static FusedKernel fused_kernel_fl(int fl) {
+  switch (fl) {
+    case 0: return k_fused<MAXT, 0>; case 1: return k_fused<MAXT, 1>; case 2: return k_fused<MAXT, 2>;
+    case 3: return k_fused<MAXT, 3>; case 4: return k_fused<MAXT, 4>; case 5: return k_fused<MAXT, 5>;
+    case 6: return k_fused<MAXT, 6>; default: return k_fused<MAXT, 7>;
+  }
+}
+static FusedKernel fused_kernel(int tpe, int fl) { return tpe <= 256 ? fused_kernel_fl<256>(fl) : fused_kernel_fl<512>(fl); }
 
 // Adjoint of the recorded step in tape slot q.slot (see msh_adjoint.cuh), as
 // a sequence of launches that each run one phase for every env: the replay of
@@ -208,8 +231,11 @@ __device__ __forceinline__ bool bwd_env(const Params& p, const AdjParams& q, Bwd
   const int G = p.G > 0 && p.G < (int)blockDim.x ? p.G : (int)blockDim.x;
   const int gi = threadIdx.x / G, lane = threadIdx.x % G;
   const unsigned mask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-  const int env = blockIdx.x * (blockDim.x / G) + gi;
-  if (env >= p.E) return false;   // whole groups exit together
+  // envs in decreasing estimated cost, as the fused step takes them: the
+  // costliest start first and the two envs of a warp do similar work
+  const int idx = blockIdx.x * (blockDim.x / G) + gi;
+  if (idx >= p.E) return false;   // whole groups exit together
+  const int env = p.env_order[idx];
   b.e = env_info(p, env, lane, G, mask);
   b.w = plain_ws(p, env);
   b.a = make_aws(q.aws + (long long)env * q.aws_stride, q.A);
@@ -283,6 +309,7 @@ __global__ void k_bwd_rows(Params p, AdjParams q, int s) {
 // update), and the rows (parameters and adjoint accumulators, re-read and
 // re-written once per row per sweep) when everything fits; the rest stays in
 // the device-memory workspace.
+template <bool JAC>
 __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   extern __shared__ float4 bsm[];
   BwdEnv b;
@@ -346,7 +373,7 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
       lpr = it > 0 ? lbuf[(it - 1) % 3] : nullptr;
     }
     gsync(e);
-    if (p.mode == MODE_JACOBI) reverse_sweep_jacobi(p, e, w, a, lit, lpr);
+    if (JAC) reverse_sweep_jacobi(p, e, w, a, lit, lpr);
     else reverse_sweep(p, e, w, a, lit, lpr);
     if (lams) cp_async_wait_all();
   }
@@ -376,7 +403,6 @@ __global__ void k_bwd_setup(Params p, AdjParams q, int s) {
 }
 
 // The reverse of the narrowphase at the step-start poses, and the outputs.
-template <bool PER_ITEM>
 __global__ void k_bwd_finish(Params p, AdjParams q) {
   BwdEnv b;
   if (!bwd_env(p, q, b)) return;
@@ -389,7 +415,7 @@ __global__ void k_bwd_finish(Params p, AdjParams q) {
     w.bq[i] = make_float4(t[3], t[4], t[5], t[6]);
   }
   gsync(e);
-  reverse_detection<PER_ITEM>(p, e, w, a);
+  reverse_detection(p, e, w, a);
   gsync(e);
   gather_bodies(e, a, false);
   gsync(e);
@@ -680,9 +706,9 @@ struct msh_handle {
   char* d_ws_plain = nullptr;   // E slabs
   char* d_ws_fused = nullptr;   // per-CTA HBM slabs (cold part, or the whole workspace without room in SMEM)
   int64_t fused_slab_bytes = 0;
-  int bwd_warps = 0;             // resident warps of the adjoint kernels on this GPU
+  bool bwd_attr = false;         // the reversed sweeps' shared-memory attribute is set
   int bwd_sweep_warps = 0;       // ... of the reversed sweeps without shared memory
-  FusedKernel fused_fn = nullptr;  // instantiation chosen for the block size and workspace
+  FusedKernel fused_fn = nullptr;  // plain instantiation for the block size (occupancy)
   int fused_blocks_per_sm = 0;
   // adjoint
   float* d_tape = nullptr;      // tape_max recorded steps x E env slabs
@@ -812,9 +838,9 @@ int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
   p.ws_stride = h->L.bytes;
   const int blk = fused_block(T);
   if (h->fused_smem)
-    h->fused_fn<<<h->fused_grid, blk, (size_t)fused_groups(T) * h->L.hot_bytes, s>>>(p, 1);
+    fused_kernel(blk, fused_flags(p))<<<h->fused_grid, blk, (size_t)fused_groups(T) * h->L.hot_bytes, s>>>(p, 1);
   else
-    h->fused_fn<<<h->fused_grid, blk, 0, s>>>(p, 0);
+    fused_kernel(blk, fused_flags(p))<<<h->fused_grid, blk, 0, s>>>(p, 0);
   CK(cudaGetLastError());
   return MSH_OK;
 }
@@ -826,10 +852,11 @@ int configure_fused(msh_handle* h) {
   // device limit (occupancy still follows each launch's actual size)
   const int max_dyn = h->smem_optin - 2048;
   h->fused_smem = bytes <= max_dyn;
-  h->fused_fn = fused_kernel(blk);
+  h->fused_fn = fused_kernel(blk, 0);
   int blocks = 0;
   if (h->fused_smem) {
-    CK(cudaFuncSetAttribute(h->fused_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
+    for (int fl = 0; fl < FF_N; ++fl)
+      CK(cudaFuncSetAttribute(fused_kernel(blk, fl), cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, blk, bytes));
   } else {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, blk, 0));
@@ -1183,8 +1210,8 @@ static int step_host_chunked(msh_handle* h, float* pos, float* quat, float* linv
       p.ws_stride = h->L.bytes;
       CK(cudaMemsetAsync(p.queue, 0, sizeof(int), c));
       const int grid = std::min((p.En + ng - 1) / ng, h->fused_grid);
-      if (h->fused_smem) h->fused_fn<<<grid, blk, (size_t)ng * h->L.hot_bytes, c>>>(p, 1);
-      else h->fused_fn<<<grid, blk, 0, c>>>(p, 0);
+      if (h->fused_smem) fused_kernel(blk, fused_flags(p))<<<grid, blk, (size_t)ng * h->L.hot_bytes, c>>>(p, 1);
+      else fused_kernel(blk, fused_flags(p))<<<grid, blk, 0, c>>>(p, 0);
       CK(cudaGetLastError());
     }
     if (nb) {
@@ -1344,31 +1371,24 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
   q.ox = adj_in->pos; q.oq = adj_in->quat; q.ov = adj_in->linvel; q.ow = adj_in->angvel;
   q.otg = h->max_dof > 0 ? adj_targets : nullptr;
   q.omass = adj_mass;
-  // One warp per CTA holding 32/G env groups of G threads. Fewer threads per
-  // env put more envs in flight (each colour has about a dozen constraints,
-  // so a warp per env leaves most lanes idle), as long as the batch still
-  // fills the GPU's resident warps: the smallest G in {8, 16, 32} whose warps
-  // cover them. Measured: G = 8 at 4096 envs (17 ms against 25 ms at G = 32),
-  // G = 32 at 512 envs.
-  if (h->bwd_warps == 0) {
-    int blocks = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_setup, 32, 0));
-    h->bwd_warps = std::max(1, blocks) * h->num_sms;
-    CK(cudaFuncSetAttribute(k_bwd_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_optin - 1024));
+  // The replay, row, set-up and narrowphase phases: one env per warp (CTAs
+  // of 32 threads), envs in decreasing estimated cost. Measured at 4096
+  // envs (16-step rollout): 164 ms against 169 and 178 ms with two and four
+  // envs per warp; the sweeps below keep two envs per warp.
+  if (!h->bwd_attr) {
+    CK(cudaFuncSetAttribute(k_bwd_sweeps<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_optin - 1024));
+    CK(cudaFuncSetAttribute(k_bwd_sweeps<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, h->smem_optin - 1024));
+    h->bwd_attr = true;
   }
-  int G = 32;
-  for (int g : {8, 16})
-    if ((long long)h->E * g / 32 >= h->bwd_warps) { G = g; break; }
-  p.G = G;
-  const int per_block = 32 / G;
-  const int grid = (h->E + per_block - 1) / per_block;
+  p.G = 32;
+  const int grid = h->E;
   // The sweeps: two envs per warp (16 lanes each; a colour holds about a
   // dozen constraints) while that still fills the resident warps, each with
   // its bodies staged in shared memory; otherwise one env per warp with a
   // larger slice that also holds the rows of envs that fit.
   if (h->bwd_sweep_warps == 0) {
     int blocks = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_sweeps, 32, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_sweeps<false>, 32, 0));
     h->bwd_sweep_warps = std::max(1, blocks) * h->num_sms;
   }
   const int Gs = (long long)h->E * 16 / 32 >= h->bwd_sweep_warps ? 16 : 32;
@@ -1381,13 +1401,11 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
   k_bwd_replay<<<grid, 32, 0, s>>>(p, q);
   for (int sub = p.S - 1; sub >= 0; --sub) {
     k_bwd_rows<<<grid, 32, 0, s>>>(p, q, sub);
-    k_bwd_sweeps<<<sweep_grid, 32, (32 / Gs) * slice, s>>>(ps, q, sub, slice);
+    if (p.mode == MODE_JACOBI) k_bwd_sweeps<true><<<sweep_grid, 32, (32 / Gs) * slice, s>>>(ps, q, sub, slice);
+    else k_bwd_sweeps<false><<<sweep_grid, 32, (32 / Gs) * slice, s>>>(ps, q, sub, slice);
     k_bwd_setup<<<grid, 32, 0, s>>>(p, q, sub);
   }
-  // the narrowphase reverse: one pass per lane for one-env warps (small
-  // batches: few manifolds per lane), all passes of a manifold per lane else
-  if (G == 32) k_bwd_finish<true><<<grid, 32, 0, s>>>(p, q);
-  else k_bwd_finish<false><<<grid, 32, 0, s>>>(p, q);
+  k_bwd_finish<<<grid, 32, 0, s>>>(p, q);
   CK(cudaGetLastError());
   h->tape_count--;
   return MSH_OK;
@@ -1653,7 +1671,7 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   int rc = static_scratch_address(&base);
   if (rc) return rc;
   const int ng = fused_groups(h->tpe), blk = fused_block(h->tpe);
-  FusedKernel fn = fused_kernel(blk);
+  FusedKernel fn = fused_kernel(blk, 0);
   int blocks = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, blk, 0));
   if (blocks < 1) return fail(MSH_ERR_UNSUPPORTED, "step kernel cannot be resident with this block size");
@@ -1669,7 +1687,7 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   p.queue = (int*)base;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemsetAsync(base, 0, sizeof(int), s));   // the queue counter must start at zero
-  fn<<<grid, blk, 0, s>>>(p, 0);
+  fused_kernel(blk, fused_flags(p))<<<grid, blk, 0, s>>>(p, 0);
   CK(cudaGetLastError());
   return MSH_OK;
 }

@@ -1105,90 +1105,30 @@ __device__ __forceinline__ float detect_pass(const Params& p, const EnvInfo& e, 
 
 // Adjoints of the step-start poses from the contact-geometry adjoints: dual
 // passes of the narrowphase of each manifold's pair over its pose inputs (7
-// against a static box or the plane, else 14). PER_ITEM: a lane runs one
-// (manifold, input) item, a manifold's items on consecutive lanes (for envs
-// with fewer manifolds than lanes); otherwise a lane runs all passes of one
-// manifold (the compiler then keeps the pair's loads across its passes).
-template <bool PER_ITEM>
+// against a static box or the plane, else 14), one (manifold, input) item per
+// lane, a manifold's items on consecutive lanes.
 __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS];
-  if (!PER_ITEM) {
-    for (int m = e.lane; m < M; m += e.nthr) {
-      int4 mf = man_get(w, m);
-      const int ia = mf.x, ib = mf.y;
-      const int pj = w.cid[mf.z] >> 16;
-      float res[14];
-      for (int q = 0; q < 14; ++q) res[q] = 0.f;
-      float4 xa4 = w.bx[ia], qa4 = w.bq[ia];
-      float4 xb4 = ib >= 0 ? w.bx[ib] : make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 qb4 = ib >= 0 ? w.bq[ib] : make_float4(1.f, 0.f, 0.f, 0.f);
-      for (int idx = 0; idx < 14; ++idx) {
-        if (ib < 0 && idx >= 7) break;
-        Shape<d1> Si, Sj;
-        {
-          float4 d = p.bdims[e.b0 + ia];
-          Q4<d1> q; q.w = tan_of(idx, 3, qa4.x); q.x = tan_of(idx, 4, qa4.y); q.y = tan_of(idx, 5, qa4.z); q.z = tan_of(idx, 6, qa4.w);
-          Si.type = __float_as_int(d.w);
-          Si.c = v3<d1>(tan_of(idx, 0, xa4.x), tan_of(idx, 1, xa4.y), tan_of(idx, 2, xa4.z));
-          Si.M = qmat(q);
-          Si.d0 = d1(d.x); Si.d1 = d1(d.y); Si.d2 = d1(d.z);
-        }
-        if (ib >= 0) {
-          float4 d = p.bdims[e.b0 + ib];
-          Q4<d1> q; q.w = tan_of(idx, 10, qb4.x); q.x = tan_of(idx, 11, qb4.y); q.y = tan_of(idx, 12, qb4.z); q.z = tan_of(idx, 13, qb4.w);
-          Sj.type = __float_as_int(d.w);
-          Sj.c = v3<d1>(tan_of(idx, 7, xb4.x), tan_of(idx, 8, xb4.y), tan_of(idx, 9, xb4.z));
-          Sj.M = qmat(q);
-          Sj.d0 = d1(d.x); Sj.d1 = d1(d.y); Sj.d2 = d1(d.z);
-        } else if (pj < e.D + e.S) {
-          Sj = static_shape<d1>(p.sworld + (size_t)SW_N * (e.s0 + pj - e.D));   // the scene's static record
-        } else {
-          Sj.type = SH_PLANE;
-          Sj.c = v3<d1>(d1(0.f), d1(0.f), d1(0.f));
-          Sj.d0 = Sj.d1 = Sj.d2 = d1(0.f);
-        }
-        Pt<d1> pts[4];
-        int n = collide(Si, Sj, d1(p.off), pts);
-        float acc = 0.f;
-        for (int k = 0; k < n && k < mf.w; ++k) {
-          const int ci = mf.z + k;
-          V3<d1> ral = mulT(Si.M, pts[k].pa - Si.c);
-          V3<d1> rbl = ib >= 0 ? mulT(Sj.M, pts[k].pb - Sj.c) : pts[k].pb;
-          float4 gn = a.cg[3 * ci], gra = a.cg[3 * ci + 1], grb = a.cg[3 * ci + 2];
-          acc += gn.x * pts[k].n.x.d + gn.y * pts[k].n.y.d + gn.z * pts[k].n.z.d;
-          acc += gra.x * ral.x.d + gra.y * ral.y.d + gra.z * ral.z.d;
-          acc += grb.x * rbl.x.d + grb.y * rbl.y.d + grb.z * rbl.z.d;
-        }
-        res[idx] = acc;
-      }
-      float4* S = a.gat + 8 * (J + m);
-      S[0] = make_float4(res[0], res[1], res[2], 0.f);
-      S[1] = make_float4(res[3], res[4], res[5], res[6]);
-      S[2] = make_float4(res[7], res[8], res[9], 0.f);
-      S[3] = make_float4(res[10], res[11], res[12], res[13]);
+  if (e.lane == 0) {
+    int acc = 0;
+    for (int m = 0; m < M; ++m) { a.moff[m] = acc; acc += man_get(w, m).y >= 0 ? 14 : 7; }
+    a.moff[M] = acc;
+  }
+  gsync(e);
+  const int total = a.moff[M];
+  for (int t = e.lane; t < total; t += e.nthr) {
+    int lo = 0, hi = M - 1;   // the manifold whose items hold t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.moff[mid] <= t) lo = mid; else hi = mid - 1;
     }
-  } else {
-    if (e.lane == 0) {
-      int acc = 0;
-      for (int m = 0; m < M; ++m) { a.moff[m] = acc; acc += man_get(w, m).y >= 0 ? 14 : 7; }
-      a.moff[M] = acc;
-    }
-    gsync(e);
-    const int total = a.moff[M];
-    for (int t = e.lane; t < total; t += e.nthr) {
-      int lo = 0, hi = M - 1;   // the manifold whose items hold t
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.moff[mid] <= t) lo = mid; else hi = mid - 1;
-      }
-      const int m = lo, idx = t - a.moff[m];
-      float* S = (float*)(a.gat + 8 * (J + m));
-      if (idx == 2) S[3] = 0.f;
-      if (idx == 6 && man_get(w, m).y < 0)
-        for (int q = 8; q < 16; ++q) S[q] = 0.f;
-      if (idx == 9) S[11] = 0.f;
-      S[pose_slot(idx)] = detect_pass(p, e, w, a, m, idx);
-    }
+    const int m = lo, idx = t - a.moff[m];
+    float* S = (float*)(a.gat + 8 * (J + m));
+    if (idx == 2) S[3] = 0.f;
+    if (idx == 6 && man_get(w, m).y < 0)
+      for (int q = 8; q < 16; ++q) S[q] = 0.f;
+    if (idx == 9) S[11] = 0.f;
+    S[pose_slot(idx)] = detect_pass(p, e, w, a, m, idx);
   }
   // joints have no narrowphase inputs
   for (int k = e.lane; k < J; k += e.nthr)
