@@ -644,6 +644,7 @@ AdjLayout make_adj_layout(const Layout& L, int md) {
   A.madj = take((long long)L.P * 4 * f4);
   A.cpose = take((long long)L.C * 4 * f4);
   A.moff = take((long long)(L.P + 1) * 4);
+  A.mord = take((long long)L.P * 4);
   A.gat = take((long long)A.Km * 8 * f4);
   A.cg = take((long long)L.C * 3 * f4);
   A.inc_off = take((L.Dm + 1) * 4); A.inc = take(2LL * A.Km * 4);

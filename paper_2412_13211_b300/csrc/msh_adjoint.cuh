@@ -48,6 +48,7 @@ struct AdjLayout {
   int madj;                           // per manifold: 4 float4 (gIw_a, gIw_b, g(1/m_a), g(1/m_b))
   int cpose;                          // per contact point: 16 floats, its pose adjoints in gather-slot order
   int moff;                           // per manifold + 1: first dual-pass item of the narrowphase reverse
+  int mord;                           // per manifold: the manifolds sorted by narrowphase routine
   int gat;                            // per constraint: 8 float4 (xa, qa, xb, qb, Iwa0, Iwa1|ima, Iwb0, Iwb1|imb)
   int cg;                             // per contact point: 3 float4 (n, ra, rb adjoints)
   int inc_off, inc, tg, bytes;
@@ -75,6 +76,7 @@ struct AWs {
   float4 *cpar, *cadj, *madj;
   float* cpose;
   int* moff;
+  int* mord;
   float4* gat;
   float4* cg;
   int *inc_off, *inc;
@@ -88,7 +90,7 @@ __device__ __forceinline__ AWs make_aws(char* b, const AdjLayout& A) {
   a.rows = (float4*)(b + A.rows); a.radj = (float4*)(b + A.radj);
   a.cpar = (float4*)(b + A.cpar); a.cadj = (float4*)(b + A.cadj); a.madj = (float4*)(b + A.madj);
   a.cpose = (float*)(b + A.cpose);
-  a.moff = (int*)(b + A.moff);
+  a.moff = (int*)(b + A.moff); a.mord = (int*)(b + A.mord);
   a.gat = (float4*)(b + A.gat); a.cg = (float4*)(b + A.cg);
   a.inc_off = (int*)(b + A.inc_off); a.inc = (int*)(b + A.inc); a.tg = (float*)(b + A.tg);
   return a;
@@ -1103,26 +1105,47 @@ __device__ __forceinline__ float detect_pass(const Params& p, const EnvInfo& e, 
   return acc;
 }
 
+// Narrowphase routine class of manifold m's pair (collide's dispatch): the
+// plane against each shape, then each unordered pair of shape types.
+__device__ __forceinline__ int routine_class(const Params& p, const EnvInfo& e, const Ws& w, int m) {
+  const int4 mf = man_get(w, m);
+  const int ta = __float_as_int(p.bdims[e.b0 + mf.x].w);
+  int tb;
+  if (mf.y >= 0) tb = __float_as_int(p.bdims[e.b0 + mf.y].w);
+  else tb = (w.cid[mf.z] >> 16) < e.D + e.S ? SH_BOX : SH_PLANE;
+  if (tb == SH_PLANE) return ta;
+  return 3 + 3 * min(ta, tb) + max(ta, tb);
+}
+
 // Adjoints of the step-start poses from the contact-geometry adjoints: dual
 // passes of the narrowphase of each manifold's pair over its pose inputs (7
 // against a static box or the plane, else 14), one (manifold, input) item per
-// lane, a manifold's items on consecutive lanes.
+// lane. The manifolds are taken sorted by routine class, a manifold's items
+// on consecutive lanes, so that the lanes of a warp mostly run the same
+// routine: its code is fetched once for all of them.
 __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS];
+  enum { NCLS = 12 };
   if (e.lane == 0) {
+    int start[NCLS];
+    for (int c = 0; c < NCLS; ++c) start[c] = 0;
+    for (int m = 0; m < M; ++m) start[routine_class(p, e, w, m)]++;
     int acc = 0;
-    for (int m = 0; m < M; ++m) { a.moff[m] = acc; acc += man_get(w, m).y >= 0 ? 14 : 7; }
+    for (int c = 0; c < NCLS; ++c) { const int n = start[c]; start[c] = acc; acc += n; }
+    for (int m = 0; m < M; ++m) a.mord[start[routine_class(p, e, w, m)]++] = m;
+    acc = 0;
+    for (int i = 0; i < M; ++i) { a.moff[i] = acc; acc += man_get(w, a.mord[i]).y >= 0 ? 14 : 7; }
     a.moff[M] = acc;
   }
   gsync(e);
   const int total = a.moff[M];
   for (int t = e.lane; t < total; t += e.nthr) {
-    int lo = 0, hi = M - 1;   // the manifold whose items hold t
+    int lo = 0, hi = M - 1;   // the sorted position whose items hold t
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (a.moff[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    const int m = lo, idx = t - a.moff[m];
+    const int m = a.mord[lo], idx = t - a.moff[lo];
     float* S = (float*)(a.gat + 8 * (J + m));
     if (idx == 2) S[3] = 0.f;
     if (idx == 6 && man_get(w, m).y < 0)
