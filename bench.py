@@ -34,7 +34,7 @@ METRIC = "env-steps/sec at 4096 envs (fwd and fwd+bwd) vs plain step; % HBM roof
 # DRAM bytes (read + write) of one k_fused launch from an ncu capture, keyed by
 # (config, envs, threads per env) and stored with the hash of the step kernel's
 # sources it was captured on; a launch of any other build reports null.
-FUSED_TRAFFIC = {(3, 4096, 16): ("110ebb5ef9aef733", 50.0224e6 + 12.38912e6)}
+FUSED_TRAFFIC = {(3, 4096, 16): ("7eb625388ad98bd1", 50.104576e6 + 12.519936e6)}
 KERNEL_SOURCES = ("msh.cu", "msh_stages.cuh", "msh_collide.cuh", "msh_math.cuh")
 WORKLOADS = {1: "falling spheres over static boxes", 2: "fixed-base arm and gripper at a counter",
              3: "apartment batch of uneven size with a mobile manipulator",

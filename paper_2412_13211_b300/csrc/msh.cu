@@ -99,107 +99,12 @@ __global__ void k_substep(Params p) {
   stage_integrate_pos(p, e, w, p.sub);
 }
 
-// One whole step per env; persistent CTAs pull envs from an atomic queue.
-// With p.G < 32 a warp holds 32 / p.G env groups, each with its own
-// workspace slice, queue entries and group-local barriers.
-__device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
-  extern __shared__ __align__(16) char smem[];
-  __shared__ int scr[33];
-  __shared__ int s_next;
-  const int G = p.G > 0 && p.G < (int)blockDim.x ? p.G : (int)blockDim.x;   // threads per env
-  const int gi = threadIdx.x / G, lane = threadIdx.x % G;
-  const unsigned mask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-  const long long slot = (long long)blockIdx.x * (blockDim.x / G) + gi;   // workspace slot of this group
-  char* slab = p.ws + slot * p.ws_stride;   // per-slot HBM slab (cold part, or all)
-  char* base = smem_ws ? smem + (size_t)gi * p.L.hot_bytes : slab;
-  Ws w = make_ws(base, slab + p.L.hot_bytes, p.L);
-  for (;;) {
-    int idx;
-    if (G < 32) {
-      int v = 0;
-      if (lane == 0) v = atomicAdd(p.queue, 1);
-      idx = __shfl_sync(mask, v, 0, G);
-    } else {
-      if (threadIdx.x == 0) s_next = atomicAdd(p.queue, 1);
-      __syncthreads();
-      idx = s_next;
-    }
-    if (idx >= p.En) break;
-    EnvInfo e = env_info(p, p.env_order[idx], lane, G, mask);
-    stage_load(p, e, w);
-    gsync(e);
-    stage_aabb(p, e, w);
-    gsync(e);
-    stage_broadphase(p, e, w, scr);
-    // contacts first land in the full-capacity cold arrays; an env with at
-    // most L.Ch of them moves them into the hot part and solves there, a
-    // larger one solves from the cold arrays (same arithmetic, other memory)
-    char* cold = slab + p.L.hot_bytes;
-    w.cn = (float4*)(cold + p.L.cnc);
-    stage_narrowphase(p, e, w, scr);
-    {
-      const int nc = w.misc[MC_CONTACTS];
-      if (nc <= p.L.Ch) {
-        float4* hcn = (float4*)(base + p.L.cn);
-        for (int i = e.lane; i < nc; i += e.nthr) hcn[i] = w.cn[i];
-        w.cn = hcn;
-        w.kra = (float4*)(base + p.L.kra); w.krb = (float4*)(base + p.L.krb); w.klam = (float4*)(base + p.L.klam);
-      } else {
-        w.kra = (float4*)(cold + p.L.krac); w.krb = (float4*)(cold + p.L.krbc); w.klam = (float4*)(cold + p.L.klamc);
-      }
-      gsync(e);
-    }
-    stage_colour(p, e, w);
-    if (p.tape) tape_collision(p, e, w);
-    for (int s = 0; s < p.S; ++s) {
-      stage_integrate_vel(p, e, w, s);
-      gsync(e);
-      stage_prep(p, e, w);
-      gsync(e);
-      for (int it = 0; it < p.N; ++it) stage_solve_iter(p, e, w, s, it);
-      stage_accum_impulse(p, e, w, s);
-      stage_integrate_pos(p, e, w, s);
-      gsync(e);
-    }
-    stage_report(p, e, w);
-    stage_store(p, e, w);
-    gsync(e);
-  }
-}
+#include "msh_fused.cuh"
 
-// Up to 256 threads per CTA the compiler's own register choice is kept
-// (measured on the 4096-env apartment batch: caps of 224, 200 or 168
-// registers, for 9, 10 or 12 one-warp CTAs per SM, were no faster or
-// slower); 512-thread CTAs need a 128-register budget.
-// One instantiation per combination of the step's optional features (the
-// Jacobi solver, tape recording, the contact report): the others' branches
-// and code drop out of the persistent loop, so it runs fewer instructions and
-// keeps a smaller instruction footprint (the 4096-env apartment batch: 1.82
-// against 1.90 ms per step). Results do not depend on the instantiation.
-enum { FF_JACOBI = 1, FF_TAPE = 2, FF_REPORT = 4, FF_N = 8 };
-template <int MAXT, int FL>
-__global__ void __launch_bounds__(MAXT) k_fused(Params p, int smem_ws) {
-  p.mode = (FL & FF_JACOBI) ? MODE_JACOBI : MODE_COLOURED;
-  if (!(FL & FF_TAPE)) p.tape = nullptr;
-  if (!(FL & FF_REPORT)) p.rep_on = 0;
-  fused_body(p, smem_ws);
+static FusedKernel fused_kernel(int blk, int tpe, int fl) {
+  if (tpe == 16) return fused_kernel_g16(fl);
+  return blk <= 256 ? fused_kernel_fl<256, 0>(fl) : fused_kernel_fl<512, 0>(fl);
 }
-
-using FusedKernel = void (*)(Params, int);
-
-// The instantiation for a launch's parameters.
-static int fused_flags(const Params& p) {
-  return (p.mode == MODE_JACOBI ? FF_JACOBI : 0) | (p.tape ? FF_TAPE : 0) | (p.rep_on ? FF_REPORT : 0);
-}
-template <int MAXT>
-static FusedKernel fused_kernel_fl(int fl) {
-  switch (fl) {
-    case 0: return k_fused<MAXT, 0>; case 1: return k_fused<MAXT, 1>; case 2: return k_fused<MAXT, 2>;
-    case 3: return k_fused<MAXT, 3>; case 4: return k_fused<MAXT, 4>; case 5: return k_fused<MAXT, 5>;
-    case 6: return k_fused<MAXT, 6>; default: return k_fused<MAXT, 7>;
-  }
-}
-static FusedKernel fused_kernel(int tpe, int fl) { return tpe <= 256 ? fused_kernel_fl<256>(fl) : fused_kernel_fl<512>(fl); }
 
 // Adjoint of the recorded step in tape slot q.slot (see msh_adjoint.cuh), as
 // a sequence of launches that each run one phase for every env: the replay of
@@ -839,9 +744,9 @@ int enqueue_step(msh_handle* h, const Params& p0, cudaStream_t s) {
   p.ws_stride = h->L.bytes;
   const int blk = fused_block(T);
   if (h->fused_smem)
-    fused_kernel(blk, fused_flags(p))<<<h->fused_grid, blk, (size_t)fused_groups(T) * h->L.hot_bytes, s>>>(p, 1);
+    fused_kernel(blk, T, fused_flags(p))<<<h->fused_grid, blk, (size_t)fused_groups(T) * h->L.hot_bytes, s>>>(p, 1);
   else
-    fused_kernel(blk, fused_flags(p))<<<h->fused_grid, blk, 0, s>>>(p, 0);
+    fused_kernel(blk, T, fused_flags(p))<<<h->fused_grid, blk, 0, s>>>(p, 0);
   CK(cudaGetLastError());
   return MSH_OK;
 }
@@ -853,11 +758,11 @@ int configure_fused(msh_handle* h) {
   // device limit (occupancy still follows each launch's actual size)
   const int max_dyn = h->smem_optin - 2048;
   h->fused_smem = bytes <= max_dyn;
-  h->fused_fn = fused_kernel(blk, 0);
+  h->fused_fn = fused_kernel(blk, h->tpe, 0);
   int blocks = 0;
   if (h->fused_smem) {
     for (int fl = 0; fl < FF_N; ++fl)
-      CK(cudaFuncSetAttribute(fused_kernel(blk, fl), cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
+      CK(cudaFuncSetAttribute(fused_kernel(blk, h->tpe, fl), cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn));
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, blk, bytes));
   } else {
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, h->fused_fn, blk, 0));
@@ -1211,8 +1116,8 @@ static int step_host_chunked(msh_handle* h, float* pos, float* quat, float* linv
       p.ws_stride = h->L.bytes;
       CK(cudaMemsetAsync(p.queue, 0, sizeof(int), c));
       const int grid = std::min((p.En + ng - 1) / ng, h->fused_grid);
-      if (h->fused_smem) fused_kernel(blk, fused_flags(p))<<<grid, blk, (size_t)ng * h->L.hot_bytes, c>>>(p, 1);
-      else fused_kernel(blk, fused_flags(p))<<<grid, blk, 0, c>>>(p, 0);
+      if (h->fused_smem) fused_kernel(blk, p.G, fused_flags(p))<<<grid, blk, (size_t)ng * h->L.hot_bytes, c>>>(p, 1);
+      else fused_kernel(blk, p.G, fused_flags(p))<<<grid, blk, 0, c>>>(p, 0);
       CK(cudaGetLastError());
     }
     if (nb) {
@@ -1672,7 +1577,7 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   int rc = static_scratch_address(&base);
   if (rc) return rc;
   const int ng = fused_groups(h->tpe), blk = fused_block(h->tpe);
-  FusedKernel fn = fused_kernel(blk, 0);
+  FusedKernel fn = fused_kernel(blk, h->tpe, 0);
   int blocks = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, blk, 0));
   if (blocks < 1) return fail(MSH_ERR_UNSUPPORTED, "step kernel cannot be resident with this block size");
@@ -1688,7 +1593,7 @@ extern "C" int msh_step_static_scratch(msh_handle* h, const msh_state* st, const
   p.queue = (int*)base;
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemsetAsync(base, 0, sizeof(int), s));   // the queue counter must start at zero
-  fused_kernel(blk, fused_flags(p))<<<grid, blk, 0, s>>>(p, 0);
+  fused_kernel(blk, p.G, fused_flags(p))<<<grid, blk, 0, s>>>(p, 0);
   CK(cudaGetLastError());
   return MSH_OK;
 }

@@ -116,7 +116,7 @@ __device__ __forceinline__ void add_sym(float* G, const V3<float>& g, const V3<f
 // ---------------------------------------------------------------------------
 // Loads the recorded step-start state into the workspace (as stage_load does
 // from the state arrays) and the joints' row information.
-__device__ void load_from_tape(const Params& p, const EnvInfo& e, const Ws& w, const float* tape) {
+static __device__ void load_from_tape(const Params& p, const EnvInfo& e, const Ws& w, const float* tape) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
     const float* t = tape + 13 * i;
     float4 inv = p.binv[e.b0 + i];
@@ -142,7 +142,7 @@ template <class T> __device__ __forceinline__ void world_inv_inertia(const Q4<T>
 }
 
 // Constraint -> body incidence lists in constraint order (for deterministic gathers).
-__device__ void build_incidence(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
+static __device__ void build_incidence(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
   if (e.lane == 0) {
     const int K = e.J + w.misc[MC_MANIFOLDS];
     for (int i = 0; i <= e.D; ++i) a.inc_off[i] = 0;
@@ -166,7 +166,7 @@ __device__ void build_incidence(const Params& p, const EnvInfo& e, const Ws& w, 
 
 // Generic rows of every constraint at the workspace poses (for the reverse
 // sweeps): la|m, aa|bias, ab|gamma, Ia|0, Ib|clamp, plus a kind code.
-__device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
+static __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
   const int nc = w.misc[MC_CONTACTS];
   for (int t = e.lane; t < e.J + nc; t += e.nthr) {
     if (t < e.J) {
@@ -531,7 +531,7 @@ __device__ __forceinline__ void reverse_constraint(const Params& p, const Ws& w,
 
 // Reverse of one sweep: colours in reverse order; within a colour (its
 // constraints share no dynamic body) the joints, then the manifolds.
-__device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* lam_it,
+static __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* lam_it,
                               const float* lam_prev) {
   const int J = e.J;
   const int ncol = w.misc[MC_COLOURS];
@@ -560,7 +560,7 @@ __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws& w, co
 // The slots are the forward's per-constraint velocity-change array.
 
 // True-mass velocity change of constraint k from its recorded lambda changes.
-__device__ void jacobi_dv(const Params& p, const Ws& w, const AWs& a, int k, int J, const float* lam_it,
+static __device__ void jacobi_dv(const Params& p, const Ws& w, const AWs& a, int k, int J, const float* lam_it,
                           const float* lam_prev) {
   V3<float> z = v3<float>(0.f, 0.f, 0.f);
   BodyVel d;
@@ -606,7 +606,7 @@ __device__ void jacobi_dv(const Params& p, const Ws& w, const AWs& a, int k, int
 
 // Phase 2 for constraint k: its reversed rows on its local copies.
 template <bool JOINT>
-__device__ void reverse_constraint_jacobi(const Params& p, const Ws& w, const AWs& a, int k, int J,
+static __device__ void reverse_constraint_jacobi(const Params& p, const Ws& w, const AWs& a, int k, int J,
                                           const float* lam_it, const float* lam_prev) {
   int A, B;
   if (JOINT) { const int4 ji = w.jinfo[k]; A = ji.x; B = ji.y; }
@@ -648,7 +648,7 @@ __device__ void reverse_constraint_jacobi(const Params& p, const Ws& w, const AW
   w.jdv[4 * k + 2] = f4(g.vb, 0.f); w.jdv[4 * k + 3] = f4(g.wb, 0.f);
 }
 
-__device__ void reverse_sweep_jacobi(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a,
+static __device__ void reverse_sweep_jacobi(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a,
                                      const float* lam_it, const float* lam_prev) {
   const int J = e.J, K = J + w.misc[MC_MANIFOLDS];
   for (int k = e.lane; k < K; k += e.nthr) jacobi_dv(p, w, a, k, J, lam_it, lam_prev);
@@ -787,7 +787,7 @@ __device__ __forceinline__ d1 tan_of(int idx, int k, float v) { return d1(v, idx
 // One dual pass of a joint's row set-up along input `idx` (x_a 0-2, q_a 3-6,
 // x_b 7-9, q_b 10-13, targets 14-16): the row adjoints contracted with the
 // rows' derivatives along that input (0 for an input the joint lacks).
-__device__ float joint_geom_pass(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int k, int idx,
+static __device__ float joint_geom_pass(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int k, int idx,
                                  const float* tg) {
   const JointDesc& j = p.joints[e.j0 + k];
   const int A = j.parent, B = j.child;
@@ -835,7 +835,7 @@ __device__ __forceinline__ void rotate_adjoint(const float4& q4, const V3<float>
 // tangent basis of the normal) for the adjoints of its normal, tangents,
 // world arms and bias: out = adjoints of x_a 0-2, q_a 3-6, x_b 7-9, q_b
 // 10-13, n 14-16, ra_l 17-19, rb_l 20-22 (a static b's anchor is in world).
-__device__ void contact_geom_adjoint(const Params& p, const Ws& w, const AWs& a, int ci, int ia, int ib,
+static __device__ void contact_geom_adjoint(const Params& p, const Ws& w, const AWs& a, int ci, int ia, int ib,
                                      float* out) {
   for (int k = 0; k < 23; ++k) out[k] = 0.f;
   const float4* Q = a.cadj + CADJ_F4 * ci;
@@ -893,7 +893,7 @@ __device__ __forceinline__ int pose_slot(int idx) { return idx < 3 ? idx : idx <
 // geometry); a contact point's pose adjoints are summed per manifold in point
 // order, its normal and arm adjoints added to the point, a joint's target
 // adjoints to its DoFs.
-__device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
+static __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS], K = J + M, nc = w.misc[MC_CONTACTS];
   for (int k = e.lane; k < K; k += e.nthr) {
     int A, B;
@@ -972,7 +972,7 @@ __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, co
 // Per body: sums the constraint gather slots in constraint order into the
 // pose adjoints (and, when `inertia`, the world-inverse-inertia and 1/m
 // adjoints into bI0/bI1).
-__device__ void gather_bodies(const EnvInfo& e, const AWs& a, bool inertia) {
+static __device__ void gather_bodies(const EnvInfo& e, const AWs& a, bool inertia) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 gx = a.bx[i], gq = a.bq[i];
     float4 I0 = make_float4(0.f, 0.f, 0.f, 0.f), I1 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -997,7 +997,7 @@ __device__ void gather_bodies(const EnvInfo& e, const AWs& a, bool inertia) {
 // World inverse inertia adjoints -> orientation adjoint and principal inverse
 // inertia adjoint (dual passes over q and the 3 principal values); 1/m
 // adjoint into the mass accumulator.
-__device__ void reverse_inertia(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
+static __device__ void reverse_inertia(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 I0 = a.bI0[i], I1 = a.bI1[i];
     const float gW[6] = {I0.x, I0.y, I0.z, I0.w, I1.x, I1.y};
@@ -1023,7 +1023,7 @@ __device__ void reverse_inertia(const Params& p, const EnvInfo& e, const Ws& w, 
 
 // Reverse of x += h v and q <- normalise(q + h/2 (0,w) q) for one substep,
 // with x_s, q_s the substep-start pose and v_e, w_e the velocities it used.
-__device__ void reverse_integrate(const Params& p, const EnvInfo& e, const AWs& a, const float* sub_tape) {
+static __device__ void reverse_integrate(const Params& p, const EnvInfo& e, const AWs& a, const float* sub_tape) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
     const float* t = sub_tape + 19 * i;
     const float qw = t[3], qx = t[4], qy = t[5], qz = t[6];
@@ -1123,7 +1123,7 @@ __device__ __forceinline__ int routine_class(const Params& p, const EnvInfo& e, 
 // lane. The manifolds are taken sorted by routine class, a manifold's items
 // on consecutive lanes, so that the lanes of a warp mostly run the same
 // routine: its code is fetched once for all of them.
-__device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
+static __device__ void reverse_detection(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS];
   enum { NCLS = 12 };
   if (e.lane == 0) {

@@ -287,7 +287,7 @@ __device__ __forceinline__ void load_jinfo(const Params& p, const EnvInfo& e, co
   }
 }
 
-__device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
+static __device__ void stage_load(const Params& p, const EnvInfo& e, const Ws& w) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
     int g = e.b0 + i;
     float4 inv = p.binv[g];
@@ -376,7 +376,7 @@ __device__ __forceinline__ Shape<nf> coll_shape(const Params& p, const Ws& w, co
 // ---------------------------------------------------------------------------
 // a2: AABBs of the bodies (static boxes: StaticWorld)
 // ---------------------------------------------------------------------------
-__device__ void stage_aabb(const Params& p, const EnvInfo& e, const Ws& w) {
+static __device__ void stage_aabb(const Params& p, const EnvInfo& e, const Ws& w) {
   // the static boxes' AABBs (computed once per scene) next to the bodies'
   for (int i = e.lane; i < e.S; i += e.nthr) {
     const float4* r = p.sworld + (size_t)SW_N * (e.s0 + i);
@@ -403,7 +403,7 @@ __device__ __forceinline__ bool jointed(const EnvInfo& e, const Ws& w, int i, in
   return false;
 }
 
-__device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w, int* scr) {
+static __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w, int* scr) {
   const int D = e.D, W = e.D + e.S;   // j in (i, W]; W is the plane
   // The candidates (i, j), i < D, i < j <= W, in row order: row i holds W - i
   // of them. A round tests nthr consecutive candidates; each thread walks its
@@ -447,7 +447,7 @@ __device__ void stage_broadphase(const Params& p, const EnvInfo& e, const Ws& w,
 // ---------------------------------------------------------------------------
 // a4: narrowphase, pairs in order, points in routine order, truncated at C
 // ---------------------------------------------------------------------------
-__device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w, int* scr) {
+static __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w, int* scr) {
   const int npairs = w.misc[MC_PAIRS];
   int cbase = 0, mbase = 0;
   bool over = false;
@@ -500,7 +500,7 @@ __device__ void stage_narrowphase(const Params& p, const EnvInfo& e, const Ws& w
 // a5 (once per step): greedy colouring of joints then manifolds, colour-sorted
 // constraint order; Jacobi split counts and body incidence lists
 // ---------------------------------------------------------------------------
-__device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
+static __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS], K = J + M;
   // The constraints of a colour share no dynamic body, so their order does
   // not change the result. A colour lists its joints first, then its
@@ -607,7 +607,7 @@ __device__ void stage_colour(const Params& p, const EnvInfo& e, const Ws& w) {
 }
 
 // Records the collision stage's results of a recorded step (tape record t4).
-__device__ void tape_collision(const Params& p, const EnvInfo& e, const Ws& w) {
+static __device__ void tape_collision(const Params& p, const EnvInfo& e, const Ws& w) {
   const Layout& L = p.L;
   float* t = tape_env(p, e.env) + tape_layout(L, p.S, p.N, p.max_dof).t4;
   const int nc = w.misc[MC_CONTACTS], nm = w.misc[MC_MANIFOLDS], K = e.J + nm, ncol = w.misc[MC_COLOURS];
@@ -627,7 +627,7 @@ __device__ void tape_collision(const Params& p, const EnvInfo& e, const Ws& w) {
 }
 
 // The recorded collision stage back into a workspace (the adjoint's replay).
-__device__ void untape_collision(const Params& p, const EnvInfo& e, const Ws& w, const float* tape) {
+static __device__ void untape_collision(const Params& p, const EnvInfo& e, const Ws& w, const float* tape) {
   const Layout& L = p.L;
   const float* t = tape + tape_layout(L, p.S, p.N, p.max_dof).t4;
   const int* misc = (const int*)(t + tc_misc(L));
@@ -649,7 +649,7 @@ __device__ void untape_collision(const Params& p, const EnvInfo& e, const Ws& w,
 // ---------------------------------------------------------------------------
 // a1: gravity; world inverse inertia
 // ---------------------------------------------------------------------------
-__device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
+static __device__ void stage_integrate_vel(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 v = w.bv[i];
     v.x = v.x + p.gx * p.h; v.y = v.y + p.gy * p.h; v.z = v.z + p.gz * p.h;
@@ -872,7 +872,7 @@ __device__ int joint_geom(const JointDesc& j, bool hasA, const V3<T>& xa, const 
 
 __device__ __forceinline__ int joint_ndof(int type) { return type == JT_PLANAR ? 3 : 1; }
 
-__device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k) {
+static __device__ void joint_rows(const Params& p, const EnvInfo& e, const Ws& w, int k) {
   const JointDesc& j = p.joints[e.j0 + k];
   const int A = j.parent, B = j.child;
   RowCtx ctx = row_ctx(w, A, B);
@@ -950,7 +950,7 @@ __device__ __forceinline__ void point_K(const RowCtx& ctx, const V3<float>* d, c
   }
 }
 
-__device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int ci) {
+static __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int ci) {
   int ids = w.cid[ci];
   int a = ids & 0xffff, bc = ids >> 16;
   int b = bc < e.D ? bc : -1;
@@ -983,7 +983,7 @@ __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int
   w.kx[ci] = make_float4(K[3], K[4], K[5], sc);
 }
 
-__device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
+static __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
   const int nc = w.misc[MC_CONTACTS];
   // joints, then contacts: two loops, so that a round of threads takes one kind
   for (int t = e.lane; t < e.J; t += e.nthr) joint_rows(p, e, w, t);
@@ -1128,7 +1128,7 @@ __device__ __forceinline__ void tape_lambdas(const Params& p, const EnvInfo& e, 
 }
 
 // One solver iteration over every constraint of the env.
-__device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w, int sub, int it) {
+static __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w, int sub, int it) {
   const int J = e.J;
   if (p.mode == MODE_COLOURED) {
     const int ncol = w.misc[MC_COLOURS];
@@ -1190,7 +1190,7 @@ __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const Ws& w,
 // ---------------------------------------------------------------------------
 // a7: positions
 // ---------------------------------------------------------------------------
-__device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
+static __device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
     float4 x = w.bx[i], v = w.bv[i], wv = w.bw[i], q = w.bq[i];
     if (p.tape) {
@@ -1224,7 +1224,7 @@ __device__ void stage_integrate_pos(const Params& p, const EnvInfo& e, const Ws&
 //     within theta_max of the finger's opening direction (F.o >= cos |F||o|).
 // ---------------------------------------------------------------------------
 // After substep `sub`'s sweeps: add each contact's lambdas to its impulse sum.
-__device__ void stage_accum_impulse(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
+static __device__ void stage_accum_impulse(const Params& p, const EnvInfo& e, const Ws& w, int sub) {
   if (!p.rep_on) return;
   const int nc = w.misc[MC_CONTACTS];
   for (int c = e.lane; c < nc; c += e.nthr) {
@@ -1243,7 +1243,7 @@ __device__ __forceinline__ bool rep_counts(const Params& p, const EnvInfo& e, in
 
 // At the end of the step (final poses); plain float arithmetic in the
 // oracle's order (the library is built without FMA contraction).
-__device__ void stage_report(const Params& p, const EnvInfo& e, const Ws& w) {
+static __device__ void stage_report(const Params& p, const EnvInfo& e, const Ws& w) {
   if (!p.rep_on) return;
   const int nc = w.misc[MC_CONTACTS];
   const int D = e.D;
@@ -1331,7 +1331,7 @@ __device__ void stage_report(const Params& p, const EnvInfo& e, const Ws& w) {
 // ---------------------------------------------------------------------------
 // a8: write back, status
 // ---------------------------------------------------------------------------
-__device__ void stage_store(const Params& p, const EnvInfo& e, const Ws& w) {
+static __device__ void stage_store(const Params& p, const EnvInfo& e, const Ws& w) {
   int bad = 0;
   for (int i = e.lane; i < e.D; i += e.nthr) {
     int g = e.b0 + i;
