@@ -317,15 +317,12 @@ __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, f
   if (B >= 0) jv = dotf(ab, v.wb) - dotf(la, v.vb);
   if (A >= 0) jv = jv + dotf(la, v.va) + dotf(aa, v.wa);
   const float u = jv + bias + gamma * lam_before;
-  bool clamped;
-  float fric_sign = 0.f;
-  if (clamp >= 0.f) clamped = lam_after == clamp || lam_after == -clamp;
-  else if (clamp == CLAMP_UNI) clamped = lam_after == 0.f;
-  else if (clamp == CLAMP_FRIC) {
-    float lim = mu * x.lam_n_after;
-    clamped = lam_after == lim || lam_after == -lim;
-    fric_sign = lam_after == lim ? 1.f : -1.f;
-  } else clamped = false;
+  // the clamp state as selects (the lanes of a warp reverse rows of
+  // different clamp kinds at the same time)
+  const float lim = clamp >= 0.f ? clamp : (clamp == CLAMP_FRIC ? mu * x.lam_n_after : 0.f);
+  const bool bounded = clamp >= 0.f || clamp == CLAMP_FRIC || clamp == CLAMP_UNI;
+  const bool clamped = bounded && (lam_after == lim || lam_after == -lim);
+  const float fric_sign = lam_after == lim ? 1.f : -1.f;
   float gpre = clamped ? 0.f : a_after;
   gfric = clamped && clamp == CLAMP_FRIC ? fric_sign * mu * a_after : 0.f;
   glam_before += gpre;
