@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libmsh.so")
-SOURCES = [os.path.join(HERE, "csrc", n) for n in ("msh.cu", "msh_fused16.cu", "msh_labels.cu", "msh_render.cu")]
+SOURCES = [os.path.join(HERE, "csrc", n) for n in ("msh.cu", "msh_fused16.cu", "msh_fused32.cu", "msh_labels.cu", "msh_render.cu")]
 DEPS = (glob.glob(os.path.join(HERE, "csrc", "*.cu")) + glob.glob(os.path.join(HERE, "csrc", "*.cuh"))
         + glob.glob(os.path.join(HERE, "csrc", "*.h"))
         + [os.path.join(ROOT, "include", "msh.h")])

@@ -103,6 +103,7 @@ __global__ void k_substep(Params p) {
 
 static FusedKernel fused_kernel(int blk, int tpe, int fl) {
   if (tpe == 16) return fused_kernel_g16(fl);
+  if (tpe == 32 && blk == 32) return fused_kernel_g32(fl);
   return blk <= 256 ? fused_kernel_fl<256, 0>(fl) : fused_kernel_fl<512, 0>(fl);
 }
 

@@ -84,9 +84,10 @@ __device__ __forceinline__ void fused_body(Params& p, int smem_ws) {
 // Jacobi solver, tape recording, the contact report): the others' branches
 // and code drop out of the persistent loop, so it runs fewer instructions and
 // keeps a smaller instruction footprint (the 4096-env apartment batch: 1.82
-// against 1.90 ms per step); the group size of 16 threads per env, the
-// autotuner's usual choice, has its own instantiations with it fixed (1.78
-// against 1.82 ms). Results do not depend on the instantiation.
+// against 1.90 ms per step); the group sizes of 16 and 32 threads per env,
+// the autotuner's usual choices, have their own instantiations with the size
+// fixed (1.78 against 1.82 ms at 16). Results do not depend on the
+// instantiation.
 enum { FF_JACOBI = 1, FF_TAPE = 2, FF_REPORT = 4, FF_N = 8 };
 template <int MAXT, int FL, int GC>
 __global__ void __launch_bounds__(MAXT) k_fused(Params p, int smem_ws) {
@@ -111,6 +112,8 @@ static FusedKernel fused_kernel_fl(int fl) {
   }
 }
 
-// The instantiations with 16 threads per env (msh_fused16.cu, its own
-// translation unit so that the library's sources compile in parallel).
+// The instantiations with 16 and 32 threads per env (msh_fused16.cu,
+// msh_fused32.cu: translation units of their own, so that the library's
+// sources compile in parallel).
 FusedKernel fused_kernel_g16(int fl);
+FusedKernel fused_kernel_g32(int fl);
