@@ -368,6 +368,8 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
  * env: joint k's row r at k * 8 + r (8 slots per joint of the largest env),
  * then contact point c's normal, first and second friction row at
  * 8 * Jmax + 3 c + {0, 1, 2}; slots the step does not use are unspecified.
+ * (The tape itself keeps 4 slots per contact point so that the step writes
+ * aligned vectors; this copy is repacked to the 3-slot layout on the host.)
  * Synchronises `stream`. Returns MSH_ERR_INVALID_ARG for an empty slot.
  */
 int32_t msh_tape_rows(const msh_handle* h);

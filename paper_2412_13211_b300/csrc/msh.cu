@@ -116,11 +116,12 @@ static FusedKernel fused_kernel(int blk, int tpe, int fl) {
 // device-memory workspaces, so the phases are separate kernels: each gets the
 // registers and instruction footprint of its own code instead of the largest
 // phase's. A CTA of 32 threads holds 32/G env groups of G threads.
-// Asynchronous 4-byte copy from device to shared memory (cp.async), its
-// group commit and the wait for every committed group of the thread.
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+// Asynchronous 16-byte copy from device to shared memory (cp.async; both
+// addresses 16-byte aligned), its group commit and the wait for every
+// committed group of the thread.
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -229,8 +230,8 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   const float* lam0 = b.tape + b.tl.t2 + (long long)s * p.N * p.tape_Rm;
   const int RJ = ROWS_PER_JOINT * e.J;                 // joint row slots in use
   const int nc = b.w.misc[MC_CONTACTS], nm = b.w.misc[MC_MANIFOLDS];
-  const int RU = ROWS_PER_JOINT * p.L.Jm + 3 * nc;     // lambda slots in use (joints of the largest env first)
-  const int RU4 = (RU + 3) / 4;                        // float4s per lambda buffer
+  const int RU = ROWS_PER_JOINT * p.L.Jm + 4 * nc;     // lambda slots in use (joints of the largest env first)
+  const int RU4 = RU / 4;                              // float4s per lambda buffer (RU is a multiple of 4)
   const int need_l = 3 * RU4 * 16;
   const int need_b = 4 * e.D * 16;
   const int need_r = (2 * RJ * ROW_F4 + (CPAR_F4 + CADJ_F4) * nc + 4 * nm) * 16;
@@ -265,7 +266,7 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
   if (lams) {
     for (int k = p.N - 1; k >= 0 && k >= p.N - 2; --k) {
       const float* src = lam0 + (long long)k * p.tape_Rm;
-      for (int i = e.lane; i < RU; i += e.nthr) cp_async4(lbuf[k % 3] + i, src + i);
+      for (int i = e.lane; i < RU4; i += e.nthr) cp_async16(lbuf[k % 3] + 4 * i, src + 4 * i);
     }
     cp_async_commit();
     cp_async_wait_all();
@@ -277,7 +278,7 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
       if (it >= 2) {
         // lbuf[(it - 2) % 3] held sweep it + 1, whose reversal has finished
         const float* src = lam0 + (long long)(it - 2) * p.tape_Rm;
-        for (int i = e.lane; i < RU; i += e.nthr) cp_async4(lbuf[(it - 2) % 3] + i, src + i);
+        for (int i = e.lane; i < RU4; i += e.nthr) cp_async16(lbuf[(it - 2) % 3] + 4 * i, src + 4 * i);
       }
       cp_async_commit();
       lit = lbuf[it % 3];
@@ -1215,7 +1216,7 @@ int msh_set_tape(msh_handle* h, int32_t max_steps) {
   drop_graph(h);
   const TapeLayout tl = tape_layout(h->L, h->cfg.substeps, h->cfg.iterations, h->max_dof);
   h->tape_slab = tl.slab;
-  h->tape_Rm = ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C;
+  h->tape_Rm = ROWS_PER_JOINT * h->L.Jm + 4 * h->L.C;
   int rc;
   if (max_steps > h->tape_cap) {
     cudaDeviceSynchronize();
@@ -1243,16 +1244,28 @@ int32_t msh_tape_count(const msh_handle* h) { return h ? h->tape_count : 0; }
 
 int32_t msh_tape_rows(const msh_handle* h) { return h ? ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C : 0; }
 
+// The tape keeps 4 slots per contact point (aligned vector stores); the
+// inspection layout has 3, so each sweep's record is repacked on the host.
+
 int msh_tape_lambdas(msh_handle* h, int32_t slot, float* out_host, void* stream) {
   if (!h || !out_host) return fail(MSH_ERR_INVALID_ARG, "NULL argument");
   if (slot < 0 || slot >= h->tape_count) return fail(MSH_ERR_INVALID_ARG, "no recorded step in that tape slot");
   const TapeLayout tl = tape_layout(h->L, h->cfg.substeps, h->cfg.iterations, h->max_dof);
-  const size_t per_env = (size_t)h->cfg.substeps * h->cfg.iterations * msh_tape_rows(h);
+  const size_t sweeps = (size_t)h->cfg.substeps * h->cfg.iterations;
+  const size_t rows = (size_t)msh_tape_rows(h), Rm = (size_t)h->tape_Rm, RJ = (size_t)ROWS_PER_JOINT * h->L.Jm;
+  std::vector<float> raw(sweeps * Rm * (size_t)h->E);
   cudaStream_t s = (cudaStream_t)stream;
   const float* src = h->d_tape + ((long long)slot * h->E) * h->tape_slab + tl.t2;
-  CK(cudaMemcpy2DAsync(out_host, per_env * 4, src, (size_t)h->tape_slab * 4, per_env * 4, (size_t)h->E,
+  CK(cudaMemcpy2DAsync(raw.data(), sweeps * Rm * 4, src, (size_t)h->tape_slab * 4, sweeps * Rm * 4, (size_t)h->E,
                        cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  for (size_t k = 0; k < sweeps * (size_t)h->E; ++k) {
+    const float* a = raw.data() + k * Rm;
+    float* o = out_host + k * rows;
+    std::memcpy(o, a, RJ * 4);
+    for (size_t c = 0; c < (size_t)h->L.C; ++c)
+      for (size_t i = 0; i < 3; ++i) o[RJ + 3 * c + i] = a[RJ + 4 * c + i];
+  }
   return MSH_OK;
 }
 
@@ -1306,7 +1319,10 @@ int msh_backward(msh_handle* h, const msh_state* adj_out, msh_state* adj_in, flo
     h->bwd_sweep_warps = std::max(1, blocks) * h->num_sms;
   }
   const int Gs = (long long)h->E * 16 / 32 >= h->bwd_sweep_warps ? 16 : 32;
-  const int lam_bytes = 3 * ((ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C + 3) / 4) * 16;
+  // three lambda buffers sized for 3/4 of the contact capacity (the
+  // shared-memory carve-out then leaves L1 the room the rows need; an env
+  // with more contacts reads its lambdas from device memory)
+  const int lam_bytes = 3 * (ROWS_PER_JOINT * h->L.Jm + 3 * h->L.C) * 4 / 16 * 16;
   const int slice = Gs == 32 ? bwd_sweep_slice(h) : lam_bytes + 4 * h->Dm * 16;
   const int sweep_grid = (h->E + 32 / Gs - 1) / (32 / Gs);
   Params ps = p;

@@ -102,7 +102,7 @@ __device__ __forceinline__ V3<float> sym_outer_diag(const V3<float>& g, const V3
 // Row index of joint k row r, or of contact point c row i (the recorded
 // lambdas of a step use this numbering).
 __device__ __forceinline__ int jrow(int k, int r) { return k * ROWS_PER_JOINT + r; }
-__device__ __forceinline__ int crow(const Layout& L, int c, int i) { return ROWS_PER_JOINT * L.Jm + 3 * c + i; }
+__device__ __forceinline__ int crow(const Layout& L, int c, int i) { return ROWS_PER_JOINT * L.Jm + 4 * c + i; }
 
 // Adds the symmetric outer product g a^T + a g^T (diagonal once) of an
 // inverse-inertia adjoint, in the entry order xx xy xz yy yz zz.
@@ -372,9 +372,11 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
   float gbias = Q3.w;
   float gl0 = Q4.w, gl1 = Q5.x, gl2 = Q5.y;
   float gK10 = Q5.z, gK20 = Q5.w, gK21 = Q6.x;
-  const float la0 = lam_it[rn], la1 = lam_it[rn + 1], la2 = lam_it[rn + 2];
-  const float lb0 = lam_prev ? lam_prev[rn] : 0.f, lb1 = lam_prev ? lam_prev[rn + 1] : 0.f,
-              lb2 = lam_prev ? lam_prev[rn + 2] : 0.f;
+  // a point's three lambdas start a 16-byte slot of the sweep's record
+  const float4 LA = *reinterpret_cast<const float4*>(lam_it + rn);
+  const float4 LB = lam_prev ? *reinterpret_cast<const float4*>(lam_prev + rn) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float la0 = LA.x, la1 = LA.y, la2 = LA.z;
+  const float lb0 = LB.x, lb1 = LB.y, lb2 = LB.z;
   const float D0 = la0 - lb0, D1 = la1 - lb1, D2 = la2 - lb2;
   // the point's impulse and the velocities before the point
   const V3<float> Pi = (n * D0 + t1 * D1) + t2 * D2;

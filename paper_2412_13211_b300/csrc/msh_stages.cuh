@@ -89,7 +89,7 @@ struct Params {
   // tape (recorded for the adjoint when non-null): slab per env, see TapeLayout
   float* tape;
   long long tape_slab;   // floats per env slab of one recorded step
-  int tape_Rm;           // row slots per env: ROWS_PER_JOINT * Jm + 3 * C
+  int tape_Rm;           // row slots per env and sweep: ROWS_PER_JOINT * Jm + 4 * C (a multiple of 4)
   // contact report (when rep_on; see stage_report)
   int rep_on;
   const int* rep_flags;      // per body: bit 0 robot link, bit 1 end-effector link
@@ -108,7 +108,7 @@ struct Params {
 // Tape of one recorded step, per env (floats):
 //   state at the step start:       Dm x 13  (x, q, v, w)
 //   per substep s:                 Dm x 19  (x_s, q_s, v_s, w_s after gravity; v, w after the solve)
-//   lambda after every sweep:      S x N x Rm (joint k row r: k*8 + r; contact c row i: 8*Jm + 3c + i)
+//   lambda after every sweep:      S x N x Rm (joint k row r: k*8 + r; contact c row i: 8*Jm + 4c + i)
 //   joint targets of the step:     max_dof
 // Tape of one recorded step, floats per env: t0 the start state (13 per
 // body), t1 per substep the poses and velocities (19 per body), t2 the
@@ -118,10 +118,10 @@ struct Params {
 struct TapeLayout { long long t0, t1, t2, t3, t4, slab; };
 __host__ __device__ __forceinline__ TapeLayout tape_layout(const Layout& L, int S, int N, int md) {
   TapeLayout t;
-  const long long Rm = (long long)ROWS_PER_JOINT * L.Jm + 3LL * L.C;
+  const long long Rm = (long long)ROWS_PER_JOINT * L.Jm + 4LL * L.C;
   t.t0 = 0;
   t.t1 = t.t0 + 13LL * L.Dm;
-  t.t2 = t.t1 + 19LL * L.Dm * S;
+  t.t2 = (t.t1 + 19LL * L.Dm * S + 3) & ~3LL;   // the sweeps' lambdas start on 16 bytes
   t.t3 = t.t2 + (long long)S * N * Rm;
   t.t4 = (t.t3 + md + 3) & ~3LL;
   t.slab = (t.t4 + ((13LL * L.C + 3) & ~3LL) + 4LL * L.P + L.K + (MAX_COLOURS + 1) + MC_N + 3) & ~3LL;
@@ -1112,21 +1112,29 @@ __device__ __forceinline__ BodyVel load_vel(const Ws& w, int a, int b) {
   return v;
 }
 
-// Records the lambdas of constraint k after its update in sweep `it`.
+// Records the lambdas of constraint k after its update in sweep `it`: a
+// joint's 8 row slots as two 16-byte stores (unused slots 0), a contact
+// point's three rows as one (4 slots per point, the last 0). The sweep's
+// record starts on 16 bytes (tape slab, t2 and tape_Rm are multiples of 4
+// floats), so these are aligned vector stores rather than scattered words.
 __device__ __forceinline__ void tape_lambdas(const Params& p, const EnvInfo& e, const Ws& w, int k, int sub, int it) {
   TapeLayout tl = tape_layout(p.L, p.S, p.N, p.max_dof);
   float* t = tape_env(p, e.env) + tl.t2 + (long long)(sub * p.N + it) * p.tape_Rm;
   if (k < e.J) {
-    const JointDesc& j = p.joints[e.j0 + k];
-    const int nr = joint_row_count(j);
-    const float4* rows = w.jr + (size_t)j.roff * ROW_F4;
-    for (int r = 0; r < nr; ++r) t[k * ROWS_PER_JOINT + r] = rows[ROW_F4 * r + 3].w;
+    const int4 ji = w.jinfo[k];   // first row, row count
+    const float4* rows = w.jr + (size_t)ji.z * ROW_F4;
+    float v[ROWS_PER_JOINT];
+#pragma unroll
+    for (int r = 0; r < ROWS_PER_JOINT; ++r) v[r] = r < ji.w ? rows[ROW_F4 * r + 3].w : 0.f;
+    float4* q = reinterpret_cast<float4*>(t + k * ROWS_PER_JOINT);
+    q[0] = make_float4(v[0], v[1], v[2], v[3]);
+    q[1] = make_float4(v[4], v[5], v[6], v[7]);
   } else {
     int4 mf = man_get(w, k - e.J);
+    float4* q = reinterpret_cast<float4*>(t + ROWS_PER_JOINT * p.L.Jm);
     for (int c = mf.z; c < mf.z + mf.w; ++c) {
-      float4 l = w.klam[c];
-      float* q = t + ROWS_PER_JOINT * p.L.Jm + 3 * c;
-      q[0] = l.x; q[1] = l.y; q[2] = l.z;
+      const float4 l = w.klam[c];
+      q[c] = make_float4(l.x, l.y, l.z, 0.f);
     }
   }
 }
