@@ -18,6 +18,7 @@ slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -146,7 +147,7 @@ def workload_config(args, scene, cfg):
     return {"workload": f"config{args.config}: {WORKLOADS.get(args.config, 'batch')}, {scene.num_envs} envs",
             "envs": scene.num_envs, "bodies": scene.num_bodies, "static_boxes": scene.num_statics,
             "joints": scene.num_joints, "dt": cfg.dt, "substeps": cfg.substeps, "iterations": cfg.iterations,
-            "solver": "coloured PGS",
+            "solver": "mass-split Jacobi" if cfg.mode == 1 else "coloured PGS",
             "l2": "GPU arm: flushed between timed steps (256 MB write); the CPU arm has no GPU cache"}
 
 
@@ -159,6 +160,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     scene, cfg = scenes.make_config(args.config, num_envs=args.envs)
+    cfg = dataclasses.replace(cfg, mode=args.mode)
     tg = scene.target_walk(args.steps + args.warmup)
     threads = os.cpu_count() or 1
     st, _ = oracle.step(scene, cfg, scene.state(), tg[:args.warmup], args.warmup, "f32", threads=threads)
@@ -453,6 +455,8 @@ def main():
     ap.add_argument("--impl", default="msh", choices=["msh", "reference"])
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--envs", type=int, default=4096)
+    ap.add_argument("--mode", type=int, default=0, choices=[0, 1],
+                    help="solver: 0 coloured PGS (the configurations' own), 1 mass-split Jacobi")
     ap.add_argument("--threads-per-env", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -497,6 +501,7 @@ def main():
     from paper_2412_13211_b300 import replicas
     start, _ = replicas.env_range(args.envs, rank)
     scene, cfg = scenes.make_config(args.config, num_envs=args.envs, env_start=start)
+    cfg = dataclasses.replace(cfg, mode=args.mode)
     from paper_2412_13211_b300 import autotune
     sim = MshSim(scene, cfg, device=dev, exec_form="fused", use_graph=True)
     total = args.warmup + args.steps
