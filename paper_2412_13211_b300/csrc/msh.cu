@@ -307,7 +307,7 @@ __global__ void k_bwd_sweeps(Params p, AdjParams q, int s, int slice) {
 __global__ void k_bwd_setup(Params p, AdjParams q, int s) {
   BwdEnv b;
   if (!bwd_env<32>(p, q, b)) return;
-  reverse_setup(p, b.e, b.w, b.a, b.tape + b.tl.t3);
+  reverse_setup(p, b.e, b.w, b.a);
   gsync(b.e);
   gather_bodies(b.e, b.a, true);
   gsync(b.e);

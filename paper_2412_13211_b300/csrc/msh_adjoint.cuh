@@ -24,10 +24,10 @@
 //     of the normal, tangents, arms, masses, bias, carried lambdas and
 //     couplings, with the inverse-inertia and inverse-mass adjoints kept per
 //     manifold;
-//   * row set-up (lever arms, Jacobians, biases, drives) and the narrowphase:
-//     local Jacobians by single-tangent dual numbers, one input direction at a
-//     time, contracted with the row/contact adjoints; the contact geometry by
-//     a hand-written reverse;
+//   * row set-up (lever arms, Jacobians, biases, drives): hand-written
+//     reverses of the joint and contact row geometry; the narrowphase: local
+//     Jacobians by single-tangent dual numbers, one input direction at a
+//     time, contracted with the contact adjoints;
 //   * effective masses, couplings and world inverse inertias: hand-written
 //     reverse.
 // Per-body sums are gathered in constraint order, so results are
@@ -783,39 +783,6 @@ __device__ __forceinline__ void contact_mass_adjoint(const AWs& a, int ci, bool 
 
 __device__ __forceinline__ d1 tan_of(int idx, int k, float v) { return d1(v, idx == k ? 1.f : 0.f); }
 
-// One dual pass of a joint's row set-up along input `idx` (x_a 0-2, q_a 3-6,
-// x_b 7-9, q_b 10-13, targets 14-16): the row adjoints contracted with the
-// rows' derivatives along that input (0 for an input the joint lacks).
-static __device__ float joint_geom_pass(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int k, int idx,
-                                 const float* tg) {
-  const JointDesc& j = p.joints[e.j0 + k];
-  const int A = j.parent, B = j.child;
-  const bool drive = j.k > 0.f || j.d > 0.f;
-  const int nd = drive ? joint_ndof(j.type) : 0;
-  if ((idx < 7 && A < 0) || (idx >= 14 && idx - 14 >= nd)) return 0.f;
-  const int nr = joint_row_count(j);
-  float4 xa4 = A >= 0 ? w.bx[A] : make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 qa4 = A >= 0 ? w.bq[A] : make_float4(1.f, 0.f, 0.f, 0.f);
-  float4 xb4 = w.bx[B], qb4 = w.bq[B];
-  V3<d1> xa = v3<d1>(tan_of(idx, 0, xa4.x), tan_of(idx, 1, xa4.y), tan_of(idx, 2, xa4.z));
-  Q4<d1> qa; qa.w = tan_of(idx, 3, qa4.x); qa.x = tan_of(idx, 4, qa4.y); qa.y = tan_of(idx, 5, qa4.z); qa.z = tan_of(idx, 6, qa4.w);
-  V3<d1> xb = v3<d1>(tan_of(idx, 7, xb4.x), tan_of(idx, 8, xb4.y), tan_of(idx, 9, xb4.z));
-  Q4<d1> qb; qb.w = tan_of(idx, 10, qb4.x); qb.x = tan_of(idx, 11, qb4.y); qb.y = tan_of(idx, 12, qb4.z); qb.z = tan_of(idx, 13, qb4.w);
-  d1 t[3];
-  for (int c = 0; c < 3; ++c) t[c] = tan_of(idx, 14 + c, c < nd ? tg[j.dof + c] : 0.f);
-  GRow<d1> g[ROWS_PER_JOINT];
-  int n = joint_geom<d1>(j, A >= 0, xa, qa, xb, qb, t, p.h, p.jbeta, g);
-  float acc = 0.f;
-  for (int r = 0; r < n && r < nr; ++r) {
-    const float4* G = a.radj + ROW_F4 * jrow(k, r);
-    acc += G[0].x * g[r].la.x.d + G[0].y * g[r].la.y.d + G[0].z * g[r].la.z.d;
-    acc += G[1].x * g[r].aa.x.d + G[1].y * g[r].aa.y.d + G[1].z * g[r].aa.z.d;
-    acc += G[2].x * g[r].ab.x.d + G[2].y * g[r].ab.y.d + G[2].z * g[r].ab.z.d;
-    acc += G[1].w * g[r].bias.d;
-  }
-  return acc;
-}
-
 // Adjoint of r = R(q) v (R the rotation matrix of the quaternion q = (w, u),
 // as qmat forms it, R v = v + 2w (u x v) + 2 u x (u x v)) for the adjoint g of
 // r: adds R^T g to gv and dr/dq^T g to gq (w, x, y, z).
@@ -828,6 +795,164 @@ __device__ __forceinline__ void rotate_adjoint(const float4& q4, const V3<float>
   gq[0] += 2.f * dot(g, cross(u, v));
   const V3<float> gu = cross(v, g) * (2.f * w) + g * (2.f * dot(u, v)) + v * (2.f * dot(u, g)) - u * (4.f * dot(v, g));
   gq[1] += gu.x; gq[2] += gu.y; gq[3] += gu.z;
+}
+
+// Hand-written reverse of a joint's row geometry (joint_geom): from the
+// adjoints of its rows' Jacobians and biases (the accumulators the reversed
+// sweeps and the mass-part reverse left in radj) to the adjoints of the poses
+// x_a (out 0-2), q_a (3-6), x_b (7-9), q_b (10-13) and of the joint's targets
+// (14-16). Each step follows the branch its forward evaluation takes (the
+// sign of q_r.w, the side of a limit's speculative bias). The forward, for
+// reference: r_a = R(q_a) p_a, r_b = R(q_b) p_b, the world anchors x + r,
+// dp = x_b + r_b - x_a - r_a, the frames q_FA = q_a q_jA and q_FB = q_b q_jB
+// with axes u_x, u_y, u_z = the columns of R(q_FA), q_r = conj(q_FA) q_FB
+// (negated when q_r.w < 0); a linear row along u has J = (-u, -(r1 x u),
+// r_b x u), an angular row (0, -u, u).
+static __device__ void joint_geom_adjoint(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, int k,
+                                          float* out) {
+  for (int i = 0; i < 17; ++i) out[i] = 0.f;
+  const JointDesc& j = p.joints[e.j0 + k];
+  const int A = j.parent, B = j.child;
+  const bool hasA = A >= 0, drive = j.k > 0.f || j.d > 0.f;
+  const float h = p.h, tb = p.jbeta / h;
+  const V3<float> z3 = v3<float>(0.f, 0.f, 0.f);
+  // the forward's values
+  const float4 xa4 = hasA ? w.bx[A] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 qa4 = hasA ? w.bq[A] : make_float4(1.f, 0.f, 0.f, 0.f);
+  const float4 xb4 = w.bx[B], qb4 = w.bq[B];
+  const V3<float> pa_l = tv<float>(j.pa), pb_l = tv<float>(j.pb);
+  const Q4<float> qjA = tq<float>(j.qa), qjB = tq<float>(j.qb);
+  V3<float> ra = z3, pa_w = pa_l, xA = pa_l;
+  Q4<float> qFA = qjA;
+  if (hasA) {
+    xA = f3(xa4);
+    ra = mul(qmat(ldq4(qa4)), pa_l);
+    pa_w = xA + ra;
+    qFA = qmul(ldq4(qa4), qjA);
+  }
+  const V3<float> rb = mul(qmat(ldq4(qb4)), pb_l), pb_w = f3(xb4) + rb;
+  const Q4<float> qFB = qmul(ldq4(qb4), qjB);
+  const M3<float> MF = qmat(qFA), MB = qmat(qFB);
+  const V3<float> ux = col(MF, 0), uy = col(MF, 1), uz = col(MF, 2);
+  const V3<float> dp = pb_w - pa_w;
+  Q4<float> qr = qmul(qconj(qFA), qFB);
+  const float sgn = qr.w < 0.f ? -1.f : 1.f;
+  if (sgn < 0.f) { qr.w = -qr.w; qr.x = -qr.x; qr.y = -qr.y; qr.z = -qr.z; }
+  const V3<float> raB = hasA ? pb_w - xA : z3;
+  // adjoints
+  V3<float> gux = z3, guy = z3, guz = z3, gra = z3, grb = z3, graB = z3, gdp = z3, gcr = z3;
+  float gq[4] = {0.f, 0.f, 0.f, 0.f};   // of q_r (w, x, y, z)
+  float gth = 0.f;                        // of the drive/limit angle
+  const float4* G0 = a.radj + ROW_F4 * jrow(k, 0);
+  int r = 0;
+  // a linear row along u with arms (r1, r_b); returns the bias adjoint
+  auto rev_lin = [&](const V3<float>& u, const V3<float>& r1, V3<float>* gu, V3<float>& gr1) {
+    const float4* G = G0 + ROW_F4 * r++;
+    const V3<float> gla = f3(G[0]), gaa = f3(G[1]), gab = f3(G[2]);
+    if (gu) *gu = ((*gu - gla) - cross(gaa, r1)) + cross(gab, rb);
+    gr1 = gr1 - cross(u, gaa);
+    grb = grb + cross(u, gab);
+    return G[1].w;
+  };
+  // an angular row about u
+  auto rev_ang = [&](V3<float>& gu) {
+    const float4* G = G0 + ROW_F4 * r++;
+    gu = (gu + f3(G[2])) - f3(G[1]);
+    return G[1].w;
+  };
+  // the soft drive's bias factor (Catto 2011), as g_soft forms it
+  const float soft = (h * j.k / (j.d + h * j.k)) / h;
+  int fbc = -1;   // column of R(q_FB) in the angular rows' error (revolute 0, planar 2)
+  if (j.type == JT_REVOLUTE) {
+    for (int c = 0; c < 3; ++c) {
+      const float gb = rev_lin(unit<float>(c), ra, nullptr, gra);
+      setc(gdp, c, comp(gdp, c) + tb * gb);
+    }
+    fbc = 0;
+    const V3<float> fb = col(MB, 0), cr = cross(ux, fb);
+    { const float gb = tb * rev_ang(guy); gcr = gcr + uy * gb; guy = guy + cr * gb; }
+    { const float gb = tb * rev_ang(guz); gcr = gcr + uz * gb; guz = guz + cr * gb; }
+    if (drive) { const float gC = soft * rev_ang(gux); gth += gC; out[14] -= gC; }
+    if (j.lo < j.hi) {
+      const float theta = 2.f * atan2f(qr.x, qr.w);
+      for (int c = 0; c < 2; ++c) {
+        V3<float> gu = z3;
+        const float gb = rev_ang(gu);
+        gux = c == 0 ? gux + gu : gux - gu;   // about u_x, then -u_x
+        const float C = c == 0 ? theta - j.lo : j.hi - theta;
+        const float gC = C > 0.f ? gb / h : tb * gb;
+        gth += c == 0 ? gC : -gC;
+      }
+    }
+    gux = gux + cross(fb, gcr);
+    gcr = cross(gcr, ux);   // now the adjoint of R(q_FB)'s column
+    const float den = qr.w * qr.w + qr.x * qr.x;
+    if (den > 0.f) { gq[1] += gth * (2.f * qr.w) / den; gq[0] -= gth * (2.f * qr.x) / den; }
+  } else if (j.type == JT_PRISMATIC) {
+    { const float gb = tb * rev_lin(uy, raB, &guy, graB); gdp = gdp + uy * gb; guy = guy + dp * gb; }
+    { const float gb = tb * rev_lin(uz, raB, &guz, graB); gdp = gdp + uz * gb; guz = guz + dp * gb; }
+    gq[1] += 2.f * tb * rev_ang(gux);
+    gq[2] += 2.f * tb * rev_ang(guy);
+    gq[3] += 2.f * tb * rev_ang(guz);
+    const float dd = dot(dp, ux);
+    float gdd = 0.f;
+    if (drive) { const float gC = soft * rev_lin(ux, raB, &gux, graB); gdd += gC; out[14] -= gC; }
+    for (int c = 0; c < 2; ++c) {
+      V3<float> gu = z3;
+      const float gb = rev_lin(c == 0 ? ux : -ux, raB, &gu, graB);
+      gux = c == 0 ? gux + gu : gux - gu;
+      const float C = c == 0 ? dd - j.lo : j.hi - dd;
+      const float gC = C > 0.f ? gb / h : tb * gb;
+      gdd += c == 0 ? gC : -gC;
+    }
+    gdp = gdp + ux * gdd;
+    gux = gux + dp * gdd;
+  } else {
+    { const float gb = tb * rev_lin(uz, raB, &guz, graB); gdp = gdp + uz * gb; guz = guz + dp * gb; }
+    fbc = 2;
+    const V3<float> fb = col(MB, 2), cr = cross(uz, fb);
+    { const float gb = tb * rev_ang(gux); gcr = gcr + ux * gb; gux = gux + cr * gb; }
+    { const float gb = tb * rev_ang(guy); gcr = gcr + uy * gb; guy = guy + cr * gb; }
+    if (drive) {
+      { const float gC = soft * rev_lin(ux, raB, &gux, graB); gdp = gdp + ux * gC; gux = gux + dp * gC; out[14] -= gC; }
+      { const float gC = soft * rev_lin(uy, raB, &guy, graB); gdp = gdp + uy * gC; guy = guy + dp * gC; out[15] -= gC; }
+      { const float gC = soft * rev_ang(guz); gth += gC; out[16] -= gC; }
+    }
+    guz = guz + cross(fb, gcr);
+    gcr = cross(gcr, uz);
+    const float den = qr.w * qr.w + qr.z * qr.z;
+    if (den > 0.f) { gq[3] += gth * (2.f * qr.w) / den; gq[0] -= gth * (2.f * qr.z) / den; }
+  }
+  // q_r = sgn conj(q_FA) q_FB
+  Q4<float> g0;
+  g0.w = sgn * gq[0]; g0.x = sgn * gq[1]; g0.y = sgn * gq[2]; g0.z = sgn * gq[3];
+  const Q4<float> gFAq = qconj(qmul(g0, qconj(qFB))), gFBq = qmul(qFA, g0);
+  float gFA[4] = {gFAq.w, gFAq.x, gFAq.y, gFAq.z}, gFB[4] = {gFBq.w, gFBq.x, gFBq.y, gFBq.z};
+  V3<float> unused = z3;
+  const float4 fa4 = make_float4(qFA.w, qFA.x, qFA.y, qFA.z), fb4 = make_float4(qFB.w, qFB.x, qFB.y, qFB.z);
+  rotate_adjoint(fa4, unit<float>(0), gux, unused, gFA);
+  rotate_adjoint(fa4, unit<float>(1), guy, unused, gFA);
+  rotate_adjoint(fa4, unit<float>(2), guz, unused, gFA);
+  if (fbc >= 0) rotate_adjoint(fb4, unit<float>(fbc), gcr, unused, gFB);
+  // q_FB = q_b q_jB, q_FA = q_a q_jA
+  Q4<float> t;
+  t.w = gFB[0]; t.x = gFB[1]; t.y = gFB[2]; t.z = gFB[3];
+  const Q4<float> gqb = qmul(t, qconj(qjB));
+  out[10] = gqb.w; out[11] = gqb.x; out[12] = gqb.y; out[13] = gqb.z;
+  // positions: dp = p_b - p_a, raB = p_b - x_a, p = x + r
+  const V3<float> gpb = gdp + graB;
+  out[7] = gpb.x; out[8] = gpb.y; out[9] = gpb.z;
+  grb = grb + gpb;
+  rotate_adjoint(qb4, pb_l, grb, unused, out + 10);
+  if (hasA) {
+    t.w = gFA[0]; t.x = gFA[1]; t.y = gFA[2]; t.z = gFA[3];
+    const Q4<float> gqa = qmul(t, qconj(qjA));
+    out[3] = gqa.w; out[4] = gqa.x; out[5] = gqa.y; out[6] = gqa.z;
+    const V3<float> gxa = (z3 - gdp) - graB;
+    out[0] = gxa.x; out[1] = gxa.y; out[2] = gxa.z;
+    gra = gra - gdp;
+    rotate_adjoint(qa4, pa_l, gra, unused, out + 3);
+  }
 }
 
 // Adjoint of one contact point's row geometry (contact_geom, then the
@@ -887,12 +1012,11 @@ __device__ __forceinline__ int pose_slot(int idx) { return idx < 3 ? idx : idx <
 
 // The reverse of the row set-up: per constraint the effective-mass part
 // (onto Jacobians, arms, inverse inertias and inverse masses, written to the
-// constraint's gather slot); then one item per joint and input (a dual pass
-// of the joint's rows) and per contact point (the hand-written reverse of its
-// geometry); a contact point's pose adjoints are summed per manifold in point
-// order, its normal and arm adjoints added to the point, a joint's target
-// adjoints to its DoFs.
-static __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
+// constraint's gather slot); then one item per joint and per contact point
+// (the hand-written reverses of their row geometry); a contact point's pose
+// adjoints are summed per manifold in point order, its normal and arm
+// adjoints added to the point, a joint's target adjoints to its DoFs.
+static __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
   const int J = e.J, M = w.misc[MC_MANIFOLDS], K = J + M, nc = w.misc[MC_CONTACTS];
   for (int k = e.lane; k < K; k += e.nthr) {
     int A, B;
@@ -925,21 +1049,19 @@ static __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws
     S[7] = make_float4(gIwb[4], gIwb[5], gimb, 0.f);
   }
   gsync(e);
-  const int NJ = 17 * J, NC = nc;
-  for (int t = e.lane; t < NJ + NC; t += e.nthr) {
-    if (t < NJ) {
-      const int k = t / 17, idx = t % 17;
-      const float v = joint_geom_pass(p, e, w, a, k, idx, tg);
-      if (idx < 14) {
-        float* S = (float*)(a.gat + 8 * k);
-        S[pose_slot(idx)] = v;
-        if (idx == 2 || idx == 9) S[pose_slot(idx) + 1] = 0.f;
-      } else {
-        const JointDesc& j = p.joints[e.j0 + k];
-        if (idx - 14 < ((j.k > 0.f || j.d > 0.f) ? joint_ndof(j.type) : 0)) a.tg[j.dof + idx - 14] += v;
-      }
+  for (int t = e.lane; t < J + nc; t += e.nthr) {
+    if (t < J) {
+      float out[17];
+      joint_geom_adjoint(p, e, w, a, t, out);
+      float* S = (float*)(a.gat + 8 * t);
+      for (int idx = 0; idx < 14; ++idx) S[pose_slot(idx)] = out[idx];
+      S[pose_slot(2) + 1] = 0.f;
+      S[pose_slot(9) + 1] = 0.f;
+      const JointDesc& j = p.joints[e.j0 + t];
+      const int nd = (j.k > 0.f || j.d > 0.f) ? joint_ndof(j.type) : 0;
+      for (int c = 0; c < nd; ++c) a.tg[j.dof + c] += out[14 + c];
     } else {
-      const int ci = t - NJ;
+      const int ci = t - J;
       const int ids = w.cid[ci];
       const int ia = ids & 0xffff, bc = ids >> 16;
       float out[23];
