@@ -1116,28 +1116,32 @@ static __device__ void gather_bodies(const EnvInfo& e, const AWs& a, bool inerti
 }
 
 // World inverse inertia adjoints -> orientation adjoint and principal inverse
-// inertia adjoint (dual passes over q and the 3 principal values); 1/m
-// adjoint into the mass accumulator.
+// inertia adjoint; 1/m adjoint into the mass accumulator. W = sum_k d_k r_k
+// r_k^T over the columns r_k of R(q) (world_inv_inertia), so with G the
+// symmetric matrix of the six entries' adjoints (off-diagonal ones split
+// between the two places) g(d_k) = r_k . G r_k and g(r_k) = 2 d_k G r_k,
+// which the column's rotation adjoint takes to q.
 static __device__ void reverse_inertia(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a) {
   for (int i = e.lane; i < e.D; i += e.nthr) {
-    float4 I0 = a.bI0[i], I1 = a.bI1[i];
-    const float gW[6] = {I0.x, I0.y, I0.z, I0.w, I1.x, I1.y};
-    float4 q4 = w.bq[i], inv = p.binv[e.b0 + i];
-    float res[7];
-    for (int idx = 0; idx < 7; ++idx) {
-      Q4<d1> q; q.w = tan_of(idx, 0, q4.x); q.x = tan_of(idx, 1, q4.y); q.y = tan_of(idx, 2, q4.z); q.z = tan_of(idx, 3, q4.w);
-      d1 dd[3] = {tan_of(idx, 4, inv.y), tan_of(idx, 5, inv.z), tan_of(idx, 6, inv.w)};
-      d1 W6[6];
-      world_inv_inertia<d1>(q, dd, W6);
-      float acc = 0.f;
-      for (int u = 0; u < 6; ++u) acc += gW[u] * W6[u].d;
-      res[idx] = acc;
+    const float4 I0 = a.bI0[i], I1 = a.bI1[i];
+    const float4 q4 = w.bq[i], inv = p.binv[e.b0 + i];
+    const float hxy = 0.5f * I0.y, hxz = 0.5f * I0.z, hyz = 0.5f * I1.x;
+    const M3<float> R = qmat(ldq4(q4));
+    const float d[3] = {inv.y, inv.z, inv.w};
+    float gq[4] = {0.f, 0.f, 0.f, 0.f}, gd[3];
+    V3<float> unused = v3<float>(0.f, 0.f, 0.f);
+    for (int k = 0; k < 3; ++k) {
+      const V3<float> r = col(R, k);
+      const V3<float> Gr = v3<float>(I0.x * r.x + hxy * r.y + hxz * r.z, hxy * r.x + I0.w * r.y + hyz * r.z,
+                                     hxz * r.x + hyz * r.y + I1.y * r.z);
+      gd[k] = dot(r, Gr);
+      rotate_adjoint(q4, unit<float>(k), Gr * (2.f * d[k]), unused, gq);
     }
-    float4 gq = a.bq[i];
-    gq.x += res[0]; gq.y += res[1]; gq.z += res[2]; gq.w += res[3];
-    a.bq[i] = gq;
+    float4 g = a.bq[i];
+    g.x += gq[0]; g.y += gq[1]; g.z += gq[2]; g.w += gq[3];
+    a.bq[i] = g;
     float4 m = a.bm[i];
-    m.x += I1.z; m.y += res[4]; m.z += res[5]; m.w += res[6];
+    m.x += I1.z; m.y += gd[0]; m.z += gd[1]; m.w += gd[2];
     a.bm[i] = m;
   }
 }
