@@ -912,14 +912,18 @@ int msh_create(const msh_scene_desc* d, const msh_solver_cfg* cfg, msh_handle** 
     }
     h->L = make_layout(h->Dm, h->Sm, h->Jm, Rm, cfg->max_pairs, C, jac, Ch);
   }
-  // envs ordered by decreasing estimated cost (longest first)
+  // envs ordered by decreasing estimated cost (longest first): broadphase
+  // candidates, bodies, joints. The order matters (4096-env apartment batch:
+  // 1.72 ms per step in this order, 1.74 with the candidates weighted 0.05,
+  // 1.98 reversed, 2.04 shuffled); ordering by the previous step's measured
+  // per-env cycles, re-sorted on the device every step, took 1.81 ms.
   std::vector<int> order(E);
   std::iota(order.begin(), order.end(), 0);
   std::vector<double> cost(E);
   for (int e = 0; e < E; ++e) {
     double D = d->body_off[e + 1] - d->body_off[e], Sb = d->static_off[e + 1] - d->static_off[e];
     double Jn = d->joint_off[e + 1] - d->joint_off[e];
-    cost[e] = D * (D + Sb) * 0.05 + 4.0 * D + 6.0 * Jn;
+    cost[e] = D * (D + Sb) * 0.02 + 4.0 * D + 6.0 * Jn;
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   h->order_host = order;
