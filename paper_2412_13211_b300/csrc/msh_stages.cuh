@@ -1048,7 +1048,7 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
 // substep), and the point's total impulse is applied to the bodies once.
 // This is the row-by-row sequential-impulse update, regrouped.
 __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e, const Ws& w, int m, BodyVel& bv,
-                                               BodyVel* dacc) {
+                                               BodyVel* dacc, float4* tq = nullptr) {
   int4 mf = man_get(w, m);
   const int a = mf.x, b = mf.y;
   const float ima = w.bIw1[a].w, imb = b >= 0 ? w.bIw1[b].w : 0.f;
@@ -1083,6 +1083,7 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
     const float nl2 = fminf(fmaxf(l2 + -cn.w * u2, -lim), lim);
     const float d2 = nl2 - l2;
     w.klam[c] = make_float4(nl0, nl1, nl2, lam.w);
+    if (tq) tq[c] = make_float4(nl0, nl1, nl2, 0.f);   // the recorded sweep's slot of this point
     // the point's impulse on b (its negative on a)
     const V3<float> P = axpyf(axpyf(n * d0, t1, d1), t2, d2);
     const V3<float> ia = smulf(Ia, crossf(ra, P));
@@ -1144,6 +1145,14 @@ static __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const
   const int J = e.J;
   if (p.mode == MODE_COLOURED) {
     const int ncol = w.misc[MC_COLOURS];
+    // a recorded step: this sweep's contact-point slots (4 per point, on 16
+    // bytes), written by the point update from its registers
+    float4* tq = nullptr;
+    if (p.tape) {
+      const TapeLayout tl = tape_layout(p.L, p.S, p.N, p.max_dof);
+      tq = reinterpret_cast<float4*>(tape_env(p, e.env) + tl.t2 + (long long)(sub * p.N + it) * p.tape_Rm +
+                                     ROWS_PER_JOINT * p.L.Jm);
+    }
     for (int c = 0; c < ncol; ++c) {
       // the colour's joints, then its manifolds (no barrier between: a
       // colour's constraints share no dynamic body)
@@ -1161,10 +1170,9 @@ static __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const
         const int k = w.corder[idx];
         const int4 mf = man_get(w, k - J);
         BodyVel bv = load_vel(w, mf.x, mf.y);
-        solve_manifold(p, e, w, k - J, bv, nullptr);
+        solve_manifold(p, e, w, k - J, bv, nullptr, tq);
         w.bv[mf.x] = f4(bv.va, 0.f); w.bw[mf.x] = f4(bv.wa, 0.f);
         if (mf.y >= 0) { w.bv[mf.y] = f4(bv.vb, 0.f); w.bw[mf.y] = f4(bv.wb, 0.f); }
-        if (p.tape) tape_lambdas(p, e, w, k, sub, it);
       }
       gsync(e);
     }
