@@ -351,9 +351,10 @@ __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, f
 // mu * lambda_n sends its adjoint to lambda_n.
 // JAC: as in reverse_row, the local velocity copies move through the split
 // inverse masses and the bodies' iteration sums (adjoint G) through the true
-// ones.
-template <bool JAC>
-__device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool bdyn, float ima, float imb,
+// ones. BDYN: b is a dynamic body (a static b's terms drop out at compile
+// time; the same values).
+template <bool JAC, bool BDYN>
+__device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, float ima, float imb,
                                               const Sym3& Iwa, const Sym3& Iwb, BodyVel& v, BodyAdj& g,
                                               const float* lam_it, const float* lam_prev, float mu, float* mi,
                                               float sa = 1.f, float sb = 1.f, const BodyAdj* GS = nullptr) {
@@ -386,7 +387,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
   if (JAC) {
     v.va = v.va + Pi * (sa * ima);
     v.wa = v.wa + smul(Iwa, ta) * sa;
-    if (bdyn) {
+    if (BDYN) {
       tb = cross(rb, Pi);
       v.vb = v.vb - Pi * (sb * imb);
       v.wb = v.wb - smul(Iwb, tb) * sb;
@@ -398,7 +399,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
     gra = gra + cross(sI, Pi);
     add_sym(mi, ewa, -ta);
     mi[12] -= dot(Pi, g.va * sa + GS->va);
-    if (bdyn) {
+    if (BDYN) {
       const V3<float> ewb = g.wb * sb + GS->wb;
       const V3<float> sJ = smul(Iwb, ewb);
       gP = gP + (g.vb * (sb * imb) + GS->vb * imb) + cross(sJ, rb);
@@ -409,7 +410,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
   } else {
     v.va = v.va + Pi * ima;
     v.wa = v.wa + smul(Iwa, ta);
-    if (bdyn) {
+    if (BDYN) {
       tb = cross(rb, Pi);
       v.vb = v.vb - Pi * imb;
       v.wb = v.wb - smul(Iwb, tb);
@@ -420,7 +421,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
     gra = gra + cross(sI, Pi);
     add_sym(mi, g.wa, -ta);
     mi[12] -= dot(Pi, g.va);
-    if (bdyn) {
+    if (BDYN) {
       const V3<float> sJ = smul(Iwb, g.wb);
       gP = gP + g.vb * imb + cross(sJ, rb);
       grb = grb + cross(Pi, sJ);
@@ -432,7 +433,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
   gd0 = gd0 + gP * D0; gd1 = gd1 + gP * D1; gd2 = gd2 + gP * D2;
   // the rows' inputs as the forward formed them
   V3<float> vr = v3<float>(0.f, 0.f, 0.f) - (v.va + cross(v.wa, ra));
-  if (bdyn) vr = vr + (v.vb + cross(v.wb, rb));
+  if (BDYN) vr = vr + (v.vb + cross(v.wb, rb));
   const float u0 = dot(n, vr);
   const float u1 = dot(t1, vr) + K10 * D0;
   const float u2 = (dot(t2, vr) + K20 * D0) + K21 * D1;
@@ -473,7 +474,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool
   g.va = g.va - gvr;
   g.wa = g.wa - cross(ra, gvr);
   gra = gra - cross(gvr, v.wa);
-  if (bdyn) {
+  if (BDYN) {
     g.vb = g.vb + gvr;
     g.wb = g.wb + cross(rb, gvr);
     grb = grb + cross(gvr, v.wb);
@@ -519,8 +520,14 @@ __device__ __forceinline__ void reverse_constraint(const Params& p, const Ws& w,
     float4* MA = a.madj + 4 * (k - J);
     float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
     float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
-    for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
-      reverse_point<false>(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
+    // a static b's terms drop out of the loop (nearly every manifold of the
+    // apartment batch has one)
+    if (B >= 0)
+      for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
+        reverse_point<false, true>(a, c, crow(p.L, c, 0), ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
+    else
+      for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
+        reverse_point<false, false>(a, c, crow(p.L, c, 0), ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
     MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
     MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
   }
@@ -637,9 +644,14 @@ static __device__ void reverse_constraint_jacobi(const Params& p, const Ws& w, c
     float4* MA = a.madj + 4 * (k - J);
     float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
     float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
-    for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
-      reverse_point<true>(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi,
-                          sa, sb, &G);
+    if (B >= 0)
+      for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
+        reverse_point<true, true>(a, c, crow(p.L, c, 0), ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi,
+                                  sa, sb, &G);
+    else
+      for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
+        reverse_point<true, false>(a, c, crow(p.L, c, 0), ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi,
+                                   sa, sb, &G);
     MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
     MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
   }

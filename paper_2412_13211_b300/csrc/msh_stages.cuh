@@ -1046,16 +1046,18 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
 // point is formed once; each row's impulse moves the later rows' relative
 // velocities by the point's coupling terms (J_x M^-1 J_y^T, fixed within a
 // substep), and the point's total impulse is applied to the bodies once.
-// This is the row-by-row sequential-impulse update, regrouped.
-__device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e, const Ws& w, int m, BodyVel& bv,
-                                               BodyVel* dacc, float4* tq = nullptr) {
-  int4 mf = man_get(w, m);
-  const int a = mf.x, b = mf.y;
-  const float ima = w.bIw1[a].w, imb = b >= 0 ? w.bIw1[b].w : 0.f;
-  const float sa = w.bIw1[a].z, sb = b >= 0 ? w.bIw1[b].z : 1.f;
-  const float ka = sa * ima, kb = sb * imb;
-  Sym3 Ia = load_Iw(w, a), Ib;
-  if (b >= 0) Ib = load_Iw(w, b);
+// This is the row-by-row sequential-impulse update, regrouped. BDYN: b is a
+// dynamic body; a static b (or the plane) has no velocity and takes no
+// impulse, so its terms drop out of the loop (the same values: with a static
+// b the relative velocity is the negated velocity of a, as in the general
+// form). Nearly every manifold of the apartment and manipulator batches has
+// a static b, so a warp's lanes mostly run the shorter loop (4096-env
+// apartment batch: 1.72 -> 1.69 ms per step; 1024-env manipulator batch:
+// 0.648 -> 0.606 ms).
+template <bool BDYN>
+__device__ __forceinline__ void manifold_points(const Params& p, const Ws& w, int4 mf, BodyVel& bv, BodyVel* dacc,
+                                                float4* tq, float ima, float imb, float sa, float sb, float ka,
+                                                float kb, const Sym3& Ia, const Sym3& Ib) {
   const int c1 = mf.z + mf.w;
   // software pipelining: the next point's data is loaded while this point's rows run
   float4 cn = w.cn[mf.z], kra = w.kra[mf.z], krb = w.krb[mf.z], lam = w.klam[mf.z], kx = w.kx[mf.z];
@@ -1069,7 +1071,7 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
     onb_with(n, kx.w, t1, t2);
     // velocity of b relative to a at the point (static b: vb = wb = 0)
     V3<float> vr = bv.va + crossf(bv.wa, ra);
-    vr = b >= 0 ? (bv.vb + crossf(bv.wb, rb)) - vr : -vr;
+    vr = BDYN ? (bv.vb + crossf(bv.wb, rb)) - vr : -vr;
     float u0 = dotf(n, vr), u1 = dotf(t1, vr), u2 = dotf(t2, vr);
     const float l0 = lam.x, l1 = lam.y, l2 = lam.z;
     const float nl0 = fmaxf(l0 + -kra.w * (u0 + krb.w), 0.f);
@@ -1090,7 +1092,7 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
     bv.va = axpyf(bv.va, P, -ka);
     bv.wa = axpyf(bv.wa, ia, -sa);
     if (dacc) { dacc->va = axpyf(dacc->va, P, -ima); dacc->wa = dacc->wa - ia; }
-    if (b >= 0) {
+    if (BDYN) {
       const V3<float> ib = smulf(Ib, crossf(rb, P));
       bv.vb = axpyf(bv.vb, P, kb);
       bv.wb = axpyf(bv.wb, ib, sb);
@@ -1098,6 +1100,18 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
     }
     cn = ncn; kra = nkra; krb = nkrb; lam = nlam; kx = nkx;
   }
+}
+
+__device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e, const Ws& w, int m, BodyVel& bv,
+                                               BodyVel* dacc, float4* tq = nullptr) {
+  int4 mf = man_get(w, m);
+  const int a = mf.x, b = mf.y;
+  const float ima = w.bIw1[a].w, imb = b >= 0 ? w.bIw1[b].w : 0.f;
+  const float sa = w.bIw1[a].z, sb = b >= 0 ? w.bIw1[b].z : 1.f;
+  const float ka = sa * ima, kb = sb * imb;
+  const Sym3 Ia = load_Iw(w, a);
+  if (b >= 0) manifold_points<true>(p, w, mf, bv, dacc, tq, ima, imb, sa, sb, ka, kb, Ia, load_Iw(w, b));
+  else manifold_points<false>(p, w, mf, bv, dacc, tq, ima, imb, sa, sb, ka, kb, Ia, Ia);
 }
 
 __device__ __forceinline__ void con_bodies(const Params& p, const EnvInfo& e, const Ws& w, int k, int J, int& a, int& b) {
