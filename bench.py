@@ -35,7 +35,7 @@ METRIC = "env-steps/sec at 4096 envs (fwd and fwd+bwd) vs plain step; % HBM roof
 # DRAM bytes (read + write) of one k_fused launch from an ncu capture, keyed by
 # (config, envs, threads per env) and stored with the hash of the step kernel's
 # sources it was captured on; a launch of any other build reports null.
-FUSED_TRAFFIC = {(3, 4096, 16): ("7e0119ba6a6b476f", 50.016256e6 + 12.19456e6)}
+FUSED_TRAFFIC = {(3, 4096, 16): ("f7de7dc6e7f021a9", 50.009856e6 + 12.298752e6)}
 KERNEL_SOURCES = ("msh.cu", "msh_fused.cuh", "msh_fused16.cu", "msh_fused32.cu", "msh_stages.cuh", "msh_collide.cuh",
                   "msh_math.cuh")
 WORKLOADS = {1: "falling spheres over static boxes", 2: "fixed-base arm and gripper at a counter",

@@ -164,6 +164,40 @@ static __device__ void build_incidence(const Params& p, const EnvInfo& e, const 
   gsync(e);
 }
 
+// One contact point's parameters for the reverse sweeps (BK: the kind of b;
+// a static b's terms drop out at compile time, the same values).
+template <int BK>
+__device__ __forceinline__ void contact_rev_rows(const Params& p, const Ws& w, const AWs& a, int ci, int ia, int ibd) {
+  const int ib = BK == BK_STATIC ? -1 : ibd;
+  const bool bdyn = b_dyn<BK>(ib >= 0);
+  RowCtx ctx = row_ctx(w, ia, ib);
+  V3<float> n = f3(w.cn[ci]);
+  V3<float> ra, rb;
+  float bias;
+  V3<float> xb = bdyn ? f3(w.bx[ib]) : v3<float>(0.f, 0.f, 0.f);
+  Q4<float> qb = bdyn ? ldq4(w.bq[ib]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
+  contact_geom<float>(f3(w.bx[ia]), ldq4(w.bq[ia]), xb, qb, bdyn, n, f3(w.cra[ci]), f3(w.crb[ci]), p.h, p.beta,
+                      p.slop, ra, rb, bias);
+  V3<float> t1, t2;
+  const float sc = onb_scale(n);
+  onb_with(n, sc, t1, t2);
+  V3<float> dirs[3] = {n, t1, t2};
+  float m[3];
+  for (int r = 0; r < 3; ++r) {
+    JRow x = blank_row();
+    x.la = -dirs[r]; x.lb = dirs[r]; x.aa = -cross(ra, dirs[r]); x.ab = cross(rb, dirs[r]);
+    finish_row(x, ctx, false);
+    m[r] = x.m;
+  }
+  float K[6];
+  point_K(ctx, dirs, ra, rb, K);   // the couplings the forward sweeps use
+  float4* P = a.cpar + CPAR_F4 * ci;
+  P[0] = f4(n, m[0]); P[1] = f4(ra, bias); P[2] = f4(rb, m[1]); P[3] = make_float4(m[2], sc, K[3], K[4]);
+  P[4] = make_float4(K[5], 0.f, 0.f, 0.f);
+  float4* G = a.cadj + CADJ_F4 * ci;
+  for (int q = 0; q < CADJ_F4; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Generic rows of every constraint at the workspace poses (for the reverse
 // sweeps): la|m, aa|bias, ab|gamma, Ia|0, Ib|clamp, plus a kind code.
 static __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w, const AWs& a, const float* tg) {
@@ -194,35 +228,10 @@ static __device__ void build_rows(const Params& p, const EnvInfo& e, const Ws& w
       }
     } else {
       const int ci = t - e.J;
-      int ids = w.cid[ci];
-      int ia = ids & 0xffff, bc = ids >> 16;
-      int ib = bc < e.D ? bc : -1;
-      RowCtx ctx = row_ctx(w, ia, ib);
-      V3<float> n = f3(w.cn[ci]);
-      V3<float> ra, rb;
-      float bias;
-      V3<float> xb = ib >= 0 ? f3(w.bx[ib]) : v3<float>(0.f, 0.f, 0.f);
-      Q4<float> qb = ib >= 0 ? ldq4(w.bq[ib]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
-      contact_geom<float>(f3(w.bx[ia]), ldq4(w.bq[ia]), xb, qb, ib >= 0, n, f3(w.cra[ci]), f3(w.crb[ci]), p.h,
-                          p.beta, p.slop, ra, rb, bias);
-      V3<float> t1, t2;
-      const float sc = onb_scale(n);
-      onb_with(n, sc, t1, t2);
-      V3<float> dirs[3] = {n, t1, t2};
-      float m[3];
-      for (int r = 0; r < 3; ++r) {
-        JRow x = blank_row();
-        x.la = -dirs[r]; x.lb = dirs[r]; x.aa = -cross(ra, dirs[r]); x.ab = cross(rb, dirs[r]);
-        finish_row(x, ctx, false);
-        m[r] = x.m;
-      }
-      float K[6];
-      point_K(ctx, dirs, ra, rb, K);   // the couplings the forward sweeps use
-      float4* P = a.cpar + CPAR_F4 * ci;
-      P[0] = f4(n, m[0]); P[1] = f4(ra, bias); P[2] = f4(rb, m[1]); P[3] = make_float4(m[2], sc, K[3], K[4]);
-      P[4] = make_float4(K[5], 0.f, 0.f, 0.f);
-      float4* G = a.cadj + CADJ_F4 * ci;
-      for (int q = 0; q < CADJ_F4; ++q) G[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int ids = w.cid[ci];
+      const int ia = ids & 0xffff, bc = ids >> 16;
+      const int ib = bc < e.D ? bc : -1;
+      by_b_kind(ib >= 0, [&](auto k) { contact_rev_rows<decltype(k)::v>(p, w, a, ci, ia, ib); });
     }
   }
   const int M = w.misc[MC_MANIFOLDS];
@@ -351,13 +360,14 @@ __device__ __forceinline__ void reverse_row(const AWs& a, int r, int A, int B, f
 // mu * lambda_n sends its adjoint to lambda_n.
 // JAC: as in reverse_row, the local velocity copies move through the split
 // inverse masses and the bodies' iteration sums (adjoint G) through the true
-// ones. BDYN: b is a dynamic body (a static b's terms drop out at compile
-// time; the same values).
-template <bool JAC, bool BDYN>
-__device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, float ima, float imb,
+// ones. BK: the kind of b (`bd`: b is dynamic, read with BK_EITHER; a static
+// b's terms drop out at compile time; the same values).
+template <bool JAC, int BK>
+__device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, bool bd, float ima, float imb,
                                               const Sym3& Iwa, const Sym3& Iwb, BodyVel& v, BodyAdj& g,
                                               const float* lam_it, const float* lam_prev, float mu, float* mi,
                                               float sa = 1.f, float sb = 1.f, const BodyAdj* GS = nullptr) {
+  const bool bdyn = b_dyn<BK>(bd);
   const float4* P = a.cpar + CPAR_F4 * ci;
   float4* Q = a.cadj + CADJ_F4 * ci;
   const float4 P0 = P[0], P1 = P[1], P2 = P[2], P3 = P[3], P4 = P[4];
@@ -387,7 +397,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, floa
   if (JAC) {
     v.va = v.va + Pi * (sa * ima);
     v.wa = v.wa + smul(Iwa, ta) * sa;
-    if (BDYN) {
+    if (bdyn) {
       tb = cross(rb, Pi);
       v.vb = v.vb - Pi * (sb * imb);
       v.wb = v.wb - smul(Iwb, tb) * sb;
@@ -399,7 +409,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, floa
     gra = gra + cross(sI, Pi);
     add_sym(mi, ewa, -ta);
     mi[12] -= dot(Pi, g.va * sa + GS->va);
-    if (BDYN) {
+    if (bdyn) {
       const V3<float> ewb = g.wb * sb + GS->wb;
       const V3<float> sJ = smul(Iwb, ewb);
       gP = gP + (g.vb * (sb * imb) + GS->vb * imb) + cross(sJ, rb);
@@ -410,7 +420,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, floa
   } else {
     v.va = v.va + Pi * ima;
     v.wa = v.wa + smul(Iwa, ta);
-    if (BDYN) {
+    if (bdyn) {
       tb = cross(rb, Pi);
       v.vb = v.vb - Pi * imb;
       v.wb = v.wb - smul(Iwb, tb);
@@ -421,7 +431,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, floa
     gra = gra + cross(sI, Pi);
     add_sym(mi, g.wa, -ta);
     mi[12] -= dot(Pi, g.va);
-    if (BDYN) {
+    if (bdyn) {
       const V3<float> sJ = smul(Iwb, g.wb);
       gP = gP + g.vb * imb + cross(sJ, rb);
       grb = grb + cross(Pi, sJ);
@@ -433,7 +443,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, floa
   gd0 = gd0 + gP * D0; gd1 = gd1 + gP * D1; gd2 = gd2 + gP * D2;
   // the rows' inputs as the forward formed them
   V3<float> vr = v3<float>(0.f, 0.f, 0.f) - (v.va + cross(v.wa, ra));
-  if (BDYN) vr = vr + (v.vb + cross(v.wb, rb));
+  if (bdyn) vr = vr + (v.vb + cross(v.wb, rb));
   const float u0 = dot(n, vr);
   const float u1 = dot(t1, vr) + K10 * D0;
   const float u2 = (dot(t2, vr) + K20 * D0) + K21 * D1;
@@ -474,7 +484,7 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, floa
   g.va = g.va - gvr;
   g.wa = g.wa - cross(ra, gvr);
   gra = gra - cross(gvr, v.wa);
-  if (BDYN) {
+  if (bdyn) {
     g.vb = g.vb + gvr;
     g.wb = g.wb + cross(rb, gvr);
     grb = grb + cross(gvr, v.wb);
@@ -484,55 +494,62 @@ __device__ __forceinline__ void reverse_point(const AWs& a, int ci, int rn, floa
   Q[6] = make_float4(gK21, 0.f, 0.f, 0.f);
 }
 
-// Reverse of one constraint's update in a sweep (JOINT: a joint's rows in
-// reverse order, else a manifold's points in reverse order).
-template <bool JOINT>
-__device__ __forceinline__ void reverse_constraint(const Params& p, const Ws& w, const AWs& a, int k, int J,
-                                                   const float* lam_it, const float* lam_prev) {
-  int A, B;
-  if (JOINT) { const int4 ji = w.jinfo[k]; A = ji.x; B = ji.y; }
-  else { const int4 mf = man_get(w, k - J); A = mf.x; B = mf.y; }
+// Reverse of one joint's update in a sweep: its rows in reverse order.
+__device__ __forceinline__ void reverse_joint(const Params& p, const Ws& w, const AWs& a, int k,
+                                              const float* lam_it, const float* lam_prev) {
+  const int4 ji = w.jinfo[k];
+  const int A = ji.x, B = ji.y;
   BodyVel v = load_vel(w, A, B);
   BodyAdj g;
   V3<float> z = v3<float>(0.f, 0.f, 0.f);
   g.va = A >= 0 ? f3(a.bv[A]) : z; g.wa = A >= 0 ? f3(a.bw[A]) : z;
-  g.vb = B >= 0 ? f3(a.bv[B]) : z; g.wb = B >= 0 ? f3(a.bw[B]) : z;
-  const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = B >= 0 ? w.bx[B].w : 0.f;
-  if (JOINT) {
-    const int jnr = w.jinfo[k].w;
-    // software pipelining: the next row's parameters, adjoints and lambdas
-    // load while this row runs (rows of a constraint never alias)
-    int r_cur = jrow(k, jnr - 1);
-    RevRow cur, nxt;
-    load_rev_row(a, r_cur, lam_it, lam_prev, -1, cur);
-    for (int i = 0; i < jnr; ++i) {
-      const int r_nxt = jrow(k, jnr - 2 - i);
-      if (i + 1 < jnr) load_rev_row(a, r_nxt, lam_it, lam_prev, -1, nxt);
-      float gfric;
-      reverse_row<false>(a, r_cur, A, B, ima, imb, v, g, cur, 0.f, gfric);
-      if (i + 1 < jnr) { cur = nxt; r_cur = r_nxt; }
-    }
-  } else {
-    const int4 mf = man_get(w, k - J);
-    const Sym3 Iwa = load_Iw(w, A);
-    Sym3 Iwb = Iwa;
-    if (B >= 0) Iwb = load_Iw(w, B);
-    float4* MA = a.madj + 4 * (k - J);
-    float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
-    float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
-    // a static b's terms drop out of the loop (nearly every manifold of the
-    // apartment batch has one)
-    if (B >= 0)
-      for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
-        reverse_point<false, true>(a, c, crow(p.L, c, 0), ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
-    else
-      for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
-        reverse_point<false, false>(a, c, crow(p.L, c, 0), ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
-    MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
-    MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
+  g.vb = f3(a.bv[B]); g.wb = f3(a.bw[B]);
+  const float ima = A >= 0 ? w.bx[A].w : 0.f, imb = w.bx[B].w;
+  const int jnr = ji.w;
+  // software pipelining: the next row's parameters, adjoints and lambdas
+  // load while this row runs (rows of a constraint never alias)
+  int r_cur = jrow(k, jnr - 1);
+  RevRow cur, nxt;
+  load_rev_row(a, r_cur, lam_it, lam_prev, -1, cur);
+  for (int i = 0; i < jnr; ++i) {
+    const int r_nxt = jrow(k, jnr - 2 - i);
+    if (i + 1 < jnr) load_rev_row(a, r_nxt, lam_it, lam_prev, -1, nxt);
+    float gfric;
+    reverse_row<false>(a, r_cur, A, B, ima, imb, v, g, cur, 0.f, gfric);
+    if (i + 1 < jnr) { cur = nxt; r_cur = r_nxt; }
   }
   if (A >= 0) { w.bv[A] = f4(v.va, 0.f); w.bw[A] = f4(v.wa, 0.f); a.bv[A] = f4(g.va, 0.f); a.bw[A] = f4(g.wa, 0.f); }
-  if (B >= 0) { w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f); }
+  w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f);
+}
+
+// Reverse of manifold m's update in a sweep: its points in reverse order.
+// BK: the kind of b; a static b (nearly every manifold of the apartment
+// batch) has no velocity or adjoint to load or store, and with BK_STATIC its
+// terms drop out of the point reverse at compile time (the same values).
+template <int BK>
+__device__ __forceinline__ void reverse_manifold(const Params& p, const Ws& w, const AWs& a, int m, int4 mf,
+                                                 const float* lam_it, const float* lam_prev) {
+  const int A = mf.x, B = BK == BK_STATIC ? -1 : mf.y;
+  const bool bdyn = b_dyn<BK>(B >= 0);
+  const V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  BodyVel v;
+  v.va = f3(w.bv[A]); v.wa = f3(w.bw[A]);
+  v.vb = bdyn ? f3(w.bv[B]) : z; v.wb = bdyn ? f3(w.bw[B]) : z;
+  BodyAdj g;
+  g.va = f3(a.bv[A]); g.wa = f3(a.bw[A]);
+  g.vb = bdyn ? f3(a.bv[B]) : z; g.wb = bdyn ? f3(a.bw[B]) : z;
+  const float ima = w.bx[A].w, imb = bdyn ? w.bx[B].w : 0.f;
+  const Sym3 Iwa = load_Iw(w, A);
+  const Sym3 Iwb = bdyn ? load_Iw(w, B) : Iwa;
+  float4* MA = a.madj + 4 * m;
+  float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
+  float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
+  for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
+    reverse_point<false, BK>(a, c, crow(p.L, c, 0), bdyn, ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi);
+  MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
+  MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
+  w.bv[A] = f4(v.va, 0.f); w.bw[A] = f4(v.wa, 0.f); a.bv[A] = f4(g.va, 0.f); a.bw[A] = f4(g.wa, 0.f);
+  if (bdyn) { w.bv[B] = f4(v.vb, 0.f); w.bw[B] = f4(v.wb, 0.f); a.bv[B] = f4(g.vb, 0.f); a.bw[B] = f4(g.wb, 0.f); }
 }
 
 // Reverse of one sweep: colours in reverse order; within a colour (its
@@ -544,9 +561,12 @@ static __device__ void reverse_sweep(const Params& p, const EnvInfo& e, const Ws
   for (int c = ncol - 1; c >= 0; --c) {
     const int v = w.coff[c], c0 = v & 0xffff, cm = c0 + (v >> 16), c1 = w.coff[c + 1] & 0xffff;
     for (int idx = c0 + e.lane; idx < cm; idx += e.nthr)
-      reverse_constraint<true>(p, w, a, w.corder[idx], J, lam_it, lam_prev);
-    for (int idx = cm + e.lane; idx < c1; idx += e.nthr)
-      reverse_constraint<false>(p, w, a, w.corder[idx], J, lam_it, lam_prev);
+      reverse_joint(p, w, a, w.corder[idx], lam_it, lam_prev);
+    for (int idx = cm + e.lane; idx < c1; idx += e.nthr) {
+      const int m = w.corder[idx] - J;
+      const int4 mf = man_get(w, m);
+      by_b_kind(mf.y >= 0, [&](auto k) { reverse_manifold<decltype(k)::v>(p, w, a, m, mf, lam_it, lam_prev); });
+    }
     gsync(e);
   }
 }
@@ -644,14 +664,11 @@ static __device__ void reverse_constraint_jacobi(const Params& p, const Ws& w, c
     float4* MA = a.madj + 4 * (k - J);
     float4 m0 = MA[0], m1 = MA[1], m2 = MA[2], m3 = MA[3];
     float mi[14] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m3.x, m3.y};
-    if (B >= 0)
+    by_b_kind(B >= 0, [&](auto kb) {
       for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
-        reverse_point<true, true>(a, c, crow(p.L, c, 0), ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi,
-                                  sa, sb, &G);
-    else
-      for (int c = mf.z + mf.w - 1; c >= mf.z; --c)
-        reverse_point<true, false>(a, c, crow(p.L, c, 0), ima, imb, Iwa, Iwb, v, g, lam_it, lam_prev, p.mu, mi,
-                                   sa, sb, &G);
+        reverse_point<true, decltype(kb)::v>(a, c, crow(p.L, c, 0), B >= 0, ima, imb, Iwa, Iwb, v, g, lam_it,
+                                             lam_prev, p.mu, mi, sa, sb, &G);
+    });
     MA[0] = make_float4(mi[0], mi[1], mi[2], mi[3]); MA[1] = make_float4(mi[4], mi[5], mi[6], mi[7]);
     MA[2] = make_float4(mi[8], mi[9], mi[10], mi[11]); MA[3] = make_float4(mi[12], mi[13], 0.f, 0.f);
   }
@@ -745,9 +762,11 @@ __device__ __forceinline__ void reverse_mass_part(const AWs& a, int r, int A, in
 // the off-diagonal (t1,n), (t2,n), (t2,t1) through the couplings of the
 // sweeps; their adjoints move onto the directions, the arms, the inverse
 // inertias and the inverse masses.
-__device__ __forceinline__ void contact_mass_adjoint(const AWs& a, int ci, bool bdyn, float ima, float imb,
+template <int BK>
+__device__ __forceinline__ void contact_mass_adjoint(const AWs& a, int ci, bool bd, float ima, float imb,
                                                      const Sym3& Iwa, const Sym3& Iwb, float* gIwa, float* gIwb,
                                                      float& gima, float& gimb, float sa, float sb) {
+  const bool bdyn = b_dyn<BK>(bd);
   const float4* P = a.cpar + CPAR_F4 * ci;
   float4* Q = a.cadj + CADJ_F4 * ci;
   const V3<float> n = f3(P[0]), ra = f3(P[1]), rb = f3(P[2]);
@@ -971,8 +990,10 @@ static __device__ void joint_geom_adjoint(const Params& p, const EnvInfo& e, con
 // tangent basis of the normal) for the adjoints of its normal, tangents,
 // world arms and bias: out = adjoints of x_a 0-2, q_a 3-6, x_b 7-9, q_b
 // 10-13, n 14-16, ra_l 17-19, rb_l 20-22 (a static b's anchor is in world).
-static __device__ void contact_geom_adjoint(const Params& p, const Ws& w, const AWs& a, int ci, int ia, int ib,
+template <int BK>
+static __device__ void contact_geom_adjoint(const Params& p, const Ws& w, const AWs& a, int ci, int ia, int ibd,
                                      float* out) {
+  const int ib = BK == BK_STATIC ? -1 : ibd;   // a static b's terms drop out at compile time
   for (int k = 0; k < 23; ++k) out[k] = 0.f;
   const float4* Q = a.cadj + CADJ_F4 * ci;
   const float4 xa4 = w.bx[ia], qa4 = w.bq[ia];
@@ -1051,8 +1072,10 @@ static __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws
       gIwa[0] = MA[0].x; gIwa[1] = MA[0].y; gIwa[2] = MA[0].z; gIwa[3] = MA[0].w; gIwa[4] = MA[1].x; gIwa[5] = MA[1].y;
       gIwb[0] = MA[1].z; gIwb[1] = MA[1].w; gIwb[2] = MA[2].x; gIwb[3] = MA[2].y; gIwb[4] = MA[2].z; gIwb[5] = MA[2].w;
       gima = MA[3].x; gimb = MA[3].y;
-      for (int ci = mf.z; ci < mf.z + mf.w; ++ci)
-        contact_mass_adjoint(a, ci, B >= 0, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb, sa, sb);
+      by_b_kind(B >= 0, [&](auto kb) {
+        for (int ci = mf.z; ci < mf.z + mf.w; ++ci)
+          contact_mass_adjoint<decltype(kb)::v>(a, ci, B >= 0, ima, imb, Iwa, Iwb, gIwa, gIwb, gima, gimb, sa, sb);
+      });
     }
     float4* S = a.gat + 8 * k;
     S[4] = make_float4(gIwa[0], gIwa[1], gIwa[2], gIwa[3]);
@@ -1077,7 +1100,8 @@ static __device__ void reverse_setup(const Params& p, const EnvInfo& e, const Ws
       const int ids = w.cid[ci];
       const int ia = ids & 0xffff, bc = ids >> 16;
       float out[23];
-      contact_geom_adjoint(p, w, a, ci, ia, bc < e.D ? bc : -1, out);
+      const int ib = bc < e.D ? bc : -1;
+      by_b_kind(ib >= 0, [&](auto k) { contact_geom_adjoint<decltype(k)::v>(p, w, a, ci, ia, ib, out); });
       float* cp = a.cpose + 16 * ci;
       for (int idx = 0; idx < 14; ++idx) cp[pose_slot(idx)] = out[idx];
       add4(a.cg[3 * ci + 0], v3<float>(out[14], out[15], out[16]));

@@ -226,6 +226,26 @@ __device__ __forceinline__ int gany(const EnvInfo& e, int v) {
   return e.nthr < 32 ? __any_sync(e.mask, v) : __syncthreads_or(v);
 }
 
+// The kind of a contact's second body b for the code paths specialised on
+// it: static (a static box or the plane: no velocity, no impulse, its terms
+// drop out at compile time), dynamic, or either (decided per lane at run
+// time). A warp takes a specialised path only when all its active lanes
+// agree, so lanes whose b differ share one path instead of running the two
+// specialised ones after each other. Every path computes the same values.
+enum { BK_STATIC = 0, BK_DYNAMIC = 1, BK_EITHER = 2 };
+template <int K> struct BKind { static constexpr int v = K; };
+template <int BK> __device__ __forceinline__ bool b_dyn(bool dyn) {
+  return BK == BK_EITHER ? dyn : BK == BK_DYNAMIC;
+}
+// Calls f(BKind<kind>()) with the kind the active lanes share (BK_EITHER if
+// they differ); all of them take the same branch.
+template <class F> __device__ __forceinline__ void by_b_kind(bool dyn, F&& f) {
+  const unsigned am = __activemask();
+  if (__all_sync(am, !dyn)) f(BKind<BK_STATIC>());
+  else if (__all_sync(am, dyn)) f(BKind<BK_DYNAMIC>());
+  else f(BKind<BK_EITHER>());
+}
+
 // Exclusive block-wide prefix sum; every thread of the block must call it.
 // `scr` is 33 ints of shared memory.
 __device__ __forceinline__ int block_exscan(int v, int* scr, int* total) {
@@ -950,22 +970,24 @@ __device__ __forceinline__ void point_K(const RowCtx& ctx, const V3<float>* d, c
   }
 }
 
-static __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int ci) {
-  int ids = w.cid[ci];
-  int a = ids & 0xffff, bc = ids >> 16;
-  int b = bc < e.D ? bc : -1;
+// BK: the kind of b (BK_STATIC: its pose, velocity and inertia terms drop
+// out at compile time).
+template <int BK>
+__device__ __forceinline__ void contact_rows_t(const Params& p, const Ws& w, int ci, int a, int bd) {
+  const int b = BK == BK_STATIC ? -1 : bd;
+  const bool bdyn = b_dyn<BK>(b >= 0);
   RowCtx ctx = row_ctx(w, a, b);
   V3<float> n = f3(w.cn[ci]);
   V3<float> ra, rb;
   float bias;
-  V3<float> xb = b >= 0 ? f3(w.bx[b]) : v3<float>(0.f, 0.f, 0.f);
-  Q4<float> qb = b >= 0 ? ldq4(w.bq[b]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
-  contact_geom<float>(f3(w.bx[a]), ldq4(w.bq[a]), xb, qb, b >= 0, n, f3(w.cra[ci]), f3(w.crb[ci]), p.h, p.beta,
+  V3<float> xb = bdyn ? f3(w.bx[b]) : v3<float>(0.f, 0.f, 0.f);
+  Q4<float> qb = bdyn ? ldq4(w.bq[b]) : ldq4(make_float4(1.f, 0.f, 0.f, 0.f));
+  contact_geom<float>(f3(w.bx[a]), ldq4(w.bq[a]), xb, qb, bdyn, n, f3(w.cra[ci]), f3(w.crb[ci]), p.h, p.beta,
                       p.slop, ra, rb, bias);
   if (p.rest > 0.f) {
     V3<float> va = f3(w.bv[a]), wa = f3(w.bw[a]);
     V3<float> dv = v3<float>(0.f, 0.f, 0.f) - (va + cross(wa, ra));
-    if (b >= 0) dv = dv + (f3(w.bv[b]) + cross(f3(w.bw[b]), rb));
+    if (bdyn) dv = dv + (f3(w.bv[b]) + cross(f3(w.bw[b]), rb));
     float vn = dot(n, dv);
     if (vn < -1.f) bias = fminf(bias, p.rest * vn);
   }
@@ -981,6 +1003,17 @@ static __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws&
   w.klam[ci] = make_float4(0.f, 0.f, 0.f, inv(K[1]));
   w.cn[ci].w = inv(K[2]);   // the separation s0 is not needed after the narrowphase
   w.kx[ci] = make_float4(K[3], K[4], K[5], sc);
+}
+
+static __device__ void contact_rows(const Params& p, const EnvInfo& e, const Ws& w, int ci) {
+  int ids = w.cid[ci];
+  int a = ids & 0xffff, bc = ids >> 16;
+  const int b = bc < e.D ? bc : -1;
+  // two kinds only: a third copy for lanes that differ grew the fused step's
+  // stack frame (1008 -> 1072 bytes) and its DRAM writes (12 -> 18 MB per
+  // launch at 4096 envs), and the set-up runs once per substep
+  if (b >= 0) contact_rows_t<BK_DYNAMIC>(p, w, ci, a, b);
+  else contact_rows_t<BK_STATIC>(p, w, ci, a, b);
 }
 
 static __device__ void stage_prep(const Params& p, const EnvInfo& e, const Ws& w) {
@@ -1046,18 +1079,19 @@ __device__ __forceinline__ void solve_joint(const Params& p, const EnvInfo& e, c
 // point is formed once; each row's impulse moves the later rows' relative
 // velocities by the point's coupling terms (J_x M^-1 J_y^T, fixed within a
 // substep), and the point's total impulse is applied to the bodies once.
-// This is the row-by-row sequential-impulse update, regrouped. BDYN: b is a
-// dynamic body; a static b (or the plane) has no velocity and takes no
-// impulse, so its terms drop out of the loop (the same values: with a static
-// b the relative velocity is the negated velocity of a, as in the general
-// form). Nearly every manifold of the apartment and manipulator batches has
-// a static b, so a warp's lanes mostly run the shorter loop (4096-env
-// apartment batch: 1.72 -> 1.69 ms per step; 1024-env manipulator batch:
-// 0.648 -> 0.606 ms).
-template <bool BDYN>
+// This is the row-by-row sequential-impulse update, regrouped. BK: the kind
+// of b; a static b (or the plane) has no velocity and takes no impulse, so
+// with BK_STATIC its terms drop out of the loop (the same values: with a
+// static b the relative velocity is the negated velocity of a, as in the
+// general form). Nearly every manifold of the apartment and manipulator
+// batches has a static b, so their warps mostly run the shorter loop
+// (4096-env apartment batch: 1.72 -> 1.69 ms per step; 1024-env manipulator
+// batch: 0.648 -> 0.606 ms).
+template <int BK>
 __device__ __forceinline__ void manifold_points(const Params& p, const Ws& w, int4 mf, BodyVel& bv, BodyVel* dacc,
                                                 float4* tq, float ima, float imb, float sa, float sb, float ka,
                                                 float kb, const Sym3& Ia, const Sym3& Ib) {
+  const bool bdyn = b_dyn<BK>(mf.y >= 0);
   const int c1 = mf.z + mf.w;
   // software pipelining: the next point's data is loaded while this point's rows run
   float4 cn = w.cn[mf.z], kra = w.kra[mf.z], krb = w.krb[mf.z], lam = w.klam[mf.z], kx = w.kx[mf.z];
@@ -1071,7 +1105,7 @@ __device__ __forceinline__ void manifold_points(const Params& p, const Ws& w, in
     onb_with(n, kx.w, t1, t2);
     // velocity of b relative to a at the point (static b: vb = wb = 0)
     V3<float> vr = bv.va + crossf(bv.wa, ra);
-    vr = BDYN ? (bv.vb + crossf(bv.wb, rb)) - vr : -vr;
+    vr = bdyn ? (bv.vb + crossf(bv.wb, rb)) - vr : -vr;
     float u0 = dotf(n, vr), u1 = dotf(t1, vr), u2 = dotf(t2, vr);
     const float l0 = lam.x, l1 = lam.y, l2 = lam.z;
     const float nl0 = fmaxf(l0 + -kra.w * (u0 + krb.w), 0.f);
@@ -1092,7 +1126,7 @@ __device__ __forceinline__ void manifold_points(const Params& p, const Ws& w, in
     bv.va = axpyf(bv.va, P, -ka);
     bv.wa = axpyf(bv.wa, ia, -sa);
     if (dacc) { dacc->va = axpyf(dacc->va, P, -ima); dacc->wa = dacc->wa - ia; }
-    if (BDYN) {
+    if (bdyn) {
       const V3<float> ib = smulf(Ib, crossf(rb, P));
       bv.vb = axpyf(bv.vb, P, kb);
       bv.wb = axpyf(bv.wb, ib, sb);
@@ -1110,8 +1144,30 @@ __device__ __forceinline__ void solve_manifold(const Params& p, const EnvInfo& e
   const float sa = w.bIw1[a].z, sb = b >= 0 ? w.bIw1[b].z : 1.f;
   const float ka = sa * ima, kb = sb * imb;
   const Sym3 Ia = load_Iw(w, a);
-  if (b >= 0) manifold_points<true>(p, w, mf, bv, dacc, tq, ima, imb, sa, sb, ka, kb, Ia, load_Iw(w, b));
-  else manifold_points<false>(p, w, mf, bv, dacc, tq, ima, imb, sa, sb, ka, kb, Ia, Ia);
+  const Sym3 Ib = b >= 0 ? load_Iw(w, b) : Ia;
+  by_b_kind(b >= 0, [&](auto k) {
+    manifold_points<decltype(k)::v>(p, w, mf, bv, dacc, tq, ima, imb, sa, sb, ka, kb, Ia, Ib);
+  });
+}
+
+// One manifold in a coloured sweep: its bodies' velocities, its points, the
+// velocities back (BK as in manifold_points; a static b has none).
+template <int BK>
+__device__ __forceinline__ void sweep_manifold(const Params& p, const Ws& w, int4 mf, float4* tq) {
+  const int a = mf.x, b = mf.y;
+  const bool bdyn = b_dyn<BK>(b >= 0);
+  const V3<float> z = v3<float>(0.f, 0.f, 0.f);
+  BodyVel bv;
+  bv.va = f3(w.bv[a]); bv.wa = f3(w.bw[a]);
+  bv.vb = bdyn ? f3(w.bv[b]) : z; bv.wb = bdyn ? f3(w.bw[b]) : z;
+  const float4 xa = w.bIw1[a];
+  const float4 xb = bdyn ? w.bIw1[b] : make_float4(0.f, 0.f, 1.f, 0.f);
+  const float ima = xa.w, imb = xb.w, sa = xa.z, sb = xb.z;
+  const Sym3 Ia = load_Iw(w, a);
+  manifold_points<BK>(p, w, mf, bv, nullptr, tq, ima, imb, sa, sb, sa * ima, sb * imb, Ia,
+                      bdyn ? load_Iw(w, b) : Ia);
+  w.bv[a] = f4(bv.va, 0.f); w.bw[a] = f4(bv.wa, 0.f);
+  if (bdyn) { w.bv[b] = f4(bv.vb, 0.f); w.bw[b] = f4(bv.wb, 0.f); }
 }
 
 __device__ __forceinline__ void con_bodies(const Params& p, const EnvInfo& e, const Ws& w, int k, int J, int& a, int& b) {
@@ -1181,12 +1237,8 @@ static __device__ void stage_solve_iter(const Params& p, const EnvInfo& e, const
         if (p.tape) tape_lambdas(p, e, w, k, sub, it);
       }
       for (int idx = cm + e.lane; idx < c1; idx += e.nthr) {
-        const int k = w.corder[idx];
-        const int4 mf = man_get(w, k - J);
-        BodyVel bv = load_vel(w, mf.x, mf.y);
-        solve_manifold(p, e, w, k - J, bv, nullptr, tq);
-        w.bv[mf.x] = f4(bv.va, 0.f); w.bw[mf.x] = f4(bv.wa, 0.f);
-        if (mf.y >= 0) { w.bv[mf.y] = f4(bv.vb, 0.f); w.bw[mf.y] = f4(bv.wb, 0.f); }
+        const int4 mf = man_get(w, w.corder[idx] - J);
+        by_b_kind(mf.y >= 0, [&](auto k) { sweep_manifold<decltype(k)::v>(p, w, mf, tq); });
       }
       gsync(e);
     }
