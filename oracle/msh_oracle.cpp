@@ -26,8 +26,10 @@
 //     with Tonge et al. 2012 mass splitting as the variant.
 // Pinned by brute force (tests/test_oracle_manifolds.py): capsule-capsule,
 // capsule-box (outside and entering), box-box face and edge manifolds,
-// sphere centres inside boxes. Parity unpinned: box-box clipping on nearly
-// degenerate polygons (the 8-vertex cap).
+// sphere centres inside boxes, and the clipper's 8-vertex cap (never reached
+// on near-degenerate face pairs, in FP32 and FP64); every dynamic pair's
+// manifold is equivariant under a rigid motion of both shapes
+// (tests/test_oracle_equivariance.py).
 //
 // Compile with -ffp-contract=off: the collision stages (AABB, broadphase,
 // narrowphase) must be bit-reproducible in FP32 from identical inputs.
